@@ -1,0 +1,266 @@
+"""FP64 CPU oracle for GBP bundle adjustment -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  It shares no code with the CUDA library; the
+two only see the same seeded inputs from ``paper_2003_03134_gb300.synth``.
+
+``build()`` compiles ``gbp_oracle.c`` with gcc into ``liboracle_gbp.so`` next
+to it; ``Oracle`` wraps one graph through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gbp_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle_gbp.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C99, -O2, no fast-math) if out of date."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "gbp_oracle.h"))):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-Wall", "-Wextra",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Cam(C.Structure):
+    _fields_ = [("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("damping", C.c_double), ("huber_nsigma", C.c_double), ("sigma_px", C.c_double),
+                ("prior_final_scale", C.c_double), ("prior_anneal_iters", C.c_int),
+                ("anchor_scale", C.c_double), ("z_min", C.c_double), ("linear", C.c_int),
+                ("relin_beta", C.c_double), ("relin_interval", C.c_int), ("undamped_iters", C.c_int)]
+
+
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        L.orc_create.restype = C.c_void_p
+        L.orc_create.argtypes = [C.POINTER(_Cam), C.POINTER(_Params), C.c_int, _D, C.c_int, _D,
+                                 C.c_int, _I, _I, _D, C.c_int, _I]
+        L.orc_destroy.argtypes = [C.c_void_p]
+        L.orc_iterate.argtypes = [C.c_void_p, C.c_int, _D]
+        L.orc_iterations_done.argtypes = [C.c_void_p]
+        L.orc_get_means.argtypes = [C.c_void_p, _D, _D]
+        L.orc_get_world.argtypes = [C.c_void_p, _D, _D]
+        L.orc_get_beliefs.argtypes = [C.c_void_p, _D, _D, _D, _D]
+        L.orc_get_prior_diag.argtypes = [C.c_void_p, _D, _D]
+        L.orc_get_messages.argtypes = [C.c_void_p, _D, _D, _D, _D]
+        L.orc_are.restype = C.c_double
+        L.orc_are.argtypes = [C.c_void_p, C.POINTER(C.c_ubyte), _I]
+        L.orc_are_vs.restype = C.c_double
+        L.orc_are_vs.argtypes = [C.c_void_p, _D, _D, _I]
+        L.orc_huber_count.argtypes = [C.c_void_p]
+        L.orc_so3_exp.argtypes = [_D, _D]
+        L.orc_so3_left_jacobian.argtypes = [_D, _D]
+        L.orc_huber_weight.restype = C.c_double
+        L.orc_huber_weight.argtypes = [C.c_double, C.c_double]
+        L.orc_prior_scale.restype = C.c_double
+        L.orc_prior_scale.argtypes = [C.POINTER(_Params), C.c_int]
+        L.orc_project.restype = C.c_double
+        L.orc_project.argtypes = [C.POINTER(_Cam), _D, _D, _D, _D, _D, _D]
+        L.orc_linearise.argtypes = [C.POINTER(_Cam), C.POINTER(_Params), _D, _D, _D, _D, _D, _D,
+                                    _D, _D, _D, _D, _D]
+        L.orc_factor_message.argtypes = [_D, _D, C.c_int, _D, _D, _D, _D]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D)
+
+
+def _ip(a):
+    return a.ctypes.data_as(_I)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a if shape is None else a.reshape(shape)
+
+
+DEFAULTS = dict(damping=0.4, huber_nsigma=0.0, sigma_px=1.0, prior_final_scale=0.01,
+                prior_anneal_iters=10, anchor_scale=1e3, z_min=0.05, linear=0,
+                relin_beta=0.01, relin_interval=10, undamped_iters=8)
+
+
+def make_params(**kw) -> _Params:
+    p = dict(DEFAULTS)
+    for k, v in kw.items():
+        if k in p:
+            p[k] = v
+    return _Params(float(p["damping"]), float(p["huber_nsigma"]), float(p["sigma_px"]),
+                   float(p["prior_final_scale"]), int(p["prior_anneal_iters"]), float(p["anchor_scale"]),
+                   float(p["z_min"]), int(p["linear"]), float(p["relin_beta"]), int(p["relin_interval"]),
+                   int(p["undamped_iters"]))
+
+
+def make_cam(fx, fy, cx, cy) -> _Cam:
+    return _Cam(float(fx), float(fy), float(cx), float(cy))
+
+
+# ---------------------------------------------------------------------------
+# unit pieces
+
+def so3_exp(w):
+    w = _f64(w)
+    R = np.zeros(9)
+    lib().orc_so3_exp(_dp(w), _dp(R))
+    return R.reshape(3, 3)
+
+
+def so3_left_jacobian(w):
+    w = _f64(w)
+    J = np.zeros(9)
+    lib().orc_so3_left_jacobian(_dp(w), _dp(J))
+    return J.reshape(3, 3)
+
+
+def huber_weight(M, nsigma):
+    return lib().orc_huber_weight(float(M), float(nsigma))
+
+
+def prior_scale(t, **kw):
+    p = make_params(**kw)
+    return lib().orc_prior_scale(C.byref(p), int(t))
+
+
+def project(cam, Rref, cref, lref, xk, xl):
+    uv = np.zeros(2)
+    c = make_cam(*cam)
+    Rref, cref, lref, xk, xl = (_f64(a) for a in (Rref, cref, lref, xk, xl))
+    depth = lib().orc_project(C.byref(c), _dp(Rref), _dp(cref), _dp(lref), _dp(xk), _dp(xl), _dp(uv))
+    return uv, depth
+
+
+def linearise(cam, Rref, cref, lref, xk, xl, z, **kw):
+    c = make_cam(*cam)
+    p = make_params(**kw)
+    J, r, k, A, cv = np.zeros(18), np.zeros(2), np.zeros(1), np.zeros(81), np.zeros(9)
+    Rref, cref, lref, xk, xl, z = (_f64(a) for a in (Rref, cref, lref, xk, xl, z))
+    active = lib().orc_linearise(C.byref(c), C.byref(p), _dp(Rref), _dp(cref), _dp(lref), _dp(xk), _dp(xl),
+                                 _dp(z), _dp(J), _dp(r), _dp(k), _dp(A), _dp(cv))
+    return dict(active=bool(active), J=J.reshape(2, 9), r=r, k=float(k[0]), A=A.reshape(9, 9), c=cv)
+
+
+def factor_message(A, c, target, lam_in, eta_in):
+    A, c, lam_in, eta_in = _f64(A), _f64(c), _f64(lam_in), _f64(eta_in)
+    na = 6 if target == 0 else 3
+    lam_out, eta_out = np.zeros(na * na), np.zeros(na)
+    rc = lib().orc_factor_message(_dp(A), _dp(c), int(target), _dp(lam_in), _dp(eta_in), _dp(lam_out), _dp(eta_out))
+    if rc != 0:
+        raise np.linalg.LinAlgError("matrix to invert is not positive definite")
+    return lam_out.reshape(na, na), eta_out
+
+
+# ---------------------------------------------------------------------------
+
+class Oracle:
+    """One GBP graph in the FP64 oracle."""
+
+    def __init__(self, problem, anchors=None, **params):
+        self.p = problem
+        self._cam = make_cam(problem.fx, problem.fy, problem.cx, problem.cy)
+        self._prm = make_params(**params)
+        self.params = dict(DEFAULTS, **{k: v for k, v in params.items() if k in DEFAULTS})
+        self._kf = _f64(problem.kf_Rt_init)
+        self._lm = _f64(problem.lm_init)
+        self._ok = np.ascontiguousarray(problem.obs_kf, dtype=np.int32)
+        self._ol = np.ascontiguousarray(problem.obs_lm, dtype=np.int32)
+        self._uv = _f64(problem.obs_uv)
+        anc = problem.anchor_kf if anchors is None else anchors
+        self._anc = np.ascontiguousarray(anc, dtype=np.int32)
+        h = lib().orc_create(C.byref(self._cam), C.byref(self._prm), problem.n_kf, _dp(self._kf),
+                             problem.n_lm, _dp(self._lm), problem.n_obs, _ip(self._ok), _ip(self._ol),
+                             _dp(self._uv), int(self._anc.size), _ip(self._anc))
+        if not h:
+            raise ValueError("oracle rejected the problem")
+        self._h = C.c_void_p(h)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.orc_destroy(h)
+            self._h = None
+
+    def iterate(self, n: int) -> float:
+        d = C.c_double(0.0)
+        if lib().orc_iterate(self._h, int(n), C.byref(d)) != 0:
+            raise FloatingPointError("a belief stopped being positive definite")
+        return d.value
+
+    def run_to_convergence(self, tol: float, max_iters: int, chunk: int = 1):
+        it = 0
+        d = np.inf
+        while it < max_iters:
+            d = self.iterate(chunk)
+            it += chunk
+            if d < tol:
+                break
+        return it, d
+
+    @property
+    def t(self) -> int:
+        return lib().orc_iterations_done(self._h)
+
+    def means(self):
+        kf, lm = np.zeros((self.p.n_kf, 6)), np.zeros((self.p.n_lm, 3))
+        lib().orc_get_means(self._h, _dp(kf), _dp(lm))
+        return kf, lm
+
+    def world(self):
+        kf, lm = np.zeros((self.p.n_kf, 12)), np.zeros((self.p.n_lm, 3))
+        lib().orc_get_world(self._h, _dp(kf), _dp(lm))
+        return kf, lm
+
+    def beliefs(self):
+        kl, ke = np.zeros((self.p.n_kf, 6, 6)), np.zeros((self.p.n_kf, 6))
+        ll, le = np.zeros((self.p.n_lm, 3, 3)), np.zeros((self.p.n_lm, 3))
+        lib().orc_get_beliefs(self._h, _dp(kl), _dp(ke), _dp(ll), _dp(le))
+        return kl, ke, ll, le
+
+    def prior_diag(self):
+        kd, ld = np.zeros((self.p.n_kf, 6)), np.zeros((self.p.n_lm, 3))
+        lib().orc_get_prior_diag(self._h, _dp(kd), _dp(ld))
+        return kd, ld
+
+    def messages(self):
+        n = self.p.n_obs
+        a, b, c, d = np.zeros((n, 6, 6)), np.zeros((n, 6)), np.zeros((n, 3, 3)), np.zeros((n, 3))
+        lib().orc_get_messages(self._h, _dp(a), _dp(b), _dp(c), _dp(d))
+        return a, b, c, d
+
+    def are(self, mask=None):
+        cnt = C.c_int(0)
+        if mask is None:
+            v = lib().orc_are(self._h, None, C.byref(cnt))
+        else:
+            m = np.ascontiguousarray(mask, dtype=np.uint8)
+            v = lib().orc_are(self._h, m.ctypes.data_as(C.POINTER(C.c_ubyte)), C.byref(cnt))
+        return v, cnt.value
+
+    def are_vs(self, ref_kf_Rt, ref_lm):
+        cnt = C.c_int(0)
+        a, b = _f64(ref_kf_Rt), _f64(ref_lm)
+        v = lib().orc_are_vs(self._h, _dp(a), _dp(b), C.byref(cnt))
+        return v, cnt.value
+
+    def huber_count(self) -> int:
+        return lib().orc_huber_count(self._h)

@@ -1,0 +1,636 @@
+/*
+ * gbp_oracle.c -- plain single-threaded FP64 GBP for bundle adjustment.
+ *
+ * TEST INFRASTRUCTURE ONLY (see gbp_oracle.h).  Written for clarity, not
+ * speed: full 9x9 factor matrices, explicit Schur complements exactly as
+ * printed in the message equations of Sec. 5, plain loops throughout.
+ *
+ * Paper references used below (Ortiz et al., "Bundle Adjustment on a Graph
+ * Processor", CVPR 2020):
+ *   Sec. 4   measurement model h = pi(R l + t), linearised factor in
+ *            information form: eta = J^T S^-1 (J x0 + z - h(x0)),
+ *            Lambda = J^T S^-1 J, J the 2x9 Jacobian.
+ *   Sec. 4   priors generated from the Jacobians, 100x weaker than the
+ *            measurements; Sec. 8 anneals them from measurement scale to
+ *            1/100 over 10 iterations.
+ *   Sec. 5   message equations (messageeta / messagelambda), belief
+ *            equations (beliefeta / belieflambda), synchronous schedule,
+ *            damping of the eta update only.
+ *   Sec. 6   Huber rescale: weight 2 N/M - N^2/M^2 when M > N.
+ */
+#include "gbp_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------
+ * dense symmetric positive definite solves (row-major n x n, n <= 9)
+ * ---------------------------------------------------------------------- */
+
+/* Cholesky factor A = L L^T.  Returns 0, or -1 if A is not positive definite. */
+static int cholesky(int n, const double* A, double* L)
+{
+    memset(L, 0, sizeof(double) * n * n);
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = A[i * n + j];
+            for (int p = 0; p < j; ++p) s -= L[i * n + p] * L[j * n + p];
+            if (i == j) {
+                if (!(s > 0.0)) return -1;
+                L[i * n + i] = sqrt(s);
+            } else {
+                L[i * n + j] = s / L[j * n + j];
+            }
+        }
+    }
+    return 0;
+}
+
+/* Solve L L^T x = b. */
+static void cholesky_solve(int n, const double* L, const double* b, double* x)
+{
+    double y[9];
+    for (int i = 0; i < n; ++i) {
+        double s = b[i];
+        for (int p = 0; p < i; ++p) s -= L[i * n + p] * y[p];
+        y[i] = s / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = y[i];
+        for (int p = i + 1; p < n; ++p) s -= L[p * n + i] * x[p];
+        x[i] = s / L[i * n + i];
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * rotations
+ * ---------------------------------------------------------------------- */
+
+static void skew(const double v[3], double S[9])
+{
+    S[0] = 0.0;   S[1] = -v[2]; S[2] = v[1];
+    S[3] = v[2];  S[4] = 0.0;   S[5] = -v[0];
+    S[6] = -v[1]; S[7] = v[0];  S[8] = 0.0;
+}
+
+static void matmul3(const double* A, const double* B, double* C)
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int p = 0; p < 3; ++p) s += A[i * 3 + p] * B[p * 3 + j];
+            C[i * 3 + j] = s;
+        }
+}
+
+/* Rodrigues' formula: Exp(w) = I + a [w]x + b [w]x^2 with
+ * a = sin(th)/th, b = (1 - cos(th))/th^2 (Taylor series for small th). */
+void orc_so3_exp(const double w[3], double R[9])
+{
+    double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double th = sqrt(th2);
+    double a, b;
+    if (th < 1e-4) {
+        a = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
+        b = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+    } else {
+        a = sin(th) / th;
+        b = (1.0 - cos(th)) / th2;
+    }
+    double W[9], W2[9];
+    skew(w, W);
+    matmul3(W, W, W2);
+    for (int i = 0; i < 9; ++i) R[i] = a * W[i] + b * W2[i];
+    R[0] += 1.0; R[4] += 1.0; R[8] += 1.0;
+}
+
+/* Left Jacobian of SO(3): Exp(w + e) = Exp(Jl(w) e) Exp(w) to first order,
+ * Jl = I + (1 - cos th)/th^2 [w]x + (th - sin th)/th^3 [w]x^2. */
+void orc_so3_left_jacobian(const double w[3], double J[9])
+{
+    double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double th = sqrt(th2);
+    double a, b;
+    if (th < 1e-4) {
+        a = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+        b = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+    } else {
+        a = (1.0 - cos(th)) / th2;
+        b = (th - sin(th)) / (th2 * th);
+    }
+    double W[9], W2[9];
+    skew(w, W);
+    matmul3(W, W, W2);
+    for (int i = 0; i < 9; ++i) J[i] = a * W[i] + b * W2[i];
+    J[0] += 1.0; J[4] += 1.0; J[8] += 1.0;
+}
+
+/* ------------------------------------------------------------------------
+ * measurement factor (Sec. 4 and Sec. 6)
+ * ---------------------------------------------------------------------- */
+
+/* Sec. 6: cost M^2 becomes M^2 (2N/M - N^2/M^2) beyond the threshold, i.e.
+ * the information of the factor is scaled by this weight. */
+double orc_huber_weight(double M, double nsigma)
+{
+    if (nsigma <= 0.0 || M <= nsigma) return 1.0;
+    return 2.0 * nsigma / M - (nsigma * nsigma) / (M * M);
+}
+
+/* Camera-frame point p = R_k (l_m - c_k) in the chart. */
+static void camera_point(const double Rref[9], const double cref[3], const double lref[3],
+                         const double xk[6], const double xl[3], double R[9], double p[3])
+{
+    double dR[9];
+    orc_so3_exp(xk + 3, dR);
+    matmul3(dR, Rref, R);
+    double d[3];
+    for (int i = 0; i < 3; ++i) d[i] = (lref[i] + xl[i]) - (cref[i] + xk[i]);
+    for (int i = 0; i < 3; ++i) p[i] = R[i * 3 + 0] * d[0] + R[i * 3 + 1] * d[1] + R[i * 3 + 2] * d[2];
+}
+
+double orc_project(const orc_cam* cam, const double Rref[9], const double cref[3], const double lref[3],
+                   const double xk[6], const double xl[3], double uv[2])
+{
+    double R[9], p[3];
+    camera_point(Rref, cref, lref, xk, xl, R, p);
+    uv[0] = cam->fx * p[0] / p[2] + cam->cx;
+    uv[1] = cam->fy * p[1] / p[2] + cam->cy;
+    return p[2];
+}
+
+int orc_linearise(const orc_cam* cam, const orc_params* prm, const double Rref[9], const double cref[3],
+                  const double lref[3], const double xk[6], const double xl[3], const double z[2],
+                  double J[18], double r[2], double* k, double A[81], double c[9])
+{
+    double R[9], p[3];
+    camera_point(Rref, cref, lref, xk, xl, R, p);
+    memset(J, 0, sizeof(double) * 18);
+    memset(A, 0, sizeof(double) * 81);
+    memset(c, 0, sizeof(double) * 9);
+    r[0] = r[1] = 0.0;
+    *k = 1.0;
+    if (p[2] < prm->z_min) return 0;
+
+    double h[2] = { cam->fx * p[0] / p[2] + cam->cx, cam->fy * p[1] / p[2] + cam->cy };
+    r[0] = z[0] - h[0];
+    r[1] = z[1] - h[1];
+
+    /* d pi / d p */
+    double Jp[6] = { cam->fx / p[2], 0.0, -cam->fx * p[0] / (p[2] * p[2]),
+                     0.0, cam->fy / p[2], -cam->fy * p[1] / (p[2] * p[2]) };
+    /* d p / d dc = -R,  d p / d dw = -[p]x Jl(dw),  d p / d dl = R */
+    double S[9], Jl[9], SJ[9];
+    skew(p, S);
+    orc_so3_left_jacobian(xk + 3, Jl);
+    matmul3(S, Jl, SJ);
+    double dp[27]; /* 3 x 9 */
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            dp[i * 9 + j] = -R[i * 3 + j];
+            dp[i * 9 + 3 + j] = -SJ[i * 3 + j];
+            dp[i * 9 + 6 + j] = R[i * 3 + j];
+        }
+    for (int a = 0; a < 2; ++a)
+        for (int j = 0; j < 9; ++j) {
+            double s = 0.0;
+            for (int i = 0; i < 3; ++i) s += Jp[a * 3 + i] * dp[i * 9 + j];
+            J[a * 9 + j] = s;
+        }
+
+    /* Sec. 6: Mahalanobis distance and Huber weight */
+    double sigma = prm->sigma_px;
+    double M = sqrt(r[0] * r[0] + r[1] * r[1]) / sigma;
+    *k = orc_huber_weight(M, prm->huber_nsigma);
+    double w = *k / (sigma * sigma);
+
+    /* Sec. 4: Lambda = J^T W J,  eta = J^T W (J x0 + r) */
+    double x0[9];
+    for (int i = 0; i < 6; ++i) x0[i] = xk[i];
+    for (int i = 0; i < 3; ++i) x0[6 + i] = xl[i];
+    double y[2];
+    for (int a = 0; a < 2; ++a) {
+        double s = r[a];
+        for (int j = 0; j < 9; ++j) s += J[a * 9 + j] * x0[j];
+        y[a] = s;
+    }
+    for (int i = 0; i < 9; ++i) {
+        for (int j = 0; j < 9; ++j) A[i * 9 + j] = w * (J[i] * J[j] + J[9 + i] * J[9 + j]);
+        c[i] = w * (J[i] * y[0] + J[9 + i] * y[1]);
+    }
+    return 1;
+}
+
+/* Sec. 5, message equations: the message to variable block a takes the
+ * product of the factor with the incoming message on block b and
+ * marginalises b:
+ *   eta_out = c_a - A_ab (A_bb + lam_in)^-1 (c_b + eta_in)
+ *   lam_out = A_aa - A_ab (A_bb + lam_in)^-1 A_ba                          */
+int orc_factor_message(const double A[81], const double c[9], int target,
+                       const double* lam_in, const double* eta_in, double* lam_out, double* eta_out)
+{
+    int a0 = target == 0 ? 0 : 6, na = target == 0 ? 6 : 3;
+    int b0 = target == 0 ? 6 : 0, nb = target == 0 ? 3 : 6;
+    double S[36], L[36], e[6];
+    for (int i = 0; i < nb; ++i) {
+        for (int j = 0; j < nb; ++j) S[i * nb + j] = A[(b0 + i) * 9 + b0 + j] + lam_in[i * nb + j];
+        e[i] = c[b0 + i] + eta_in[i];
+    }
+    if (cholesky(nb, S, L) != 0) return -1;
+    /* X = S^-1 A_ba (nb x na), y = S^-1 e */
+    double X[54], col[6], sol[6], y[6];
+    for (int j = 0; j < na; ++j) {
+        for (int i = 0; i < nb; ++i) col[i] = A[(b0 + i) * 9 + a0 + j];
+        cholesky_solve(nb, L, col, sol);
+        for (int i = 0; i < nb; ++i) X[i * na + j] = sol[i];
+    }
+    cholesky_solve(nb, L, e, y);
+    for (int i = 0; i < na; ++i) {
+        for (int j = 0; j < na; ++j) {
+            double s = A[(a0 + i) * 9 + a0 + j];
+            for (int p = 0; p < nb; ++p) s -= A[(a0 + i) * 9 + b0 + p] * X[p * na + j];
+            lam_out[i * na + j] = s;
+        }
+        double s = c[a0 + i];
+        for (int p = 0; p < nb; ++p) s -= A[(a0 + i) * 9 + b0 + p] * y[p];
+        eta_out[i] = s;
+    }
+    return 0;
+}
+
+/* Sec. 8: priors start at the measurement scale and weaken geometrically to
+ * prior_final_scale over prior_anneal_iters iterations. */
+double orc_prior_scale(const orc_params* prm, int t)
+{
+    int T = prm->prior_anneal_iters;
+    if (T <= 0) return prm->prior_final_scale;
+    int tt = t < T ? t : T;
+    return pow(prm->prior_final_scale, (double)tt / (double)T);
+}
+
+/* ------------------------------------------------------------------------
+ * graph
+ * ---------------------------------------------------------------------- */
+
+struct orc_graph {
+    orc_cam cam;
+    orc_params prm;
+    int n_kf, n_lm, n_f, t;
+    double *Rref, *cref, *lref;          /* references (initial values)          */
+    int *fk, *fm;
+    double *z;
+    unsigned char *anchored;
+    double *Dk, *Dl;                     /* prior diagonals                      */
+    double *kf_lam, *kf_eta, *lm_lam, *lm_eta;   /* beliefs b^t              */
+    double *kf_mu, *lm_mu;                       /* means of b^t             */
+    double *mk_lam, *mk_eta, *ml_lam, *ml_eta;   /* messages m^t             */
+    double *nk_lam, *nk_eta, *nl_lam, *nl_eta;   /* messages m^{t+1}         */
+    double *linA, *linc;                 /* current linearisation of each factor */
+    double *x0;                          /* its linearisation point [xk; xl]     */
+    int *tlin;                           /* iteration at which it was taken      */
+};
+
+static void* zalloc(size_t n) { return calloc(n ? n : 1, 1); }
+
+/* Belief b^t of every variable: prior(t) + sum of the current messages
+ * (Sec. 5, belief equations); then its mean by a Cholesky solve. */
+static int update_beliefs(orc_graph* g, double* max_dmu)
+{
+    double s = orc_prior_scale(&g->prm, g->t);
+    for (int v = 0; v < g->n_kf; ++v) {
+        double* L = g->kf_lam + 36 * v;
+        double* e = g->kf_eta + 6 * v;
+        memset(L, 0, sizeof(double) * 36);
+        memset(e, 0, sizeof(double) * 6);
+        for (int i = 0; i < 6; ++i) {
+            L[i * 6 + i] = s * g->Dk[6 * v + i];
+            if (g->anchored[v]) L[i * 6 + i] += g->prm.anchor_scale * g->Dk[6 * v + i];
+        }
+    }
+    for (int v = 0; v < g->n_lm; ++v) {
+        double* L = g->lm_lam + 9 * v;
+        memset(L, 0, sizeof(double) * 9);
+        memset(g->lm_eta + 3 * v, 0, sizeof(double) * 3);
+        for (int i = 0; i < 3; ++i) L[i * 3 + i] = s * g->Dl[3 * v + i];
+    }
+    for (int f = 0; f < g->n_f; ++f) {
+        int k = g->fk[f], m = g->fm[f];
+        for (int i = 0; i < 36; ++i) g->kf_lam[36 * k + i] += g->mk_lam[36 * f + i];
+        for (int i = 0; i < 6; ++i) g->kf_eta[6 * k + i] += g->mk_eta[6 * f + i];
+        for (int i = 0; i < 9; ++i) g->lm_lam[9 * m + i] += g->ml_lam[9 * f + i];
+        for (int i = 0; i < 3; ++i) g->lm_eta[3 * m + i] += g->ml_eta[3 * f + i];
+    }
+    double dmu = 0.0;
+    double Lf[36], mu[6];
+    for (int v = 0; v < g->n_kf; ++v) {
+        if (cholesky(6, g->kf_lam + 36 * v, Lf) != 0) return -1;
+        cholesky_solve(6, Lf, g->kf_eta + 6 * v, mu);
+        for (int i = 0; i < 6; ++i) {
+            double d = fabs(mu[i] - g->kf_mu[6 * v + i]);
+            if (d > dmu) dmu = d;
+            g->kf_mu[6 * v + i] = mu[i];
+        }
+    }
+    for (int v = 0; v < g->n_lm; ++v) {
+        if (cholesky(3, g->lm_lam + 9 * v, Lf) != 0) return -1;
+        cholesky_solve(3, Lf, g->lm_eta + 3 * v, mu);
+        for (int i = 0; i < 3; ++i) {
+            double d = fabs(mu[i] - g->lm_mu[3 * v + i]);
+            if (d > dmu) dmu = d;
+            g->lm_mu[3 * v + i] = mu[i];
+        }
+    }
+    if (max_dmu) *max_dmu = dmu;
+    return 0;
+}
+
+orc_graph* orc_create(const orc_cam* cam, const orc_params* prm,
+                      int n_kf, const double* kf_Rt, int n_lm, const double* lm_xyz,
+                      int n_obs, const int* obs_kf, const int* obs_lm, const double* obs_uv,
+                      int n_anchor, const int* anchor_kf)
+{
+    if (!cam || !prm || n_kf < 0 || n_lm < 0 || n_obs < 0 || n_anchor < 0) return NULL;
+    for (int f = 0; f < n_obs; ++f)
+        if (obs_kf[f] < 0 || obs_kf[f] >= n_kf || obs_lm[f] < 0 || obs_lm[f] >= n_lm) return NULL;
+    for (int a = 0; a < n_anchor; ++a)
+        if (anchor_kf[a] < 0 || anchor_kf[a] >= n_kf) return NULL;
+
+    orc_graph* g = (orc_graph*)zalloc(sizeof(orc_graph));
+    g->cam = *cam;
+    g->prm = *prm;
+    g->n_kf = n_kf; g->n_lm = n_lm; g->n_f = n_obs; g->t = 0;
+    size_t F = (size_t)n_obs;
+    g->Rref = zalloc(sizeof(double) * 9 * n_kf);
+    g->cref = zalloc(sizeof(double) * 3 * n_kf);
+    g->lref = zalloc(sizeof(double) * 3 * n_lm);
+    g->fk = zalloc(sizeof(int) * F);
+    g->fm = zalloc(sizeof(int) * F);
+    g->z = zalloc(sizeof(double) * 2 * F);
+    g->anchored = zalloc((size_t)n_kf);
+    g->Dk = zalloc(sizeof(double) * 6 * n_kf);
+    g->Dl = zalloc(sizeof(double) * 3 * n_lm);
+    g->kf_lam = zalloc(sizeof(double) * 36 * n_kf);
+    g->kf_eta = zalloc(sizeof(double) * 6 * n_kf);
+    g->lm_lam = zalloc(sizeof(double) * 9 * n_lm);
+    g->lm_eta = zalloc(sizeof(double) * 3 * n_lm);
+    g->kf_mu = zalloc(sizeof(double) * 6 * n_kf);
+    g->lm_mu = zalloc(sizeof(double) * 3 * n_lm);
+    g->mk_lam = zalloc(sizeof(double) * 36 * F);
+    g->mk_eta = zalloc(sizeof(double) * 6 * F);
+    g->ml_lam = zalloc(sizeof(double) * 9 * F);
+    g->ml_eta = zalloc(sizeof(double) * 3 * F);
+    g->nk_lam = zalloc(sizeof(double) * 36 * F);
+    g->nk_eta = zalloc(sizeof(double) * 6 * F);
+    g->nl_lam = zalloc(sizeof(double) * 9 * F);
+    g->nl_eta = zalloc(sizeof(double) * 3 * F);
+
+    /* references: R, and camera centre c = -R^T t */
+    for (int v = 0; v < n_kf; ++v) {
+        const double* Rt = kf_Rt + 12 * v;
+        for (int i = 0; i < 9; ++i) g->Rref[9 * v + i] = Rt[i];
+        for (int i = 0; i < 3; ++i)
+            g->cref[3 * v + i] = -(Rt[0 * 3 + i] * Rt[9] + Rt[1 * 3 + i] * Rt[10] + Rt[2 * 3 + i] * Rt[11]);
+    }
+    memcpy(g->lref, lm_xyz, sizeof(double) * 3 * n_lm);
+    for (int f = 0; f < n_obs; ++f) {
+        g->fk[f] = obs_kf[f];
+        g->fm[f] = obs_lm[f];
+        g->z[2 * f] = obs_uv[2 * f];
+        g->z[2 * f + 1] = obs_uv[2 * f + 1];
+    }
+    for (int a = 0; a < n_anchor; ++a) g->anchored[anchor_kf[a]] = 1;
+
+    /* Sec. 4 and Sec. 8: priors generated from the Jacobians at the initial
+     * point, at "the same scale as the measurement constraints": a variable's
+     * prior precision is the diagonal of the information one of its
+     * measurement factors gives it (Huber weight 1), averaged over its
+     * factors. */
+    orc_params p1 = *prm;
+    p1.huber_nsigma = 0.0;
+    double zero6[6] = { 0 }, J[18], r[2], k, A[81], c[9];
+    for (int f = 0; f < n_obs; ++f) {
+        int kk = g->fk[f], m = g->fm[f];
+        orc_linearise(cam, &p1, g->Rref + 9 * kk, g->cref + 3 * kk, g->lref + 3 * m, zero6, zero6,
+                      g->z + 2 * f, J, r, &k, A, c);
+        for (int i = 0; i < 6; ++i) g->Dk[6 * kk + i] += A[i * 9 + i];
+        for (int i = 0; i < 3; ++i) g->Dl[3 * m + i] += A[(6 + i) * 9 + 6 + i];
+    }
+    {
+        int* deg_k = zalloc(sizeof(int) * (n_kf ? n_kf : 1));
+        int* deg_l = zalloc(sizeof(int) * (n_lm ? n_lm : 1));
+        for (int f = 0; f < n_obs; ++f) { deg_k[g->fk[f]]++; deg_l[g->fm[f]]++; }
+        for (int v = 0; v < n_kf; ++v)
+            if (deg_k[v]) for (int i = 0; i < 6; ++i) g->Dk[6 * v + i] /= deg_k[v];
+        for (int v = 0; v < n_lm; ++v)
+            if (deg_l[v]) for (int i = 0; i < 3; ++i) g->Dl[3 * v + i] /= deg_l[v];
+        free(deg_k);
+        free(deg_l);
+    }
+    /* floor: a zero diagonal entry would leave the prior singular */
+    for (int v = 0; v < n_kf; ++v) {
+        double mx = 0.0;
+        for (int i = 0; i < 6; ++i) if (g->Dk[6 * v + i] > mx) mx = g->Dk[6 * v + i];
+        for (int i = 0; i < 6; ++i) {
+            if (mx <= 0.0) g->Dk[6 * v + i] = 1.0;
+            else if (g->Dk[6 * v + i] < 1e-9 * mx) g->Dk[6 * v + i] = 1e-9 * mx;
+        }
+    }
+    for (int v = 0; v < n_lm; ++v) {
+        double mx = 0.0;
+        for (int i = 0; i < 3; ++i) if (g->Dl[3 * v + i] > mx) mx = g->Dl[3 * v + i];
+        for (int i = 0; i < 3; ++i) {
+            if (mx <= 0.0) g->Dl[3 * v + i] = 1.0;
+            else if (g->Dl[3 * v + i] < 1e-9 * mx) g->Dl[3 * v + i] = 1e-9 * mx;
+        }
+    }
+
+    /* every factor is first linearised at the initial point (x0 = 0) */
+    g->linA = zalloc(sizeof(double) * 81 * F);
+    g->linc = zalloc(sizeof(double) * 9 * F);
+    g->x0 = zalloc(sizeof(double) * 9 * F);
+    g->tlin = zalloc(sizeof(int) * F);
+    for (int f = 0; f < n_obs; ++f) {
+        int kk = g->fk[f], m = g->fm[f];
+        orc_linearise(cam, prm, g->Rref + 9 * kk, g->cref + 3 * kk, g->lref + 3 * m, zero6, zero6,
+                      g->z + 2 * f, J, r, &k, g->linA + 81 * f, g->linc + 9 * f);
+    }
+    /* b^0 = prior(0), messages zero */
+    if (update_beliefs(g, NULL) != 0) {
+        orc_destroy(g);
+        return NULL;
+    }
+    return g;
+}
+
+void orc_destroy(orc_graph* g)
+{
+    if (!g) return;
+    void* ptrs[] = { g->Rref, g->cref, g->lref, g->fk, g->fm, g->z, g->anchored, g->Dk, g->Dl,
+                     g->kf_lam, g->kf_eta, g->lm_lam, g->lm_eta, g->kf_mu, g->lm_mu,
+                     g->mk_lam, g->mk_eta, g->ml_lam, g->ml_eta, g->nk_lam, g->nk_eta, g->nl_lam, g->nl_eta,
+                     g->linA, g->linc, g->x0, g->tlin };
+    for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
+    free(g);
+}
+
+int orc_iterate(orc_graph* g, int n, double* max_dmu)
+{
+    double J[18], r[2], k;
+    double lam_in[36], eta_in[6];
+    for (int it = 0; it < n; ++it) {
+        for (int f = 0; f < g->n_f; ++f) {
+            int kk = g->fk[f], m = g->fm[f];
+            double* x0 = g->x0 + 9 * f;
+            if (!g->prm.linear && g->t - g->tlin[f] >= g->prm.relin_interval) {
+                /* Sec. 5 / Sec. 8: relinearise when the adjacent beliefs moved
+                 * more than beta from the factor's linearisation point, at
+                 * most once every relin_interval iterations */
+                double dist2 = 0.0;
+                for (int i = 0; i < 6; ++i) dist2 += (g->kf_mu[6 * kk + i] - x0[i]) * (g->kf_mu[6 * kk + i] - x0[i]);
+                for (int i = 0; i < 3; ++i) dist2 += (g->lm_mu[3 * m + i] - x0[6 + i]) * (g->lm_mu[3 * m + i] - x0[6 + i]);
+                if (sqrt(dist2) > g->prm.relin_beta) {
+                    orc_linearise(&g->cam, &g->prm, g->Rref + 9 * kk, g->cref + 3 * kk, g->lref + 3 * m,
+                                  g->kf_mu + 6 * kk, g->lm_mu + 3 * m, g->z + 2 * f, J, r, &k,
+                                  g->linA + 81 * f, g->linc + 9 * f);
+                    for (int i = 0; i < 6; ++i) x0[i] = g->kf_mu[6 * kk + i];
+                    for (int i = 0; i < 3; ++i) x0[6 + i] = g->lm_mu[3 * m + i];
+                    g->tlin[f] = g->t;
+                }
+            }
+            const double* A = g->linA + 81 * f;
+            const double* c = g->linc + 9 * f;
+            /* to the keyframe: the landmark's belief divided by this factor's
+             * previous message to it is the variable-to-factor message */
+            for (int i = 0; i < 9; ++i) lam_in[i] = g->lm_lam[9 * m + i] - g->ml_lam[9 * f + i];
+            for (int i = 0; i < 3; ++i) eta_in[i] = g->lm_eta[3 * m + i] - g->ml_eta[3 * f + i];
+            if (orc_factor_message(A, c, 0, lam_in, eta_in, g->nk_lam + 36 * f, g->nk_eta + 6 * f) != 0) return -1;
+            /* to the landmark */
+            for (int i = 0; i < 36; ++i) lam_in[i] = g->kf_lam[36 * kk + i] - g->mk_lam[36 * f + i];
+            for (int i = 0; i < 6; ++i) eta_in[i] = g->kf_eta[6 * kk + i] - g->mk_eta[6 * f + i];
+            if (orc_factor_message(A, c, 1, lam_in, eta_in, g->nl_lam + 9 * f, g->nl_eta + 3 * f) != 0) return -1;
+            /* damping of the eta update (Sec. 5).  Messages stay undamped for
+             * undamped_iters iterations after a (re)linearisation (Sec. 8);
+             * the message sent in the iteration of a (re)linearisation --
+             * including a factor's first message -- is never damped. */
+            int hold = g->prm.undamped_iters > 1 ? g->prm.undamped_iters : 1;
+            if (g->t - g->tlin[f] >= hold) {
+                double d = g->prm.damping;
+                for (int i = 0; i < 6; ++i) g->nk_eta[6 * f + i] = (1.0 - d) * g->nk_eta[6 * f + i] + d * g->mk_eta[6 * f + i];
+                for (int i = 0; i < 3; ++i) g->nl_eta[3 * f + i] = (1.0 - d) * g->nl_eta[3 * f + i] + d * g->ml_eta[3 * f + i];
+            }
+        }
+        /* synchronous schedule: every factor used m^t; now m^{t+1} replaces it */
+        double* tmp;
+        tmp = g->mk_lam; g->mk_lam = g->nk_lam; g->nk_lam = tmp;
+        tmp = g->mk_eta; g->mk_eta = g->nk_eta; g->nk_eta = tmp;
+        tmp = g->ml_lam; g->ml_lam = g->nl_lam; g->nl_lam = tmp;
+        tmp = g->ml_eta; g->ml_eta = g->nl_eta; g->nl_eta = tmp;
+        g->t += 1;
+        if (update_beliefs(g, max_dmu) != 0) return -1;
+    }
+    return 0;
+}
+
+int orc_iterations_done(const orc_graph* g) { return g->t; }
+
+void orc_get_means(const orc_graph* g, double* kf_mu, double* lm_mu)
+{
+    memcpy(kf_mu, g->kf_mu, sizeof(double) * 6 * g->n_kf);
+    memcpy(lm_mu, g->lm_mu, sizeof(double) * 3 * g->n_lm);
+}
+
+void orc_get_world(const orc_graph* g, double* kf_Rt, double* lm_xyz)
+{
+    for (int v = 0; v < g->n_kf; ++v) {
+        double dR[9], R[9], c[3];
+        orc_so3_exp(g->kf_mu + 6 * v + 3, dR);
+        matmul3(dR, g->Rref + 9 * v, R);
+        for (int i = 0; i < 3; ++i) c[i] = g->cref[3 * v + i] + g->kf_mu[6 * v + i];
+        for (int i = 0; i < 9; ++i) kf_Rt[12 * v + i] = R[i];
+        for (int i = 0; i < 3; ++i) kf_Rt[12 * v + 9 + i] = -(R[i * 3] * c[0] + R[i * 3 + 1] * c[1] + R[i * 3 + 2] * c[2]);
+    }
+    for (int v = 0; v < g->n_lm; ++v)
+        for (int i = 0; i < 3; ++i) lm_xyz[3 * v + i] = g->lref[3 * v + i] + g->lm_mu[3 * v + i];
+}
+
+void orc_get_beliefs(const orc_graph* g, double* kf_lam, double* kf_eta, double* lm_lam, double* lm_eta)
+{
+    memcpy(kf_lam, g->kf_lam, sizeof(double) * 36 * g->n_kf);
+    memcpy(kf_eta, g->kf_eta, sizeof(double) * 6 * g->n_kf);
+    memcpy(lm_lam, g->lm_lam, sizeof(double) * 9 * g->n_lm);
+    memcpy(lm_eta, g->lm_eta, sizeof(double) * 3 * g->n_lm);
+}
+
+void orc_get_prior_diag(const orc_graph* g, double* kf_d, double* lm_d)
+{
+    memcpy(kf_d, g->Dk, sizeof(double) * 6 * g->n_kf);
+    memcpy(lm_d, g->Dl, sizeof(double) * 3 * g->n_lm);
+}
+
+void orc_get_messages(const orc_graph* g, double* mk_lam, double* mk_eta, double* ml_lam, double* ml_eta)
+{
+    memcpy(mk_lam, g->mk_lam, sizeof(double) * 36 * g->n_f);
+    memcpy(mk_eta, g->mk_eta, sizeof(double) * 6 * g->n_f);
+    memcpy(ml_lam, g->ml_lam, sizeof(double) * 9 * g->n_f);
+    memcpy(ml_eta, g->ml_eta, sizeof(double) * 3 * g->n_f);
+}
+
+/* Sec. 9.1: average reprojection error over the measurements. */
+double orc_are(const orc_graph* g, const unsigned char* mask, int* count)
+{
+    double sum = 0.0;
+    int n = 0;
+    for (int f = 0; f < g->n_f; ++f) {
+        if (mask && !mask[f]) continue;
+        int kk = g->fk[f], m = g->fm[f];
+        double uv[2];
+        double depth = orc_project(&g->cam, g->Rref + 9 * kk, g->cref + 3 * kk, g->lref + 3 * m,
+                                   g->kf_mu + 6 * kk, g->lm_mu + 3 * m, uv);
+        if (depth < g->prm.z_min) continue;
+        double du = g->z[2 * f] - uv[0], dv = g->z[2 * f + 1] - uv[1];
+        sum += sqrt(du * du + dv * dv);
+        ++n;
+    }
+    if (count) *count = n;
+    return n ? sum / n : 0.0;
+}
+
+double orc_are_vs(const orc_graph* g, const double* ref_kf_Rt, const double* ref_lm, int* count)
+{
+    double sum = 0.0;
+    int n = 0;
+    for (int f = 0; f < g->n_f; ++f) {
+        int kk = g->fk[f], m = g->fm[f];
+        double uv[2];
+        double depth = orc_project(&g->cam, g->Rref + 9 * kk, g->cref + 3 * kk, g->lref + 3 * m,
+                                   g->kf_mu + 6 * kk, g->lm_mu + 3 * m, uv);
+        const double* Rt = ref_kf_Rt + 12 * kk;
+        const double* X = ref_lm + 3 * m;
+        double p[3];
+        for (int i = 0; i < 3; ++i) p[i] = Rt[i * 3] * X[0] + Rt[i * 3 + 1] * X[1] + Rt[i * 3 + 2] * X[2] + Rt[9 + i];
+        if (depth < g->prm.z_min || p[2] < g->prm.z_min) continue;
+        double du = g->cam.fx * p[0] / p[2] + g->cam.cx - uv[0];
+        double dv = g->cam.fy * p[1] / p[2] + g->cam.cy - uv[1];
+        sum += sqrt(du * du + dv * dv);
+        ++n;
+    }
+    if (count) *count = n;
+    return n ? sum / n : 0.0;
+}
+
+int orc_huber_count(const orc_graph* g)
+{
+    int n = 0;
+    if (g->prm.huber_nsigma <= 0.0) return 0;
+    for (int f = 0; f < g->n_f; ++f) {
+        int kk = g->fk[f], m = g->fm[f];
+        double uv[2];
+        double depth = orc_project(&g->cam, g->Rref + 9 * kk, g->cref + 3 * kk, g->lref + 3 * m,
+                                   g->kf_mu + 6 * kk, g->lm_mu + 3 * m, uv);
+        if (depth < g->prm.z_min) continue;
+        double du = g->z[2 * f] - uv[0], dv = g->z[2 * f + 1] - uv[1];
+        if (sqrt(du * du + dv * dv) / g->prm.sigma_px > g->prm.huber_nsigma) ++n;
+    }
+    return n;
+}

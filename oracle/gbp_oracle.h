@@ -1,0 +1,115 @@
+/*
+ * gbp_oracle.h -- plain FP64 Gaussian Belief Propagation for bundle adjustment.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the slow, obviously-correct CPU oracle
+ * that the CUDA path is checked against.  Only the tests, the smoke check
+ * and the benchmark's CPU-baseline leg may load it; the product path never
+ * does.  It shares no code, header or table with the CUDA library.
+ *
+ * Model (Sec. 4): keyframe poses x_k and landmark points l_m, measurement
+ * h(x_k, l_m) = pi(R_k l_m + t_k) with a pinhole pi, Gaussian pixel noise
+ * sigma^2 I, weak Gaussian priors on every variable, optional Huber
+ * rescaling of each measurement factor (Sec. 6).
+ *
+ * Chart (the paper only says R_k, t_k are "derived from" x_k): every variable
+ * is a perturbation of a fixed reference equal to its initial value.
+ *   keyframe  x_k = [dc (3), dw (3)]:  R_k = Exp(dw) Rref_k,  c_k = cref_k + dc,
+ *             t_k = -R_k c_k  (c_k is the camera centre in the world frame)
+ *   landmark  x_m = [dl (3)]:          l_m = lref_m + dl
+ * so h = pi(R_k (l_m - c_k)).
+ *
+ * Schedule (Sec. 5): synchronous.  Iteration t reads beliefs b^t and the
+ * previous factor-to-variable messages m^t, writes m^{t+1} for every factor,
+ * then forms b^{t+1} = prior(t+1) + sum of m^{t+1}.
+ */
+#ifndef GBP_ORACLE_H
+#define GBP_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    double fx, fy, cx, cy;
+} orc_cam;
+
+typedef struct {
+    double damping;            /* d in the damping rule of Sec. 5 (0.4 in Sec. 8)             */
+    double huber_nsigma;       /* N_sigma of Sec. 6 in Mahalanobis units; <= 0 disables      */
+    double sigma_px;           /* measurement noise std, Sigma_M = sigma^2 I                  */
+    double prior_final_scale;  /* priors end this factor of the measurement scale (Sec. 4, 8) */
+    int    prior_anneal_iters; /* iterations over which priors weaken (Sec. 8); 0 = fixed      */
+    double anchor_scale;       /* strength of the anchor prior on anchored keyframes          */
+    double z_min;              /* a factor whose point has depth < z_min sends zero information*/
+    int    linear;             /* 1: linearise once at the initial point and never again      */
+    double relin_beta;         /* relinearise when |mu - x0| > beta (Sec. 5, 8: 0.01)          */
+    int    relin_interval;     /* ... but at most every this many iterations (Sec. 8: 10)      */
+    int    undamped_iters;     /* messages undamped this many iterations after (Sec. 8: 8)     */
+} orc_params;
+
+typedef struct orc_graph orc_graph;
+
+/* kf_Rt: n_kf x 12 (R row-major, t), world->camera.  lm_xyz: n_lm x 3.
+ * obs_*: n_obs observations (keyframe index, landmark index, pixel).
+ * Returns NULL on invalid input. */
+orc_graph* orc_create(const orc_cam* cam, const orc_params* prm,
+                      int n_kf, const double* kf_Rt, int n_lm, const double* lm_xyz,
+                      int n_obs, const int* obs_kf, const int* obs_lm, const double* obs_uv,
+                      int n_anchor, const int* anchor_kf);
+void orc_destroy(orc_graph* g);
+
+/* Run n synchronous iterations.  Returns 0, or -1 if a belief stopped being
+ * positive definite.  *max_dmu (nullable) = max_v |mu_v^{t+1} - mu_v^t|_inf of
+ * the last iteration. */
+int orc_iterate(orc_graph* g, int n, double* max_dmu);
+int orc_iterations_done(const orc_graph* g);
+
+/* Chart means of the current beliefs. */
+void orc_get_means(const orc_graph* g, double* kf_mu /* n_kf x 6 */, double* lm_mu /* n_lm x 3 */);
+/* World-frame estimates of the current beliefs. */
+void orc_get_world(const orc_graph* g, double* kf_Rt /* n_kf x 12 */, double* lm_xyz /* n_lm x 3 */);
+/* Current beliefs in information form (full symmetric matrices). */
+void orc_get_beliefs(const orc_graph* g, double* kf_lam /* n_kf x 36 */, double* kf_eta /* n_kf x 6 */,
+                     double* lm_lam /* n_lm x 9 */, double* lm_eta /* n_lm x 3 */);
+/* Prior diagonals generated at creation (before annealing). */
+void orc_get_prior_diag(const orc_graph* g, double* kf_d /* n_kf x 6 */, double* lm_d /* n_lm x 3 */);
+/* Current factor-to-variable messages (full symmetric matrices). */
+void orc_get_messages(const orc_graph* g, double* mk_lam /* n_f x 36 */, double* mk_eta /* n_f x 6 */,
+                      double* ml_lam /* n_f x 9 */, double* ml_eta /* n_f x 3 */);
+
+/* Average reprojection error over measurements whose point lies in front of
+ * the camera (depth >= z_min).  mask (nullable) selects measurements.
+ * *count (nullable) receives the number averaged. */
+double orc_are(const orc_graph* g, const unsigned char* mask, int* count);
+/* Average distance between the projections at the current means and at a
+ * reference world solution (ref_kf_Rt n_kf x 12, ref_lm n_lm x 3). */
+double orc_are_vs(const orc_graph* g, const double* ref_kf_Rt, const double* ref_lm, int* count);
+/* Number of factors currently in the Huber (linear-loss) regime. */
+int orc_huber_count(const orc_graph* g);
+
+/* ---- pieces exposed for unit pins ---- */
+void orc_so3_exp(const double w[3], double R[9]);
+void orc_so3_left_jacobian(const double w[3], double J[9]);
+double orc_huber_weight(double M, double nsigma);
+double orc_prior_scale(const orc_params* prm, int t);
+/* Projection in the chart; returns the depth p_z. */
+double orc_project(const orc_cam* cam, const double Rref[9], const double cref[3], const double lref[3],
+                   const double xk[6], const double xl[3], double uv[2]);
+/* Linearised factor at (xk, xl): J (2x9 row-major), residual r = z - h,
+ * Huber weight k, information matrix A (9x9) and vector c (9).
+ * Returns 1 if active, 0 if the point is closer than z_min (A = c = 0). */
+int orc_linearise(const orc_cam* cam, const orc_params* prm, const double Rref[9], const double cref[3],
+                  const double lref[3], const double xk[6], const double xl[3], const double z[2],
+                  double J[18], double r[2], double* k, double A[81], double c[9]);
+/* Factor-to-variable message from a 9x9 factor (A, c).  target 0: to the
+ * keyframe block (0..5), marginalising the landmark block; target 1: to the
+ * landmark block (6..8), marginalising the keyframe block.  lam_in/eta_in is
+ * the message arriving from the marginalised variable.  Returns 0, or -1 if
+ * the matrix to invert is not positive definite. */
+int orc_factor_message(const double A[81], const double c[9], int target,
+                       const double* lam_in, const double* eta_in, double* lam_out, double* eta_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
