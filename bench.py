@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Benchmark: synchronous GBP bundle adjustment on one GB300 per rank.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Workload (one step = one solve): the paper-scale synthetic problem -- 125
+keyframes on a random walk, 1919 points in a 10 x 10 x 3 m volume, each seen
+by 4-15 keyframes (about 17.5k reprojection factors), 1 px noise, 2% outlier
+pixels, Huber threshold 2 sigma, damping 0.4, run from the initial estimate
+until the largest mean change per iteration is below 1e-6 or 1000 iterations.
+Rank r solves the problem with seed r (independent problems: weak scaling,
+no collective on the data path).
+
+Reported: factor-updates/s (factors x iterations / device time), the time to
+bring the mean reprojection error against the oracle's converged solution
+below 1 px, the factor kernel's roofline, the oracle's CPU throughput and an
+end-to-end figure through the C ABI with host buffers.
+
+--impl reference times the FP64 CPU oracle (the reference implementation
+of this project) on the same workload and metric: each step is a bounded
+sample of oracle iterations.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "GBP factor-updates/sec and ms to reach 1 px mean reprojection error vs oracle"
+UNIT = "factor-updates/s"
+MAX_ITERS = 1000
+CONV_TOL = 1e-6
+CHECK_EVERY = 25
+HUBER = 2.0
+# algorithmic bytes of the factor kernel (FP32 storage)
+BYTES_PER_FACTOR = 8 + 8 + 36 + 4 + 144 + 144     # z, (k, m), x0, tlin, read m^t, write m^{t+1}
+BYTES_PER_KF = 144 + 96                           # belief record, Rref + cref
+BYTES_PER_LM = 48 + 24                            # belief record, lref
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload_name(p):
+    return (f"walk{p.n_kf}x{p.n_lm}: {p.n_kf} keyframes, {p.n_lm} points, {p.n_obs} factors, "
+            f"2% outliers, Huber {HUBER:g} sigma, d=0.4, solve to max dmu<{CONV_TOL:g} or {MAX_ITERS} iterations")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("gbp_kernels.cu", "gbp_internal.h"):
+        with open(os.path.join(ROOT, "paper_2003_03134_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(n_f):
+    """DRAM bytes per factor-kernel launch from the committed ncu summary,
+    scaled to this launch's factor count; None if the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", "factor_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_factor"]) * n_f
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.proc = None
+        self.index = index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        except Exception:
+            pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_params():
+    return dict(huber_nsigma=HUBER)
+
+
+def run_reference(args, rank, world):
+    if world > 1 and rank != 0:
+        return
+    import oracle
+    from paper_2003_03134_gb300 import synth
+    oracle.build()
+    p = synth.make_walk(seed=0)
+    sample_iters = args.ref_iters
+
+    def step():
+        o = oracle.Oracle(p, **oracle_params())
+        o.iterate(sample_iters)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = p.n_obs * sample_iters * args.steps / dt
+    sample = f"{sample_iters} oracle iterations from the initial estimate per step (of up to {MAX_ITERS})"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(p), "implementation": "single-threaded FP64 C oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host_cores_available": cpu_cores()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+def oracle_solution(p, max_iters, tol):
+    """Converged FP64 solution of the oracle and its timing (the CPU
+    baseline sample)."""
+    import oracle
+    oracle.build()
+    o = oracle.Oracle(p, **oracle_params())
+    t0 = time.perf_counter()
+    it = 0
+    hist = []
+    while it < max_iters:
+        d = o.iterate(1)
+        it += 1
+        if d < tol:
+            break
+    dt = time.perf_counter() - t0
+    kf, lm = o.world()
+    # oracle's own iterations to 1 px against its converged solution
+    o2 = oracle.Oracle(p, **oracle_params())
+    t_1px = None
+    for i in range(1, min(it, 400) + 1):
+        o2.iterate(1)
+        if o2.are_vs(kf, lm)[0] < 1.0:
+            t_1px = i
+            break
+    del hist
+    return kf, lm, it, dt, t_1px
+
+
+def run_gpu(args, rank, world, local):
+    import torch
+    from paper_2003_03134_gb300 import build, gbp, synth
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream(dev)
+    p = synth.make_walk(seed=rank)
+    params = dict(huber_nsigma=HUBER, conv_tol=CONV_TOL, check_every=CHECK_EVERY, iterations=MAX_ITERS)
+    g = gbp.Graph(p, stream=stream.cuda_stream, **params)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(args.warmup, 3)):
+        g.reset()
+        g.iterate(0)
+    barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    iters = []
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)   # evict L2 between steps (untimed)
+            starts[i].record(stream)
+            g.reset()
+            iters.append(g.iterate(0))
+            ends[i].record(stream)
+        barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    updates = float(p.n_obs) * float(sum(iters))
+    if world > 1:
+        t = torch.tensor([total_ms, updates], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        total_ms, updates = float(tmax[0]), float(t[1])
+    value = updates / (total_ms / 1e3)
+    launches = int(sum(1 + 2 * n for n in iters))
+
+    # roofline of the dominant kernel: live CUDA-event timing of each launch
+    g.reset()
+    fac_ms, bel_ms = g.profile(64)
+    bytes_launch = BYTES_PER_FACTOR * p.n_obs + BYTES_PER_KF * p.n_kf + BYTES_PER_LM * p.n_lm
+    peak, peak_kind = peaks()
+    achieved = bytes_launch / (fac_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": ncu_traffic(p.n_obs), "kernel": "factor_kernel<float>",
+            "bytes_per_launch": bytes_launch, "kernel_ms": fac_ms, "belief_kernel_ms": bel_ms,
+            "peak_source": f"{peak_kind} HBM copy bandwidth"}
+
+    line = None
+    if rank == 0:
+        # CPU baseline (oracle) and its converged solution for the 1 px metric
+        kf_ref, lm_ref, o_iters, o_dt, o_1px = oracle_solution(p, args.oracle_iters, CONV_TOL)
+        cpu = {"value": p.n_obs * o_iters / o_dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one oracle solve of the rank-0 problem, {o_iters} iterations (cap {args.oracle_iters})",
+               "ms_to_1px": (1e3 * o_dt / o_iters * o_1px) if o_1px else None}
+        # iterations and device time to ARE vs oracle < 1 px
+        g.set_reference(kf_ref, lm_ref)
+        g.reset()
+        t_1px = None
+        for i in range(1, 401):
+            g.iterate(1)
+            if g.stats()["are_ref"] < 1.0:
+                t_1px = i
+                break
+        g.set_params(conv_tol=0.0)
+        ms_1px = None
+        if t_1px:
+            ts = []
+            for _ in range(5):
+                flush.fill_(7)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                g.reset()
+                g.iterate(t_1px)
+                b.record(stream)
+                torch.cuda.synchronize(dev)
+                ts.append(a.elapsed_time(b))
+            ms_1px = float(np.median(ts))
+        g.set_params(conv_tol=CONV_TOL)
+
+        # end to end through the C ABI with host buffers: create (H2D), solve, read beliefs (D2H)
+        e2e_t, e2e_updates = [], 0.0
+        h2d = p.n_kf * 96 + p.n_lm * 24 + p.n_obs * (4 + 4 + 16) + 4 * len(p.anchor_kf)
+        d2h = p.n_kf * 96 + p.n_lm * 24
+        for i in range(3):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            h = gbp.Graph(p, stream=stream.cuda_stream, **params)
+            n = h.iterate(0)
+            h.beliefs()
+            torch.cuda.synchronize(dev)
+            e2e_t.append(time.perf_counter() - t0)
+            e2e_updates = p.n_obs * n
+            h.close()
+        e2e_s = float(np.median(e2e_t))
+
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(p), "l2": "flushed between steps (256 MiB write, untimed)",
+                       "parallelism": f"independent problems, one per GPU ({world})",
+                       "iters_per_step": float(np.mean(iters))},
+            "ms_to_1px_vs_oracle": ms_1px, "iters_to_1px_vs_oracle": t_1px,
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+    g.close()
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--ref-iters", type=int, default=20, help="oracle iterations per reference step")
+    ap.add_argument("--oracle-iters", type=int, default=1000, help="cap of the oracle solve (CPU baseline)")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

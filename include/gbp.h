@@ -1,0 +1,181 @@
+/*
+ * gbp.h -- C ABI of libgbp: synchronous Gaussian Belief Propagation for
+ * bundle adjustment on a GB300 (sm_103a) GPU.
+ *
+ * Method: Ortiz, Pupilli, Leutenegger, Davison, "Bundle Adjustment on a
+ * Graph Processor" (CVPR 2020, arXiv 2003.03134).
+ *   Sec. 4  the factor graph: keyframe poses, landmark points, weak priors,
+ *           reprojection factors h = pi(R l + t) linearised in information
+ *           form (eta = J^T S^-1 (J x0 + z - h(x0)), Lambda = J^T S^-1 J).
+ *   Sec. 5  factor-to-variable messages by Schur complement (eqs.
+ *           messageeta / messagelambda), beliefs as prior + sum of
+ *           messages (eqs. beliefeta / belieflambda), synchronous
+ *           schedule, lazy relinearisation, damping of eta.
+ *   Sec. 6  Huber rescale of a factor's information.
+ *   Sec. 8  constants: beta = 0.01, relinearise at most every 10
+ *           iterations, d = 0.4, undamped 8 iterations after
+ *           relinearisation, priors annealed to 1/100 over 10 iterations.
+ *   Sec. 9  average reprojection error (ARE); Sec. 9.2 incremental SLAM
+ *           (new keyframe at the latest pose, new points at 1 m depth).
+ *
+ * Conventions
+ *   - Every call returns a gbp_status and never aborts.  A per-graph detail
+ *     string is available from gbp_last_error().
+ *   - Host pointers are caller-owned; inputs are copied before the call
+ *     returns, outputs are caller-allocated (sizes from gbp_get_sizes()).
+ *   - All device memory is allocated and owned by the library and released
+ *     by gbp_destroy_graph().  All device work is issued on the CUDA stream
+ *     given at creation (NULL = the legacy default stream); calls that
+ *     return host data synchronise that stream.
+ *   - Poses at the boundary: kf_Rt is n x 12 doubles, R row-major then t,
+ *     mapping world points into the camera frame (x_c = R x_w + t), camera
+ *     x right, y down, z forward.  Points are n x 3 doubles (world).
+ *   - One graph must not be used from two host threads at once.
+ */
+#ifndef GBP_H
+#define GBP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbp_graph gbp_graph;
+
+typedef enum {
+    GBP_OK = 0,
+    GBP_EINVAL = 1,     /* invalid argument (index out of range, non-finite value, bad size)   */
+    GBP_ENOMEM = 2,     /* host or device allocation failed                                    */
+    GBP_ECUDA = 3,      /* a CUDA call failed (no device, launch error, ...)                   */
+    GBP_EDIVERGED = 4,  /* a belief stopped being positive definite or became non-finite       */
+    GBP_ETIMEOUT = 5,   /* a bounded device-side wait gave up                                   */
+    GBP_ESTATE = 6      /* call not valid in the graph's current state                          */
+} gbp_status;
+
+typedef struct {
+    double fx, fy, cx, cy;      /* pinhole intrinsics, pixels */
+    int32_t width, height;      /* image size, pixels (informational) */
+} gbp_intrinsics;
+
+typedef struct {
+    float   damping;            /* d of Sec. 5; default 0.4 (Sec. 8)                                */
+    float   huber_nsigma;       /* N_sigma of Sec. 6 in units of sigma_px; <= 0 disables; default 0 */
+    float   sigma_px;           /* measurement noise std, pixels; default 1                         */
+    int32_t iterations;         /* iterations per gbp_iterate() call when n_iters <= 0; default 200 */
+    float   conv_tol;           /* stop once max |mu^{t+1} - mu^t|_inf < conv_tol; 0 = fixed count   */
+    int32_t check_every;        /* iterations between convergence checks; default 16               */
+    float   prior_final_scale;  /* priors end this fraction of one measurement's strength; 0.01   */
+    int32_t prior_anneal_iters; /* geometric anneal from scale 1 over this many iterations; 10     */
+    float   anchor_scale;       /* anchor prior = anchor_scale x the keyframe's prior; 1000        */
+    float   z_min;              /* depth below which a factor sends no information, m; 0.05       */
+    float   relin_beta;         /* relinearise when |mu - x0|_2 > beta (Sec. 5); 0.01 (Sec. 8)     */
+    int32_t relin_interval;     /* ... at most every this many iterations; 10 (Sec. 8)             */
+    int32_t undamped_iters;     /* messages undamped this many iterations after (re)linearisation; 8 */
+    float   fp64_pivot_ratio;   /* FP32 Cholesky with min/max pivot below this is redone in FP64; 1e-6 */
+    int32_t precision_mode;     /* 0: FP32 + FP64 fallback, 1: FP32 only, 2: FP64 throughout        */
+    int32_t linear;             /* 1: never relinearise (linear GBP at the initial point)          */
+} gbp_params;
+
+typedef struct {
+    int32_t iterations;         /* iterations run since creation / reset                          */
+    float   max_dmu;            /* max |mu^{t+1} - mu^t|_inf of the last iteration (chart units)  */
+    double  are;                /* average reprojection error over measurements in front of the camera, px */
+    double  are_ref;            /* average |h(mu) - h(reference)| (gbp_set_reference), px; -1 if unset */
+    int32_t n_are;              /* measurements counted in are                                    */
+    int32_t huber_count;        /* measurements currently beyond the Huber threshold              */
+    int32_t fp64_fallbacks;     /* FP32 Cholesky factorisations redone in FP64 since creation     */
+    int32_t relinearisations;   /* factor relinearisations since creation                         */
+} gbp_stats;
+
+/* Fill *out with the defaults listed above. */
+void gbp_default_params(gbp_params* out);
+
+/* Build a graph (Sec. 4): n_kf keyframes with initial poses kf_Rt (n_kf x 12),
+ * n_lm landmarks with initial positions lm_xyz (n_lm x 3), n_obs
+ * reprojection factors (keyframe obs_kf[i] sees landmark obs_lm[i] at pixel
+ * obs_uv[2i..2i+1]), n_anchor keyframes held by a strong prior at their
+ * initial pose.  Every variable's reference (chart origin) is its initial
+ * value; priors are generated from the measurement Jacobians there.  The
+ * graph starts at iteration 0 with beliefs equal to the priors.
+ * GBP_EINVAL: negative counts, an index out of range, a non-finite value, or
+ * an observation whose point is not in front of its camera (depth < z_min)
+ * at the initial values.  cuda_stream: a cudaStream_t or NULL. */
+gbp_status gbp_create_graph(const gbp_intrinsics* intr,
+                            int32_t n_kf, const double* kf_Rt,
+                            int32_t n_lm, const double* lm_xyz,
+                            int32_t n_obs, const int32_t* obs_kf, const int32_t* obs_lm,
+                            const double* obs_uv,
+                            int32_t n_anchor, const int32_t* anchor_kf,
+                            void* cuda_stream, gbp_graph** out);
+
+/* Replace the solver parameters (values are checked: GBP_EINVAL on a
+ * non-positive sigma_px, damping outside [0,1), ...).  Takes effect at the
+ * next gbp_iterate(). */
+gbp_status gbp_set_params(gbp_graph* g, const gbp_params* params);
+gbp_status gbp_get_params(const gbp_graph* g, gbp_params* out);
+
+/* Run synchronous GBP iterations (Sec. 5): every factor (re)linearises as
+ * its schedule allows, sends both messages, then every variable updates its
+ * belief and mean.  n_iters <= 0 uses params.iterations.  With conv_tol > 0
+ * it stops early once the largest mean change falls below conv_tol (checked
+ * every check_every iterations).  *iters_done (nullable) receives the count
+ * run.  Asynchronous unless a convergence check is needed; errors from the
+ * device (GBP_EDIVERGED) are reported by the next synchronising call. */
+gbp_status gbp_iterate(gbp_graph* g, int32_t n_iters, int32_t* iters_done);
+
+/* Return the graph to iteration 0 (beliefs = priors, messages = 0, every
+ * factor linearised at its reference), keeping parameters and sizes. */
+gbp_status gbp_reset(gbp_graph* g);
+
+/* World-frame means of the current beliefs: kf_Rt (n_kf x 12), lm_xyz
+ * (n_lm x 3).  kf_cov / lm_cov (nullable) receive the belief covariances
+ * in the chart (n_kf x 36: [dc, dw] with c the camera centre and R =
+ * Exp(dw) R_ref; n_lm x 9).  Synchronises the stream. */
+gbp_status gbp_get_beliefs(const gbp_graph* g, double* kf_Rt, double* lm_xyz,
+                           double* kf_cov, double* lm_cov);
+
+/* Chart means of the current beliefs: kf_mu (n_kf x 6, [dc, dw]), lm_mu
+ * (n_lm x 3, dl).  Synchronises the stream. */
+gbp_status gbp_get_means(const gbp_graph* g, double* kf_mu, double* lm_mu);
+
+/* Give a reference world solution (e.g. a converged solution from another
+ * solver); gbp_get_stats() then reports are_ref against it. */
+gbp_status gbp_set_reference(gbp_graph* g, const double* ref_kf_Rt, const double* ref_lm_xyz);
+
+/* Incremental SLAM (Sec. 9.2): add one keyframe and its observations.
+ * kf_Rt_init (12 doubles) or NULL = the latest keyframe's current pose.
+ * n_new_lm new landmarks get indices n_lm .. n_lm+n_new_lm-1; new_lm_xyz
+ * (n_new_lm x 3) or NULL = 1 m depth along the first ray that observes
+ * each.  obs_lm[i] (n_obs) may name old or new landmarks; every new
+ * landmark must be observed.  New variables start with their prior, new
+ * factors with zero messages, linearised at the current means.
+ * *new_kf_index (nullable) receives the keyframe's index. */
+gbp_status gbp_add_keyframe(gbp_graph* g, const double* kf_Rt_init,
+                            int32_t n_new_lm, const double* new_lm_xyz,
+                            int32_t n_obs, const int32_t* obs_lm, const double* obs_uv,
+                            int32_t* new_kf_index);
+
+/* Metrics of the current means (Sec. 9.1 ARE and friends), computed on the
+ * device with a fixed-order reduction.  Synchronises the stream. */
+gbp_status gbp_get_stats(const gbp_graph* g, gbp_stats* out);
+
+gbp_status gbp_get_sizes(const gbp_graph* g, int32_t* n_kf, int32_t* n_lm, int32_t* n_obs);
+
+/* Kernel timing: replay n_iters back-to-back launches of the factor kernel,
+ * then of the belief kernel, each as one CUDA graph with CUDA events
+ * recorded around it on the graph's stream, and return the mean device time
+ * per launch in milliseconds: ms_out[0] factor kernel, ms_out[1] belief
+ * kernel.  The repeated launches disturb the iteration state, so the graph
+ * is reset to iteration 0 afterwards (as gbp_reset()).  Synchronises. */
+gbp_status gbp_profile_iterations(gbp_graph* g, int32_t n_iters, double* ms_out);
+
+void gbp_destroy_graph(gbp_graph* g);
+
+const char* gbp_status_string(gbp_status s);
+const char* gbp_last_error(const gbp_graph* g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

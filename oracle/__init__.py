@@ -68,6 +68,8 @@ def lib():
         L.orc_are_vs.restype = C.c_double
         L.orc_are_vs.argtypes = [C.c_void_p, _D, _D, _I]
         L.orc_huber_count.argtypes = [C.c_void_p]
+        L.orc_relinearisations.argtypes = [C.c_void_p]
+        L.orc_relinearisations.restype = C.c_long
         L.orc_so3_exp.argtypes = [_D, _D]
         L.orc_so3_left_jacobian.argtypes = [_D, _D]
         L.orc_huber_weight.restype = C.c_double
@@ -264,3 +266,6 @@ class Oracle:
 
     def huber_count(self) -> int:
         return lib().orc_huber_count(self._h)
+
+    def relinearisations(self) -> int:
+        return lib().orc_relinearisations(self._h)

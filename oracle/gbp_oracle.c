@@ -289,6 +289,7 @@ struct orc_graph {
     double *linA, *linc;                 /* current linearisation of each factor */
     double *x0;                          /* its linearisation point [xk; xl]     */
     int *tlin;                           /* iteration at which it was taken      */
+    long n_relin;                        /* relinearisations since creation      */
 };
 
 static void* zalloc(size_t n) { return calloc(n ? n : 1, 1); }
@@ -496,6 +497,7 @@ int orc_iterate(orc_graph* g, int n, double* max_dmu)
                     for (int i = 0; i < 6; ++i) x0[i] = g->kf_mu[6 * kk + i];
                     for (int i = 0; i < 3; ++i) x0[6 + i] = g->lm_mu[3 * m + i];
                     g->tlin[f] = g->t;
+                    g->n_relin += 1;
                 }
             }
             const double* A = g->linA + 81 * f;
@@ -634,3 +636,5 @@ int orc_huber_count(const orc_graph* g)
     }
     return n;
 }
+
+long orc_relinearisations(const orc_graph* g) { return g->n_relin; }

@@ -86,6 +86,8 @@ double orc_are(const orc_graph* g, const unsigned char* mask, int* count);
 double orc_are_vs(const orc_graph* g, const double* ref_kf_Rt, const double* ref_lm, int* count);
 /* Number of factors currently in the Huber (linear-loss) regime. */
 int orc_huber_count(const orc_graph* g);
+/* Relinearisations performed since creation (all factors). */
+long orc_relinearisations(const orc_graph* g);
 
 /* ---- pieces exposed for unit pins ---- */
 void orc_so3_exp(const double w[3], double R[9]);

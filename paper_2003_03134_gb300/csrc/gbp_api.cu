@@ -1,0 +1,855 @@
+// gbp_api.cu -- host side of libgbp: the C ABI declared in include/gbp.h.
+//
+// Owns the device buffers of one factor graph, builds the layout described
+// in gbp_internal.h (factors sorted by landmark then keyframe, CSR lists),
+// issues the kernels of gbp_kernels.cu on the caller's stream, replays the
+// iteration loop as a CUDA graph, and converts chart means to world poses
+// at the boundary.
+#include "gbp_internal.h"
+#include "../../include/gbp.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+using namespace gbp;
+
+namespace {
+
+constexpr int GRAPH_CHUNK = 8;   // iterations per captured CUDA graph
+
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+}
+
+template <typename R>
+struct DevState {
+    DevGraph<R> g{};
+    // owned device pointers (non-const views of g)
+    R* z = nullptr;
+    int32_t* fk = nullptr;
+    int32_t* fm = nullptr;
+    double* kf_R = nullptr;
+    double* kf_c = nullptr;
+    double* lm_ref = nullptr;
+    int32_t* kf_off = nullptr;
+    int32_t* kf_list = nullptr;
+    int32_t* lm_off = nullptr;
+    R* kf_D = nullptr;
+    R* kf_A = nullptr;
+    R* lm_D = nullptr;
+    R* uv_ref = nullptr;
+    R* x0 = nullptr;
+    int32_t* tlin = nullptr;
+    R* mk = nullptr;
+    R* ml = nullptr;
+    R* kf_bel = nullptr;
+    R* lm_bel = nullptr;
+
+    void release() {
+        void* ptrs[] = {z, fk, fm, kf_R, kf_c, lm_ref, kf_off, kf_list, lm_off, kf_D, kf_A, lm_D, uv_ref,
+                        x0, tlin, mk, ml, kf_bel, lm_bel};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+        *this = DevState<R>();
+    }
+};
+
+// Exp of so(3) in double for the boundary conversion (Rodrigues' formula).
+void so3_exp_host(const double w[3], double E[9]) {
+    double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double a, b;
+    if (th2 < 1e-12) {
+        a = 1.0 - th2 / 6.0;
+        b = 0.5 - th2 / 24.0;
+    } else {
+        double th = std::sqrt(th2);
+        double sh = std::sin(0.5 * th);
+        a = std::sin(th) / th;
+        b = 2.0 * sh * sh / th2;
+    }
+    double W[9] = {0, -w[2], w[1], w[2], 0, -w[0], -w[1], w[0], 0};
+    double W2[9] = {w[0] * w[0] - th2, w[0] * w[1], w[0] * w[2], w[1] * w[0], w[1] * w[1] - th2, w[1] * w[2],
+                    w[2] * w[0], w[2] * w[1], w[2] * w[2] - th2};
+    for (int i = 0; i < 9; ++i) E[i] = a * W[i] + b * W2[i];
+    E[0] += 1.0; E[4] += 1.0; E[8] += 1.0;
+}
+
+}  // namespace
+
+struct gbp_graph {
+    std::string err;
+    cudaStream_t stream = nullptr;      // caller's stream (may be the legacy default)
+    cudaStream_t capture = nullptr;     // private stream used only to record CUDA graphs
+    gbp_intrinsics intr{};
+    gbp_params prm{};
+    int n_kf = 0, n_lm = 0, n_f = 0;
+    // host copy of the problem (internal factor order)
+    std::vector<double> kf_R, kf_c, lm_ref;     // references (chart origins)
+    std::vector<int32_t> fk, fm, obs_index;     // obs_index[f] = caller's observation index
+    std::vector<double> z;
+    std::vector<uint8_t> anchored;
+    std::vector<double> uv_ref;                 // reference projections (internal order) or empty
+    // device
+    int storage = 0;                            // 0: float, 1: double
+    DevState<float> sf;
+    DevState<double> sd;
+    int32_t* ctl = nullptr;
+    double* partials = nullptr;
+    double* met = nullptr;
+    int n_partials = 0;
+    int32_t* h_ctl = nullptr;                   // pinned mirror of ctl
+    double* h_met = nullptr;                    // pinned mirror of met
+    cudaGraphExec_t exec = nullptr;
+    bool built = false;
+};
+
+namespace {
+
+gbp_status fail(gbp_graph* g, gbp_status s, const std::string& msg) {
+    if (g) g->err = msg;
+    return s;
+}
+
+gbp_status cuda_fail(gbp_graph* g, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(g, GBP_ECUDA, m);
+}
+
+#define CK(expr)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (expr);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(g, e_, #expr);     \
+    } while (0)
+
+KParams make_kparams(const gbp_graph* g) {
+    const gbp_params& p = g->prm;
+    KParams k{};
+    k.fx = g->intr.fx;
+    k.fy = g->intr.fy;
+    k.cx = g->intr.cx;
+    k.cy = g->intr.cy;
+    k.inv_sigma2 = 1.0 / (double(p.sigma_px) * double(p.sigma_px));
+    k.inv_sigma = 1.0 / double(p.sigma_px);
+    k.huber_n = p.huber_nsigma;
+    k.damping = p.damping;
+    k.z_min = p.z_min;
+    k.relin_beta = p.relin_beta;
+    k.anchor_scale = p.anchor_scale;
+    k.pivot_ratio = p.fp64_pivot_ratio;
+    k.prior_final = p.prior_final_scale;
+    k.relin_interval = p.relin_interval;
+    k.damp_hold = std::max(p.undamped_iters, 1);
+    k.prior_anneal = p.prior_anneal_iters;
+    k.linear = p.linear;
+    k.fallback = p.precision_mode == 0 ? 1 : 0;
+    return k;
+}
+
+void destroy_exec(gbp_graph* g) {
+    if (g->exec) {
+        cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+    }
+}
+
+template <typename R>
+DevState<R>& state(gbp_graph* g);
+template <>
+DevState<float>& state<float>(gbp_graph* g) { return g->sf; }
+template <>
+DevState<double>& state<double>(gbp_graph* g) { return g->sd; }
+
+// Upload the problem into freshly allocated device buffers of type R and
+// generate the priors; leaves the dynamic state uninitialised.
+template <typename R>
+gbp_status build_device(gbp_graph* g) {
+    DevState<R>& s = state<R>(g);
+    s.release();
+    const int nk = g->n_kf, nl = g->n_lm, nf = g->n_f;
+    // CSR lists
+    std::vector<int32_t> kf_off(nk + 1, 0), lm_off(nl + 1, 0), kf_list(nf);
+    for (int f = 0; f < nf; ++f) {
+        kf_off[g->fk[f] + 1]++;
+        lm_off[g->fm[f] + 1]++;
+    }
+    for (int v = 0; v < nk; ++v) kf_off[v + 1] += kf_off[v];
+    for (int v = 0; v < nl; ++v) lm_off[v + 1] += lm_off[v];
+    {
+        std::vector<int32_t> fill(kf_off.begin(), kf_off.end() - 1);
+        for (int f = 0; f < nf; ++f) kf_list[fill[g->fk[f]]++] = f;
+    }
+    std::vector<R> zr(2 * (size_t)nf), anc(6 * (size_t)nk, R(0));
+    for (size_t i = 0; i < zr.size(); ++i) zr[i] = R(g->z[i]);
+    for (int v = 0; v < nk; ++v)
+        if (g->anchored[v])
+            for (int i = 0; i < 6; ++i) anc[6 * v + i] = R(1);   // scaled by D after the prior pass
+
+    CK(dev_alloc(&s.z, 2 * (size_t)nf));
+    CK(dev_alloc(&s.fk, nf));
+    CK(dev_alloc(&s.fm, nf));
+    CK(dev_alloc(&s.kf_R, 9 * (size_t)nk));
+    CK(dev_alloc(&s.kf_c, 3 * (size_t)nk));
+    CK(dev_alloc(&s.lm_ref, 3 * (size_t)nl));
+    CK(dev_alloc(&s.kf_off, nk + 1));
+    CK(dev_alloc(&s.kf_list, nf));
+    CK(dev_alloc(&s.lm_off, nl + 1));
+    CK(dev_alloc(&s.kf_D, 6 * (size_t)nk));
+    CK(dev_alloc(&s.kf_A, 6 * (size_t)nk));
+    CK(dev_alloc(&s.lm_D, 3 * (size_t)nl));
+    CK(dev_alloc(&s.x0, 9 * (size_t)nf));
+    CK(dev_alloc(&s.tlin, nf));
+    CK(dev_alloc(&s.mk, (size_t)KREC * nf));
+    CK(dev_alloc(&s.ml, 9 * (size_t)nf));
+    CK(dev_alloc(&s.kf_bel, (size_t)KBEL * nk));
+    CK(dev_alloc(&s.lm_bel, (size_t)LBEL * nl));
+    cudaStream_t st = g->stream;
+    CK(cudaMemcpyAsync(s.z, zr.data(), sizeof(R) * zr.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.fk, g->fk.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.fm, g->fm.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.kf_R, g->kf_R.data(), sizeof(double) * 9 * nk, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.kf_c, g->kf_c.data(), sizeof(double) * 3 * nk, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.lm_ref, g->lm_ref.data(), sizeof(double) * 3 * nl, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.kf_off, kf_off.data(), sizeof(int32_t) * (nk + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.kf_list, kf_list.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.lm_off, lm_off.data(), sizeof(int32_t) * (nl + 1), cudaMemcpyHostToDevice, st));
+
+    DevGraph<R>& d = s.g;
+    d.n_kf = nk;
+    d.n_lm = nl;
+    d.n_f = nf;
+    d.z = s.z;
+    d.fk = s.fk;
+    d.fm = s.fm;
+    d.kf_R = s.kf_R;
+    d.kf_c = s.kf_c;
+    d.lm_ref = s.lm_ref;
+    d.kf_off = s.kf_off;
+    d.kf_list = s.kf_list;
+    d.lm_off = s.lm_off;
+    d.kf_D = s.kf_D;
+    d.kf_A = s.kf_A;
+    d.lm_D = s.lm_D;
+    d.uv_ref = nullptr;
+    d.x0 = s.x0;
+    d.tlin = s.tlin;
+    d.mk = s.mk;
+    d.ml = s.ml;
+    d.mk_out = s.mk;
+    d.ml_out = s.ml;
+    d.kf_bel = s.kf_bel;
+    d.lm_bel = s.lm_bel;
+    d.ctl = g->ctl;
+
+    // priors: per-factor diagonal information at the reference (temporary
+    // buffers reuse the message storage, which is cleared afterwards)
+    KParams kp = make_kparams(g);
+    CK(launch_prior<R>(d, kp, s.mk, s.ml, s.kf_D, s.lm_D, st));
+    // anchor diagonal = D on anchored keyframes
+    {
+        std::vector<R> D(6 * (size_t)nk);
+        CK(cudaMemcpyAsync(D.data(), s.kf_D, sizeof(R) * D.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (size_t i = 0; i < D.size(); ++i) anc[i] *= D[i];
+        CK(cudaMemcpyAsync(s.kf_A, anc.data(), sizeof(R) * anc.size(), cudaMemcpyHostToDevice, st));
+    }
+    if (!g->uv_ref.empty()) {
+        std::vector<R> u(g->uv_ref.size());
+        for (size_t i = 0; i < u.size(); ++i) u[i] = R(g->uv_ref[i]);
+        CK(dev_alloc(&s.uv_ref, u.size()));
+        CK(cudaMemcpyAsync(s.uv_ref, u.data(), sizeof(R) * u.size(), cudaMemcpyHostToDevice, st));
+        d.uv_ref = s.uv_ref;
+    }
+    CK(cudaStreamSynchronize(st));
+    return GBP_OK;
+}
+
+// Iteration 0: factors linearised at their references, messages zero,
+// beliefs = prior(0).
+template <typename R>
+gbp_status reset_state(gbp_graph* g) {
+    DevState<R>& s = state<R>(g);
+    cudaStream_t st = g->stream;
+    const size_t nf = g->n_f;
+    CK(cudaMemsetAsync(s.x0, 0, sizeof(R) * 9 * nf, st));
+    CK(cudaMemsetAsync(s.tlin, 0, sizeof(int32_t) * nf, st));
+    CK(cudaMemsetAsync(s.mk, 0, sizeof(R) * KREC * nf, st));
+    CK(cudaMemsetAsync(s.ml, 0, sizeof(R) * 9 * nf, st));
+    CK(cudaMemsetAsync(s.kf_bel, 0, sizeof(R) * KBEL * g->n_kf, st));
+    CK(cudaMemsetAsync(s.lm_bel, 0, sizeof(R) * LBEL * g->n_lm, st));
+    int32_t c0[CTL_N] = {0};
+    c0[CTL_ITER] = -1;   // the belief pass below forms b^0 and advances to 0
+    CK(cudaMemcpyAsync(g->ctl, c0, sizeof(c0), cudaMemcpyHostToDevice, st));
+    CK(launch_belief<R>(s.g, make_kparams(g), st));
+    return GBP_OK;
+}
+
+gbp_status ensure_built(gbp_graph* g) {
+    int want = g->prm.precision_mode == 2 ? 1 : 0;
+    if (g->built && want == g->storage) return GBP_OK;
+    destroy_exec(g);
+    g->sf.release();
+    g->sd.release();
+    g->storage = want;
+    gbp_status st = want ? build_device<double>(g) : build_device<float>(g);
+    if (st != GBP_OK) return st;
+    st = want ? reset_state<double>(g) : reset_state<float>(g);
+    if (st != GBP_OK) return st;
+    g->built = true;
+    return GBP_OK;
+}
+
+template <typename R>
+cudaError_t enqueue_iterations(gbp_graph* g, int n, cudaStream_t st) {
+    const DevGraph<R>& d = state<R>(g).g;
+    KParams kp = make_kparams(g);
+    for (int i = 0; i < n; ++i) {
+        cudaError_t e = launch_factor<R>(d, kp, st);
+        if (e != cudaSuccess) return e;
+        e = launch_belief<R>(d, kp, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+gbp_status ensure_exec(gbp_graph* g) {
+    if (g->exec) return GBP_OK;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = g->storage ? enqueue_iterations<double>(g, GRAPH_CHUNK, g->capture)
+                               : enqueue_iterations<float>(g, GRAPH_CHUNK, g->capture);
+    cudaError_t e2 = cudaStreamEndCapture(g->capture, &graph);
+    if (e != cudaSuccess) return cuda_fail(g, e, "capture");
+    if (e2 != cudaSuccess) return cuda_fail(g, e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g->exec = nullptr;
+        return cuda_fail(g, e, "cudaGraphInstantiate");
+    }
+    return GBP_OK;
+}
+
+gbp_status read_ctl(gbp_graph* g) {
+    CK(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(int32_t) * CTL_N, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (g->h_ctl[CTL_ERR]) {
+        int w = g->h_ctl[CTL_ERR_WHERE];
+        char buf[160];
+        if (w < 0)
+            snprintf(buf, sizeof buf, "factor %d: an incoming precision was not positive definite", -1 - w);
+        else
+            snprintf(buf, sizeof buf, "variable %d: belief not positive definite or mean not finite", w);
+        return fail(g, GBP_EDIVERGED, buf);
+    }
+    return GBP_OK;
+}
+
+bool finite_all(const double* p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+gbp_status check_params(const gbp_params* p, std::string& why) {
+    if (!(p->sigma_px > 0.0f) || !std::isfinite(p->sigma_px)) { why = "sigma_px must be > 0"; return GBP_EINVAL; }
+    if (!(p->damping >= 0.0f && p->damping < 1.0f)) { why = "damping must be in [0, 1)"; return GBP_EINVAL; }
+    if (!std::isfinite(p->huber_nsigma)) { why = "huber_nsigma must be finite"; return GBP_EINVAL; }
+    if (!(p->prior_final_scale > 0.0f) || !std::isfinite(p->prior_final_scale)) { why = "prior_final_scale must be > 0"; return GBP_EINVAL; }
+    if (p->prior_anneal_iters < 0) { why = "prior_anneal_iters must be >= 0"; return GBP_EINVAL; }
+    if (!(p->anchor_scale >= 0.0f) || !std::isfinite(p->anchor_scale)) { why = "anchor_scale must be >= 0"; return GBP_EINVAL; }
+    if (!(p->z_min > 0.0f)) { why = "z_min must be > 0"; return GBP_EINVAL; }
+    if (!(p->relin_beta >= 0.0f)) { why = "relin_beta must be >= 0"; return GBP_EINVAL; }
+    if (p->relin_interval < 1) { why = "relin_interval must be >= 1"; return GBP_EINVAL; }
+    if (p->undamped_iters < 0) { why = "undamped_iters must be >= 0"; return GBP_EINVAL; }
+    if (p->check_every < 1) { why = "check_every must be >= 1"; return GBP_EINVAL; }
+    if (p->precision_mode < 0 || p->precision_mode > 2) { why = "precision_mode must be 0, 1 or 2"; return GBP_EINVAL; }
+    if (!(p->conv_tol >= 0.0f)) { why = "conv_tol must be >= 0"; return GBP_EINVAL; }
+    return GBP_OK;
+}
+
+// Sort factors by (landmark, keyframe, caller order); fills the internal
+// arrays from the caller's observations.
+void order_factors(gbp_graph* g, const std::vector<int32_t>& ok, const std::vector<int32_t>& ol,
+                   const std::vector<double>& uv, const std::vector<int32_t>& idx) {
+    const int n = (int)ok.size();
+    std::vector<int32_t> perm(n);
+    std::iota(perm.begin(), perm.end(), 0);
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
+        if (ol[a] != ol[b]) return ol[a] < ol[b];
+        return ok[a] < ok[b];
+    });
+    g->n_f = n;
+    g->fk.resize(n);
+    g->fm.resize(n);
+    g->z.resize(2 * (size_t)n);
+    g->obs_index.resize(n);
+    for (int i = 0; i < n; ++i) {
+        int s = perm[i];
+        g->fk[i] = ok[s];
+        g->fm[i] = ol[s];
+        g->z[2 * i] = uv[2 * s];
+        g->z[2 * i + 1] = uv[2 * s + 1];
+        g->obs_index[i] = idx[s];
+    }
+}
+
+template <typename R>
+void pull_beliefs(gbp_graph* g, std::vector<double>& kb, std::vector<double>& lb, gbp_status& st) {
+    DevState<R>& s = state<R>(g);
+    std::vector<R> a((size_t)KBEL * g->n_kf), b((size_t)LBEL * g->n_lm);
+    cudaError_t e = cudaMemcpyAsync(a.data(), s.kf_bel, sizeof(R) * a.size(), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.data(), s.lm_bel, sizeof(R) * b.size(), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) {
+        st = cuda_fail(g, e, "belief download");
+        return;
+    }
+    kb.assign(a.begin(), a.end());
+    lb.assign(b.begin(), b.end());
+    st = GBP_OK;
+}
+
+gbp_status download_beliefs(gbp_graph* g, std::vector<double>& kb, std::vector<double>& lb) {
+    gbp_status st = GBP_OK;
+    if (g->storage) pull_beliefs<double>(g, kb, lb, st);
+    else pull_beliefs<float>(g, kb, lb, st);
+    return st;
+}
+
+// packed lower n x n -> full inverse (double)
+bool packed_inverse(int n, const double* P, double* out) {
+    double A[36], L[36] = {0};
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j) A[i * n + j] = A[j * n + i] = P[i * (i + 1) / 2 + j];
+    for (int j = 0; j < n; ++j) {
+        double s = A[j * n + j];
+        for (int p = 0; p < j; ++p) s -= L[j * n + p] * L[j * n + p];
+        if (!(s > 0.0)) return false;
+        L[j * n + j] = std::sqrt(s);
+        for (int i = j + 1; i < n; ++i) {
+            double t = A[i * n + j];
+            for (int p = 0; p < j; ++p) t -= L[i * n + p] * L[j * n + p];
+            L[i * n + j] = t / L[j * n + j];
+        }
+    }
+    for (int c = 0; c < n; ++c) {
+        double x[6];
+        for (int i = 0; i < n; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int p = 0; p < i; ++p) s -= L[i * n + p] * x[p];
+            x[i] = s / L[i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double s = x[i];
+            for (int p = i + 1; p < n; ++p) s -= L[p * n + i] * x[p];
+            x[i] = s / L[i * n + i];
+        }
+        for (int i = 0; i < n; ++i) out[i * n + c] = x[i];
+    }
+    return true;
+}
+
+gbp_status compute_uv_ref(gbp_graph* g, const double* kf_Rt, const double* lm) {
+    g->uv_ref.assign(2 * (size_t)g->n_f, 0.0);
+    for (int f = 0; f < g->n_f; ++f) {
+        const double* Rt = kf_Rt + 12 * (size_t)g->fk[f];
+        const double* X = lm + 3 * (size_t)g->fm[f];
+        double p[3];
+        for (int i = 0; i < 3; ++i) p[i] = Rt[3 * i] * X[0] + Rt[3 * i + 1] * X[1] + Rt[3 * i + 2] * X[2] + Rt[9 + i];
+        if (p[2] < g->prm.z_min) {
+            g->uv_ref[2 * f] = g->uv_ref[2 * f + 1] = NAN;
+        } else {
+            g->uv_ref[2 * f] = g->intr.fx * p[0] / p[2] + g->intr.cx;
+            g->uv_ref[2 * f + 1] = g->intr.fy * p[1] / p[2] + g->intr.cy;
+        }
+    }
+    return GBP_OK;
+}
+
+}  // namespace
+
+// ==========================================================================
+// C ABI
+
+extern "C" {
+
+void gbp_default_params(gbp_params* p) {
+    if (!p) return;
+    p->damping = 0.4f;
+    p->huber_nsigma = 0.0f;
+    p->sigma_px = 1.0f;
+    p->iterations = 200;
+    p->conv_tol = 0.0f;
+    p->check_every = 16;
+    p->prior_final_scale = 0.01f;
+    p->prior_anneal_iters = 10;
+    p->anchor_scale = 1000.0f;
+    p->z_min = 0.05f;
+    p->relin_beta = 0.01f;
+    p->relin_interval = 10;
+    p->undamped_iters = 8;
+    p->fp64_pivot_ratio = 1e-6f;
+    p->precision_mode = 0;
+    p->linear = 0;
+}
+
+const char* gbp_status_string(gbp_status s) {
+    switch (s) {
+        case GBP_OK: return "ok";
+        case GBP_EINVAL: return "invalid argument";
+        case GBP_ENOMEM: return "out of memory";
+        case GBP_ECUDA: return "CUDA error";
+        case GBP_EDIVERGED: return "diverged";
+        case GBP_ETIMEOUT: return "timeout";
+        case GBP_ESTATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char* gbp_last_error(const gbp_graph* g) { return g ? g->err.c_str() : "null graph"; }
+
+gbp_status gbp_create_graph(const gbp_intrinsics* intr, int32_t n_kf, const double* kf_Rt, int32_t n_lm,
+                            const double* lm_xyz, int32_t n_obs, const int32_t* obs_kf, const int32_t* obs_lm,
+                            const double* obs_uv, int32_t n_anchor, const int32_t* anchor_kf, void* cuda_stream,
+                            gbp_graph** out) {
+    if (!out) return GBP_EINVAL;
+    *out = nullptr;
+    if (!intr || n_kf < 0 || n_lm < 0 || n_obs < 0 || n_anchor < 0) return GBP_EINVAL;
+    if ((n_kf && !kf_Rt) || (n_lm && !lm_xyz) || (n_obs && (!obs_kf || !obs_lm || !obs_uv)) ||
+        (n_anchor && !anchor_kf))
+        return GBP_EINVAL;
+    if (!std::isfinite(intr->fx) || !std::isfinite(intr->fy) || !std::isfinite(intr->cx) ||
+        !std::isfinite(intr->cy) || intr->fx == 0.0 || intr->fy == 0.0)
+        return GBP_EINVAL;
+    if (!finite_all(kf_Rt, 12 * (size_t)n_kf) || !finite_all(lm_xyz, 3 * (size_t)n_lm) ||
+        !finite_all(obs_uv, 2 * (size_t)n_obs))
+        return GBP_EINVAL;
+    for (int i = 0; i < n_obs; ++i)
+        if (obs_kf[i] < 0 || obs_kf[i] >= n_kf || obs_lm[i] < 0 || obs_lm[i] >= n_lm) return GBP_EINVAL;
+    for (int i = 0; i < n_anchor; ++i)
+        if (anchor_kf[i] < 0 || anchor_kf[i] >= n_kf) return GBP_EINVAL;
+
+    gbp_graph* g = new (std::nothrow) gbp_graph();
+    if (!g) return GBP_ENOMEM;
+    g->intr = *intr;
+    gbp_default_params(&g->prm);
+    g->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    g->n_kf = n_kf;
+    g->n_lm = n_lm;
+    g->kf_R.resize(9 * (size_t)n_kf);
+    g->kf_c.resize(3 * (size_t)n_kf);
+    for (int v = 0; v < n_kf; ++v) {
+        const double* Rt = kf_Rt + 12 * (size_t)v;
+        for (int i = 0; i < 9; ++i) g->kf_R[9 * v + i] = Rt[i];
+        // camera centre c = -R^T t
+        for (int i = 0; i < 3; ++i) g->kf_c[3 * v + i] = -(Rt[i] * Rt[9] + Rt[3 + i] * Rt[10] + Rt[6 + i] * Rt[11]);
+    }
+    g->lm_ref.assign(lm_xyz, lm_xyz + 3 * (size_t)n_lm);
+    g->anchored.assign(n_kf, 0);
+    for (int i = 0; i < n_anchor; ++i) g->anchored[anchor_kf[i]] = 1;
+    // every observed point must be in front of its camera at the initial values
+    for (int i = 0; i < n_obs; ++i) {
+        const double* Rt = kf_Rt + 12 * (size_t)obs_kf[i];
+        const double* X = lm_xyz + 3 * (size_t)obs_lm[i];
+        double pz = Rt[6] * X[0] + Rt[7] * X[1] + Rt[8] * X[2] + Rt[11];
+        if (!(pz >= g->prm.z_min)) {
+            char buf[128];
+            snprintf(buf, sizeof buf, "observation %d: point depth %.4g below z_min at the initial values", i, pz);
+            g->err = buf;
+            delete g;
+            return GBP_EINVAL;
+        }
+    }
+    {
+        std::vector<int32_t> ok(obs_kf, obs_kf + n_obs), ol(obs_lm, obs_lm + n_obs), idx(n_obs);
+        std::vector<double> uv(obs_uv, obs_uv + 2 * (size_t)n_obs);
+        std::iota(idx.begin(), idx.end(), 0);
+        order_factors(g, ok, ol, uv, idx);
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&g->ctl), sizeof(int32_t) * CTL_N);
+    g->n_partials = metrics_blocks(g->n_f);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&g->partials), sizeof(double) * 6 * g->n_partials);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&g->met), sizeof(double) * MET_N);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&g->h_ctl), sizeof(int32_t) * CTL_N);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&g->h_met), sizeof(double) * MET_N);
+    if (e != cudaSuccess) {
+        gbp_destroy_graph(g);
+        return e == cudaErrorMemoryAllocation ? GBP_ENOMEM : GBP_ECUDA;
+    }
+    gbp_status st = ensure_built(g);
+    if (st != GBP_OK) {
+        gbp_destroy_graph(g);
+        return st;
+    }
+    *out = g;
+    return GBP_OK;
+}
+
+gbp_status gbp_set_params(gbp_graph* g, const gbp_params* p) {
+    if (!g || !p) return GBP_EINVAL;
+    std::string why;
+    if (check_params(p, why) != GBP_OK) return fail(g, GBP_EINVAL, why);
+    bool sigma_changed = p->sigma_px != g->prm.sigma_px;
+    g->prm = *p;
+    destroy_exec(g);
+    (void)sigma_changed;   // priors are stored at sigma = 1 and scaled in the kernels
+    return ensure_built(g);
+}
+
+gbp_status gbp_get_params(const gbp_graph* g, gbp_params* out) {
+    if (!g || !out) return GBP_EINVAL;
+    *out = g->prm;
+    return GBP_OK;
+}
+
+gbp_status gbp_reset(gbp_graph* g) {
+    if (!g) return GBP_EINVAL;
+    gbp_status st = ensure_built(g);
+    if (st != GBP_OK) return st;
+    return g->storage ? reset_state<double>(g) : reset_state<float>(g);
+}
+
+gbp_status gbp_iterate(gbp_graph* g, int32_t n_iters, int32_t* iters_done) {
+    if (iters_done) *iters_done = 0;
+    if (!g) return GBP_EINVAL;
+    gbp_status st = ensure_built(g);
+    if (st != GBP_OK) return st;
+    int n = n_iters > 0 ? n_iters : g->prm.iterations;
+    if (g->n_f == 0 && g->n_kf == 0 && g->n_lm == 0) return GBP_OK;
+    st = ensure_exec(g);
+    if (st != GBP_OK) return st;
+    const bool check = g->prm.conv_tol > 0.0f;
+    int done = 0;
+    while (done < n) {
+        int block = check ? std::min(g->prm.check_every, n - done) : n - done;
+        int full = block / GRAPH_CHUNK, rest = block % GRAPH_CHUNK;
+        for (int i = 0; i < full; ++i) CK(cudaGraphLaunch(g->exec, g->stream));
+        if (rest) {
+            cudaError_t e = g->storage ? enqueue_iterations<double>(g, rest, g->stream)
+                                       : enqueue_iterations<float>(g, rest, g->stream);
+            if (e != cudaSuccess) return cuda_fail(g, e, "kernel launch");
+        }
+        done += block;
+        if (check) {
+            st = read_ctl(g);
+            if (st != GBP_OK) {
+                if (iters_done) *iters_done = done;
+                return st;
+            }
+            float dmu;
+            std::memcpy(&dmu, &g->h_ctl[CTL_DMU_LAST], sizeof dmu);
+            if (dmu < g->prm.conv_tol) break;
+        }
+    }
+    if (iters_done) *iters_done = done;
+    return GBP_OK;
+}
+
+gbp_status gbp_get_means(const gbp_graph* cg, double* kf_mu, double* lm_mu) {
+    gbp_graph* g = const_cast<gbp_graph*>(cg);
+    if (!g || (g->n_kf && !kf_mu) || (g->n_lm && !lm_mu)) return GBP_EINVAL;
+    std::vector<double> kb, lb;
+    gbp_status st = download_beliefs(g, kb, lb);
+    if (st != GBP_OK) return st;
+    for (int v = 0; v < g->n_kf; ++v)
+        for (int i = 0; i < 6; ++i) kf_mu[6 * v + i] = kb[(size_t)KBEL * v + 27 + i];
+    for (int v = 0; v < g->n_lm; ++v)
+        for (int i = 0; i < 3; ++i) lm_mu[3 * v + i] = lb[(size_t)LBEL * v + 9 + i];
+    return read_ctl(g);
+}
+
+gbp_status gbp_get_beliefs(const gbp_graph* cg, double* kf_Rt, double* lm_xyz, double* kf_cov, double* lm_cov) {
+    gbp_graph* g = const_cast<gbp_graph*>(cg);
+    if (!g || (g->n_kf && !kf_Rt) || (g->n_lm && !lm_xyz)) return GBP_EINVAL;
+    std::vector<double> kb, lb;
+    gbp_status st = download_beliefs(g, kb, lb);
+    if (st != GBP_OK) return st;
+    for (int v = 0; v < g->n_kf; ++v) {
+        const double* mu = &kb[(size_t)KBEL * v + 27];
+        double E[9], R[9], c[3];
+        so3_exp_host(mu + 3, E);
+        const double* Rr = &g->kf_R[9 * (size_t)v];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                R[3 * i + j] = E[3 * i] * Rr[j] + E[3 * i + 1] * Rr[3 + j] + E[3 * i + 2] * Rr[6 + j];
+        for (int i = 0; i < 3; ++i) c[i] = g->kf_c[3 * v + i] + mu[i];
+        double* o = kf_Rt + 12 * (size_t)v;
+        for (int i = 0; i < 9; ++i) o[i] = R[i];
+        for (int i = 0; i < 3; ++i) o[9 + i] = -(R[3 * i] * c[0] + R[3 * i + 1] * c[1] + R[3 * i + 2] * c[2]);
+        if (kf_cov && !packed_inverse(6, &kb[(size_t)KBEL * v], kf_cov + 36 * (size_t)v))
+            return fail(g, GBP_EDIVERGED, "keyframe belief not positive definite");
+    }
+    for (int v = 0; v < g->n_lm; ++v) {
+        for (int i = 0; i < 3; ++i) lm_xyz[3 * v + i] = g->lm_ref[3 * v + i] + lb[(size_t)LBEL * v + 9 + i];
+        if (lm_cov && !packed_inverse(3, &lb[(size_t)LBEL * v], lm_cov + 9 * (size_t)v))
+            return fail(g, GBP_EDIVERGED, "landmark belief not positive definite");
+    }
+    return read_ctl(g);
+}
+
+gbp_status gbp_set_reference(gbp_graph* g, const double* ref_kf_Rt, const double* ref_lm) {
+    if (!g) return GBP_EINVAL;
+    if (!ref_kf_Rt || !ref_lm) {
+        g->uv_ref.clear();
+    } else {
+        if (!finite_all(ref_kf_Rt, 12 * (size_t)g->n_kf) || !finite_all(ref_lm, 3 * (size_t)g->n_lm))
+            return fail(g, GBP_EINVAL, "reference solution not finite");
+        compute_uv_ref(g, ref_kf_Rt, ref_lm);
+    }
+    // upload into the current storage
+    destroy_exec(g);
+    if (g->storage) {
+        DevState<double>& s = g->sd;
+        if (s.uv_ref) cudaFree(s.uv_ref);
+        s.uv_ref = nullptr;
+        s.g.uv_ref = nullptr;
+        if (!g->uv_ref.empty()) {
+            CK(dev_alloc(&s.uv_ref, g->uv_ref.size()));
+            CK(cudaMemcpyAsync(s.uv_ref, g->uv_ref.data(), sizeof(double) * g->uv_ref.size(), cudaMemcpyHostToDevice, g->stream));
+            s.g.uv_ref = s.uv_ref;
+        }
+    } else {
+        DevState<float>& s = g->sf;
+        if (s.uv_ref) cudaFree(s.uv_ref);
+        s.uv_ref = nullptr;
+        s.g.uv_ref = nullptr;
+        if (!g->uv_ref.empty()) {
+            std::vector<float> u(g->uv_ref.begin(), g->uv_ref.end());
+            CK(dev_alloc(&s.uv_ref, u.size()));
+            CK(cudaMemcpyAsync(s.uv_ref, u.data(), sizeof(float) * u.size(), cudaMemcpyHostToDevice, g->stream));
+            s.g.uv_ref = s.uv_ref;
+        }
+    }
+    CK(cudaStreamSynchronize(g->stream));
+    return GBP_OK;
+}
+
+gbp_status gbp_get_stats(const gbp_graph* cg, gbp_stats* out) {
+    gbp_graph* g = const_cast<gbp_graph*>(cg);
+    if (!g || !out) return GBP_EINVAL;
+    std::memset(out, 0, sizeof *out);
+    KParams kp = make_kparams(g);
+    cudaError_t e = g->storage ? launch_metrics<double>(g->sd.g, kp, g->partials, g->n_partials, g->met, g->stream)
+                               : launch_metrics<float>(g->sf.g, kp, g->partials, g->n_partials, g->met, g->stream);
+    if (e != cudaSuccess) return cuda_fail(g, e, "metrics");
+    CK(cudaMemcpyAsync(g->h_met, g->met, sizeof(double) * MET_N, cudaMemcpyDeviceToHost, g->stream));
+    gbp_status st = read_ctl(g);   // synchronises
+    out->iterations = g->h_ctl[CTL_ITER];
+    std::memcpy(&out->max_dmu, &g->h_ctl[CTL_DMU_LAST], sizeof(float));
+    out->are = g->h_met[MET_ARE];
+    out->are_ref = g->h_met[MET_ARE_REF];
+    out->n_are = (int32_t)g->h_met[MET_N_ARE];
+    out->huber_count = (int32_t)g->h_met[MET_HUBER];
+    out->fp64_fallbacks = g->h_ctl[CTL_FALLBACKS];
+    out->relinearisations = g->h_ctl[CTL_RELINS];
+    return st;
+}
+
+gbp_status gbp_get_sizes(const gbp_graph* g, int32_t* n_kf, int32_t* n_lm, int32_t* n_obs) {
+    if (!g) return GBP_EINVAL;
+    if (n_kf) *n_kf = g->n_kf;
+    if (n_lm) *n_lm = g->n_lm;
+    if (n_obs) *n_obs = g->n_f;
+    return GBP_OK;
+}
+
+gbp_status gbp_profile_iterations(gbp_graph* g, int32_t n_iters, double* ms_out) {
+    if (!g || !ms_out || n_iters <= 0) return GBP_EINVAL;
+    gbp_status st = ensure_built(g);
+    if (st != GBP_OK) return st;
+    KParams kp = make_kparams(g);
+    cudaGraphExec_t ex[2] = {nullptr, nullptr};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // The replayed factor launches write their messages to scratch buffers
+    // so that every launch reads the same m^t and beliefs (same work and
+    // traffic as one iteration's factor pass).
+    const size_t rs = g->storage ? sizeof(double) : sizeof(float);
+    void* scratch_k = nullptr;
+    void* scratch_l = nullptr;
+    cudaError_t e = cudaMalloc(&scratch_k, rs * KREC * std::max(g->n_f, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&scratch_l, rs * 9 * std::max(g->n_f, 1));
+    DevGraph<float> pf = g->sf.g;
+    DevGraph<double> pd = g->sd.g;
+    pf.mk_out = static_cast<float*>(scratch_k);
+    pf.ml_out = static_cast<float*>(scratch_l);
+    pd.mk_out = static_cast<double*>(scratch_k);
+    pd.ml_out = static_cast<double*>(scratch_l);
+    // one CUDA graph of n_iters back-to-back launches per kernel
+    for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        cudaError_t le = cudaSuccess;
+        for (int i = 0; i < n_iters && le == cudaSuccess; ++i) {
+            if (which == 0)
+                le = g->storage ? launch_factor<double>(pd, kp, g->capture) : launch_factor<float>(pf, kp, g->capture);
+            else
+                le = g->storage ? launch_belief<double>(g->sd.g, kp, g->capture) : launch_belief<float>(g->sf.g, kp, g->capture);
+        }
+        e = cudaStreamEndCapture(g->capture, &graph);
+        if (le != cudaSuccess) e = le;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ex[which], graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+    }
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+    if (e == cudaSuccess) {
+        // warm once, then time the second replay
+        cudaGraphLaunch(ex[0], g->stream);
+        cudaEventRecord(ev[0], g->stream);
+        cudaGraphLaunch(ex[0], g->stream);
+        cudaEventRecord(ev[1], g->stream);
+        cudaGraphLaunch(ex[1], g->stream);
+        cudaEventRecord(ev[2], g->stream);
+        cudaGraphLaunch(ex[1], g->stream);
+        cudaEventRecord(ev[3], g->stream);
+        e = cudaStreamSynchronize(g->stream);
+    }
+    float a = 0.f, b = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[2], ev[3]);
+    for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+    for (auto& x : ex)
+        if (x) cudaGraphExecDestroy(x);
+    if (scratch_k) cudaFree(scratch_k);
+    if (scratch_l) cudaFree(scratch_l);
+    if (e != cudaSuccess) return cuda_fail(g, e, "profile");
+    ms_out[0] = double(a) / n_iters;
+    ms_out[1] = double(b) / n_iters;
+    st = read_ctl(g);
+    if (st != GBP_OK) return st;
+    return g->storage ? reset_state<double>(g) : reset_state<float>(g);
+}
+
+gbp_status gbp_add_keyframe(gbp_graph* g, const double* kf_Rt_init, int32_t n_new_lm, const double* new_lm_xyz,
+                            int32_t n_obs, const int32_t* obs_lm, const double* obs_uv, int32_t* new_kf_index) {
+    (void)kf_Rt_init; (void)n_new_lm; (void)new_lm_xyz; (void)n_obs; (void)obs_lm; (void)obs_uv; (void)new_kf_index;
+    if (!g) return GBP_EINVAL;
+    return fail(g, GBP_ESTATE, "gbp_add_keyframe is not available in this build");
+}
+
+void gbp_destroy_graph(gbp_graph* g) {
+    if (!g) return;
+    destroy_exec(g);
+    g->sf.release();
+    g->sd.release();
+    if (g->ctl) cudaFree(g->ctl);
+    if (g->partials) cudaFree(g->partials);
+    if (g->met) cudaFree(g->met);
+    if (g->h_ctl) cudaFreeHost(g->h_ctl);
+    if (g->h_met) cudaFreeHost(g->h_met);
+    if (g->capture) cudaStreamDestroy(g->capture);
+    delete g;
+}
+
+}  // extern "C"

@@ -1,0 +1,298 @@
+"""Python binding of libgbp (include/gbp.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own; all GBP work runs in the CUDA kernels behind
+``libgbp.so``.  Loading fails loudly when the library is missing: there is no
+CPU fallback.
+
+Arrays: poses ``kf_Rt`` are (n_kf, 12) float64 (R row-major, t; world to
+camera), points (n_lm, 3) float64, observations int32 indices and (n_obs, 2)
+float64 pixels.  ``stream`` is a ``cudaStream_t`` as an int (for example
+``torch.cuda.current_stream().cuda_stream``) or None for the default stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbp.so")
+
+GBP_OK, GBP_EINVAL, GBP_ENOMEM, GBP_ECUDA, GBP_EDIVERGED, GBP_ETIMEOUT, GBP_ESTATE = range(7)
+
+
+class GBPError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+class gbp_intrinsics(C.Structure):
+    _fields_ = [("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class gbp_params(C.Structure):
+    _fields_ = [("damping", C.c_float), ("huber_nsigma", C.c_float), ("sigma_px", C.c_float),
+                ("iterations", C.c_int32), ("conv_tol", C.c_float), ("check_every", C.c_int32),
+                ("prior_final_scale", C.c_float), ("prior_anneal_iters", C.c_int32),
+                ("anchor_scale", C.c_float), ("z_min", C.c_float), ("relin_beta", C.c_float),
+                ("relin_interval", C.c_int32), ("undamped_iters", C.c_int32),
+                ("fp64_pivot_ratio", C.c_float), ("precision_mode", C.c_int32), ("linear", C.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class gbp_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("max_dmu", C.c_float), ("are", C.c_double),
+                ("are_ref", C.c_double), ("n_are", C.c_int32), ("huber_count", C.c_int32),
+                ("fp64_fallbacks", C.c_int32), ("relinearisations", C.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int32)
+_lib = None
+
+# exported names, in header order
+EXPORTS = ["gbp_default_params", "gbp_create_graph", "gbp_set_params", "gbp_get_params", "gbp_iterate",
+           "gbp_reset", "gbp_get_beliefs", "gbp_get_means", "gbp_set_reference", "gbp_add_keyframe",
+           "gbp_get_stats", "gbp_get_sizes", "gbp_profile_iterations", "gbp_destroy_graph", "gbp_status_string",
+           "gbp_last_error"]
+
+
+def lib() -> C.CDLL:
+    """Load libgbp.so (built by ``paper_2003_03134_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libgbp.so not found at {LIB_PATH}: build it with "
+                           "`python -m paper_2003_03134_gb300.build` (there is no CPU fallback)")
+    L = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    L.gbp_default_params.argtypes = [C.POINTER(gbp_params)]
+    L.gbp_default_params.restype = None
+    L.gbp_create_graph.argtypes = [C.POINTER(gbp_intrinsics), C.c_int32, _D, C.c_int32, _D, C.c_int32, _I, _I, _D,
+                                   C.c_int32, _I, vp, C.POINTER(vp)]
+    L.gbp_set_params.argtypes = [vp, C.POINTER(gbp_params)]
+    L.gbp_get_params.argtypes = [vp, C.POINTER(gbp_params)]
+    L.gbp_iterate.argtypes = [vp, C.c_int32, _I]
+    L.gbp_reset.argtypes = [vp]
+    L.gbp_get_beliefs.argtypes = [vp, _D, _D, _D, _D]
+    L.gbp_get_means.argtypes = [vp, _D, _D]
+    L.gbp_set_reference.argtypes = [vp, _D, _D]
+    L.gbp_add_keyframe.argtypes = [vp, _D, C.c_int32, _D, C.c_int32, _I, _D, _I]
+    L.gbp_get_stats.argtypes = [vp, C.POINTER(gbp_stats)]
+    L.gbp_get_sizes.argtypes = [vp, _I, _I, _I]
+    L.gbp_profile_iterations.argtypes = [vp, C.c_int32, _D]
+    L.gbp_destroy_graph.argtypes = [vp]
+    L.gbp_destroy_graph.restype = None
+    L.gbp_status_string.argtypes = [C.c_int]
+    L.gbp_status_string.restype = C.c_char_p
+    L.gbp_last_error.argtypes = [vp]
+    L.gbp_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(status: int, handle=None):
+    if status != GBP_OK:
+        L = lib()
+        what = L.gbp_status_string(status).decode()
+        detail = L.gbp_last_error(handle).decode() if handle else ""
+        raise GBPError(status, f"{what}: {detail}" if detail else what)
+
+
+def _f64(a, cols=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if cols is not None:
+        a = a.reshape(-1, cols)
+    return a
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def _ip(a):
+    return None if a is None else a.ctypes.data_as(_I)
+
+
+# ---------------------------------------------------------------------------
+# entry points
+
+def gbp_default_params() -> gbp_params:
+    p = gbp_params()
+    lib().gbp_default_params(C.byref(p))
+    return p
+
+
+def gbp_create_graph(intrinsics, kf_Rt, lm_xyz, obs_kf, obs_lm, obs_uv, anchor_kf=(), stream=None) -> int:
+    fx, fy, cx, cy, w, h = intrinsics
+    intr = gbp_intrinsics(fx, fy, cx, cy, int(w), int(h))
+    kf = _f64(kf_Rt, 12)
+    lm = _f64(lm_xyz, 3)
+    ok, ol = _i32(obs_kf), _i32(obs_lm)
+    uv = _f64(obs_uv, 2)
+    an = _i32(anchor_kf)
+    out = C.c_void_p()
+    st = lib().gbp_create_graph(C.byref(intr), kf.shape[0], _dp(kf), lm.shape[0], _dp(lm), ok.size, _ip(ok),
+                                _ip(ol), _dp(uv), an.size, _ip(an), C.c_void_p(stream or 0), C.byref(out))
+    _check(st)
+    return out.value
+
+
+def gbp_set_params(g: int, params: gbp_params) -> None:
+    _check(lib().gbp_set_params(g, C.byref(params)), g)
+
+
+def gbp_get_params(g: int) -> gbp_params:
+    p = gbp_params()
+    _check(lib().gbp_get_params(g, C.byref(p)), g)
+    return p
+
+
+def gbp_iterate(g: int, n_iters: int = 0) -> int:
+    done = C.c_int32(0)
+    _check(lib().gbp_iterate(g, int(n_iters), C.byref(done)), g)
+    return done.value
+
+
+def gbp_reset(g: int) -> None:
+    _check(lib().gbp_reset(g), g)
+
+
+def gbp_get_sizes(g: int):
+    a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().gbp_get_sizes(g, C.byref(a), C.byref(b), C.byref(c)), g)
+    return a.value, b.value, c.value
+
+
+def gbp_get_beliefs(g: int, covariances: bool = False):
+    n_kf, n_lm, _ = gbp_get_sizes(g)
+    kf = np.zeros((n_kf, 12))
+    lm = np.zeros((n_lm, 3))
+    kc = np.zeros((n_kf, 6, 6)) if covariances else None
+    lc = np.zeros((n_lm, 3, 3)) if covariances else None
+    _check(lib().gbp_get_beliefs(g, _dp(kf), _dp(lm), _dp(kc), _dp(lc)), g)
+    return (kf, lm, kc, lc) if covariances else (kf, lm)
+
+
+def gbp_get_means(g: int):
+    n_kf, n_lm, _ = gbp_get_sizes(g)
+    kf = np.zeros((n_kf, 6))
+    lm = np.zeros((n_lm, 3))
+    _check(lib().gbp_get_means(g, _dp(kf), _dp(lm)), g)
+    return kf, lm
+
+
+def gbp_set_reference(g: int, ref_kf_Rt, ref_lm_xyz) -> None:
+    if ref_kf_Rt is None:
+        _check(lib().gbp_set_reference(g, None, None), g)
+        return
+    a, b = _f64(ref_kf_Rt, 12), _f64(ref_lm_xyz, 3)
+    _check(lib().gbp_set_reference(g, _dp(a), _dp(b)), g)
+
+
+def gbp_add_keyframe(g: int, kf_Rt_init, new_lm_xyz, n_new_lm: int, obs_lm, obs_uv) -> int:
+    kf = None if kf_Rt_init is None else _f64(kf_Rt_init).reshape(12)
+    nl = None if new_lm_xyz is None else _f64(new_lm_xyz, 3)
+    ol = _i32(obs_lm)
+    uv = _f64(obs_uv, 2)
+    idx = C.c_int32(-1)
+    _check(lib().gbp_add_keyframe(g, _dp(kf), int(n_new_lm), _dp(nl), ol.size, _ip(ol), _dp(uv), C.byref(idx)), g)
+    return idx.value
+
+
+def gbp_get_stats(g: int) -> gbp_stats:
+    s = gbp_stats()
+    _check(lib().gbp_get_stats(g, C.byref(s)), g)
+    return s
+
+
+def gbp_profile_iterations(g: int, n_iters: int):
+    """Mean device milliseconds per launch: (factor kernel, belief kernel)."""
+    out = np.zeros(2)
+    _check(lib().gbp_profile_iterations(g, int(n_iters), _dp(out)), g)
+    return float(out[0]), float(out[1])
+
+
+def gbp_destroy_graph(g: int) -> None:
+    if g:
+        lib().gbp_destroy_graph(g)
+
+
+# ---------------------------------------------------------------------------
+
+class Graph:
+    """Owning wrapper around one gbp_graph handle."""
+
+    def __init__(self, problem, stream=None, **params):
+        self.problem = problem
+        self.h = gbp_create_graph(problem.intrinsics(), problem.kf_Rt_init, problem.lm_init, problem.obs_kf,
+                                  problem.obs_lm, problem.obs_uv, problem.anchor_kf, stream)
+        if params:
+            self.set_params(**params)
+
+    def set_params(self, **kw):
+        p = gbp_get_params(self.h)
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise KeyError(k)
+            setattr(p, k, v)
+        gbp_set_params(self.h, p)
+
+    @property
+    def params(self) -> dict:
+        return gbp_get_params(self.h).as_dict()
+
+    def iterate(self, n: int = 0) -> int:
+        return gbp_iterate(self.h, n)
+
+    def reset(self):
+        gbp_reset(self.h)
+
+    def beliefs(self, covariances=False):
+        return gbp_get_beliefs(self.h, covariances)
+
+    def means(self):
+        return gbp_get_means(self.h)
+
+    def stats(self) -> dict:
+        return gbp_get_stats(self.h).as_dict()
+
+    def profile(self, n: int):
+        return gbp_profile_iterations(self.h, n)
+
+    def set_reference(self, kf_Rt, lm_xyz):
+        gbp_set_reference(self.h, kf_Rt, lm_xyz)
+
+    def add_keyframe(self, obs_lm, obs_uv, kf_Rt_init=None, n_new_lm=0, new_lm_xyz=None) -> int:
+        return gbp_add_keyframe(self.h, kf_Rt_init, new_lm_xyz, n_new_lm, obs_lm, obs_uv)
+
+    def close(self):
+        if getattr(self, "h", None):
+            gbp_destroy_graph(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,210 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances: FP32 path -- per-variable relative error of the world-frame mean
+|x_gpu - x_orc| / max(|x_orc|, 1) <= 1e-5 and |ARE_gpu - ARE_orc| <= 1e-3 px
+after a fixed number of iterations; FP64 path -- the same quantities to
+1e-9, which pins the kernel logic independently of FP32 rounding."""
+import copy
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2003_03134_gb300 import build, gbp, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+TOL64 = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    oracle.build()
+    gbp.lib()
+
+
+def rel_err(kf, lm, okf, olm):
+    ek = np.linalg.norm(kf - okf, axis=1) / np.maximum(np.linalg.norm(okf, axis=1), 1.0)
+    el = np.linalg.norm(lm - olm, axis=1) / np.maximum(np.linalg.norm(olm, axis=1), 1.0)
+    return np.concatenate([ek, el])
+
+
+def run_pair(p, n, gpu_params=None, orc_params=None):
+    gpu_params = dict(gpu_params or {})
+    orc_params = dict(orc_params or {})
+    g = gbp.Graph(p, **gpu_params)
+    assert g.iterate(n) == n
+    kf, lm = g.beliefs()
+    st = g.stats()
+    o = oracle.Oracle(p, **orc_params)
+    o.iterate(n)
+    okf, olm = o.world()
+    g.close()
+    return kf, lm, st, okf, olm, o
+
+
+def test_fp64_mode_matches_oracle_tightly():
+    p = synth.make_circle(0)
+    kf, lm, st, okf, olm, o = run_pair(p, 200, dict(precision_mode=2))
+    assert rel_err(kf, lm, okf, olm).max() < TOL64
+    assert abs(st["are"] - o.are()[0]) < 1e-9
+
+
+def test_fp64_mode_walk_with_huber_and_relinearisation():
+    p = synth.make_walk(1, n_kf=30, n_lm=400)
+    kf, lm, st, okf, olm, o = run_pair(p, 120, dict(precision_mode=2, huber_nsigma=2.0), dict(huber_nsigma=2.0))
+    assert rel_err(kf, lm, okf, olm).max() < 1e-8
+    assert st["huber_count"] == o.huber_count()
+    assert st["relinearisations"] > 0
+
+
+def test_fp32_circle_matches_oracle():
+    p = synth.make_circle(0)
+    kf, lm, st, okf, olm, o = run_pair(p, 200)
+    e = rel_err(kf, lm, okf, olm)
+    assert e.max() <= TOL32, (e.max(), np.median(e))
+    assert abs(st["are"] - o.are()[0]) <= 1e-3
+
+
+# The relinearisation test |mu - x0| > beta (Sec. 5) is a threshold on a
+# floating-point distance: FP32 and FP64 means differ by ~1e-7 relative, so a
+# factor whose distance sits within that of beta can relinearise on one side
+# and not the other, and the two trajectories then part.  Element-wise
+# parity is therefore checked with the schedule made deterministic (beta = 0:
+# every factor relinearises exactly every relin_interval iterations), which
+# leaves every other step of the arithmetic unchanged.
+DET = dict(relin_beta=0.0, relin_interval=10)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_fp32_walk_matches_oracle(seed):
+    p = synth.make_walk(seed, n_kf=40, n_lm=600)
+    kf, lm, st, okf, olm, o = run_pair(p, 150, dict(huber_nsigma=2.0, **DET), dict(huber_nsigma=2.0, **DET))
+    e = rel_err(kf, lm, okf, olm)
+    assert e.max() <= TOL32, (e.max(), np.median(e))
+    assert abs(st["are"] - o.are()[0]) <= 1e-3
+    assert st["relinearisations"] == o.relinearisations()
+
+
+def test_fp32_paper_scale_walk_matches_oracle():
+    """The benchmark's workload (125 keyframes, 1919 points, ~17k factors)."""
+    p = synth.make_walk(0)
+    kf, lm, st, okf, olm, o = run_pair(p, 200, dict(huber_nsigma=2.0, **DET), dict(huber_nsigma=2.0, **DET))
+    e = rel_err(kf, lm, okf, olm)
+    assert e.max() <= TOL32, (e.max(), np.median(e), np.percentile(e, 99))
+    assert abs(st["are"] - o.are()[0]) <= 1e-3
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_fp32_paper_schedule_properties(seed):
+    """With the paper's beta = 0.01 compare what threshold decisions cannot
+    move: relinearisation counts, the mean reprojection error and the bulk of
+    the per-variable errors."""
+    p = synth.make_walk(seed) if seed == 0 else synth.make_walk(seed, n_kf=40, n_lm=600)
+    kf, lm, st, okf, olm, o = run_pair(p, 200, dict(huber_nsigma=2.0), dict(huber_nsigma=2.0))
+    e = rel_err(kf, lm, okf, olm)
+    assert abs(st["relinearisations"] - o.relinearisations()) <= max(2, 1e-3 * o.relinearisations())
+    assert abs(st["are"] - o.are()[0]) <= 1e-3
+    assert np.median(e) <= 5e-6
+    assert np.mean(e <= TOL32) >= 0.9
+
+
+def test_linear_mode_matches_oracle():
+    p = synth.make_circle(3, n_kf=6, n_lm=40)
+    kf, lm, st, okf, olm, o = run_pair(p, 300, dict(linear=1, precision_mode=2), dict(linear=1))
+    assert rel_err(kf, lm, okf, olm).max() < TOL64
+
+
+def test_inactive_factors_match_oracle():
+    """Raising z_min after creation deactivates the factors whose point is
+    closer than z_min at their linearisation point; both sides must send
+    zero information from them."""
+    p = synth.make_circle(0)
+    zmin = 1.9
+    kf, lm, st, okf, olm, o = run_pair(p, 100, dict(z_min=zmin, precision_mode=2), dict(z_min=zmin))
+    assert st["n_are"] < p.n_obs
+    assert rel_err(kf, lm, okf, olm).max() < TOL64
+
+
+def test_no_observations_keeps_the_initial_estimate():
+    p = synth.make_circle(0, n_kf=3, n_lm=5)
+    q = copy.deepcopy(p)
+    q.obs_kf = q.obs_kf[:0]
+    q.obs_lm = q.obs_lm[:0]
+    q.obs_uv = q.obs_uv[:0]
+    g = gbp.Graph(q)
+    g.iterate(5)
+    kf, lm = g.beliefs()
+    np.testing.assert_allclose(kf, q.kf_Rt_init, atol=1e-12)
+    np.testing.assert_allclose(lm, q.lm_init, atol=1e-12)
+    g.close()
+
+
+def test_single_observation_landmark_and_uneven_degrees():
+    p = synth.make_walk(3, n_kf=12, n_lm=60)
+    # drop all but one observation of the first 5 landmarks
+    keep = np.ones(p.n_obs, bool)
+    for m in range(5):
+        idx = np.nonzero(p.obs_lm == m)[0]
+        keep[idx[1:]] = False
+    q = copy.deepcopy(p)
+    q.obs_kf, q.obs_lm, q.obs_uv, q.obs_outlier = p.obs_kf[keep], p.obs_lm[keep], p.obs_uv[keep], p.obs_outlier[keep]
+    kf, lm, st, okf, olm, o = run_pair(q, 60, dict(precision_mode=2), {})
+    # a point seen once is fixed along its ray only by its weak prior: the
+    # conditioning (~1e4) amplifies rounding-order differences
+    assert rel_err(kf, lm, okf, olm).max() < 1e-8
+
+
+def test_bitwise_deterministic_and_reset():
+    p = synth.make_walk(0, n_kf=30, n_lm=300)
+    a = gbp.Graph(p, huber_nsigma=2.0)
+    b = gbp.Graph(p, huber_nsigma=2.0)
+    a.iterate(37)
+    b.iterate(37)
+    ma, mb = a.means(), b.means()
+    for x, y in zip(ma, mb):
+        np.testing.assert_array_equal(x, y)
+    a.reset()
+    a.iterate(37)
+    for x, y in zip(a.means(), mb):
+        np.testing.assert_array_equal(x, y)
+    a.close()
+    b.close()
+
+
+def test_convergence_tolerance_stops_early():
+    p = synth.make_circle(2)
+    g = gbp.Graph(p, conv_tol=1e-4, check_every=5)
+    done = g.iterate(1000)
+    assert done < 1000
+    assert g.stats()["max_dmu"] < 1e-4
+    g.close()
+
+
+def test_are_against_reference_solution():
+    p = synth.make_circle(1)
+    g = gbp.Graph(p)
+    g.iterate(50)
+    o = oracle.Oracle(p)
+    o.iterate(50)
+    g.set_reference(p.kf_Rt_true, p.lm_true)
+    st = g.stats()
+    are_vs, _ = o.are_vs(p.kf_Rt_true, p.lm_true)
+    assert abs(st["are_ref"] - are_vs) < 1e-3
+    g.close()
+
+
+def test_invalid_params_rejected():
+    p = synth.make_circle(0, n_kf=3, n_lm=5)
+    g = gbp.Graph(p)
+    for bad in (dict(sigma_px=0.0), dict(damping=1.0), dict(relin_interval=0), dict(precision_mode=5)):
+        with pytest.raises(gbp.GBPError) as e:
+            g.set_params(**bad)
+        assert e.value.status == gbp.GBP_EINVAL
+    g.close()
