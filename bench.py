@@ -28,6 +28,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -96,7 +97,8 @@ class ClockSampler:
     def __init__(self, index):
         self.proc = None
         self.index = index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        out_dir = os.environ.get("GBP_BENCH_OUT", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, f"gbp_clocks_rank{index}.csv")
 
     def __enter__(self):
         try:
