@@ -172,6 +172,41 @@ gbp_status gbp_profile_iterations(gbp_graph* g, int32_t n_iters, double* ms_out)
 
 void gbp_destroy_graph(gbp_graph* g);
 
+/* Largest n_obs that gbp_reprojection_error_noalloc() accepts. */
+#define GBP_NOALLOC_MAX_OBS (1 << 20)
+
+/* Average reprojection error of caller-owned DEVICE arrays, computed without
+ * allocating any memory.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they need the
+ * number -- for example a real-time loop that reserves all device memory at
+ * start-up and must not pay cudaMalloc's device-wide synchronisation later,
+ * or an application whose own allocator owns all device memory.
+ *   intr      pinhole intrinsics (host pointer)
+ *   z_min     observations whose point lies closer than z_min to the camera
+ *             are left out of the average
+ *   kf_Rt     device, n_kf x 12 doubles (R row-major, t; world to camera)
+ *   lm_xyz    device, n_lm x 3 doubles
+ *   obs_kf, obs_lm  device, n_obs int32 indices (not range-checked here)
+ *   obs_uv    device, n_obs x 2 doubles (pixels)
+ *   out       device, 2 doubles: out[0] = mean |z - pi(R l + t)| in pixels,
+ *             out[1] = number of observations averaged
+ *   cuda_stream  stream to run on (NULL = legacy default stream); the call
+ *             is asynchronous on it.
+ * Scratch: a fixed 64 KiB array in the library's device memory, present on
+ * every GPU that loads the library until the process exits; no cudaMalloc,
+ * cudaFree or allocating library routine is called.  The first call on a
+ * device looks up that array's device address (make it before any stream
+ * capture).  All calls share the array and it keeps the last call's partial
+ * sums, so calls whose kernels overlap on the GPU (different streams, or
+ * several host threads) race and must be serialised by the caller.
+ * GBP_EINVAL: n_obs < 0, n_obs > GBP_NOALLOC_MAX_OBS (the scratch array's
+ * capacity), or a required pointer is NULL.  GBP_ECUDA: no device or a
+ * launch failed. */
+gbp_status gbp_reprojection_error_noalloc(const gbp_intrinsics* intr, double z_min, const double* kf_Rt,
+                                          const double* lm_xyz, int32_t n_obs, const int32_t* obs_kf,
+                                          const int32_t* obs_lm, const double* obs_uv, double* out,
+                                          void* cuda_stream);
+
 const char* gbp_status_string(gbp_status s);
 const char* gbp_last_error(const gbp_graph* g);
 

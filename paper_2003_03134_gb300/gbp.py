@@ -63,7 +63,8 @@ _lib = None
 EXPORTS = ["gbp_default_params", "gbp_create_graph", "gbp_set_params", "gbp_get_params", "gbp_iterate",
            "gbp_reset", "gbp_get_beliefs", "gbp_get_means", "gbp_set_reference", "gbp_add_keyframe",
            "gbp_get_stats", "gbp_get_sizes", "gbp_profile_iterations", "gbp_destroy_graph", "gbp_status_string",
-           "gbp_last_error"]
+           "gbp_last_error", "gbp_reprojection_error_noalloc"]
+GBP_NOALLOC_MAX_OBS = 1 << 20
 
 
 def lib() -> C.CDLL:
@@ -97,6 +98,8 @@ def lib() -> C.CDLL:
     L.gbp_status_string.restype = C.c_char_p
     L.gbp_last_error.argtypes = [vp]
     L.gbp_last_error.restype = C.c_char_p
+    L.gbp_reprojection_error_noalloc.argtypes = [C.POINTER(gbp_intrinsics), C.c_double, vp, vp, C.c_int32, vp, vp,
+                                                 vp, vp, vp]
     _lib = L
     return L
 
@@ -225,6 +228,18 @@ def gbp_profile_iterations(g: int, n_iters: int):
     out = np.zeros(2)
     _check(lib().gbp_profile_iterations(g, int(n_iters), _dp(out)), g)
     return float(out[0]), float(out[1])
+
+
+def gbp_reprojection_error_noalloc(intrinsics, z_min, kf_Rt_ptr, lm_xyz_ptr, n_obs, obs_kf_ptr, obs_lm_ptr,
+                                   obs_uv_ptr, out_ptr, stream=None) -> None:
+    """Average reprojection error of caller-owned device arrays (raw device
+    pointers as ints) into out_ptr[0:2] = (mean error px, count), with no
+    allocation: for callers that cannot allocate device memory at that
+    point.  Asynchronous on ``stream``."""
+    fx, fy, cx, cy, w, h = intrinsics
+    intr = gbp_intrinsics(fx, fy, cx, cy, int(w), int(h))
+    _check(lib().gbp_reprojection_error_noalloc(C.byref(intr), float(z_min), kf_Rt_ptr, lm_xyz_ptr, int(n_obs),
+                                                obs_kf_ptr, obs_lm_ptr, obs_uv_ptr, out_ptr, C.c_void_p(stream or 0)))
 
 
 def gbp_destroy_graph(g: int) -> None:
