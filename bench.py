@@ -42,7 +42,7 @@ MAX_ITERS = 1000
 CONV_TOL = 1e-6
 CHECK_EVERY = 25
 HUBER = 2.0
-# algorithmic bytes of the factor kernel (FP32 storage)
+# algorithmic bytes of one iteration (FP32 storage)
 BYTES_PER_FACTOR = 8 + 8 + 36 + 4 + 144 + 144     # z, (k, m), x0, tlin, read m^t, write m^{t+1}
 BYTES_PER_KF = 144 + 96                           # belief record, Rref + cref
 BYTES_PER_LM = 48 + 24                            # belief record, lref
@@ -225,6 +225,34 @@ def oracle_solution(p, max_iters, tol):
     return kf, lm, it, dt, t_1px
 
 
+def roofline(p, iter_ms, fac_ms, mode):
+    bytes_iter = BYTES_PER_FACTOR * p.n_obs + BYTES_PER_KF * p.n_kf + BYTES_PER_LM * p.n_lm
+    peak, peak_kind = peaks()
+    achieved = bytes_iter / (iter_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": ncu_traffic(p.n_obs),
+            "kernel": "persistent_kernel<float>" if mode == 1 else "factor_kernel<float> + belief_kernel<float>",
+            "launch_mode": mode, "bytes_per_iteration": bytes_iter, "ms_per_iteration": iter_ms,
+            "factor_kernel_ms": fac_ms, "peak_source": f"{peak_kind} HBM copy bandwidth"}
+
+
+def measure_at_scale(gbp, synth, stream, n_distinct=16, copies=8, iters=30):
+    """Throughput and HBM roofline on a batch of independent paper-scale
+    problems in one graph (state far larger than L2)."""
+    base = [synth.make_walk(seed=100 + i) for i in range(n_distinct)]
+    big = synth.concat(base * copies, name=f"batch{n_distinct * copies}")
+    g = gbp.Graph(big, stream=stream.cuda_stream, huber_nsigma=HUBER)
+    mode, ms1, ms2 = g.autotune(10)
+    iter_ms, fac_ms = g.profile(iters)
+    st = g.stats()
+    g.close()
+    return {"workload": f"{n_distinct * copies} independent walk problems in one graph "
+                        f"({big.n_kf} keyframes, {big.n_lm} points, {big.n_obs} factors)",
+            "value": big.n_obs / (iter_ms * 1e-3), "unit": UNIT, "ms_per_iteration": iter_ms,
+            "autotune_ms_per_iteration": {"persistent": ms1, "per_phase": ms2},
+            "roofline": roofline(big, iter_ms, fac_ms, mode), "fp64_fallbacks": st["fp64_fallbacks"]}
+
+
 def run_gpu(args, rank, world, local):
     import torch
     from paper_2003_03134_gb300 import build, gbp, synth
@@ -253,6 +281,7 @@ def run_gpu(args, rank, world, local):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     iters = []
+    launches0 = g.stats()["kernel_launches"]
     with ClockSampler(local) as clk:
         for i in range(args.steps):
             flush.fill_(i & 0xFF)   # evict L2 between steps (untimed)
@@ -271,18 +300,15 @@ def run_gpu(args, rank, world, local):
         torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
         total_ms, updates = float(tmax[0]), float(t[1])
     value = updates / (total_ms / 1e3)
-    launches = int(sum(1 + 2 * n for n in iters))
+    st_timed = g.stats()
+    launches = int(st_timed["kernel_launches"] - launches0)   # counted by the library
 
-    # roofline of the dominant kernel: live CUDA-event timing of each launch
+    # roofline of one iteration: live CUDA-event timing (profile replays
+    # iterations in the mode gbp_iterate used, and the factor kernel alone)
     g.reset()
-    fac_ms, bel_ms = g.profile(64)
-    bytes_launch = BYTES_PER_FACTOR * p.n_obs + BYTES_PER_KF * p.n_kf + BYTES_PER_LM * p.n_lm
-    peak, peak_kind = peaks()
-    achieved = bytes_launch / (fac_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": ncu_traffic(p.n_obs), "kernel": "factor_kernel<float>",
-            "bytes_per_launch": bytes_launch, "kernel_ms": fac_ms, "belief_kernel_ms": bel_ms,
-            "peak_source": f"{peak_kind} HBM copy bandwidth"}
+    iter_ms, fac_ms = g.profile(64)
+    roof = roofline(p, iter_ms, fac_ms, st_timed["launch_mode"])
+    at_scale = measure_at_scale(gbp, synth, stream) if (rank == 0 and not args.no_scale) else None
 
     line = None
     if rank == 0:
@@ -340,7 +366,7 @@ def run_gpu(args, rank, world, local):
                        "parallelism": f"independent problems, one per GPU ({world})",
                        "iters_per_step": float(np.mean(iters))},
             "ms_to_1px_vs_oracle": ms_1px, "iters_to_1px_vs_oracle": t_1px,
-            "roofline": roof, "cpu_baseline": cpu,
+            "roofline": roof, "at_scale": at_scale, "cpu_baseline": cpu,
             "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s},
             "gpu_launches": launches,
@@ -362,6 +388,7 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--ref-iters", type=int, default=20, help="oracle iterations per reference step")
     ap.add_argument("--oracle-iters", type=int, default=1000, help="cap of the oracle solve (CPU baseline)")
+    ap.add_argument("--no-scale", action="store_true", help="skip the batched at-scale measurement")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":

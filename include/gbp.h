@@ -75,6 +75,10 @@ typedef struct {
     float   fp64_pivot_ratio;   /* FP32 Cholesky with min/max pivot below this is redone in FP64; 1e-6 */
     int32_t precision_mode;     /* 0: FP32 + FP64 fallback, 1: FP32 only, 2: FP64 throughout        */
     int32_t linear;             /* 1: never relinearise (linear GBP at the initial point)          */
+    int32_t launch_mode;        /* 0: auto (gbp_autotune on first use), 1: one persistent launch per
+                                   gbp_iterate call with a grid barrier between phases, 2: one launch
+                                   per phase (factor kernel, belief kernel) replayed as a CUDA graph.
+                                   All modes give bitwise identical results.                        */
 } gbp_params;
 
 typedef struct {
@@ -86,6 +90,9 @@ typedef struct {
     int32_t huber_count;        /* measurements currently beyond the Huber threshold              */
     int32_t fp64_fallbacks;     /* FP32 Cholesky factorisations redone in FP64 since creation     */
     int32_t relinearisations;   /* factor relinearisations since creation                         */
+    int32_t launch_mode;        /* launch mode gbp_iterate() used last (1 persistent, 2 per phase) */
+    int64_t kernel_launches;    /* kernels this graph has launched since creation (graph replays
+                                   count each kernel they contain)                                 */
 } gbp_stats;
 
 /* Fill *out with the defaults listed above. */
@@ -162,13 +169,21 @@ gbp_status gbp_get_stats(const gbp_graph* g, gbp_stats* out);
 
 gbp_status gbp_get_sizes(const gbp_graph* g, int32_t* n_kf, int32_t* n_lm, int32_t* n_obs);
 
-/* Kernel timing: replay n_iters back-to-back launches of the factor kernel,
- * then of the belief kernel, each as one CUDA graph with CUDA events
- * recorded around it on the graph's stream, and return the mean device time
- * per launch in milliseconds: ms_out[0] factor kernel, ms_out[1] belief
- * kernel.  The repeated launches disturb the iteration state, so the graph
- * is reset to iteration 0 afterwards (as gbp_reset()).  Synchronises. */
+/* Kernel timing.  ms_out[0]: mean device time per iteration in the current
+ * launch mode (n_iters iterations from reset, CUDA events on the graph's
+ * stream).  ms_out[1]: mean device time of one factor-kernel launch (phase
+ * A alone), replayed n_iters times as a CUDA graph with its outputs sent to
+ * scratch buffers so that every launch does the same work.  The graph is
+ * reset to iteration 0 afterwards (as gbp_reset()).  Synchronises. */
 gbp_status gbp_profile_iterations(gbp_graph* g, int32_t n_iters, double* ms_out);
+
+/* Autotuner: run n_trial iterations from the current state in each launch
+ * mode, timing them with CUDA events, restore the state, and remember the
+ * faster mode for launch_mode = 0.  *chosen (nullable) receives 1 or 2;
+ * ms_out (nullable, 2 doubles) the mean time per iteration of modes 1 and 2
+ * (a mode that cannot launch, e.g. a persistent grid that does not fit,
+ * reports -1).  Synchronises the stream. */
+gbp_status gbp_autotune(gbp_graph* g, int32_t n_trial, int32_t* chosen, double* ms_out);
 
 void gbp_destroy_graph(gbp_graph* g);
 

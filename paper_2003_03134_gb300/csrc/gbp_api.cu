@@ -42,7 +42,11 @@ struct DevState {
     double* lm_ref = nullptr;
     int32_t* kf_off = nullptr;
     int32_t* kf_list = nullptr;
+    int32_t* kpos = nullptr;
     int32_t* lm_off = nullptr;
+    int32_t* tile_start = nullptr;
+    int32_t* big_lm = nullptr;
+    int32_t* orphan = nullptr;
     R* kf_D = nullptr;
     R* kf_A = nullptr;
     R* lm_D = nullptr;
@@ -50,13 +54,15 @@ struct DevState {
     R* x0 = nullptr;
     int32_t* tlin = nullptr;
     R* mk = nullptr;
+    R* mk2 = nullptr;
     R* ml = nullptr;
     R* kf_bel = nullptr;
     R* lm_bel = nullptr;
+    R* prior_s = nullptr;      // prior scale table, prior_anneal_iters + 1 entries
 
     void release() {
-        void* ptrs[] = {z, fk, fm, kf_R, kf_c, lm_ref, kf_off, kf_list, lm_off, kf_D, kf_A, lm_D, uv_ref,
-                        x0, tlin, mk, ml, kf_bel, lm_bel};
+        void* ptrs[] = {z, fk, fm, kf_R, kf_c, lm_ref, kf_off, kf_list, kpos, lm_off, tile_start, big_lm, orphan, kf_D, kf_A, lm_D,
+                        uv_ref, x0, tlin, mk, mk2, ml, kf_bel, lm_bel, prior_s};
         for (void* p : ptrs)
             if (p) cudaFree(p);
         *this = DevState<R>();
@@ -110,6 +116,9 @@ struct gbp_graph {
     double* h_met = nullptr;                    // pinned mirror of met
     cudaGraphExec_t exec = nullptr;
     bool built = false;
+    int tuned_mode = 0;                         // autotuner's choice (1 or 2), 0 = not tuned
+    int last_mode = 0;                          // launch mode of the last gbp_iterate()
+    int64_t launches = 0;                       // kernels launched (graph replays count their kernels)
 };
 
 namespace {
@@ -130,25 +139,29 @@ gbp_status cuda_fail(gbp_graph* g, cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(g, e_, #expr);     \
     } while (0)
 
-KParams make_kparams(const gbp_graph* g) {
+template <typename R>
+DevState<R>& state(gbp_graph* g);
+
+template <typename R>
+KParams<R> make_kparams(gbp_graph* g) {
     const gbp_params& p = g->prm;
-    KParams k{};
-    k.fx = g->intr.fx;
-    k.fy = g->intr.fy;
-    k.cx = g->intr.cx;
-    k.cy = g->intr.cy;
-    k.inv_sigma2 = 1.0 / (double(p.sigma_px) * double(p.sigma_px));
-    k.inv_sigma = 1.0 / double(p.sigma_px);
-    k.huber_n = p.huber_nsigma;
-    k.damping = p.damping;
-    k.z_min = p.z_min;
-    k.relin_beta = p.relin_beta;
-    k.anchor_scale = p.anchor_scale;
-    k.pivot_ratio = p.fp64_pivot_ratio;
-    k.prior_final = p.prior_final_scale;
+    KParams<R> k{};
+    k.fx = R(g->intr.fx);
+    k.fy = R(g->intr.fy);
+    k.cx = R(g->intr.cx);
+    k.cy = R(g->intr.cy);
+    k.inv_sigma2 = R(1.0 / (double(p.sigma_px) * double(p.sigma_px)));
+    k.inv_sigma = R(1.0 / double(p.sigma_px));
+    k.huber_n = R(p.huber_nsigma);
+    k.damping = R(p.damping);
+    k.z_min = R(p.z_min);
+    k.relin_beta = R(p.relin_beta);
+    k.anchor_scale = R(p.anchor_scale);
+    k.pivot_ratio = R(p.fp64_pivot_ratio);
+    k.prior_s = state<R>(g).prior_s;
+    k.prior_T = std::max(p.prior_anneal_iters, 0);
     k.relin_interval = p.relin_interval;
     k.damp_hold = std::max(p.undamped_iters, 1);
-    k.prior_anneal = p.prior_anneal_iters;
     k.linear = p.linear;
     k.fallback = p.precision_mode == 0 ? 1 : 0;
     return k;
@@ -161,12 +174,29 @@ void destroy_exec(gbp_graph* g) {
     }
 }
 
-template <typename R>
-DevState<R>& state(gbp_graph* g);
 template <>
 DevState<float>& state<float>(gbp_graph* g) { return g->sf; }
 template <>
 DevState<double>& state<double>(gbp_graph* g) { return g->sd; }
+
+// Sec. 8: prior scale s(t) = prior_final_scale^(min(t, T) / T), tabulated
+// for t = 0..T (T = prior_anneal_iters; T = 0 means the final scale
+// throughout) and uploaded for the kernels.
+template <typename R>
+gbp_status upload_prior_table(gbp_graph* g) {
+    DevState<R>& s = state<R>(g);
+    const int T = std::max(g->prm.prior_anneal_iters, 0);
+    std::vector<R> tab(T + 1);
+    for (int t = 0; t <= T; ++t)
+        tab[t] = T == 0 ? R(g->prm.prior_final_scale)
+                        : R(std::pow(double(g->prm.prior_final_scale), double(t) / double(T)));
+    if (s.prior_s) cudaFree(s.prior_s);
+    s.prior_s = nullptr;
+    CK(dev_alloc(&s.prior_s, tab.size()));
+    CK(cudaMemcpyAsync(s.prior_s, tab.data(), sizeof(R) * tab.size(), cudaMemcpyHostToDevice, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return GBP_OK;
+}
 
 // Upload the problem into freshly allocated device buffers of type R and
 // generate the priors; leaves the dynamic state uninitialised.
@@ -183,10 +213,47 @@ gbp_status build_device(gbp_graph* g) {
     }
     for (int v = 0; v < nk; ++v) kf_off[v + 1] += kf_off[v];
     for (int v = 0; v < nl; ++v) lm_off[v + 1] += lm_off[v];
+    std::vector<int32_t> kpos(nf);
     {
         std::vector<int32_t> fill(kf_off.begin(), kf_off.end() - 1);
-        for (int f = 0; f < nf; ++f) kf_list[fill[g->fk[f]]++] = f;
+        for (int f = 0; f < nf; ++f) {
+            kpos[f] = fill[g->fk[f]]++;
+            kf_list[kpos[f]] = f;
+        }
     }
+    // warp tiles: consecutive whole landmarks, at most 32 factors per tile;
+    // a landmark with more factors gets tiles of its own and its belief is
+    // formed in the belief phase.  Variables without factors are orphans.
+    std::vector<int32_t> tiles(1, 0), orphan, big;
+    for (int v = 0; v < nk; ++v)
+        if (kf_off[v + 1] == kf_off[v]) orphan.push_back(v);
+    {
+        int cur = 0;
+        for (int m = 0; m < nl; ++m) {
+            const int lo = lm_off[m], hi = lm_off[m + 1], d = hi - lo;
+            if (d == 0) {
+                orphan.push_back(nk + m);
+                continue;
+            }
+            if (d > 32) {
+                if (cur > 0) {
+                    tiles.push_back(lo);
+                    cur = 0;
+                }
+                for (int x = lo + 32; x < hi; x += 32) tiles.push_back(x);
+                tiles.push_back(hi);
+                big.push_back(m);
+                continue;
+            }
+            if (cur + d > 32) {
+                tiles.push_back(lo);
+                cur = 0;
+            }
+            cur += d;
+        }
+        if (cur > 0) tiles.push_back(nf);
+    }
+    const int n_tiles = (int)tiles.size() - 1;
     std::vector<R> zr(2 * (size_t)nf), anc(6 * (size_t)nk, R(0));
     for (size_t i = 0; i < zr.size(); ++i) zr[i] = R(g->z[i]);
     for (int v = 0; v < nk; ++v)
@@ -201,13 +268,18 @@ gbp_status build_device(gbp_graph* g) {
     CK(dev_alloc(&s.lm_ref, 3 * (size_t)nl));
     CK(dev_alloc(&s.kf_off, nk + 1));
     CK(dev_alloc(&s.kf_list, nf));
+    CK(dev_alloc(&s.kpos, nf));
     CK(dev_alloc(&s.lm_off, nl + 1));
+    CK(dev_alloc(&s.tile_start, tiles.size()));
+    CK(dev_alloc(&s.big_lm, big.size()));
+    CK(dev_alloc(&s.orphan, orphan.size()));
     CK(dev_alloc(&s.kf_D, 6 * (size_t)nk));
     CK(dev_alloc(&s.kf_A, 6 * (size_t)nk));
     CK(dev_alloc(&s.lm_D, 3 * (size_t)nl));
     CK(dev_alloc(&s.x0, 9 * (size_t)nf));
     CK(dev_alloc(&s.tlin, nf));
     CK(dev_alloc(&s.mk, (size_t)KREC * nf));
+    CK(dev_alloc(&s.mk2, (size_t)KREC * nf));
     CK(dev_alloc(&s.ml, 9 * (size_t)nf));
     CK(dev_alloc(&s.kf_bel, (size_t)KBEL * nk));
     CK(dev_alloc(&s.lm_bel, (size_t)LBEL * nl));
@@ -220,7 +292,13 @@ gbp_status build_device(gbp_graph* g) {
     CK(cudaMemcpyAsync(s.lm_ref, g->lm_ref.data(), sizeof(double) * 3 * nl, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.kf_off, kf_off.data(), sizeof(int32_t) * (nk + 1), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.kf_list, kf_list.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.kpos, kpos.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.lm_off, lm_off.data(), sizeof(int32_t) * (nl + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.tile_start, tiles.data(), sizeof(int32_t) * tiles.size(), cudaMemcpyHostToDevice, st));
+    if (!orphan.empty())
+        CK(cudaMemcpyAsync(s.orphan, orphan.data(), sizeof(int32_t) * orphan.size(), cudaMemcpyHostToDevice, st));
+    if (!big.empty())
+        CK(cudaMemcpyAsync(s.big_lm, big.data(), sizeof(int32_t) * big.size(), cudaMemcpyHostToDevice, st));
 
     DevGraph<R>& d = s.g;
     d.n_kf = nk;
@@ -234,7 +312,14 @@ gbp_status build_device(gbp_graph* g) {
     d.lm_ref = s.lm_ref;
     d.kf_off = s.kf_off;
     d.kf_list = s.kf_list;
+    d.kpos = s.kpos;
     d.lm_off = s.lm_off;
+    d.tile_start = s.tile_start;
+    d.big_lm = s.big_lm;
+    d.orphan = s.orphan;
+    d.n_tiles = n_tiles;
+    d.n_big = (int32_t)big.size();
+    d.n_orphan = (int32_t)orphan.size();
     d.kf_D = s.kf_D;
     d.kf_A = s.kf_A;
     d.lm_D = s.lm_D;
@@ -242,16 +327,23 @@ gbp_status build_device(gbp_graph* g) {
     d.x0 = s.x0;
     d.tlin = s.tlin;
     d.mk = s.mk;
+    d.mk2 = s.mk2;
+    d.mk_redirect = nullptr;
     d.ml = s.ml;
-    d.mk_out = s.mk;
     d.ml_out = s.ml;
     d.kf_bel = s.kf_bel;
     d.lm_bel = s.lm_bel;
+    d.kf_bel_out = s.kf_bel;
+    d.lm_bel_out = s.lm_bel;
     d.ctl = g->ctl;
 
     // priors: per-factor diagonal information at the reference (temporary
     // buffers reuse the message storage, which is cleared afterwards)
-    KParams kp = make_kparams(g);
+    {
+        gbp_status pst = upload_prior_table<R>(g);
+        if (pst != GBP_OK) return pst;
+    }
+    KParams<R> kp = make_kparams<R>(g);
     CK(launch_prior<R>(d, kp, s.mk, s.ml, s.kf_D, s.lm_D, st));
     // anchor diagonal = D on anchored keyframes
     {
@@ -282,13 +374,14 @@ gbp_status reset_state(gbp_graph* g) {
     CK(cudaMemsetAsync(s.x0, 0, sizeof(R) * 9 * nf, st));
     CK(cudaMemsetAsync(s.tlin, 0, sizeof(int32_t) * nf, st));
     CK(cudaMemsetAsync(s.mk, 0, sizeof(R) * KREC * nf, st));
+    CK(cudaMemsetAsync(s.mk2, 0, sizeof(R) * KREC * nf, st));
     CK(cudaMemsetAsync(s.ml, 0, sizeof(R) * 9 * nf, st));
     CK(cudaMemsetAsync(s.kf_bel, 0, sizeof(R) * KBEL * g->n_kf, st));
     CK(cudaMemsetAsync(s.lm_bel, 0, sizeof(R) * LBEL * g->n_lm, st));
     int32_t c0[CTL_N] = {0};
-    c0[CTL_ITER] = -1;   // the belief pass below forms b^0 and advances to 0
     CK(cudaMemcpyAsync(g->ctl, c0, sizeof(c0), cudaMemcpyHostToDevice, st));
-    CK(launch_belief<R>(s.g, make_kparams(g), st));
+    CK(launch_init<R>(s.g, make_kparams<R>(g), st));
+    g->launches += 1;
     return GBP_OK;
 }
 
@@ -310,7 +403,7 @@ gbp_status ensure_built(gbp_graph* g) {
 template <typename R>
 cudaError_t enqueue_iterations(gbp_graph* g, int n, cudaStream_t st) {
     const DevGraph<R>& d = state<R>(g).g;
-    KParams kp = make_kparams(g);
+    KParams<R> kp = make_kparams<R>(g);
     for (int i = 0; i < n; ++i) {
         cudaError_t e = launch_factor<R>(d, kp, st);
         if (e != cudaSuccess) return e;
@@ -341,6 +434,8 @@ gbp_status ensure_exec(gbp_graph* g) {
 gbp_status read_ctl(gbp_graph* g) {
     CK(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(int32_t) * CTL_N, cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
+    if (g->h_ctl[CTL_ERR] == 2)
+        return fail(g, GBP_ETIMEOUT, "grid barrier wait exceeded its limit (blocks not co-resident?)");
     if (g->h_ctl[CTL_ERR]) {
         int w = g->h_ctl[CTL_ERR_WHERE];
         char buf[160];
@@ -372,6 +467,7 @@ gbp_status check_params(const gbp_params* p, std::string& why) {
     if (p->undamped_iters < 0) { why = "undamped_iters must be >= 0"; return GBP_EINVAL; }
     if (p->check_every < 1) { why = "check_every must be >= 1"; return GBP_EINVAL; }
     if (p->precision_mode < 0 || p->precision_mode > 2) { why = "precision_mode must be 0, 1 or 2"; return GBP_EINVAL; }
+    if (p->launch_mode < 0 || p->launch_mode > 2) { why = "launch_mode must be 0, 1 or 2"; return GBP_EINVAL; }
     if (!(p->conv_tol >= 0.0f)) { why = "conv_tol must be >= 0"; return GBP_EINVAL; }
     return GBP_OK;
 }
@@ -477,6 +573,67 @@ gbp_status compute_uv_ref(gbp_graph* g, const double* kf_Rt, const double* lm) {
 
 }  // namespace
 
+// One launch per phase (factor kernel, belief kernel), replayed from a
+// captured CUDA graph; with conv_tol > 0 the host checks the largest mean
+// change every check_every iterations.
+gbp_status iterate_phases(gbp_graph* g, int n, float conv_tol, int* done_out) {
+    gbp_status st = ensure_exec(g);
+    if (st != GBP_OK) return st;
+    const bool check = conv_tol > 0.0f;
+    int done = 0;
+    while (done < n) {
+        int block = check ? std::min(g->prm.check_every, n - done) : n - done;
+        int full = block / GRAPH_CHUNK, rest = block % GRAPH_CHUNK;
+        for (int i = 0; i < full; ++i) CK(cudaGraphLaunch(g->exec, g->stream));
+        if (rest) {
+            cudaError_t e = g->storage ? enqueue_iterations<double>(g, rest, g->stream)
+                                       : enqueue_iterations<float>(g, rest, g->stream);
+            if (e != cudaSuccess) return cuda_fail(g, e, "kernel launch");
+        }
+        g->launches += 2 * (int64_t)block;
+        done += block;
+        *done_out = done;
+        if (check) {
+            st = read_ctl(g);
+            if (st != GBP_OK) return st;
+            float dmu;
+            std::memcpy(&dmu, &g->h_ctl[CTL_DMU_LAST], sizeof dmu);
+            if (dmu < conv_tol) break;
+        }
+    }
+    return GBP_OK;
+}
+
+// One cooperative launch for all n iterations; the convergence test (same
+// cadence as above) runs on the device.
+gbp_status iterate_persistent(gbp_graph* g, int n, float conv_tol, int* done_out) {
+    const int grid = g->storage ? persistent_grid<double>(g->sd.g) : persistent_grid<float>(g->sf.g);
+    if (grid <= 0) return fail(g, GBP_ECUDA, "persistent launch: occupancy query failed");
+    cudaError_t e = g->storage
+        ? launch_persistent<double>(g->sd.g, make_kparams<double>(g), n, conv_tol, g->prm.check_every, grid, g->stream)
+        : launch_persistent<float>(g->sf.g, make_kparams<float>(g), n, conv_tol, g->prm.check_every, grid, g->stream);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cooperative launch");
+    g->launches += 1;
+    if (conv_tol > 0.0f) {
+        gbp_status st = read_ctl(g);
+        *done_out = g->h_ctl[CTL_ITERS_RUN];
+        return st;
+    }
+    *done_out = n;
+    return GBP_OK;
+}
+
+// Device buffers that make up the iteration state (for snapshots).
+template <typename R>
+std::vector<std::pair<void*, size_t>> state_buffers(gbp_graph* g) {
+    DevState<R>& s = state<R>(g);
+    const size_t nf = g->n_f, nk = g->n_kf, nl = g->n_lm;
+    return {{s.x0, sizeof(R) * 9 * nf},        {s.tlin, sizeof(int32_t) * nf},   {s.mk, sizeof(R) * KREC * nf},
+            {s.mk2, sizeof(R) * KREC * nf},
+            {s.ml, sizeof(R) * 9 * nf},        {s.kf_bel, sizeof(R) * KBEL * nk}, {s.lm_bel, sizeof(R) * LBEL * nl},
+            {g->ctl, sizeof(int32_t) * CTL_N}};
+}
+
 // ==========================================================================
 // C ABI
 
@@ -500,6 +657,7 @@ void gbp_default_params(gbp_params* p) {
     p->fp64_pivot_ratio = 1e-6f;
     p->precision_mode = 0;
     p->linear = 0;
+    p->launch_mode = 0;
 }
 
 const char* gbp_status_string(gbp_status s) {
@@ -600,10 +758,13 @@ gbp_status gbp_set_params(gbp_graph* g, const gbp_params* p) {
     std::string why;
     if (check_params(p, why) != GBP_OK) return fail(g, GBP_EINVAL, why);
     bool sigma_changed = p->sigma_px != g->prm.sigma_px;
+    if (p->precision_mode != g->prm.precision_mode) g->tuned_mode = 0;
     g->prm = *p;
     destroy_exec(g);
     (void)sigma_changed;   // priors are stored at sigma = 1 and scaled in the kernels
-    return ensure_built(g);
+    gbp_status st = ensure_built(g);
+    if (st != GBP_OK) return st;
+    return g->storage ? upload_prior_table<double>(g) : upload_prior_table<float>(g);
 }
 
 gbp_status gbp_get_params(const gbp_graph* g, gbp_params* out) {
@@ -626,33 +787,19 @@ gbp_status gbp_iterate(gbp_graph* g, int32_t n_iters, int32_t* iters_done) {
     if (st != GBP_OK) return st;
     int n = n_iters > 0 ? n_iters : g->prm.iterations;
     if (g->n_f == 0 && g->n_kf == 0 && g->n_lm == 0) return GBP_OK;
-    st = ensure_exec(g);
-    if (st != GBP_OK) return st;
-    const bool check = g->prm.conv_tol > 0.0f;
-    int done = 0;
-    while (done < n) {
-        int block = check ? std::min(g->prm.check_every, n - done) : n - done;
-        int full = block / GRAPH_CHUNK, rest = block % GRAPH_CHUNK;
-        for (int i = 0; i < full; ++i) CK(cudaGraphLaunch(g->exec, g->stream));
-        if (rest) {
-            cudaError_t e = g->storage ? enqueue_iterations<double>(g, rest, g->stream)
-                                       : enqueue_iterations<float>(g, rest, g->stream);
-            if (e != cudaSuccess) return cuda_fail(g, e, "kernel launch");
+    int mode = g->prm.launch_mode;
+    if (mode == 0) {
+        if (!g->tuned_mode) {
+            st = gbp_autotune(g, 8, nullptr, nullptr);
+            if (st != GBP_OK) return st;
         }
-        done += block;
-        if (check) {
-            st = read_ctl(g);
-            if (st != GBP_OK) {
-                if (iters_done) *iters_done = done;
-                return st;
-            }
-            float dmu;
-            std::memcpy(&dmu, &g->h_ctl[CTL_DMU_LAST], sizeof dmu);
-            if (dmu < g->prm.conv_tol) break;
-        }
+        mode = g->tuned_mode;
     }
+    int done = 0;
+    g->last_mode = mode;
+    st = mode == 1 ? iterate_persistent(g, n, g->prm.conv_tol, &done) : iterate_phases(g, n, g->prm.conv_tol, &done);
     if (iters_done) *iters_done = done;
-    return GBP_OK;
+    return st;
 }
 
 gbp_status gbp_get_means(const gbp_graph* cg, double* kf_mu, double* lm_mu) {
@@ -738,9 +885,9 @@ gbp_status gbp_get_stats(const gbp_graph* cg, gbp_stats* out) {
     gbp_graph* g = const_cast<gbp_graph*>(cg);
     if (!g || !out) return GBP_EINVAL;
     std::memset(out, 0, sizeof *out);
-    KParams kp = make_kparams(g);
-    cudaError_t e = g->storage ? launch_metrics<double>(g->sd.g, kp, g->partials, g->n_partials, g->met, g->stream)
-                               : launch_metrics<float>(g->sf.g, kp, g->partials, g->n_partials, g->met, g->stream);
+    cudaError_t e = g->storage
+        ? launch_metrics<double>(g->sd.g, make_kparams<double>(g), g->partials, g->n_partials, g->met, g->stream)
+        : launch_metrics<float>(g->sf.g, make_kparams<float>(g), g->partials, g->n_partials, g->met, g->stream);
     if (e != cudaSuccess) return cuda_fail(g, e, "metrics");
     CK(cudaMemcpyAsync(g->h_met, g->met, sizeof(double) * MET_N, cudaMemcpyDeviceToHost, g->stream));
     gbp_status st = read_ctl(g);   // synchronises
@@ -752,6 +899,8 @@ gbp_status gbp_get_stats(const gbp_graph* cg, gbp_stats* out) {
     out->huber_count = (int32_t)g->h_met[MET_HUBER];
     out->fp64_fallbacks = g->h_ctl[CTL_FALLBACKS];
     out->relinearisations = g->h_ctl[CTL_RELINS];
+    out->launch_mode = g->last_mode;
+    out->kernel_launches = g->launches;
     return st;
 }
 
@@ -767,68 +916,135 @@ gbp_status gbp_profile_iterations(gbp_graph* g, int32_t n_iters, double* ms_out)
     if (!g || !ms_out || n_iters <= 0) return GBP_EINVAL;
     gbp_status st = ensure_built(g);
     if (st != GBP_OK) return st;
-    KParams kp = make_kparams(g);
-    cudaGraphExec_t ex[2] = {nullptr, nullptr};
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    // The replayed factor launches write their messages to scratch buffers
-    // so that every launch reads the same m^t and beliefs (same work and
-    // traffic as one iteration's factor pass).
-    const size_t rs = g->storage ? sizeof(double) : sizeof(float);
-    void* scratch_k = nullptr;
-    void* scratch_l = nullptr;
-    cudaError_t e = cudaMalloc(&scratch_k, rs * KREC * std::max(g->n_f, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&scratch_l, rs * 9 * std::max(g->n_f, 1));
-    DevGraph<float> pf = g->sf.g;
-    DevGraph<double> pd = g->sd.g;
-    pf.mk_out = static_cast<float*>(scratch_k);
-    pf.ml_out = static_cast<float*>(scratch_l);
-    pd.mk_out = static_cast<double*>(scratch_k);
-    pd.ml_out = static_cast<double*>(scratch_l);
-    // one CUDA graph of n_iters back-to-back launches per kernel
-    for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
-        cudaGraph_t graph = nullptr;
-        e = cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) break;
-        cudaError_t le = cudaSuccess;
-        for (int i = 0; i < n_iters && le == cudaSuccess; ++i) {
-            if (which == 0)
-                le = g->storage ? launch_factor<double>(pd, kp, g->capture) : launch_factor<float>(pf, kp, g->capture);
-            else
-                le = g->storage ? launch_belief<double>(g->sd.g, kp, g->capture) : launch_belief<float>(g->sf.g, kp, g->capture);
-        }
-        e = cudaStreamEndCapture(g->capture, &graph);
-        if (le != cudaSuccess) e = le;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&ex[which], graph, 0);
-        if (graph) cudaGraphDestroy(graph);
-    }
-    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
-    if (e == cudaSuccess) {
-        // warm once, then time the second replay
-        cudaGraphLaunch(ex[0], g->stream);
+    int mode = g->prm.launch_mode ? g->prm.launch_mode : (g->tuned_mode ? g->tuned_mode : 2);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaEventCreate");
+    // (a) whole iterations in the current launch mode, from reset
+    st = g->storage ? reset_state<double>(g) : reset_state<float>(g);
+    int done = 0;
+    if (st == GBP_OK && mode == 2) st = ensure_exec(g);
+    if (st == GBP_OK) {
         cudaEventRecord(ev[0], g->stream);
-        cudaGraphLaunch(ex[0], g->stream);
+        st = mode == 1 ? iterate_persistent(g, n_iters, 0.0f, &done) : iterate_phases(g, n_iters, 0.0f, &done);
         cudaEventRecord(ev[1], g->stream);
-        cudaGraphLaunch(ex[1], g->stream);
-        cudaEventRecord(ev[2], g->stream);
-        cudaGraphLaunch(ex[1], g->stream);
-        cudaEventRecord(ev[3], g->stream);
-        e = cudaStreamSynchronize(g->stream);
     }
-    float a = 0.f, b = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[2], ev[3]);
+    float ms_iter = 0.f;
+    if (st == GBP_OK) {
+        e = cudaStreamSynchronize(g->stream);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_iter, ev[0], ev[1]);
+    }
+    // (b) the factor kernel alone, replayed with its outputs in scratch
+    const size_t rs = g->storage ? sizeof(double) : sizeof(float);
+    void* scratch[3] = {nullptr, nullptr, nullptr};
+    const size_t sizes[3] = {rs * KREC * std::max(g->n_f, 1), rs * 9 * std::max(g->n_f, 1),
+                             rs * LBEL * std::max(g->n_lm, 1)};
+    cudaGraphExec_t ex = nullptr;
+    float ms_fac = 0.f;
+    if (st == GBP_OK && e == cudaSuccess) {
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc(&scratch[i], sizes[i]);
+        DevGraph<float> pf = g->sf.g;
+        DevGraph<double> pd = g->sd.g;
+        pf.mk_redirect = static_cast<float*>(scratch[0]);
+        pf.ml_out = static_cast<float*>(scratch[1]);
+        pf.lm_bel_out = static_cast<float*>(scratch[2]);
+        pd.mk_redirect = static_cast<double*>(scratch[0]);
+        pd.ml_out = static_cast<double*>(scratch[1]);
+        pd.lm_bel_out = static_cast<double*>(scratch[2]);
+        const KParams<float> kf_ = make_kparams<float>(g);
+        const KParams<double> kd_ = make_kparams<double>(g);
+        cudaGraph_t graph = nullptr;
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t le = cudaSuccess;
+            for (int i = 0; i < n_iters && le == cudaSuccess; ++i)
+                le = g->storage ? launch_factor<double>(pd, kd_, g->capture) : launch_factor<float>(pf, kf_, g->capture);
+            e = cudaStreamEndCapture(g->capture, &graph);
+            if (le != cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e == cudaSuccess) {
+            cudaGraphLaunch(ex, g->stream);
+            cudaEventRecord(ev[0], g->stream);
+            cudaGraphLaunch(ex, g->stream);
+            cudaEventRecord(ev[1], g->stream);
+            e = cudaStreamSynchronize(g->stream);
+        }
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_fac, ev[0], ev[1]);
+    }
     for (auto& x : ev)
         if (x) cudaEventDestroy(x);
-    for (auto& x : ex)
-        if (x) cudaGraphExecDestroy(x);
-    if (scratch_k) cudaFree(scratch_k);
-    if (scratch_l) cudaFree(scratch_l);
+    if (ex) cudaGraphExecDestroy(ex);
+    for (auto& p : scratch)
+        if (p) cudaFree(p);
+    if (st != GBP_OK) return st;
     if (e != cudaSuccess) return cuda_fail(g, e, "profile");
-    ms_out[0] = double(a) / n_iters;
-    ms_out[1] = double(b) / n_iters;
+    ms_out[0] = double(ms_iter) / n_iters;
+    ms_out[1] = double(ms_fac) / n_iters;
     st = read_ctl(g);
     if (st != GBP_OK) return st;
     return g->storage ? reset_state<double>(g) : reset_state<float>(g);
+}
+
+gbp_status gbp_autotune(gbp_graph* g, int32_t n_trial, int32_t* chosen, double* ms_out) {
+    if (!g || n_trial <= 0) return GBP_EINVAL;
+    gbp_status st = ensure_built(g);
+    if (st != GBP_OK) return st;
+    auto bufs = g->storage ? state_buffers<double>(g) : state_buffers<float>(g);
+    std::vector<void*> snap(bufs.size(), nullptr);
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < bufs.size() && e == cudaSuccess; ++i) {
+        e = cudaMalloc(&snap[i], std::max<size_t>(bufs[i].second, 1));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(snap[i], bufs[i].first, bufs[i].second, cudaMemcpyDeviceToDevice, g->stream);
+    }
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+    double ms[2] = {-1.0, -1.0};
+    for (int mode = 1; mode <= 2 && e == cudaSuccess; ++mode) {
+        if (mode == 2) {
+            st = ensure_exec(g);
+            if (st != GBP_OK) break;
+        }
+        int done = 0;
+        // one untimed warm run, then the timed run, each from the snapshot
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+            cudaEventRecord(ev[0], g->stream);
+            gbp_status ms_st = mode == 1 ? iterate_persistent(g, n_trial, 0.0f, &done)
+                                         : iterate_phases(g, n_trial, 0.0f, &done);
+            cudaEventRecord(ev[1], g->stream);
+            e = cudaStreamSynchronize(g->stream);
+            if (ms_st != GBP_OK) {
+                g->err.clear();
+                cudaGetLastError();
+                e = cudaSuccess;
+                ms[mode - 1] = -1.0;
+            } else if (e == cudaSuccess && rep == 1) {
+                float t = 0.f;
+                e = cudaEventElapsedTime(&t, ev[0], ev[1]);
+                ms[mode - 1] = double(t) / n_trial;
+            }
+            for (size_t i = 0; i < bufs.size() && e == cudaSuccess; ++i)
+                e = cudaMemcpyAsync(bufs[i].first, snap[i], bufs[i].second, cudaMemcpyDeviceToDevice, g->stream);
+            if (ms_st != GBP_OK) break;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+    for (auto& p : snap)
+        if (p) cudaFree(p);
+    if (st != GBP_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(g, e, "autotune");
+    if (ms[0] < 0 && ms[1] < 0) return fail(g, GBP_ECUDA, "autotune: no launch mode ran");
+    g->tuned_mode = (ms[0] >= 0 && (ms[1] < 0 || ms[0] <= ms[1])) ? 1 : 2;
+    if (chosen) *chosen = g->tuned_mode;
+    if (ms_out) {
+        ms_out[0] = ms[0];
+        ms_out[1] = ms[1];
+    }
+    return GBP_OK;
 }
 
 gbp_status gbp_add_keyframe(gbp_graph* g, const double* kf_Rt_init, int32_t n_new_lm, const double* new_lm_xyz,

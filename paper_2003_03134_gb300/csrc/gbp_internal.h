@@ -6,7 +6,10 @@
 //   per factor, dynamic:  x0  -- linearisation point [dc dw | dl], 9 Real, SoA (9 x n_f)
 //                         tlin -- iteration of the last (re)linearisation, int32
 //                         mk  -- message to the keyframe, AoS record of KREC Real:
-//                                Lambda packed lower 6x6 (21), eta (6), pad
+//                                Lambda packed lower 6x6 (21), eta (6), pad;
+//                                stored in keyframe CSR order (slot kpos[f]) so
+//                                that a keyframe's messages are contiguous; two
+//                                buffers, alternating by iteration parity
 //                         ml  -- message to the landmark, SoA (9 x n_f):
 //                                Lambda packed lower 3x3 (6), eta (3)
 //   per keyframe:         Rref (9 double), cref (3 double), prior diagonal D (6),
@@ -15,7 +18,8 @@
 //   per landmark:         lref (3 double), prior diagonal (3), belief record
 //                         LBEL Real: Lambda (6), eta (3), mu (3)
 //   CSR keyframe -> factor list (kf_off, kf_list); landmark -> contiguous
-//   factor range (lm_off), since factors are sorted by landmark.
+//   factor range (lm_off), since factors are sorted by landmark; warp tiles
+//   of whole landmarks (tile_start); per-variable arrival counters.
 // Packed symmetric storage: element (i, j), j <= i, at i*(i+1)/2 + j.
 #pragma once
 #include <cuda_runtime.h>
@@ -27,20 +31,23 @@ constexpr int KREC = 28;   // keyframe message record (Real elements)
 constexpr int KBEL = 36;   // keyframe belief record
 constexpr int LBEL = 12;   // landmark belief record
 
+// Solver parameters as the kernels see them, in the kernel's own precision
+// (no double-to-float conversions in the hot loop).
+template <typename R>
 struct KParams {
-    double fx, fy, cx, cy;
-    double inv_sigma2;        // 1 / sigma^2
-    double inv_sigma;         // 1 / sigma
-    double huber_n;           // <= 0 disables
-    double damping;
-    double z_min;
-    double relin_beta;
-    double anchor_scale;
-    double pivot_ratio;
-    double prior_final;       // final prior scale
+    R fx, fy, cx, cy;
+    R inv_sigma2;             // 1 / sigma^2
+    R inv_sigma;              // 1 / sigma
+    R huber_n;                // <= 0 disables
+    R damping;
+    R z_min;
+    R relin_beta;
+    R anchor_scale;
+    R pivot_ratio;
+    const R* prior_s;         // device table: prior scale at iteration t is prior_s[min(t, prior_T)]
+    int32_t prior_T;
     int32_t relin_interval;
     int32_t damp_hold;        // damping applies when t - tlin >= damp_hold (>= 1)
-    int32_t prior_anneal;
     int32_t linear;
     int32_t fallback;         // FP32 path: redo ill-conditioned factorisations in FP64
 };
@@ -57,7 +64,12 @@ struct DevGraph {
     const double* lm_ref;     // n_lm x 3
     const int32_t* kf_off;    // n_kf + 1
     const int32_t* kf_list;   // n_f
+    const int32_t* kpos;      // n_f: slot of factor f's keyframe message = its position in kf_list
     const int32_t* lm_off;    // n_lm + 1
+    const int32_t* tile_start;// n_tiles + 1: warp tiles of whole landmarks (<= 32 factors each)
+    const int32_t* big_lm;    // landmarks split across tiles (more than 32 factors)
+    const int32_t* orphan;    // variables without factors: keyframe v, or n_kf + landmark
+    int32_t n_tiles, n_big, n_orphan;
     const R* kf_D;            // n_kf x 6, prior diagonal at sigma = 1
     const R* kf_A;            // n_kf x 6, anchor diagonal at sigma = 1 (0 = not anchored)
     const R* lm_D;            // n_lm x 3
@@ -65,12 +77,15 @@ struct DevGraph {
     // dynamic
     R* x0;                    // 9 x n_f
     int32_t* tlin;            // n_f
-    R* mk;                    // n_f x KREC   (read by the factor kernel)
+    R* mk;                    // n_f x KREC, messages of even iterations
+    R* mk2;                   // n_f x KREC, messages of odd iterations
+    R* mk_redirect;           // if set, receives the keyframe-message writes (kernel timing)
     R* ml;                    // 9 x n_f      (read by the factor kernel)
-    R* mk_out;                // where the factor kernel writes m^{t+1} (normally == mk)
-    R* ml_out;                // (normally == ml)
-    R* kf_bel;                // n_kf x KBEL
-    R* lm_bel;                // n_lm x LBEL
+    R* ml_out;                // where the factor kernel writes m^{t+1} (normally == ml)
+    R* kf_bel;                // n_kf x KBEL  (read as b^t)
+    R* lm_bel;                // n_lm x LBEL  (read as b^t)
+    R* kf_bel_out;            // where b^{t+1} is written (normally == kf_bel)
+    R* lm_bel_out;            // (normally == lm_bel)
     // control block
     int32_t* ctl;             // see Ctl
 };
@@ -79,28 +94,35 @@ struct DevGraph {
 enum Ctl : int {
     CTL_ITER = 0,          // completed iterations
     CTL_DONE = 1,          // blocks finished in the current belief launch
-    CTL_DMU_ACC = 2,       // running max |dmu| (float bits), current iteration
+    CTL_DMU_ACC = 2,       // running max |dmu| (float bits) of even iterations
     CTL_DMU_LAST = 3,      // max |dmu| of the last completed iteration (float bits)
     CTL_FALLBACKS = 4,     // FP64 redo count
     CTL_RELINS = 5,        // relinearisation count
-    CTL_ERR = 6,           // nonzero: a belief lost positive definiteness / became non-finite
-    CTL_ERR_WHERE = 7,     // first variable / factor index that raised CTL_ERR
+    CTL_ERR = 6,           // 1: a belief lost positive definiteness / became non-finite; 2: barrier timeout
+    CTL_ERR_WHERE = 7,     // first variable / factor index that raised CTL_ERR = 1
+    CTL_DMU_ACC1 = 8,      // running max |dmu| of odd iterations
+    CTL_BAR_COUNT = 9,     // grid barrier arrivals
+    CTL_BAR_GEN = 10,      // grid barrier generation
+    CTL_ITERS_RUN = 11,    // iterations run by the last persistent launch
     CTL_N = 16
 };
 
 // metrics reduction output (double slots)
 enum Met : int { MET_ARE = 0, MET_ARE_REF = 1, MET_N_ARE = 2, MET_HUBER = 3, MET_N = 4 };
 
-constexpr int FACTOR_BLOCK = 128;
-constexpr int BELIEF_BLOCK = 128;
+constexpr int FACTOR_BLOCK = 128;   // 4 warps per block (every kernel of the iteration)
 constexpr int METRIC_BLOCK = 256;
 
 // kernel launchers (gbp_kernels.cu)
-template <typename R> cudaError_t launch_factor(const DevGraph<R>& g, const KParams& p, cudaStream_t s);
-template <typename R> cudaError_t launch_belief(const DevGraph<R>& g, const KParams& p, cudaStream_t s);
-template <typename R> cudaError_t launch_prior(const DevGraph<R>& g, const KParams& p, R* tmp_k, R* tmp_l,
+template <typename R> cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s);
+template <typename R> cudaError_t launch_init(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s);
+template <typename R> cudaError_t launch_belief(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s);
+template <typename R> int persistent_grid(const DevGraph<R>& g);   // co-resident blocks to use; 0 on error
+template <typename R> cudaError_t launch_persistent(const DevGraph<R>& g, const KParams<R>& p, int n_iters,
+                                                    float conv_tol, int check_every, int grid, cudaStream_t s);
+template <typename R> cudaError_t launch_prior(const DevGraph<R>& g, const KParams<R>& p, R* tmp_k, R* tmp_l,
                                                R* kf_D, R* lm_D, cudaStream_t s);
-template <typename R> cudaError_t launch_metrics(const DevGraph<R>& g, const KParams& p, double* partials,
+template <typename R> cudaError_t launch_metrics(const DevGraph<R>& g, const KParams<R>& p, double* partials,
                                                  int n_partials, double* out, cudaStream_t s);
 int metrics_blocks(int n_f);
 

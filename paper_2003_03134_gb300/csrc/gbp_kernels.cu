@@ -31,6 +31,8 @@
 
 #include <math.h>
 
+#include <algorithm>
+
 namespace gbp {
 
 // ------------------------------------------------------------------------
@@ -38,63 +40,107 @@ namespace gbp {
 
 __host__ __device__ constexpr int pk(int i, int j) { return i * (i + 1) / 2 + j; }  // j <= i
 
+// 1/x: correctly rounded reciprocal in FP32 (cheaper than a division),
+// plain division in FP64.
 template <typename R>
-__device__ __forceinline__ R rsqrt_exact(R x) { return R(1) / sqrt(x); }
+__device__ __forceinline__ R rcp(R x) {
+    if constexpr (sizeof(R) == 4) return __frcp_rn(x);
+    else return R(1) / x;
+}
+
+// (sqrt(s), 1/sqrt(s)) for s > 0.  FP32: hardware reciprocal square root
+// refined by one Newton-Raphson step y <- y (3 - s y^2) / 2; FP64: exact.
+template <typename R>
+__device__ __forceinline__ void sqrt_pair(R s, R& d, R& id) {
+    if constexpr (sizeof(R) == 4) {
+        float y = rsqrtf(fmaxf(s, 1.17549435e-38f));
+        y = y * (1.5f - 0.5f * s * y * y);
+        id = y;
+        d = s * y;
+    } else {
+        d = sqrt(fmax(s, R(0)));
+        id = R(1) / d;
+    }
+}
 
 // In-place Cholesky of a packed lower-triangular n x n SPD matrix.
 // On return A holds L (packed) and inv_d[i] = 1 / L_ii.  Returns false if a
 // pivot is not positive and finite; pivot_ratio = min pivot / max pivot.
+// Columns (and rows of the substitutions) recurse on a template index so
+// that every loop bound is a compile-time constant and the packed matrix
+// stays in registers.
+template <typename R, int n, int j>
+struct CholCol {
+    static __device__ __forceinline__ void run(R* A, R* inv_d, R& pmin, R& pmax, bool& ok) {
+        if constexpr (j < n) {
+            R s = A[pk(j, j)];
+#pragma unroll
+            for (int p = 0; p < j; ++p) s -= A[pk(j, p)] * A[pk(j, p)];
+            ok = ok && (s > R(0)) && isfinite(s);
+            if (j == 0) { pmin = s; pmax = s; }
+            pmin = fmin(pmin, s);
+            pmax = fmax(pmax, s);
+            R d, id;
+            sqrt_pair<R>(s, d, id);
+            A[pk(j, j)] = d;
+            inv_d[j] = id;
+#pragma unroll
+            for (int i = j + 1; i < n; ++i) {
+                R t = A[pk(i, j)];
+#pragma unroll
+                for (int p = 0; p < j; ++p) t -= A[pk(i, p)] * A[pk(j, p)];
+                A[pk(i, j)] = t * id;
+            }
+            CholCol<R, n, j + 1>::run(A, inv_d, pmin, pmax, ok);
+        }
+    }
+};
+
 template <typename R, int n>
 __device__ __forceinline__ bool chol_packed(R* A, R* inv_d, R& pivot_ratio) {
     R pmin = R(0), pmax = R(0);
     bool ok = true;
-#pragma unroll
-    for (int j = 0; j < n; ++j) {
-        R s = A[pk(j, j)];
-#pragma unroll
-        for (int p = 0; p < j; ++p) s -= A[pk(j, p)] * A[pk(j, p)];
-        ok = ok && (s > R(0)) && isfinite(s);
-        if (j == 0) { pmin = s; pmax = s; }
-        pmin = fmin(pmin, s);
-        pmax = fmax(pmax, s);
-        R d = sqrt(fmax(s, R(0)));
-        R id = R(1) / d;
-        A[pk(j, j)] = d;
-        inv_d[j] = id;
-#pragma unroll
-        for (int i = j + 1; i < n; ++i) {
-            R t = A[pk(i, j)];
-#pragma unroll
-            for (int p = 0; p < j; ++p) t -= A[pk(i, p)] * A[pk(j, p)];
-            A[pk(i, j)] = t * id;
-        }
-    }
-    pivot_ratio = ok ? pmin / pmax : R(0);
+    CholCol<R, n, 0>::run(A, inv_d, pmin, pmax, ok);
+    pivot_ratio = ok ? pmin * rcp(pmax) : R(0);
     return ok;
 }
+
+template <typename R, int n, int i>
+struct FwdRow {
+    static __device__ __forceinline__ void run(const R* L, const R* inv_d, R* b) {
+        if constexpr (i < n) {
+            R s = b[i];
+#pragma unroll
+            for (int p = 0; p < i; ++p) s -= L[pk(i, p)] * b[p];
+            b[i] = s * inv_d[i];
+            FwdRow<R, n, i + 1>::run(L, inv_d, b);
+        }
+    }
+};
 
 // b <- L^-1 b (forward substitution with a packed Cholesky factor)
 template <typename R, int n>
 __device__ __forceinline__ void fwd_solve(const R* L, const R* inv_d, R* b) {
-#pragma unroll
-    for (int i = 0; i < n; ++i) {
-        R s = b[i];
-#pragma unroll
-        for (int p = 0; p < i; ++p) s -= L[pk(i, p)] * b[p];
-        b[i] = s * inv_d[i];
-    }
+    FwdRow<R, n, 0>::run(L, inv_d, b);
 }
+
+template <typename R, int n, int i>
+struct BwdRow {
+    static __device__ __forceinline__ void run(const R* L, const R* inv_d, R* b) {
+        if constexpr (i >= 0) {
+            R s = b[i];
+#pragma unroll
+            for (int p = i + 1; p < n; ++p) s -= L[pk(p, i)] * b[p];
+            b[i] = s * inv_d[i];
+            BwdRow<R, n, i - 1>::run(L, inv_d, b);
+        }
+    }
+};
 
 // b <- L^-T b (backward substitution)
 template <typename R, int n>
 __device__ __forceinline__ void bwd_solve(const R* L, const R* inv_d, R* b) {
-#pragma unroll
-    for (int i = n - 1; i >= 0; --i) {
-        R s = b[i];
-#pragma unroll
-        for (int p = i + 1; p < n; ++p) s -= L[pk(p, i)] * b[p];
-        b[i] = s * inv_d[i];
-    }
+    BwdRow<R, n, n - 1>::run(L, inv_d, b);
 }
 
 // ------------------------------------------------------------------------
@@ -108,21 +154,19 @@ template <typename R>
 __device__ __forceinline__ void so3_exp_jl(const R w[3], R E[9], R J[9]) {
     R th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
     R a, b, c;
-    if (th2 < R(1e-8)) {
-        a = R(1) - th2 / R(6);
-        b = R(0.5) - th2 / R(24);
-    } else {
-        R th = sqrt(th2);
-        R sh = sin(R(0.5) * th);
-        a = sin(th) / th;
-        b = R(2) * sh * sh / th2;
-    }
     if (th2 < R(0.25)) {
+        // |w| < 0.5: Taylor series of sin(x)/x, (1 - cos x)/x^2 and
+        // (x - sin x)/x^3 in x^2; the first omitted term is below 3e-11
+        a = R(1) + th2 * (R(-1.0 / 6.0) + th2 * (R(1.0 / 120.0) + th2 * (R(-1.0 / 5040.0) + th2 * R(1.0 / 362880.0))));
+        b = R(0.5) + th2 * (R(-1.0 / 24.0) + th2 * (R(1.0 / 720.0) + th2 * (R(-1.0 / 40320.0) + th2 * R(1.0 / 3628800.0))));
         c = R(1.0 / 6.0) + th2 * (R(-1.0 / 120.0) + th2 * (R(1.0 / 5040.0) +
             th2 * (R(-1.0 / 362880.0) + th2 * R(1.0 / 39916800.0))));
     } else {
         R th = sqrt(th2);
-        c = (th - sin(th)) / (th2 * th);
+        R st = sin(th), sh = sin(R(0.5) * th);
+        a = st / th;
+        b = R(2) * sh * sh / th2;
+        c = (th - st) / (th2 * th);
     }
     // W^2 = w w^T - th2 I
     R W2[9] = {w[0] * w[0] - th2, w[0] * w[1], w[0] * w[2],
@@ -154,7 +198,7 @@ struct Lin {
 };
 
 template <typename R>
-__device__ __forceinline__ void linearise(const KParams& P, const double* __restrict__ Rref,
+__device__ __forceinline__ void linearise(const KParams<R>& P, const double* __restrict__ Rref,
                                           const double* __restrict__ cref, const double* __restrict__ lref,
                                           const R x0[9], R zu, R zv, Lin<R>& L) {
     R w[3] = {x0[3], x0[4], x0[5]};
@@ -177,7 +221,7 @@ __device__ __forceinline__ void linearise(const KParams& P, const double* __rest
 #pragma unroll
     for (int i = 0; i < 3; ++i) p[i] = Rm[i * 3 + 0] * d[0] + Rm[i * 3 + 1] * d[1] + Rm[i * 3 + 2] * d[2];
 
-    if (!(p[2] >= R(P.z_min))) {
+    if (!(p[2] >= P.z_min)) {
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
 #pragma unroll
@@ -190,11 +234,11 @@ __device__ __forceinline__ void linearise(const KParams& P, const double* __rest
         L.r2 = R(0);
         return;
     }
-    const R fx = R(P.fx), fy = R(P.fy);
-    R iz = R(1) / p[2];
+    const R fx = P.fx, fy = P.fy;
+    R iz = rcp(p[2]);
     R u = fx * p[0] * iz, v = fy * p[1] * iz;
-    R r0 = zu - (u + R(P.cx));
-    R r1 = zv - (v + R(P.cy));
+    R r0 = zu - (u + P.cx);
+    R r1 = zv - (v + P.cy);
     // d pi / d p rows
     R q[2][3] = {{fx * iz, R(0), -u * iz}, {R(0), fy * iz, -v * iz}};
 #pragma unroll
@@ -216,12 +260,15 @@ __device__ __forceinline__ void linearise(const KParams& P, const double* __rest
     // Huber weight (Sec. 6) on the Mahalanobis distance M = |r| / sigma
     R r2 = r0 * r0 + r1 * r1;
     R k = R(1);
-    if (P.huber_n > 0.0) {
-        R M = sqrt(r2) * R(P.inv_sigma);
-        R N = R(P.huber_n);
-        if (M > N) k = R(2) * N / M - (N * N) / (M * M);
+    if (P.huber_n > R(0)) {
+        R M = sqrt(r2) * P.inv_sigma;
+        R N = P.huber_n;
+        if (M > N) {
+            R iM = rcp(M);
+            k = R(2) * N * iM - (N * N) * (iM * iM);
+        }
     }
-    L.W = k * R(P.inv_sigma2);
+    L.W = k * P.inv_sigma2;
     L.r2 = r2;
     // y = J x0 + r ;  J x0 = Jk[:,0:3] (dc - dl) + Jk[:,3:6] dw
 #pragma unroll
@@ -262,7 +309,7 @@ __device__ __forceinline__ bool message(C* Pb, const C* qb, const C Jb[2][nb], c
     }
     // N = (I + W Q)^-1
     C a00 = C(1) + W * Q00, a01 = W * Q01, a11 = C(1) + W * Q11;
-    C idet = C(1) / (a00 * a11 - a01 * a01);
+    C idet = rcp(a00 * a11 - a01 * a01);
     C N00 = a11 * idet, N01 = -a01 * idet, N11 = a00 * idet;
     C M00 = W * N00, M01 = W * N01, M11 = W * N11;
     C e0 = y[0] - s0, e1 = y[1] - s1;
@@ -281,20 +328,37 @@ __device__ __forceinline__ bool message(C* Pb, const C* qb, const C Jb[2][nb], c
     return ok;
 }
 
-// The same message in FP64 from FP32 inputs (the fallback for an
-// ill-conditioned FP32 factorisation).
-template <typename R, int na, int nb>
-__device__ __noinline__ bool message_fp64(const R* Pb_in, const R* qb, const R Jb[2][nb], const R Ja[2][na],
-                                          const R y[2], R W, R* lam, R* eta) {
-    double Pb[nb * (nb + 1) / 2], q[nb], jb[2][nb], ja[2][na], yy[2], l[na * (na + 1) / 2], e[na], ratio;
-    for (int i = 0; i < nb * (nb + 1) / 2; ++i) Pb[i] = double(Pb_in[i]);
-    for (int i = 0; i < nb; ++i) { q[i] = double(qb[i]); jb[0][i] = double(Jb[0][i]); jb[1][i] = double(Jb[1][i]); }
-    for (int i = 0; i < na; ++i) { ja[0][i] = double(Ja[0][i]); ja[1][i] = double(Ja[1][i]); }
-    yy[0] = double(y[0]);
-    yy[1] = double(y[1]);
-    bool ok = message<double, na, nb>(Pb, q, jb, ja, yy, double(W), l, e, ratio);
-    for (int i = 0; i < na * (na + 1) / 2; ++i) lam[i] = R(l[i]);
-    for (int i = 0; i < na; ++i) eta[i] = R(e[i]);
+// FP64 redo of one message of factor f from FP32 state (the fallback for an
+// ill-conditioned FP32 factorisation).  It re-reads its inputs -- the
+// factor's linearisation point, the adjacent belief and the factor's
+// previous message, none of which the calling thread has overwritten yet --
+// and writes the undamped message to out (element i at out[i * out_stride]),
+// so that the FP32 path keeps all of its operands in registers.
+template <typename R, bool to_landmark>
+__device__ __noinline__ bool message_fp64(const R* __restrict__ x0s, int n_f, int f, const double* __restrict__ Rref,
+                                          const double* __restrict__ cref, const double* __restrict__ lref,
+                                          const R* __restrict__ zf, const R* __restrict__ bel_other,
+                                          const R* __restrict__ msg_other, int stride_other, R* out, int out_stride,
+                                          double fx, double fy, double cx, double cy, double inv_sigma2,
+                                          double inv_sigma, double huber_n, double z_min) {
+    KParams<double> P{};
+    P.fx = fx; P.fy = fy; P.cx = cx; P.cy = cy;
+    P.inv_sigma2 = inv_sigma2; P.inv_sigma = inv_sigma; P.huber_n = huber_n; P.z_min = z_min;
+    double x0[9];
+    for (int i = 0; i < 9; ++i) x0[i] = double(x0s[(size_t)i * n_f + f]);
+    Lin<double> L;
+    linearise<double>(P, Rref, cref, lref, x0, double(zf[0]), double(zf[1]), L);
+    constexpr int na = to_landmark ? 3 : 6, nb = to_landmark ? 6 : 3;
+    constexpr int pa = na * (na + 1) / 2, pb = nb * (nb + 1) / 2;
+    double Pb[pb], q[nb], lam[pa], eta[na], ratio;
+    // incoming = belief of the marginalised variable / previous message to it
+    for (int i = 0; i < pb; ++i) Pb[i] = double(bel_other[i]) - double(msg_other[(size_t)i * stride_other]);
+    for (int i = 0; i < nb; ++i) q[i] = double(bel_other[pb + i]) - double(msg_other[(size_t)(pb + i) * stride_other]);
+    bool ok;
+    if constexpr (to_landmark) ok = message<double, 3, 6>(Pb, q, L.Jk, L.Jl, L.y, L.W, lam, eta, ratio);
+    else ok = message<double, 6, 3>(Pb, q, L.Jl, L.Jk, L.y, L.W, lam, eta, ratio);
+    for (int i = 0; i < pa; ++i) out[(size_t)i * out_stride] = R(lam[i]);
+    for (int i = 0; i < na; ++i) out[(size_t)(pa + i) * out_stride] = R(eta[i]);
     return ok;
 }
 
@@ -331,125 +395,13 @@ __device__ __forceinline__ void raise_error(int32_t* ctl, int where) {
 }
 
 // ------------------------------------------------------------------------
-// factor kernel
+// shared pieces of the belief updates
 
+// Sec. 8: prior scale at iteration t (geometric anneal to the final scale),
+// tabulated on the host.
 template <typename R>
-__global__ void __launch_bounds__(FACTOR_BLOCK) factor_kernel(DevGraph<R> g, KParams P) {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= g.n_f) return;
-    const int n_f = g.n_f;
-    const int t = g.ctl[CTL_ITER];
-    const int k = g.fk[f], m = g.fm[f];
-
-    R kb[KBEL], lb[LBEL];
-    load_rec<R, KBEL>(g.kf_bel + (size_t)k * KBEL, kb);
-    load_rec<R, LBEL>(g.lm_bel + (size_t)m * LBEL, lb);
-
-    R x0[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) x0[i] = g.x0[(size_t)i * n_f + f];
-    int tl = g.tlin[f];
-
-    // Sec. 5 / Sec. 8: relinearise when the adjacent means moved more than
-    // beta from the linearisation point, at most every relin_interval
-    // iterations.
-    if (!P.linear && t - tl >= P.relin_interval) {
-        R mu[9] = {kb[27], kb[28], kb[29], kb[30], kb[31], kb[32], lb[9], lb[10], lb[11]};
-        R d2 = R(0);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) d2 += (mu[i] - x0[i]) * (mu[i] - x0[i]);
-        if (sqrt(d2) > R(P.relin_beta)) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                x0[i] = mu[i];
-                g.x0[(size_t)i * n_f + f] = mu[i];
-            }
-            tl = t;
-            g.tlin[f] = t;
-            atomicAdd(&g.ctl[CTL_RELINS], 1);
-        }
-    }
-
-    Lin<R> L;
-    linearise<R>(P, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3, g.lm_ref + (size_t)m * 3, x0,
-                 g.z[2 * (size_t)f], g.z[2 * (size_t)f + 1], L);
-
-    // previous messages m^t
-    R mk[KREC];
-    load_rec<R, KREC>(g.mk + (size_t)f * KREC, mk);
-    R ml[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) ml[i] = g.ml[(size_t)i * n_f + f];
-
-    // ---- message to the keyframe: marginalise the landmark ----
-    // incoming = landmark belief / this factor's previous message to it
-    R Pm[6], qm[3];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) Pm[i] = lb[i] - ml[i];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) qm[i] = lb[6 + i] - ml[6 + i];
-    R Pm_copy[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) Pm_copy[i] = Pm[i];
-    R lam_k[21], eta_k[6], ratio_m;
-    bool ok_m = message<R, 6, 3>(Pm, qm, L.Jl, L.Jk, L.y, L.W, lam_k, eta_k, ratio_m);
-
-    // ---- message to the landmark: marginalise the keyframe (6x6) ----
-    R Pk[21], qk[6];
-#pragma unroll
-    for (int i = 0; i < 21; ++i) Pk[i] = kb[i] - mk[i];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) qk[i] = kb[21 + i] - mk[21 + i];
-    R Pk_copy[21];
-#pragma unroll
-    for (int i = 0; i < 21; ++i) Pk_copy[i] = Pk[i];
-    R lam_m[6], eta_m[3], ratio_k;
-    bool ok_k = message<R, 3, 6>(Pk, qk, L.Jk, L.Jl, L.y, L.W, lam_m, eta_m, ratio_k);
-
-    if (sizeof(R) == 4 && P.fallback) {
-        if (!ok_k || ratio_k < R(P.pivot_ratio)) {
-            ok_k = message_fp64<R, 3, 6>(Pk_copy, qk, L.Jk, L.Jl, L.y, L.W, lam_m, eta_m);
-            atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
-        }
-        if (!ok_m) {
-            ok_m = message_fp64<R, 6, 3>(Pm_copy, qm, L.Jl, L.Jk, L.y, L.W, lam_k, eta_k);
-            atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
-        }
-    }
-    if (!ok_k || !ok_m) raise_error(g.ctl, n_f > 0 ? -1 - f : -1);
-
-    // damping of eta (Sec. 5); undamped in the iteration of a (re)linearisation
-    // and for the next damp_hold - 1 iterations (Sec. 8)
-    if (t - tl >= P.damp_hold) {
-        const R d = R(P.damping);
-#pragma unroll
-        for (int i = 0; i < 6; ++i) eta_k[i] = (R(1) - d) * eta_k[i] + d * mk[21 + i];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) eta_m[i] = (R(1) - d) * eta_m[i] + d * ml[6 + i];
-    }
-
-    R out[KREC];
-#pragma unroll
-    for (int i = 0; i < 21; ++i) out[i] = lam_k[i];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) out[21 + i] = eta_k[i];
-    out[27] = R(0);
-    store_rec<R, KREC>(g.mk_out + (size_t)f * KREC, out);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) g.ml_out[(size_t)i * n_f + f] = lam_m[i];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) g.ml_out[(size_t)(6 + i) * n_f + f] = eta_m[i];
-}
-
-// ------------------------------------------------------------------------
-// belief kernel: blocks [0, n_kf) one keyframe each; then one thread per
-// landmark.  Forms b^{t+1} = prior(t+1) + sum of messages and its mean.
-
-// Sec. 8: prior scale at iteration t (geometric anneal to prior_final).
-__device__ __forceinline__ double prior_scale(const KParams& P, int t) {
-    if (P.prior_anneal <= 0) return P.prior_final;
-    int tt = t < P.prior_anneal ? t : P.prior_anneal;
-    return pow(P.prior_final, double(tt) / double(P.prior_anneal));
+__device__ __forceinline__ R prior_scale(const KParams<R>& P, int t) {
+    return P.prior_s[t < P.prior_T ? t : P.prior_T];
 }
 
 template <typename R, int n>
@@ -463,13 +415,16 @@ __device__ __forceinline__ bool solve_mean(R* lam_packed_copy, const R* eta, R* 
     return ok;
 }
 
+// FP64 redo of a belief mean: reads Lambda (packed) and eta from the
+// belief record in global memory and writes mu back into it.
 template <typename R, int n>
-__device__ __noinline__ bool solve_mean_fp64(const R* lam, const R* eta, R* mu) {
-    double A[n * (n + 1) / 2], e[n], m[n], ratio;
-    for (int i = 0; i < n * (n + 1) / 2; ++i) A[i] = double(lam[i]);
-    for (int i = 0; i < n; ++i) e[i] = double(eta[i]);
+__device__ __noinline__ bool solve_mean_fp64(R* rec) {
+    constexpr int p = n * (n + 1) / 2;
+    double A[p], e[n], m[n], ratio;
+    for (int i = 0; i < p; ++i) A[i] = double(rec[i]);
+    for (int i = 0; i < n; ++i) e[i] = double(rec[p + i]);
     bool ok = solve_mean<double, n>(A, e, m, ratio);
-    for (int i = 0; i < n; ++i) mu[i] = R(m[i]);
+    for (int i = 0; i < n; ++i) rec[p + n + i] = R(m[i]);
     return ok;
 }
 
@@ -479,135 +434,542 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
+// Landmark belief b^{t+1} = s(t+1) D + sum of messages (eqs. beliefeta /
+// belieflambda) and its mean; writes the record, returns |dmu|_inf.
 template <typename R>
-__global__ void __launch_bounds__(BELIEF_BLOCK) belief_kernel(DevGraph<R> g, KParams P) {
-    __shared__ R red[27][BELIEF_BLOCK];
-    __shared__ float wmax[BELIEF_BLOCK / 32];
-    __shared__ int is_last;
-    const int tid = threadIdx.x;
-    const int t1 = g.ctl[CTL_ITER] + 1;
-    const R s = R(prior_scale(P, t1));
-    const R isig2 = R(P.inv_sigma2);
+__device__ __forceinline__ float finish_landmark(const DevGraph<R>& g, const KParams<R>& P, int m, R s, const R* sum,
+                                                 const R* mu_old, R* out_bel) {
+    R lam[6], eta[3], mu[3], work[6], ratio;
+    const R isig2 = P.inv_sigma2;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) lam[j] = sum[j];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) eta[j] = sum[6 + j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) lam[pk(i, i)] += s * g.lm_D[m * 3 + i] * isig2;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) work[j] = lam[j];
+    bool ok = solve_mean<R, 3>(work, eta, mu, ratio);
+    R out[LBEL];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) out[j] = lam[j];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) { out[6 + j] = eta[j]; out[9 + j] = mu[j]; }
+    R* rec = out_bel + (size_t)m * LBEL;
+    store_rec<R, LBEL>(rec, out);
+    if (sizeof(R) == 4 && P.fallback && !ok) {
+        ok = solve_mean_fp64<R, 3>(rec);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) mu[i] = rec[9 + i];
+        atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
+    }
     float dmu = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (!isfinite(mu[i])) ok = false;
+        dmu = fmaxf(dmu, float(fabs(mu[i] - mu_old[i])));
+    }
+    if (!ok) raise_error(g.ctl, g.n_kf + m);
+    return dmu;
+}
 
-    if ((int)blockIdx.x < g.n_kf) {
-        const int k = blockIdx.x;
+// Keyframe belief b^{t+1} = s(t+1) D + anchor + sum of messages and its
+// mean from the (already reduced) sums; writes the record to out and
+// returns |dmu|_inf against mu_old.
+template <typename R>
+__device__ __forceinline__ float finish_keyframe(const DevGraph<R>& g, const KParams<R>& P, int k, R s,
+                                                 const R* sum, const R* mu_old, R* out_bel) {
+    R lam[21], eta[6], mu[6], work[21], ratio;
+    const R isig2 = P.inv_sigma2;
+#pragma unroll
+    for (int j = 0; j < 21; ++j) lam[j] = sum[j];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) eta[j] = sum[21 + j];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) lam[pk(i, i)] += (s * g.kf_D[k * 6 + i] + P.anchor_scale * g.kf_A[k * 6 + i]) * isig2;
+#pragma unroll
+    for (int j = 0; j < 21; ++j) work[j] = lam[j];
+    bool ok = solve_mean<R, 6>(work, eta, mu, ratio);
+    R out[KBEL];
+#pragma unroll
+    for (int j = 0; j < 21; ++j) out[j] = lam[j];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) { out[21 + j] = eta[j]; out[27 + j] = mu[j]; }
+    out[33] = out[34] = out[35] = R(0);
+    R* rec = out_bel + (size_t)k * KBEL;
+    store_rec<R, KBEL>(rec, out);
+    if (sizeof(R) == 4 && P.fallback && (!ok || ratio < P.pivot_ratio)) {
+        ok = solve_mean_fp64<R, 6>(rec);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) mu[i] = rec[27 + i];
+        atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
+    }
+    float dmu = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        if (!isfinite(mu[i])) ok = false;
+        dmu = fmaxf(dmu, float(fabs(mu[i] - mu_old[i])));
+    }
+    if (!ok) raise_error(g.ctl, k);
+    return dmu;
+}
+
+// L2-coherent loads (bypass L1) for data that other SMs write during the
+// same launch (the persistent kernel runs many iterations in one launch).
+template <typename R, int N>
+__device__ __forceinline__ void load_rec_cg(const R* src, R* dst) {
+    if constexpr (sizeof(R) == 4) {
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i) {
+            float4 v = __ldcg(s4 + i);
+            dst[4 * i + 0] = v.x; dst[4 * i + 1] = v.y; dst[4 * i + 2] = v.z; dst[4 * i + 3] = v.w;
+        }
+    } else {
+        const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            double2 v = __ldcg(s2 + i);
+            dst[2 * i + 0] = v.x; dst[2 * i + 1] = v.y;
+        }
+    }
+}
+
+// Keyframe messages are double-buffered by iteration parity: iteration t
+// reads m^t from buffer t & 1 and writes m^{t+1} to the other buffer
+// (mk_redirect, when set, receives the writes instead).
+template <typename R>
+__device__ __forceinline__ const R* mk_read(const DevGraph<R>& g, int t) { return (t & 1) ? g.mk2 : g.mk; }
+template <typename R>
+__device__ __forceinline__ R* mk_write(const DevGraph<R>& g, int t) {
+    return g.mk_redirect ? g.mk_redirect : ((t & 1) ? g.mk : g.mk2);
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int dmu_slot(int t) { return (t & 1) ? CTL_DMU_ACC1 : CTL_DMU_ACC; }
+
+__device__ __forceinline__ void dmu_atomic_max_slot(int32_t* ctl, int slot, float v) {
+    if (!(v >= 0.0f)) v = INFINITY;
+    atomicMax(reinterpret_cast<unsigned int*>(&ctl[slot]), __float_as_uint(v));
+}
+
+// ------------------------------------------------------------------------
+// Phase A: one warp, one tile of whole landmarks (at most 32 factors,
+// consecutive in landmark order), one lane per factor -- relinearisation
+// test, Jacobian, Huber weight, both messages, damping (Sec. 4-6, 8); then
+// the landmark messages of the tile are summed per landmark by a segmented
+// warp scan (fixed lane order) and each landmark's last lane forms its
+// belief b^{t+1} and mean (a landmark wholly inside a tile is read by no
+// other warp).  Returns this lane's max |dmu|.
+
+template <typename R>
+__device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R>& P, int tile, int t, R s_next,
+                                           int lane) {
+    const int n_f = g.n_f;
+    const int ts = g.tile_start[tile], te = g.tile_start[tile + 1];
+    const int f = ts + lane;
+    const bool active = f < te;
+
+    R sum[9];           // this lane's new landmark message (Lambda 6, eta 3)
+    R mu_m_old[3] = {R(0), R(0), R(0)};
+    int m = -1, lo = 0, hi = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) sum[i] = R(0);
+
+    if (active) {
+        const int k = g.fk[f];
+        const size_t ks = (size_t)g.kpos[f] * KREC;   // this factor's keyframe-message slot
+        m = g.fm[f];
+        lo = g.lm_off[m];
+        hi = g.lm_off[m + 1];
+        const R* kbp = g.kf_bel + (size_t)k * KBEL;
+        R lb[LBEL];
+        load_rec_cg<R, LBEL>(g.lm_bel + (size_t)m * LBEL, lb);
+        mu_m_old[0] = lb[9];
+        mu_m_old[1] = lb[10];
+        mu_m_old[2] = lb[11];
+        R ml[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) ml[i] = g.ml[(size_t)i * n_f + f];
+        R x0[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) x0[i] = g.x0[(size_t)i * n_f + f];
+        int tl = g.tlin[f];
+
+        // Sec. 5 / Sec. 8: relinearise when the adjacent means moved more
+        // than beta from the linearisation point, at most every
+        // relin_interval iterations.
+        if (!P.linear && t - tl >= P.relin_interval) {
+            R mu[9];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) mu[i] = __ldcg(kbp + 27 + i);
+            mu[6] = lb[9];
+            mu[7] = lb[10];
+            mu[8] = lb[11];
+            R d2 = R(0);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) d2 += (mu[i] - x0[i]) * (mu[i] - x0[i]);
+            if (d2 > P.relin_beta * P.relin_beta) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    x0[i] = mu[i];
+                    g.x0[(size_t)i * n_f + f] = mu[i];
+                }
+                tl = t;
+                g.tlin[f] = t;
+                atomicAdd(&g.ctl[CTL_RELINS], 1);
+            }
+        }
+
+        Lin<R> L;
+        linearise<R>(P, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3, g.lm_ref + (size_t)m * 3, x0,
+                     g.z[2 * (size_t)f], g.z[2 * (size_t)f + 1], L);
+        const bool damp = t - tl >= P.damp_hold;
+        const R d = P.damping;
+
+        // ---- message to the keyframe: marginalise the landmark ----
+        // incoming = landmark belief / this factor's previous message to it
+        {
+            R Pm[6], qm[3];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) Pm[i] = lb[i] - ml[i];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) qm[i] = lb[6 + i] - ml[6 + i];
+            R lam_k[21], eta_k[6], ratio_m;
+            bool ok_m = message<R, 6, 3>(Pm, qm, L.Jl, L.Jk, L.y, L.W, lam_k, eta_k, ratio_m);
+            if (sizeof(R) == 4 && P.fallback && !ok_m) {
+                R* o = mk_write(g, t) + ks;
+                ok_m = message_fp64<R, false>(g.x0, n_f, f, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3,
+                                              g.lm_ref + (size_t)m * 3, g.z + 2 * (size_t)f,
+                                              g.lm_bel + (size_t)m * LBEL, g.ml + f, n_f, o, 1,
+                                              double(P.fx), double(P.fy), double(P.cx), double(P.cy),
+                                              double(P.inv_sigma2), double(P.inv_sigma), double(P.huber_n),
+                                              double(P.z_min));
+#pragma unroll
+                for (int i = 0; i < 21; ++i) lam_k[i] = o[i];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) eta_k[i] = o[21 + i];
+                atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
+            }
+            if (!ok_m) raise_error(g.ctl, -1 - f);
+            // incoming for the landmark side: keyframe belief / this
+            // factor's previous message to the keyframe (read before the new
+            // message overwrites it)
+            R Pk[21], qk[6];
+            {
+                R kb[28], mk[KREC];
+                load_rec_cg<R, 28>(kbp, kb);
+                load_rec<R, KREC>(mk_read(g, t) + ks, mk);
+#pragma unroll
+                for (int i = 0; i < 21; ++i) Pk[i] = kb[i] - mk[i];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) qk[i] = kb[21 + i] - mk[21 + i];
+                // damping of eta (Sec. 5); undamped in the iteration of a
+                // (re)linearisation and for the next damp_hold - 1
+                // iterations (Sec. 8)
+                if (damp) {
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) eta_k[i] = (R(1) - d) * eta_k[i] + d * mk[21 + i];
+                }
+            }
+            // the keyframe-side fallback (rare) re-reads the previous
+            // landmark-side message, which is still intact here
+            R out[KREC];
+#pragma unroll
+            for (int i = 0; i < 21; ++i) out[i] = lam_k[i];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) out[21 + i] = eta_k[i];
+            out[27] = R(0);
+            store_rec<R, KREC>(mk_write(g, t) + ks, out);
+
+            // ---- message to the landmark: marginalise the keyframe (6x6) ----
+            R lam_m[6], eta_m[3], ratio_k;
+            bool ok_k = message<R, 3, 6>(Pk, qk, L.Jk, L.Jl, L.y, L.W, lam_m, eta_m, ratio_k);
+            if (sizeof(R) == 4 && P.fallback && (!ok_k || ratio_k < P.pivot_ratio)) {
+                R* o = g.ml_out + f;
+                ok_k = message_fp64<R, true>(g.x0, n_f, f, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3,
+                                             g.lm_ref + (size_t)m * 3, g.z + 2 * (size_t)f,
+                                             g.kf_bel + (size_t)k * KBEL, mk_read(g, t) + ks, 1, o, n_f,
+                                             double(P.fx), double(P.fy), double(P.cx), double(P.cy),
+                                             double(P.inv_sigma2), double(P.inv_sigma), double(P.huber_n),
+                                             double(P.z_min));
+#pragma unroll
+                for (int i = 0; i < 6; ++i) lam_m[i] = o[(size_t)i * n_f];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) eta_m[i] = o[(size_t)(6 + i) * n_f];
+                atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
+            }
+            if (!ok_k) raise_error(g.ctl, -1 - f);
+            if (damp) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) eta_m[i] = (R(1) - d) * eta_m[i] + d * ml[6 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                g.ml_out[(size_t)i * n_f + f] = lam_m[i];
+                sum[i] = lam_m[i];
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                g.ml_out[(size_t)(6 + i) * n_f + f] = eta_m[i];
+                sum[6 + i] = eta_m[i];
+            }
+        }
+    }
+
+    // landmarks wholly inside the tile: segmented inclusive scan over the
+    // lanes holding the same landmark (landmark ranges are contiguous)
+    const bool whole = active && lo >= ts && hi <= te;
+    const int seg0 = whole ? lo - ts : lane;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            R o = __shfl_up_sync(0xffffffffu, sum[j], d);
+            if (lane - d >= seg0) sum[j] += o;
+        }
+    }
+    float dmu = 0.0f;
+    if (whole && lane == hi - ts - 1) dmu = finish_landmark<R>(g, P, m, s_next, sum, mu_m_old, g.lm_bel_out);
+    return dmu;
+}
+
+// ------------------------------------------------------------------------
+// Phase B: one warp per keyframe (a fixed-order reduction of its messages,
+// which are stored contiguously in the keyframe's CSR order: lane l takes
+// entries l, l + 32, ...; then a fixed shuffle tree; lane 0 forms the
+// belief), one warp per landmark split
+// across tiles, and prior-only beliefs for variables without factors (32
+// per warp).  Work item w: [0, n_kf) keyframes, then split landmarks, then
+// orphan groups.  Returns max |dmu| in lane 0.
+
+template <typename R>
+__device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParams<R>& P, int w, int t, R s_next,
+                                              int lane) {
+    float dmu = 0.0f;
+    if (w < g.n_kf) {
+        const int k = w;
+        const R* msgs = mk_write(g, t);
         R acc[27];
 #pragma unroll
         for (int j = 0; j < 27; ++j) acc[j] = R(0);
         const int b0 = g.kf_off[k], b1 = g.kf_off[k + 1];
-        for (int i = b0 + tid; i < b1; i += BELIEF_BLOCK) {
+#pragma unroll 4
+        for (int i = b0 + lane; i < b1; i += 32) {
             R rec[KREC];
-            load_rec<R, KREC>(g.mk + (size_t)g.kf_list[i] * KREC, rec);
+            load_rec_cg<R, KREC>(msgs + (size_t)i * KREC, rec);
 #pragma unroll
             for (int j = 0; j < 27; ++j) acc[j] += rec[j];
         }
 #pragma unroll
-        for (int j = 0; j < 27; ++j) red[j][tid] = acc[j];
-        __syncthreads();
-        for (int st = BELIEF_BLOCK / 2; st > 0; st >>= 1) {
-            if (tid < st) {
+        for (int j = 0; j < 27; ++j) acc[j] = warp_sum(acc[j]);
+        if (lane == 0) {
+            const R* old = g.kf_bel + (size_t)k * KBEL;
+            R mu_old[6];
 #pragma unroll
-                for (int j = 0; j < 27; ++j) red[j][tid] += red[j][tid + st];
-            }
-            __syncthreads();
+            for (int i = 0; i < 6; ++i) mu_old[i] = __ldcg(old + 27 + i);
+            dmu = finish_keyframe<R>(g, P, k, s_next, acc, mu_old, g.kf_bel_out);
         }
-        if (tid == 0) {
-            R lam[21], eta[6], mu[6], ratio;
+    } else if (w < g.n_kf + g.n_big) {
+        const int m = g.big_lm[w - g.n_kf];
+        R acc[9];
 #pragma unroll
-            for (int j = 0; j < 21; ++j) lam[j] = red[j][0];
+        for (int j = 0; j < 9; ++j) acc[j] = R(0);
+        const int b0 = g.lm_off[m], b1 = g.lm_off[m + 1];
+        for (int f = b0 + lane; f < b1; f += 32) {
 #pragma unroll
-            for (int j = 0; j < 6; ++j) eta[j] = red[21 + j][0];
+            for (int j = 0; j < 9; ++j) acc[j] += __ldcg(g.ml_out + (size_t)j * g.n_f + f);
+        }
 #pragma unroll
-            for (int i = 0; i < 6; ++i)
-                lam[pk(i, i)] += (s * g.kf_D[k * 6 + i] + R(P.anchor_scale) * g.kf_A[k * 6 + i]) * isig2;
-            R work[21];
-#pragma unroll
-            for (int j = 0; j < 21; ++j) work[j] = lam[j];
-            bool ok = solve_mean<R, 6>(work, eta, mu, ratio);
-            if (sizeof(R) == 4 && P.fallback && (!ok || ratio < R(P.pivot_ratio))) {
-                ok = solve_mean_fp64<R, 6>(lam, eta, mu);
-                atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
-            }
-            R* rec = g.kf_bel + (size_t)k * KBEL;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                if (!isfinite(mu[i])) ok = false;
-                dmu = fmaxf(dmu, float(fabs(mu[i] - rec[27 + i])));
-            }
-            if (!ok) raise_error(g.ctl, k);
-            R out[KBEL];
-#pragma unroll
-            for (int j = 0; j < 21; ++j) out[j] = lam[j];
-#pragma unroll
-            for (int j = 0; j < 6; ++j) { out[21 + j] = eta[j]; out[27 + j] = mu[j]; }
-            out[33] = out[34] = out[35] = R(0);
-            store_rec<R, KBEL>(rec, out);
+        for (int j = 0; j < 9; ++j) acc[j] = warp_sum(acc[j]);
+        if (lane == 0) {
+            const R* old = g.lm_bel + (size_t)m * LBEL;
+            R mu_old[3] = {__ldcg(old + 9), __ldcg(old + 10), __ldcg(old + 11)};
+            dmu = finish_landmark<R>(g, P, m, s_next, acc, mu_old, g.lm_bel_out);
         }
     } else {
-        const int m = (blockIdx.x - g.n_kf) * BELIEF_BLOCK + tid;
-        if (m < g.n_lm) {
-            R acc[9];
+        // variables without factors: prior-only beliefs, mean 0
+        const int i = (w - g.n_kf - g.n_big) * 32 + lane;
+        if (i < g.n_orphan) {
+            const int v = g.orphan[i];
+            const R isig2 = P.inv_sigma2;
+            if (v < g.n_kf) {
+                R out[KBEL];
 #pragma unroll
-            for (int j = 0; j < 9; ++j) acc[j] = R(0);
-            const int b0 = g.lm_off[m], b1 = g.lm_off[m + 1];
-            for (int f = b0; f < b1; ++f) {
+                for (int j = 0; j < KBEL; ++j) out[j] = R(0);
 #pragma unroll
-                for (int j = 0; j < 9; ++j) acc[j] += g.ml[(size_t)j * g.n_f + f];
+                for (int q = 0; q < 6; ++q)
+                    out[pk(q, q)] = (s_next * g.kf_D[v * 6 + q] + P.anchor_scale * g.kf_A[v * 6 + q]) * isig2;
+                store_rec<R, KBEL>(g.kf_bel_out + (size_t)v * KBEL, out);
+            } else {
+                const int mm = v - g.n_kf;
+                R out[LBEL];
+#pragma unroll
+                for (int j = 0; j < LBEL; ++j) out[j] = R(0);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) out[pk(q, q)] = s_next * g.lm_D[mm * 3 + q] * isig2;
+                store_rec<R, LBEL>(g.lm_bel_out + (size_t)mm * LBEL, out);
             }
-            R lam[6], eta[3], mu[3], ratio;
-#pragma unroll
-            for (int j = 0; j < 6; ++j) lam[j] = acc[j];
-#pragma unroll
-            for (int j = 0; j < 3; ++j) eta[j] = acc[6 + j];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) lam[pk(i, i)] += s * g.lm_D[m * 3 + i] * isig2;
-            R work[6];
-#pragma unroll
-            for (int j = 0; j < 6; ++j) work[j] = lam[j];
-            bool ok = solve_mean<R, 3>(work, eta, mu, ratio);
-            if (sizeof(R) == 4 && P.fallback && !ok) {
-                ok = solve_mean_fp64<R, 3>(lam, eta, mu);
-                atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
-            }
-            R* rec = g.lm_bel + (size_t)m * LBEL;
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                if (!isfinite(mu[i])) ok = false;
-                dmu = fmaxf(dmu, float(fabs(mu[i] - rec[9 + i])));
-            }
-            if (!ok) raise_error(g.ctl, g.n_kf + m);
-            R out[LBEL];
-#pragma unroll
-            for (int j = 0; j < 6; ++j) out[j] = lam[j];
-#pragma unroll
-            for (int j = 0; j < 3; ++j) { out[6 + j] = eta[j]; out[9 + j] = mu[j]; }
-            store_rec<R, LBEL>(rec, out);
         }
     }
+    return dmu;
+}
 
-    // max |dmu| over the grid: max is order independent, so an atomic on
-    // the (non-negative) float bits stays deterministic
+template <typename R>
+__host__ __device__ inline int phase_b_items(const DevGraph<R>& g) {
+    return g.n_kf + g.n_big + (g.n_orphan + 31) / 32;
+}
+
+// ------------------------------------------------------------------------
+// Two-kernel iteration (the launch-per-phase path).
+
+template <typename R>
+__global__ void __launch_bounds__(FACTOR_BLOCK) factor_kernel(DevGraph<R> g, KParams<R> P) {
+    const int lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * (FACTOR_BLOCK / 32) + (threadIdx.x >> 5);
+    if (tile >= g.n_tiles) return;   // uniform per warp
+    const int t = g.ctl[CTL_ITER];
+    float dmu = tile_work<R>(g, P, tile, t, prior_scale(P, t + 1), lane);
     dmu = warp_max(dmu);
-    if ((tid & 31) == 0) wmax[tid >> 5] = dmu;
+    if (lane == 0 && dmu > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), dmu);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(FACTOR_BLOCK) belief_kernel(DevGraph<R> g, KParams<R> P) {
+    __shared__ int is_last;
+    const int lane = threadIdx.x & 31;
+    const int w = blockIdx.x * (FACTOR_BLOCK / 32) + (threadIdx.x >> 5);
+    const int t = g.ctl[CTL_ITER];
+    float dmu = 0.0f;
+    if (w < phase_b_items(g)) dmu = phase_b_item<R>(g, P, w, t, prior_scale(P, t + 1), lane);
+    // the last block to finish closes the iteration (max is order
+    // independent, so the atomic on non-negative float bits is deterministic)
+    dmu = warp_max(dmu);
+    if (lane == 0 && dmu > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), dmu);
     __syncthreads();
-    if (tid == 0) {
-        float v = 0.0f;
-        for (int i = 0; i < BELIEF_BLOCK / 32; ++i) v = fmaxf(v, wmax[i]);
-        if (!(v >= 0.0f)) v = INFINITY;
-        atomicMax(reinterpret_cast<unsigned int*>(&g.ctl[CTL_DMU_ACC]), __float_as_uint(v));
+    if (threadIdx.x == 0) {
         __threadfence();
         int ticket = atomicAdd(&g.ctl[CTL_DONE], 1);
         is_last = (ticket == (int)gridDim.x - 1);
     }
     __syncthreads();
-    if (is_last && tid == 0) {
-        // the last block to finish closes the iteration
+    if (is_last && threadIdx.x == 0) {
         __threadfence();
-        int acc = atomicExch(&g.ctl[CTL_DMU_ACC], 0);
-        g.ctl[CTL_DMU_LAST] = acc;
+        g.ctl[CTL_DMU_LAST] = atomicAdd(&g.ctl[dmu_slot(t)], 0);
+        g.ctl[dmu_slot(t + 1)] = 0;   // slot of the next iteration starts empty
         g.ctl[CTL_DONE] = 0;
-        g.ctl[CTL_ITER] = t1;
+        g.ctl[CTL_ITER] = t + 1;
+    }
+}
+
+// ------------------------------------------------------------------------
+// Persistent iteration kernel: one cooperative launch runs up to n_iters
+// iterations; the two phases are separated by a grid barrier.  The barrier's
+// wait is bounded: after ~1 s without progress the block records a timeout
+// (CTL_ERR = 2) and every block leaves the loop.
+
+constexpr long long BARRIER_SPIN_LIMIT = 10000000;   // x ~100 ns sleeps
+
+__device__ __forceinline__ bool grid_barrier(int32_t* ctl, int nblocks, int* flag_sh) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile int32_t* vgen = ctl + CTL_BAR_GEN;
+        volatile int32_t* verr = ctl + CTL_ERR;
+        const int gen = *vgen;
+        __threadfence();
+        const int arrived = atomicAdd(&ctl[CTL_BAR_COUNT], 1);
+        int ok = 1;
+        if (arrived == nblocks - 1) {
+            atomicExch(&ctl[CTL_BAR_COUNT], 0);
+            __threadfence();
+            atomicAdd(&ctl[CTL_BAR_GEN], 1);
+        } else {
+            long long spins = 0;
+            while (*vgen == gen) {
+                if (*verr == 2 || ++spins > BARRIER_SPIN_LIMIT) {
+                    atomicCAS(&ctl[CTL_ERR], 0, 2);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        *flag_sh = ok && (*verr != 2);
+    }
+    __syncthreads();
+    return *flag_sh;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(FACTOR_BLOCK) persistent_kernel(DevGraph<R> g, KParams<R> P, int n_iters,
+                                                                    float conv_tol, int check_every) {
+    __shared__ int flag_sh;
+    constexpr int WPB = FACTOR_BLOCK / 32;
+    const int lane = threadIdx.x & 31;
+    const int gwarp = blockIdx.x * WPB + (threadIdx.x >> 5);
+    const int nwarps = gridDim.x * WPB;
+    const int nb = gridDim.x;
+    const int t0 = __ldcg(&g.ctl[CTL_ITER]);
+    const int items = phase_b_items(g);
+    int done = 0;
+    float last = 0.0f;
+    for (int it = 0; it < n_iters; ++it) {
+        const int t = t0 + it;
+        const R s_next = prior_scale(P, t + 1);
+        // phase A: factors and landmarks wholly inside a tile
+        float dmu = 0.0f;
+        for (int tile = gwarp; tile < g.n_tiles; tile += nwarps)
+            dmu = fmaxf(dmu, tile_work<R>(g, P, tile, t, s_next, lane));
+        dmu = warp_max(dmu);
+        if (lane == 0 && dmu > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), dmu);
+        if (!grid_barrier(g.ctl, nb, &flag_sh)) break;
+        // phase B: keyframes, split landmarks, orphans
+        if (blockIdx.x == 0 && threadIdx.x == 0) g.ctl[dmu_slot(t + 1)] = 0;   // every block has read it
+        float d2 = 0.0f;
+        for (int w = gwarp; w < items; w += nwarps) d2 = fmaxf(d2, phase_b_item<R>(g, P, w, t, s_next, lane));
+        d2 = warp_max(d2);
+        if (lane == 0 && d2 > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), d2);
+        if (!grid_barrier(g.ctl, nb, &flag_sh)) break;
+        done = it + 1;
+        last = __int_as_float(__ldcg(&g.ctl[dmu_slot(t)]));
+        if (conv_tol > 0.0f && done % check_every == 0 && last < conv_tol) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        g.ctl[CTL_ITER] = t0 + done;
+        g.ctl[CTL_DMU_LAST] = __float_as_int(last);
+        g.ctl[CTL_ITERS_RUN] = done;
+    }
+}
+
+// Beliefs of iteration 0: b^0 = prior(0) (+ anchor), mean 0.
+template <typename R>
+__global__ void init_beliefs_kernel(DevGraph<R> g, KParams<R> P) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const R s = prior_scale(P, 0);
+    const R isig2 = P.inv_sigma2;
+    if (v < g.n_kf) {
+        R out[KBEL];
+#pragma unroll
+        for (int j = 0; j < KBEL; ++j) out[j] = R(0);
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            out[pk(i, i)] = (s * g.kf_D[v * 6 + i] + P.anchor_scale * g.kf_A[v * 6 + i]) * isig2;
+        store_rec<R, KBEL>(g.kf_bel + (size_t)v * KBEL, out);
+    } else if (v < g.n_kf + g.n_lm) {
+        const int m = v - g.n_kf;
+        R out[LBEL];
+#pragma unroll
+        for (int j = 0; j < LBEL; ++j) out[j] = R(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) out[pk(i, i)] = s * g.lm_D[m * 3 + i] * isig2;
+        store_rec<R, LBEL>(g.lm_bel + (size_t)m * LBEL, out);
     }
 }
 
@@ -616,14 +978,14 @@ __global__ void __launch_bounds__(BELIEF_BLOCK) belief_kernel(DevGraph<R> g, KPa
 // diag(J_v^T J_v) at the reference point with Huber weight 1 and sigma = 1.
 
 template <typename R>
-__global__ void __launch_bounds__(FACTOR_BLOCK) prior_factor_kernel(DevGraph<R> g, KParams P, R* tmp_k, R* tmp_l) {
+__global__ void __launch_bounds__(FACTOR_BLOCK) prior_factor_kernel(DevGraph<R> g, KParams<R> P, R* tmp_k, R* tmp_l) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= g.n_f) return;
     const int k = g.fk[f], m = g.fm[f];
-    KParams Q = P;
-    Q.huber_n = 0.0;
-    Q.inv_sigma2 = 1.0;
-    Q.inv_sigma = 1.0;
+    KParams<R> Q = P;
+    Q.huber_n = R(0);
+    Q.inv_sigma2 = R(1);
+    Q.inv_sigma = R(1);
     R x0[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) x0[i] = R(0);
@@ -685,7 +1047,7 @@ __global__ void prior_reduce_kernel(DevGraph<R> g, const R* tmp_k, const R* tmp_
 // order reduction through per-block partials.
 
 template <typename R>
-__global__ void __launch_bounds__(METRIC_BLOCK) metrics_kernel(DevGraph<R> g, KParams P, double* partials) {
+__global__ void __launch_bounds__(METRIC_BLOCK) metrics_kernel(DevGraph<R> g, KParams<R> P, double* partials) {
     __shared__ double red[4][METRIC_BLOCK];
     const int tid = threadIdx.x;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -694,8 +1056,8 @@ __global__ void __launch_bounds__(METRIC_BLOCK) metrics_kernel(DevGraph<R> g, KP
         const R* kb = g.kf_bel + (size_t)k * KBEL;
         const R* lb = g.lm_bel + (size_t)m * LBEL;
         R x[9] = {kb[27], kb[28], kb[29], kb[30], kb[31], kb[32], lb[9], lb[10], lb[11]};
-        KParams Q = P;
-        Q.huber_n = 0.0;
+        KParams<R> Q = P;
+        Q.huber_n = R(0);
         Lin<R> L;
         linearise<R>(Q, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3, g.lm_ref + (size_t)m * 3, x,
                      g.z[2 * (size_t)f], g.z[2 * (size_t)f + 1], L);
@@ -703,7 +1065,7 @@ __global__ void __launch_bounds__(METRIC_BLOCK) metrics_kernel(DevGraph<R> g, KP
             double e = sqrt(double(L.r2));
             v[0] += e;
             v[2] += 1.0;
-            if (P.huber_n > 0.0 && e * P.inv_sigma > P.huber_n) v[3] += 1.0;
+            if (P.huber_n > R(0) && e * double(P.inv_sigma) > double(P.huber_n)) v[3] += 1.0;
         }
     }
     for (int j = 0; j < 4; ++j) red[j][tid] = v[j];
@@ -720,7 +1082,7 @@ __global__ void __launch_bounds__(METRIC_BLOCK) metrics_kernel(DevGraph<R> g, KP
 // reference-projection distance needs the residual vector, not only |r|:
 // recompute h(mu) per factor
 template <typename R>
-__global__ void __launch_bounds__(METRIC_BLOCK) metrics_ref_kernel(DevGraph<R> g, KParams P, double* partials) {
+__global__ void __launch_bounds__(METRIC_BLOCK) metrics_ref_kernel(DevGraph<R> g, KParams<R> P, double* partials) {
     __shared__ double red[2][METRIC_BLOCK];
     const int tid = threadIdx.x;
     double acc = 0.0, cnt = 0.0;
@@ -729,8 +1091,8 @@ __global__ void __launch_bounds__(METRIC_BLOCK) metrics_ref_kernel(DevGraph<R> g
         const R* kb = g.kf_bel + (size_t)k * KBEL;
         const R* lb = g.lm_bel + (size_t)m * LBEL;
         R x[9] = {kb[27], kb[28], kb[29], kb[30], kb[31], kb[32], lb[9], lb[10], lb[11]};
-        KParams Q = P;
-        Q.huber_n = 0.0;
+        KParams<R> Q = P;
+        Q.huber_n = R(0);
         Lin<R> L;
         // with z = reference pixel the residual is ref - h(mu)
         R ru = g.uv_ref[2 * (size_t)f], rv = g.uv_ref[2 * (size_t)f + 1];
@@ -780,22 +1142,54 @@ int metrics_blocks(int n_f) {
 }
 
 template <typename R>
-cudaError_t launch_factor(const DevGraph<R>& g, const KParams& p, cudaStream_t s) {
-    if (g.n_f == 0) return cudaSuccess;
-    factor_kernel<R><<<(g.n_f + FACTOR_BLOCK - 1) / FACTOR_BLOCK, FACTOR_BLOCK, 0, s>>>(g, p);
+cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s) {
+    if (g.n_tiles == 0) return cudaSuccess;
+    constexpr int wpb = FACTOR_BLOCK / 32;
+    factor_kernel<R><<<(g.n_tiles + wpb - 1) / wpb, FACTOR_BLOCK, 0, s>>>(g, p);
     return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_belief(const DevGraph<R>& g, const KParams& p, cudaStream_t s) {
-    int blocks = g.n_kf + (g.n_lm + BELIEF_BLOCK - 1) / BELIEF_BLOCK;
+cudaError_t launch_belief(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s) {
+    constexpr int wpb = FACTOR_BLOCK / 32;
+    int blocks = (phase_b_items(g) + wpb - 1) / wpb;
     if (blocks < 1) blocks = 1;
-    belief_kernel<R><<<blocks, BELIEF_BLOCK, 0, s>>>(g, p);
+    belief_kernel<R><<<blocks, FACTOR_BLOCK, 0, s>>>(g, p);
     return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_prior(const DevGraph<R>& g, const KParams& p, R* tmp_k, R* tmp_l, R* kf_D, R* lm_D,
+int persistent_grid(const DevGraph<R>& g) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<R>, FACTOR_BLOCK, 0) != cudaSuccess)
+        return 0;
+    constexpr int wpb = FACTOR_BLOCK / 32;
+    const int cap = sms * per_sm;
+    const int want = (std::max(g.n_tiles, phase_b_items(g)) + wpb - 1) / wpb;
+    return std::max(1, std::min(cap, want));
+}
+
+template <typename R>
+cudaError_t launch_persistent(const DevGraph<R>& g, const KParams<R>& p, int n_iters, float conv_tol,
+                              int check_every, int grid, cudaStream_t s) {
+    DevGraph<R> gg = g;
+    KParams<R> pp = p;
+    void* args[] = {&gg, &pp, &n_iters, &conv_tol, &check_every};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(persistent_kernel<R>), dim3(grid), dim3(FACTOR_BLOCK),
+                                       args, 0, s);
+}
+
+template <typename R>
+cudaError_t launch_init(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s) {
+    int nv = g.n_kf + g.n_lm;
+    if (nv > 0) init_beliefs_kernel<R><<<(nv + 127) / 128, 128, 0, s>>>(g, p);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_prior(const DevGraph<R>& g, const KParams<R>& p, R* tmp_k, R* tmp_l, R* kf_D, R* lm_D,
                          cudaStream_t s) {
     if (g.n_f > 0) prior_factor_kernel<R><<<(g.n_f + FACTOR_BLOCK - 1) / FACTOR_BLOCK, FACTOR_BLOCK, 0, s>>>(g, p, tmp_k, tmp_l);
     int nv = g.n_kf + g.n_lm;
@@ -804,7 +1198,7 @@ cudaError_t launch_prior(const DevGraph<R>& g, const KParams& p, R* tmp_k, R* tm
 }
 
 template <typename R>
-cudaError_t launch_metrics(const DevGraph<R>& g, const KParams& p, double* partials, int nb, double* out,
+cudaError_t launch_metrics(const DevGraph<R>& g, const KParams<R>& p, double* partials, int nb, double* out,
                            cudaStream_t s) {
     metrics_kernel<R><<<nb, METRIC_BLOCK, 0, s>>>(g, p, partials);
     if (g.uv_ref) metrics_ref_kernel<R><<<nb, METRIC_BLOCK, 0, s>>>(g, p, partials);
@@ -812,11 +1206,14 @@ cudaError_t launch_metrics(const DevGraph<R>& g, const KParams& p, double* parti
     return cudaGetLastError();
 }
 
-#define GBP_INSTANTIATE(R)                                                                              \
-    template cudaError_t launch_factor<R>(const DevGraph<R>&, const KParams&, cudaStream_t);            \
-    template cudaError_t launch_belief<R>(const DevGraph<R>&, const KParams&, cudaStream_t);            \
-    template cudaError_t launch_prior<R>(const DevGraph<R>&, const KParams&, R*, R*, R*, R*, cudaStream_t); \
-    template cudaError_t launch_metrics<R>(const DevGraph<R>&, const KParams&, double*, int, double*, cudaStream_t);
+#define GBP_INSTANTIATE(R)                                                                                 \
+    template cudaError_t launch_factor<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t);            \
+    template cudaError_t launch_init<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t);              \
+    template cudaError_t launch_belief<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t);            \
+    template int persistent_grid<R>(const DevGraph<R>&);                                                   \
+    template cudaError_t launch_persistent<R>(const DevGraph<R>&, const KParams<R>&, int, float, int, int, cudaStream_t); \
+    template cudaError_t launch_prior<R>(const DevGraph<R>&, const KParams<R>&, R*, R*, R*, R*, cudaStream_t); \
+    template cudaError_t launch_metrics<R>(const DevGraph<R>&, const KParams<R>&, double*, int, double*, cudaStream_t);
 
 GBP_INSTANTIATE(float)
 GBP_INSTANTIATE(double)

@@ -40,7 +40,8 @@ class gbp_params(C.Structure):
                 ("prior_final_scale", C.c_float), ("prior_anneal_iters", C.c_int32),
                 ("anchor_scale", C.c_float), ("z_min", C.c_float), ("relin_beta", C.c_float),
                 ("relin_interval", C.c_int32), ("undamped_iters", C.c_int32),
-                ("fp64_pivot_ratio", C.c_float), ("precision_mode", C.c_int32), ("linear", C.c_int32)]
+                ("fp64_pivot_ratio", C.c_float), ("precision_mode", C.c_int32), ("linear", C.c_int32),
+                ("launch_mode", C.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -49,7 +50,8 @@ class gbp_params(C.Structure):
 class gbp_stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("max_dmu", C.c_float), ("are", C.c_double),
                 ("are_ref", C.c_double), ("n_are", C.c_int32), ("huber_count", C.c_int32),
-                ("fp64_fallbacks", C.c_int32), ("relinearisations", C.c_int32)]
+                ("fp64_fallbacks", C.c_int32), ("relinearisations", C.c_int32), ("launch_mode", C.c_int32),
+                ("kernel_launches", C.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -63,7 +65,7 @@ _lib = None
 EXPORTS = ["gbp_default_params", "gbp_create_graph", "gbp_set_params", "gbp_get_params", "gbp_iterate",
            "gbp_reset", "gbp_get_beliefs", "gbp_get_means", "gbp_set_reference", "gbp_add_keyframe",
            "gbp_get_stats", "gbp_get_sizes", "gbp_profile_iterations", "gbp_destroy_graph", "gbp_status_string",
-           "gbp_last_error", "gbp_reprojection_error_noalloc"]
+           "gbp_last_error", "gbp_reprojection_error_noalloc", "gbp_autotune"]
 GBP_NOALLOC_MAX_OBS = 1 << 20
 
 
@@ -92,6 +94,7 @@ def lib() -> C.CDLL:
     L.gbp_get_stats.argtypes = [vp, C.POINTER(gbp_stats)]
     L.gbp_get_sizes.argtypes = [vp, _I, _I, _I]
     L.gbp_profile_iterations.argtypes = [vp, C.c_int32, _D]
+    L.gbp_autotune.argtypes = [vp, C.c_int32, _I, _D]
     L.gbp_destroy_graph.argtypes = [vp]
     L.gbp_destroy_graph.restype = None
     L.gbp_status_string.argtypes = [C.c_int]
@@ -223,8 +226,16 @@ def gbp_get_stats(g: int) -> gbp_stats:
     return s
 
 
+def gbp_autotune(g: int, n_trial: int = 8):
+    """Time both launch modes; returns (chosen mode, ms/iteration of mode 1, of mode 2)."""
+    chosen = C.c_int32(0)
+    ms = np.zeros(2)
+    _check(lib().gbp_autotune(g, int(n_trial), C.byref(chosen), _dp(ms)), g)
+    return chosen.value, float(ms[0]), float(ms[1])
+
+
 def gbp_profile_iterations(g: int, n_iters: int):
-    """Mean device milliseconds per launch: (factor kernel, belief kernel)."""
+    """(mean device ms per iteration in the current launch mode, mean ms of one factor-kernel launch)."""
     out = np.zeros(2)
     _check(lib().gbp_profile_iterations(g, int(n_iters), _dp(out)), g)
     return float(out[0]), float(out[1])
@@ -288,6 +299,9 @@ class Graph:
 
     def profile(self, n: int):
         return gbp_profile_iterations(self.h, n)
+
+    def autotune(self, n_trial: int = 8):
+        return gbp_autotune(self.h, n_trial)
 
     def set_reference(self, kf_Rt, lm_xyz):
         gbp_set_reference(self.h, kf_Rt, lm_xyz)

@@ -23,7 +23,7 @@ import numpy as np
 from scipy.spatial.transform import Rotation
 
 __all__ = ["Problem", "make_circle", "make_walk", "make_loop", "make_batch",
-           "make_chain", "make_stream", "workload"]
+           "make_chain", "make_stream", "concat", "workload"]
 
 
 @dataclass
@@ -373,6 +373,24 @@ def make_stream(seed: int = 0, n_kf: int = 500, n_lm: int = 8000, start_kf: int 
         sel = np.nonzero(p.obs_kf == k)[0]
         steps.append(dict(kf=k, obs=sel, new_lm=np.nonzero(first_kf == k)[0]))
     return p, first_kf, steps
+
+
+def concat(problems: list[Problem], name: str | None = None) -> Problem:
+    """Several independent problems as one disconnected graph: keyframe,
+    landmark and observation arrays are stacked with index offsets (a batch
+    of problems for one launch).  All problems must share the camera."""
+    kf_off = np.cumsum([0] + [p.n_kf for p in problems])
+    lm_off = np.cumsum([0] + [p.n_lm for p in problems])
+    p0 = problems[0]
+    cat = lambda attr: np.concatenate([getattr(p, attr) for p in problems])
+    return Problem(name=name or f"batch{len(problems)}", seed=p0.seed, fx=p0.fx, fy=p0.fy, cx=p0.cx, cy=p0.cy,
+                   width=p0.width, height=p0.height, kf_Rt_true=cat("kf_Rt_true"), kf_Rt_init=cat("kf_Rt_init"),
+                   lm_true=cat("lm_true"), lm_init=cat("lm_init"),
+                   obs_kf=np.concatenate([p.obs_kf + kf_off[i] for i, p in enumerate(problems)]).astype(np.int32),
+                   obs_lm=np.concatenate([p.obs_lm + lm_off[i] for i, p in enumerate(problems)]).astype(np.int32),
+                   obs_uv=cat("obs_uv"), obs_outlier=cat("obs_outlier"),
+                   anchor_kf=np.concatenate([p.anchor_kf + kf_off[i] for i, p in enumerate(problems)]).astype(np.int32),
+                   params=dict(p0.params))
 
 
 def workload(name: str, seed: int = 0) -> Problem:

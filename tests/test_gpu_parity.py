@@ -208,3 +208,53 @@ def test_invalid_params_rejected():
             g.set_params(**bad)
         assert e.value.status == gbp.GBP_EINVAL
     g.close()
+
+
+def test_launch_modes_are_bitwise_identical():
+    """One persistent launch with grid barriers (mode 1) and one launch per
+    phase (mode 2) run the same device code in the same order."""
+    p = synth.make_walk(4, n_kf=40, n_lm=500)
+    res = []
+    for mode in (1, 2):
+        g = gbp.Graph(p, huber_nsigma=2.0, launch_mode=mode)
+        g.iterate(45)
+        res.append(g.means())
+        g.close()
+    for x, y in zip(*res):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_convergence_stops_at_the_same_iteration_in_both_modes():
+    p = synth.make_circle(2)
+    done = []
+    for mode in (1, 2):
+        g = gbp.Graph(p, conv_tol=2e-5, check_every=5, launch_mode=mode)
+        done.append(g.iterate(2000))
+        assert g.stats()["max_dmu"] < 2e-5
+        g.close()
+    assert done[0] == done[1] < 2000
+
+
+def test_autotune_restores_the_state():
+    p = synth.make_walk(5, n_kf=30, n_lm=300)
+    a = gbp.Graph(p, launch_mode=2)
+    b = gbp.Graph(p, launch_mode=2)
+    a.iterate(20)
+    b.iterate(20)
+    chosen, ms1, ms2 = a.autotune(6)
+    assert chosen in (1, 2) and max(ms1, ms2) > 0
+    a.iterate(15)
+    b.iterate(15)
+    for x, y in zip(a.means(), b.means()):
+        np.testing.assert_array_equal(x, y)
+    a.close()
+    b.close()
+
+
+def test_landmark_split_across_tiles():
+    """A point seen by more than 32 keyframes has its factors in several warp
+    tiles; its belief is then formed in the belief phase."""
+    p = synth.make_circle(0, n_kf=40, n_lm=30, radius=3.0, obs_range=(34, 40))
+    assert np.bincount(p.obs_lm).max() > 32
+    kf, lm, st, okf, olm, o = run_pair(p, 60, dict(precision_mode=2), {})
+    assert rel_err(kf, lm, okf, olm).max() < 1e-8
