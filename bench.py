@@ -236,21 +236,48 @@ def roofline(p, iter_ms, fac_ms, mode):
             "factor_kernel_ms": fac_ms, "peak_source": f"{peak_kind} HBM copy bandwidth"}
 
 
-def measure_at_scale(gbp, synth, stream, n_distinct=16, copies=8, iters=30):
-    """Throughput and HBM roofline on a batch of independent paper-scale
-    problems in one graph (state far larger than L2)."""
-    base = [synth.make_walk(seed=100 + i) for i in range(n_distinct)]
-    big = synth.concat(base * copies, name=f"batch{n_distinct * copies}")
-    g = gbp.Graph(big, stream=stream.cuda_stream, huber_nsigma=HUBER)
-    mode, ms1, ms2 = g.autotune(10)
+def _make_batch_problem(seed):
+    from paper_2003_03134_gb300 import synth
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n_kf = int(rng.integers(10, 201))
+    n_lm = int(rng.integers(100, 5001))
+    return synth.make_walk(seed=seed, n_kf=n_kf, n_lm=n_lm, name=f"batch{seed}")
+
+
+def batch_problems(n, first_seed=0):
+    """The batched workload: n independent walk problems, problem i seeded by
+    i with U{10..200} keyframes and U{100..5000} points (generated in a
+    spawn-context process pool)."""
+    import multiprocessing as mp
+    seeds = list(range(first_seed, first_seed + n))
+    try:
+        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+            return pool.map(_make_batch_problem, seeds)
+    except Exception:
+        return [_make_batch_problem(s) for s in seeds]
+
+
+def measure_at_scale(gbp, stream, n_problems=256, iters=20):
+    """Throughput and HBM roofline on the batched workload: n_problems
+    independent problems of uneven size in one graph (one persistent launch
+    per gbp_iterate), state far larger than L2."""
+    probs = batch_problems(n_problems)
+    g = gbp.Graph(probs, stream=stream.cuda_stream, huber_nsigma=HUBER)
+    n_kf, n_lm, n_f = gbp.gbp_get_sizes(g.h)
+    mode, ms1, ms2 = g.autotune(8)
     iter_ms, fac_ms = g.profile(iters)
     st = g.stats()
     g.close()
-    return {"workload": f"{n_distinct * copies} independent walk problems in one graph "
-                        f"({big.n_kf} keyframes, {big.n_lm} points, {big.n_obs} factors)",
-            "value": big.n_obs / (iter_ms * 1e-3), "unit": UNIT, "ms_per_iteration": iter_ms,
+
+    class _Size:
+        pass
+    sz = _Size()
+    sz.n_obs, sz.n_kf, sz.n_lm = n_f, n_kf, n_lm
+    return {"workload": f"{n_problems} independent walk problems of uneven size in one graph "
+                        f"({n_kf} keyframes, {n_lm} points, {n_f} factors)",
+            "value": n_f / (iter_ms * 1e-3), "unit": UNIT, "ms_per_iteration": iter_ms,
             "autotune_ms_per_iteration": {"persistent": ms1, "per_phase": ms2},
-            "roofline": roofline(big, iter_ms, fac_ms, mode), "fp64_fallbacks": st["fp64_fallbacks"]}
+            "roofline": roofline(sz, iter_ms, fac_ms, mode), "fp64_fallbacks": st["fp64_fallbacks"]}
 
 
 def run_gpu(args, rank, world, local):
@@ -308,7 +335,7 @@ def run_gpu(args, rank, world, local):
     g.reset()
     iter_ms, fac_ms = g.profile(64)
     roof = roofline(p, iter_ms, fac_ms, st_timed["launch_mode"])
-    at_scale = measure_at_scale(gbp, synth, stream) if (rank == 0 and not args.no_scale) else None
+    at_scale = measure_at_scale(gbp, stream) if (rank == 0 and not args.no_scale) else None
 
     line = None
     if rank == 0:

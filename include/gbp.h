@@ -116,6 +116,44 @@ gbp_status gbp_create_graph(const gbp_intrinsics* intr,
                             int32_t n_anchor, const int32_t* anchor_kf,
                             void* cuda_stream, gbp_graph** out);
 
+/* One problem of a batch (all host pointers, indices local to the problem). */
+typedef struct {
+    int32_t n_kf;
+    const double* kf_Rt;        /* n_kf x 12 */
+    int32_t n_lm;
+    const double* lm_xyz;       /* n_lm x 3  */
+    int32_t n_obs;
+    const int32_t* obs_kf;
+    const int32_t* obs_lm;
+    const double* obs_uv;       /* n_obs x 2 */
+    int32_t n_anchor;
+    const int32_t* anchor_kf;
+} gbp_problem_desc;
+
+/* Batching: n_problems independent problems (same intrinsics) as one
+ * disconnected graph, so that one launch iterates all of them.  Variables
+ * are numbered problem by problem (gbp_get_batch_info gives the offsets);
+ * every other call treats the batch as one graph.  No warp tile spans two
+ * problems, so each problem's results are bitwise identical to solving it
+ * alone with the same parameters and iteration count.  The convergence test
+ * (conv_tol) uses the largest mean change over all problems.  Errors as for
+ * gbp_create_graph. */
+gbp_status gbp_create_batch(const gbp_intrinsics* intr, int32_t n_problems, const gbp_problem_desc* problems,
+                            void* cuda_stream, gbp_graph** out);
+
+/* Problem table of a graph (a single graph is one problem): *n_problems;
+ * kf_offsets / lm_offsets (nullable, n_problems + 1 entries) the first
+ * keyframe / landmark of each problem and the totals; obs_counts (nullable,
+ * n_problems) the observations of each. */
+gbp_status gbp_get_batch_info(const gbp_graph* g, int32_t* n_problems, int32_t* kf_offsets, int32_t* lm_offsets,
+                              int32_t* obs_counts);
+
+/* Average reprojection error (Sec. 9.1) of each problem at the current
+ * means: are[n_problems]; n_are / huber (nullable) the measurements counted
+ * and those beyond the Huber threshold.  One fixed-order reduction per
+ * problem on the device.  Synchronises the stream. */
+gbp_status gbp_get_problem_are(const gbp_graph* g, double* are, int32_t* n_are, int32_t* huber);
+
 /* Replace the solver parameters (values are checked: GBP_EINVAL on a
  * non-positive sigma_px, damping outside [0,1), ...).  Takes effect at the
  * next gbp_iterate(). */

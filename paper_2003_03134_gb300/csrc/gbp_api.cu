@@ -103,6 +103,9 @@ struct gbp_graph {
     std::vector<int32_t> fk, fm, obs_index;     // obs_index[f] = caller's observation index
     std::vector<double> z;
     std::vector<uint8_t> anchored;
+    std::vector<int32_t> prob_kf0, prob_lm0;    // problem table (n_problems + 1 entries, last = totals)
+    std::vector<int32_t> prob_f0;               // first internal factor of each problem (+ total)
+    int32_t* d_prob_f0 = nullptr;               // device copy for the per-problem metrics
     std::vector<double> uv_ref;                 // reference projections (internal order) or empty
     // device
     int storage = 0;                            // 0: float, 1: double
@@ -229,8 +232,16 @@ gbp_status build_device(gbp_graph* g) {
         if (kf_off[v + 1] == kf_off[v]) orphan.push_back(v);
     {
         int cur = 0;
+        size_t next_prob = 1;   // a tile never spans two problems of a batch
         for (int m = 0; m < nl; ++m) {
             const int lo = lm_off[m], hi = lm_off[m + 1], d = hi - lo;
+            while (next_prob + 1 < g->prob_lm0.size() && g->prob_lm0[next_prob] <= m) {
+                if (g->prob_lm0[next_prob] == m && cur > 0) {
+                    tiles.push_back(lo);
+                    cur = 0;
+                }
+                ++next_prob;
+            }
             if (d == 0) {
                 orphan.push_back(nk + m);
                 continue;
@@ -675,10 +686,15 @@ const char* gbp_status_string(gbp_status s) {
 
 const char* gbp_last_error(const gbp_graph* g) { return g ? g->err.c_str() : "null graph"; }
 
-gbp_status gbp_create_graph(const gbp_intrinsics* intr, int32_t n_kf, const double* kf_Rt, int32_t n_lm,
-                            const double* lm_xyz, int32_t n_obs, const int32_t* obs_kf, const int32_t* obs_lm,
-                            const double* obs_uv, int32_t n_anchor, const int32_t* anchor_kf, void* cuda_stream,
-                            gbp_graph** out) {
+namespace {
+
+// Shared body of gbp_create_graph and gbp_create_batch.  prob_kf0 / prob_lm0
+// hold the first keyframe / landmark of every problem plus the totals.
+gbp_status create_impl(const gbp_intrinsics* intr, int32_t n_kf, const double* kf_Rt, int32_t n_lm,
+                       const double* lm_xyz, int32_t n_obs, const int32_t* obs_kf, const int32_t* obs_lm,
+                       const double* obs_uv, int32_t n_anchor, const int32_t* anchor_kf,
+                       const std::vector<int32_t>& prob_kf0, const std::vector<int32_t>& prob_lm0, void* cuda_stream,
+                       gbp_graph** out) {
     if (!out) return GBP_EINVAL;
     *out = nullptr;
     if (!intr || n_kf < 0 || n_lm < 0 || n_obs < 0 || n_anchor < 0) return GBP_EINVAL;
@@ -703,6 +719,8 @@ gbp_status gbp_create_graph(const gbp_intrinsics* intr, int32_t n_kf, const doub
     g->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     g->n_kf = n_kf;
     g->n_lm = n_lm;
+    g->prob_kf0 = prob_kf0;
+    g->prob_lm0 = prob_lm0;
     g->kf_R.resize(9 * (size_t)n_kf);
     g->kf_c.resize(3 * (size_t)n_kf);
     for (int v = 0; v < n_kf; ++v) {
@@ -732,6 +750,12 @@ gbp_status gbp_create_graph(const gbp_intrinsics* intr, int32_t n_kf, const doub
         std::vector<double> uv(obs_uv, obs_uv + 2 * (size_t)n_obs);
         std::iota(idx.begin(), idx.end(), 0);
         order_factors(g, ok, ol, uv, idx);
+        // factors are sorted by landmark, and each problem's landmarks are
+        // contiguous: a problem's factors are one contiguous range
+        const int np = (int)g->prob_lm0.size() - 1;
+        g->prob_f0.assign(np + 1, 0);
+        for (int p = 0; p <= np; ++p)
+            g->prob_f0[p] = (int32_t)(std::lower_bound(g->fm.begin(), g->fm.end(), g->prob_lm0[p]) - g->fm.begin());
     }
     cudaError_t e = cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&g->ctl), sizeof(int32_t) * CTL_N);
@@ -740,6 +764,9 @@ gbp_status gbp_create_graph(const gbp_intrinsics* intr, int32_t n_kf, const doub
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&g->met), sizeof(double) * MET_N);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&g->h_ctl), sizeof(int32_t) * CTL_N);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&g->h_met), sizeof(double) * MET_N);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&g->d_prob_f0), sizeof(int32_t) * g->prob_f0.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->d_prob_f0, g->prob_f0.data(), sizeof(int32_t) * g->prob_f0.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         gbp_destroy_graph(g);
         return e == cudaErrorMemoryAllocation ? GBP_ENOMEM : GBP_ECUDA;
@@ -751,6 +778,97 @@ gbp_status gbp_create_graph(const gbp_intrinsics* intr, int32_t n_kf, const doub
     }
     *out = g;
     return GBP_OK;
+}
+
+}  // namespace
+
+gbp_status gbp_create_graph(const gbp_intrinsics* intr, int32_t n_kf, const double* kf_Rt, int32_t n_lm,
+                            const double* lm_xyz, int32_t n_obs, const int32_t* obs_kf, const int32_t* obs_lm,
+                            const double* obs_uv, int32_t n_anchor, const int32_t* anchor_kf, void* cuda_stream,
+                            gbp_graph** out) {
+    if (n_kf < 0 || n_lm < 0) return GBP_EINVAL;
+    return create_impl(intr, n_kf, kf_Rt, n_lm, lm_xyz, n_obs, obs_kf, obs_lm, obs_uv, n_anchor, anchor_kf,
+                       {0, n_kf}, {0, n_lm}, cuda_stream, out);
+}
+
+gbp_status gbp_create_batch(const gbp_intrinsics* intr, int32_t n_problems, const gbp_problem_desc* probs,
+                            void* cuda_stream, gbp_graph** out) {
+    if (!out) return GBP_EINVAL;
+    *out = nullptr;
+    if (!intr || n_problems < 0 || (n_problems && !probs)) return GBP_EINVAL;
+    std::vector<int32_t> kf0(1, 0), lm0(1, 0);
+    int64_t nk = 0, nl = 0, no = 0, na = 0;
+    for (int p = 0; p < n_problems; ++p) {
+        const gbp_problem_desc& d = probs[p];
+        if (d.n_kf < 0 || d.n_lm < 0 || d.n_obs < 0 || d.n_anchor < 0) return GBP_EINVAL;
+        if ((d.n_kf && !d.kf_Rt) || (d.n_lm && !d.lm_xyz) || (d.n_obs && (!d.obs_kf || !d.obs_lm || !d.obs_uv)) ||
+            (d.n_anchor && !d.anchor_kf))
+            return GBP_EINVAL;
+        for (int i = 0; i < d.n_obs; ++i)
+            if (d.obs_kf[i] < 0 || d.obs_kf[i] >= d.n_kf || d.obs_lm[i] < 0 || d.obs_lm[i] >= d.n_lm) return GBP_EINVAL;
+        for (int i = 0; i < d.n_anchor; ++i)
+            if (d.anchor_kf[i] < 0 || d.anchor_kf[i] >= d.n_kf) return GBP_EINVAL;
+        nk += d.n_kf;
+        nl += d.n_lm;
+        no += d.n_obs;
+        na += d.n_anchor;
+        if (nk > INT32_MAX || nl > INT32_MAX || no > INT32_MAX) return GBP_EINVAL;
+        kf0.push_back((int32_t)nk);
+        lm0.push_back((int32_t)nl);
+    }
+    std::vector<double> kf(12 * (size_t)nk), lm(3 * (size_t)nl), uv(2 * (size_t)no);
+    std::vector<int32_t> ok(no), ol(no), an(na);
+    size_t o = 0, a = 0;
+    for (int p = 0; p < n_problems; ++p) {
+        const gbp_problem_desc& d = probs[p];
+        std::copy(d.kf_Rt, d.kf_Rt + 12 * (size_t)d.n_kf, kf.begin() + 12 * (size_t)kf0[p]);
+        std::copy(d.lm_xyz, d.lm_xyz + 3 * (size_t)d.n_lm, lm.begin() + 3 * (size_t)lm0[p]);
+        for (int i = 0; i < d.n_obs; ++i, ++o) {
+            ok[o] = d.obs_kf[i] + kf0[p];
+            ol[o] = d.obs_lm[i] + lm0[p];
+            uv[2 * o] = d.obs_uv[2 * i];
+            uv[2 * o + 1] = d.obs_uv[2 * i + 1];
+        }
+        for (int i = 0; i < d.n_anchor; ++i, ++a) an[a] = d.anchor_kf[i] + kf0[p];
+    }
+    return create_impl(intr, (int32_t)nk, kf.data(), (int32_t)nl, lm.data(), (int32_t)no, ok.data(), ol.data(),
+                       uv.data(), (int32_t)na, an.data(), kf0, lm0, cuda_stream, out);
+}
+
+gbp_status gbp_get_batch_info(const gbp_graph* g, int32_t* n_problems, int32_t* kf_offsets, int32_t* lm_offsets,
+                              int32_t* obs_counts) {
+    if (!g) return GBP_EINVAL;
+    const int np = (int)g->prob_kf0.size() - 1;
+    if (n_problems) *n_problems = np;
+    for (int p = 0; p <= np; ++p) {
+        if (kf_offsets) kf_offsets[p] = g->prob_kf0[p];
+        if (lm_offsets) lm_offsets[p] = g->prob_lm0[p];
+        if (obs_counts && p < np) obs_counts[p] = g->prob_f0[p + 1] - g->prob_f0[p];
+    }
+    return GBP_OK;
+}
+
+gbp_status gbp_get_problem_are(const gbp_graph* cg, double* are, int32_t* n_are, int32_t* huber) {
+    gbp_graph* g = const_cast<gbp_graph*>(cg);
+    if (!g || !are) return GBP_EINVAL;
+    const int np = (int)g->prob_kf0.size() - 1;
+    if (np == 0) return GBP_OK;
+    double* d_out = nullptr;
+    CK(cudaMalloc(reinterpret_cast<void**>(&d_out), sizeof(double) * 3 * np));
+    cudaError_t e = g->storage
+        ? launch_problem_metrics<double>(g->sd.g, make_kparams<double>(g), g->d_prob_f0, np, d_out, g->stream)
+        : launch_problem_metrics<float>(g->sf.g, make_kparams<float>(g), g->d_prob_f0, np, d_out, g->stream);
+    std::vector<double> h(3 * (size_t)np);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    cudaFree(d_out);
+    if (e != cudaSuccess) return cuda_fail(g, e, "problem metrics");
+    for (int p = 0; p < np; ++p) {
+        are[p] = h[3 * p + 1] > 0 ? h[3 * p] / h[3 * p + 1] : 0.0;
+        if (n_are) n_are[p] = (int32_t)h[3 * p + 1];
+        if (huber) huber[p] = (int32_t)h[3 * p + 2];
+    }
+    return read_ctl(g);
 }
 
 gbp_status gbp_set_params(gbp_graph* g, const gbp_params* p) {
@@ -1062,6 +1180,7 @@ void gbp_destroy_graph(gbp_graph* g) {
     if (g->ctl) cudaFree(g->ctl);
     if (g->partials) cudaFree(g->partials);
     if (g->met) cudaFree(g->met);
+    if (g->d_prob_f0) cudaFree(g->d_prob_f0);
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
     if (g->h_met) cudaFreeHost(g->h_met);
     if (g->capture) cudaStreamDestroy(g->capture);

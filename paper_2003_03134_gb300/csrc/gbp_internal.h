@@ -124,6 +124,9 @@ template <typename R> cudaError_t launch_prior(const DevGraph<R>& g, const KPara
                                                R* kf_D, R* lm_D, cudaStream_t s);
 template <typename R> cudaError_t launch_metrics(const DevGraph<R>& g, const KParams<R>& p, double* partials,
                                                  int n_partials, double* out, cudaStream_t s);
+template <typename R> cudaError_t launch_problem_metrics(const DevGraph<R>& g, const KParams<R>& p,
+                                                         const int32_t* prob_f0, int n_problems, double* out,
+                                                         cudaStream_t s);
 int metrics_blocks(int n_f);
 
 }  // namespace gbp

@@ -582,21 +582,58 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
 #pragma unroll
     for (int i = 0; i < 9; ++i) sum[i] = R(0);
 
+    // previous landmark messages m^t of the tile's lanes
+    R ml[9];
     if (active) {
-        const int k = g.fk[f];
-        const size_t ks = (size_t)g.kpos[f] * KREC;   // this factor's keyframe-message slot
         m = g.fm[f];
         lo = g.lm_off[m];
         hi = g.lm_off[m + 1];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) ml[i] = g.ml[(size_t)i * n_f + f];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) ml[i] = R(0);
+    }
+    // For a landmark wholly inside the tile the incoming message (belief
+    // divided by this factor's previous message) is formed as prior(t) plus
+    // the sum of the OTHER factors' previous messages -- exclusive prefix
+    // and suffix sums over the landmark's lanes -- which equals b^t - m^t
+    // without the cancellation of subtracting one message from the belief.
+    const bool whole = active && lo >= ts && hi <= te;
+    const int seg0 = whole ? lo - ts : lane;
+    const int seg1 = whole ? hi - ts - 1 : lane;
+    R cav[9];
+    {
+        R fw[9], bw[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) { fw[j] = ml[j]; bw[j] = ml[j]; }
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                R o = __shfl_up_sync(0xffffffffu, fw[j], d);
+                if (lane - d >= seg0) fw[j] += o;
+                R u = __shfl_down_sync(0xffffffffu, bw[j], d);
+                if (lane + d <= seg1) bw[j] += u;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            R pre = __shfl_up_sync(0xffffffffu, fw[j], 1);
+            R suf = __shfl_down_sync(0xffffffffu, bw[j], 1);
+            cav[j] = (lane - 1 >= seg0 ? pre : R(0)) + (lane + 1 <= seg1 ? suf : R(0));
+        }
+    }
+
+    if (active) {
+        const int k = g.fk[f];
+        const size_t ks = (size_t)g.kpos[f] * KREC;   // this factor's keyframe-message slot
         const R* kbp = g.kf_bel + (size_t)k * KBEL;
         R lb[LBEL];
         load_rec_cg<R, LBEL>(g.lm_bel + (size_t)m * LBEL, lb);
         mu_m_old[0] = lb[9];
         mu_m_old[1] = lb[10];
         mu_m_old[2] = lb[11];
-        R ml[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) ml[i] = g.ml[(size_t)i * n_f + f];
         R x0[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) x0[i] = g.x0[(size_t)i * n_f + f];
@@ -637,10 +674,21 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
         // incoming = landmark belief / this factor's previous message to it
         {
             R Pm[6], qm[3];
+            if (whole) {
+                const R sp = prior_scale(P, t) * P.inv_sigma2;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) Pm[i] = lb[i] - ml[i];
+                for (int i = 0; i < 6; ++i) Pm[i] = cav[i];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) qm[i] = lb[6 + i] - ml[6 + i];
+                for (int i = 0; i < 3; ++i) {
+                    Pm[pk(i, i)] += sp * g.lm_D[m * 3 + i];
+                    qm[i] = cav[6 + i];
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 6; ++i) Pm[i] = lb[i] - ml[i];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) qm[i] = lb[6 + i] - ml[6 + i];
+            }
             R lam_k[21], eta_k[6], ratio_m;
             bool ok_m = message<R, 6, 3>(Pm, qm, L.Jl, L.Jk, L.y, L.W, lam_k, eta_k, ratio_m);
             if (sizeof(R) == 4 && P.fallback && !ok_m) {
@@ -725,8 +773,6 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
 
     // landmarks wholly inside the tile: segmented inclusive scan over the
     // lanes holding the same landmark (landmark ranges are contiguous)
-    const bool whole = active && lo >= ts && hi <= te;
-    const int seg0 = whole ? lo - ts : lane;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
 #pragma unroll
@@ -1118,6 +1164,43 @@ __global__ void __launch_bounds__(METRIC_BLOCK) metrics_ref_kernel(DevGraph<R> g
     }
 }
 
+// Per-problem reprojection statistics of a batch: one block per problem
+// over its contiguous factor range, fixed-order block reduction.
+// out[3p] = sum of errors, out[3p+1] = count, out[3p+2] = Huber-regime count.
+template <typename R>
+__global__ void __launch_bounds__(METRIC_BLOCK) problem_metrics_kernel(DevGraph<R> g, KParams<R> P,
+                                                                       const int32_t* prob_f0, double* out) {
+    __shared__ double red[3][METRIC_BLOCK];
+    const int tid = threadIdx.x, p = blockIdx.x;
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int f = prob_f0[p] + tid; f < prob_f0[p + 1]; f += METRIC_BLOCK) {
+        const int k = g.fk[f], m = g.fm[f];
+        const R* kb = g.kf_bel + (size_t)k * KBEL;
+        const R* lb = g.lm_bel + (size_t)m * LBEL;
+        R x[9] = {kb[27], kb[28], kb[29], kb[30], kb[31], kb[32], lb[9], lb[10], lb[11]};
+        KParams<R> Q = P;
+        Q.huber_n = R(0);
+        Lin<R> L;
+        linearise<R>(Q, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3, g.lm_ref + (size_t)m * 3, x,
+                     g.z[2 * (size_t)f], g.z[2 * (size_t)f + 1], L);
+        if (L.W > R(0)) {
+            double e = sqrt(double(L.r2));
+            v[0] += e;
+            v[1] += 1.0;
+            if (P.huber_n > R(0) && e * double(P.inv_sigma) > double(P.huber_n)) v[2] += 1.0;
+        }
+    }
+    for (int j = 0; j < 3; ++j) red[j][tid] = v[j];
+    __syncthreads();
+    for (int st = METRIC_BLOCK / 2; st > 0; st >>= 1) {
+        if (tid < st)
+            for (int j = 0; j < 3; ++j) red[j][tid] += red[j][tid + st];
+        __syncthreads();
+    }
+    if (tid == 0)
+        for (int j = 0; j < 3; ++j) out[3 * (size_t)p + j] = red[j][0];
+}
+
 __global__ void metrics_finish_kernel(const double* partials, int nb, int with_ref, double* out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double s[6] = {0, 0, 0, 0, 0, 0};
@@ -1206,10 +1289,18 @@ cudaError_t launch_metrics(const DevGraph<R>& g, const KParams<R>& p, double* pa
     return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t launch_problem_metrics(const DevGraph<R>& g, const KParams<R>& p, const int32_t* prob_f0, int n_problems,
+                                   double* out, cudaStream_t s) {
+    if (n_problems > 0) problem_metrics_kernel<R><<<n_problems, METRIC_BLOCK, 0, s>>>(g, p, prob_f0, out);
+    return cudaGetLastError();
+}
+
 #define GBP_INSTANTIATE(R)                                                                                 \
     template cudaError_t launch_factor<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t);            \
     template cudaError_t launch_init<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t);              \
     template cudaError_t launch_belief<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t);            \
+    template cudaError_t launch_problem_metrics<R>(const DevGraph<R>&, const KParams<R>&, const int32_t*, int, double*, cudaStream_t); \
     template int persistent_grid<R>(const DevGraph<R>&);                                                   \
     template cudaError_t launch_persistent<R>(const DevGraph<R>&, const KParams<R>&, int, float, int, int, cudaStream_t); \
     template cudaError_t launch_prior<R>(const DevGraph<R>&, const KParams<R>&, R*, R*, R*, R*, cudaStream_t); \

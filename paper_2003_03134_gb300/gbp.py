@@ -47,6 +47,13 @@ class gbp_params(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class gbp_problem_desc(C.Structure):
+    _fields_ = [("n_kf", C.c_int32), ("kf_Rt", C.POINTER(C.c_double)), ("n_lm", C.c_int32),
+                ("lm_xyz", C.POINTER(C.c_double)), ("n_obs", C.c_int32), ("obs_kf", C.POINTER(C.c_int32)),
+                ("obs_lm", C.POINTER(C.c_int32)), ("obs_uv", C.POINTER(C.c_double)), ("n_anchor", C.c_int32),
+                ("anchor_kf", C.POINTER(C.c_int32))]
+
+
 class gbp_stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("max_dmu", C.c_float), ("are", C.c_double),
                 ("are_ref", C.c_double), ("n_are", C.c_int32), ("huber_count", C.c_int32),
@@ -65,7 +72,8 @@ _lib = None
 EXPORTS = ["gbp_default_params", "gbp_create_graph", "gbp_set_params", "gbp_get_params", "gbp_iterate",
            "gbp_reset", "gbp_get_beliefs", "gbp_get_means", "gbp_set_reference", "gbp_add_keyframe",
            "gbp_get_stats", "gbp_get_sizes", "gbp_profile_iterations", "gbp_destroy_graph", "gbp_status_string",
-           "gbp_last_error", "gbp_reprojection_error_noalloc", "gbp_autotune"]
+           "gbp_last_error", "gbp_reprojection_error_noalloc", "gbp_autotune", "gbp_create_batch",
+           "gbp_get_batch_info", "gbp_get_problem_are"]
 GBP_NOALLOC_MAX_OBS = 1 << 20
 
 
@@ -95,6 +103,10 @@ def lib() -> C.CDLL:
     L.gbp_get_sizes.argtypes = [vp, _I, _I, _I]
     L.gbp_profile_iterations.argtypes = [vp, C.c_int32, _D]
     L.gbp_autotune.argtypes = [vp, C.c_int32, _I, _D]
+    L.gbp_create_batch.argtypes = [C.POINTER(gbp_intrinsics), C.c_int32, C.POINTER(gbp_problem_desc), vp,
+                                   C.POINTER(vp)]
+    L.gbp_get_batch_info.argtypes = [vp, _I, _I, _I, _I]
+    L.gbp_get_problem_are.argtypes = [vp, _D, _I, _I]
     L.gbp_destroy_graph.argtypes = [vp]
     L.gbp_destroy_graph.restype = None
     L.gbp_status_string.argtypes = [C.c_int]
@@ -156,6 +168,45 @@ def gbp_create_graph(intrinsics, kf_Rt, lm_xyz, obs_kf, obs_lm, obs_uv, anchor_k
                                 _ip(ol), _dp(uv), an.size, _ip(an), C.c_void_p(stream or 0), C.byref(out))
     _check(st)
     return out.value
+
+
+def gbp_create_batch(intrinsics, problems, stream=None) -> int:
+    """problems: sequence of objects with kf_Rt_init, lm_init, obs_kf, obs_lm,
+    obs_uv, anchor_kf (e.g. synth.Problem)."""
+    fx, fy, cx, cy, w, h = intrinsics
+    intr = gbp_intrinsics(fx, fy, cx, cy, int(w), int(h))
+    keep = []
+    descs = (gbp_problem_desc * len(problems))()
+    for i, p in enumerate(problems):
+        kf, lm = _f64(p.kf_Rt_init, 12), _f64(p.lm_init, 3)
+        ok, ol, uv, an = _i32(p.obs_kf), _i32(p.obs_lm), _f64(p.obs_uv, 2), _i32(p.anchor_kf)
+        keep += [kf, lm, ok, ol, uv, an]
+        descs[i] = gbp_problem_desc(kf.shape[0], _dp(kf), lm.shape[0], _dp(lm), ok.size, _ip(ok), _ip(ol), _dp(uv),
+                                    an.size, _ip(an))
+    out = C.c_void_p()
+    st = lib().gbp_create_batch(C.byref(intr), len(problems), descs, C.c_void_p(stream or 0), C.byref(out))
+    _check(st)
+    return out.value
+
+
+def gbp_get_batch_info(g: int):
+    n = C.c_int32()
+    _check(lib().gbp_get_batch_info(g, C.byref(n), None, None, None), g)
+    kf = np.zeros(n.value + 1, np.int32)
+    lm = np.zeros(n.value + 1, np.int32)
+    obs = np.zeros(max(n.value, 1), np.int32)
+    _check(lib().gbp_get_batch_info(g, C.byref(n), _ip(kf), _ip(lm), _ip(obs)), g)
+    return kf, lm, obs[:n.value]
+
+
+def gbp_get_problem_are(g: int):
+    kf, _, _ = gbp_get_batch_info(g)
+    n = kf.size - 1
+    are = np.zeros(max(n, 1))
+    cnt = np.zeros(max(n, 1), np.int32)
+    hub = np.zeros(max(n, 1), np.int32)
+    _check(lib().gbp_get_problem_are(g, _dp(are), _ip(cnt), _ip(hub)), g)
+    return are[:n], cnt[:n], hub[:n]
 
 
 def gbp_set_params(g: int, params: gbp_params) -> None:
@@ -261,14 +312,24 @@ def gbp_destroy_graph(g: int) -> None:
 # ---------------------------------------------------------------------------
 
 class Graph:
-    """Owning wrapper around one gbp_graph handle."""
+    """Owning wrapper around one gbp_graph handle.  ``problem`` is one
+    problem or a list of problems (a batch, see gbp_create_batch)."""
 
     def __init__(self, problem, stream=None, **params):
         self.problem = problem
-        self.h = gbp_create_graph(problem.intrinsics(), problem.kf_Rt_init, problem.lm_init, problem.obs_kf,
-                                  problem.obs_lm, problem.obs_uv, problem.anchor_kf, stream)
+        if isinstance(problem, (list, tuple)):
+            self.h = gbp_create_batch(problem[0].intrinsics(), problem, stream)
+        else:
+            self.h = gbp_create_graph(problem.intrinsics(), problem.kf_Rt_init, problem.lm_init, problem.obs_kf,
+                                      problem.obs_lm, problem.obs_uv, problem.anchor_kf, stream)
         if params:
             self.set_params(**params)
+
+    def batch_info(self):
+        return gbp_get_batch_info(self.h)
+
+    def problem_are(self):
+        return gbp_get_problem_are(self.h)
 
     def set_params(self, **kw):
         p = gbp_get_params(self.h)

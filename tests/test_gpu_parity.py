@@ -258,3 +258,48 @@ def test_landmark_split_across_tiles():
     assert np.bincount(p.obs_lm).max() > 32
     kf, lm, st, okf, olm, o = run_pair(p, 60, dict(precision_mode=2), {})
     assert rel_err(kf, lm, okf, olm).max() < 1e-8
+
+
+def _batch_problems():
+    return [synth.make_walk(11, n_kf=25, n_lm=200), synth.make_circle(3, n_kf=8, n_lm=60),
+            synth.make_walk(12, n_kf=40, n_lm=450)]
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_batch_results_equal_single_problem_runs_bitwise(mode):
+    """Problems solved together in one graph (one launch per iteration or one
+    launch in all) give exactly the bits of solving each alone."""
+    probs = _batch_problems()
+    b = gbp.Graph(probs, huber_nsigma=2.0, launch_mode=mode)
+    b.iterate(40)
+    kf_b, lm_b = b.means()
+    kf_off, lm_off, obs = b.batch_info()
+    assert list(obs) == [p.n_obs for p in probs]
+    for i, p in enumerate(probs):
+        s = gbp.Graph(p, huber_nsigma=2.0, launch_mode=mode)
+        s.iterate(40)
+        kf_s, lm_s = s.means()
+        np.testing.assert_array_equal(kf_b[kf_off[i]:kf_off[i + 1]], kf_s)
+        np.testing.assert_array_equal(lm_b[lm_off[i]:lm_off[i + 1]], lm_s)
+        s.close()
+    b.close()
+
+
+def test_batch_per_problem_are_and_oracle_parity():
+    probs = _batch_problems()
+    b = gbp.Graph(probs, huber_nsigma=2.0, **DET)
+    b.iterate(60)
+    kf, lm = b.beliefs()
+    are, cnt, hub = b.problem_are()
+    kf_off, lm_off, _ = b.batch_info()
+    for i, p in enumerate(probs):
+        o = oracle.Oracle(p, huber_nsigma=2.0, **DET)
+        o.iterate(60)
+        okf, olm = o.world()
+        e = rel_err(kf[kf_off[i]:kf_off[i + 1]], lm[lm_off[i]:lm_off[i + 1]], okf, olm)
+        assert e.max() <= TOL32
+        oa, on = o.are()
+        assert cnt[i] == on
+        assert abs(are[i] - oa) <= 1e-3
+        assert hub[i] == o.huber_count()
+    b.close()
