@@ -69,6 +69,8 @@ def lib():
         L.orc_are_vs.argtypes = [C.c_void_p, _D, _D, _I]
         L.orc_huber_count.argtypes = [C.c_void_p]
         L.orc_relinearisations.argtypes = [C.c_void_p]
+        L.orc_add_keyframe.argtypes = [C.c_void_p, _D, C.c_int, _D, C.c_int, _I, _D]
+        L.orc_sizes.argtypes = [C.c_void_p, _I, _I, _I]
         L.orc_relinearisations.restype = C.c_long
         L.orc_so3_exp.argtypes = [_D, _D]
         L.orc_so3_left_jacobian.argtypes = [_D, _D]
@@ -223,28 +225,32 @@ class Oracle:
         return lib().orc_iterations_done(self._h)
 
     def means(self):
-        kf, lm = np.zeros((self.p.n_kf, 6)), np.zeros((self.p.n_lm, 3))
+        nk, nl, _ = self.sizes()
+        kf, lm = np.zeros((nk, 6)), np.zeros((nl, 3))
         lib().orc_get_means(self._h, _dp(kf), _dp(lm))
         return kf, lm
 
     def world(self):
-        kf, lm = np.zeros((self.p.n_kf, 12)), np.zeros((self.p.n_lm, 3))
+        nk, nl, _ = self.sizes()
+        kf, lm = np.zeros((nk, 12)), np.zeros((nl, 3))
         lib().orc_get_world(self._h, _dp(kf), _dp(lm))
         return kf, lm
 
     def beliefs(self):
-        kl, ke = np.zeros((self.p.n_kf, 6, 6)), np.zeros((self.p.n_kf, 6))
-        ll, le = np.zeros((self.p.n_lm, 3, 3)), np.zeros((self.p.n_lm, 3))
+        nk, nl, _ = self.sizes()
+        kl, ke = np.zeros((nk, 6, 6)), np.zeros((nk, 6))
+        ll, le = np.zeros((nl, 3, 3)), np.zeros((nl, 3))
         lib().orc_get_beliefs(self._h, _dp(kl), _dp(ke), _dp(ll), _dp(le))
         return kl, ke, ll, le
 
     def prior_diag(self):
-        kd, ld = np.zeros((self.p.n_kf, 6)), np.zeros((self.p.n_lm, 3))
+        nk, nl, _ = self.sizes()
+        kd, ld = np.zeros((nk, 6)), np.zeros((nl, 3))
         lib().orc_get_prior_diag(self._h, _dp(kd), _dp(ld))
         return kd, ld
 
     def messages(self):
-        n = self.p.n_obs
+        n = self.sizes()[2]
         a, b, c, d = np.zeros((n, 6, 6)), np.zeros((n, 6)), np.zeros((n, 3, 3)), np.zeros((n, 3))
         lib().orc_get_messages(self._h, _dp(a), _dp(b), _dp(c), _dp(d))
         return a, b, c, d
@@ -266,6 +272,25 @@ class Oracle:
 
     def huber_count(self) -> int:
         return lib().orc_huber_count(self._h)
+
+    def add_keyframe(self, obs_lm, obs_uv, kf_Rt_init=None, n_new_lm=0, new_lm_xyz=None) -> int:
+        ol = np.ascontiguousarray(obs_lm, dtype=np.int32)
+        uv = _f64(obs_uv)
+        kf = None if kf_Rt_init is None else _f64(kf_Rt_init)
+        nl = None if new_lm_xyz is None else _f64(new_lm_xyz)
+        r = lib().orc_add_keyframe(self._h, None if kf is None else _dp(kf), int(n_new_lm),
+                                   None if nl is None else _dp(nl), ol.size, _ip(ol), _dp(uv))
+        if r < 0:
+            raise ValueError("oracle rejected the keyframe")
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        lib().orc_sizes(self._h, C.byref(a), C.byref(b), C.byref(c))
+        self.n_kf, self.n_lm, self.n_obs = a.value, b.value, c.value
+        return r
+
+    def sizes(self):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        lib().orc_sizes(self._h, C.byref(a), C.byref(b), C.byref(c))
+        return a.value, b.value, c.value
 
     def relinearisations(self) -> int:
         return lib().orc_relinearisations(self._h)

@@ -281,6 +281,7 @@ struct orc_graph {
     int *fk, *fm;
     double *z;
     unsigned char *anchored;
+    int *kf_birth, *lm_birth;            /* iteration at which each variable was added */
     double *Dk, *Dl;                     /* prior diagonals                      */
     double *kf_lam, *kf_eta, *lm_lam, *lm_eta;   /* beliefs b^t              */
     double *kf_mu, *lm_mu;                       /* means of b^t             */
@@ -298,8 +299,8 @@ static void* zalloc(size_t n) { return calloc(n ? n : 1, 1); }
  * (Sec. 5, belief equations); then its mean by a Cholesky solve. */
 static int update_beliefs(orc_graph* g, double* max_dmu)
 {
-    double s = orc_prior_scale(&g->prm, g->t);
     for (int v = 0; v < g->n_kf; ++v) {
+        double s = orc_prior_scale(&g->prm, g->t - g->kf_birth[v]);
         double* L = g->kf_lam + 36 * v;
         double* e = g->kf_eta + 6 * v;
         memset(L, 0, sizeof(double) * 36);
@@ -310,6 +311,7 @@ static int update_beliefs(orc_graph* g, double* max_dmu)
         }
     }
     for (int v = 0; v < g->n_lm; ++v) {
+        double s = orc_prior_scale(&g->prm, g->t - g->lm_birth[v]);
         double* L = g->lm_lam + 9 * v;
         memset(L, 0, sizeof(double) * 9);
         memset(g->lm_eta + 3 * v, 0, sizeof(double) * 3);
@@ -369,6 +371,8 @@ orc_graph* orc_create(const orc_cam* cam, const orc_params* prm,
     g->fm = zalloc(sizeof(int) * F);
     g->z = zalloc(sizeof(double) * 2 * F);
     g->anchored = zalloc((size_t)n_kf);
+    g->kf_birth = zalloc(sizeof(int) * (n_kf ? n_kf : 1));
+    g->lm_birth = zalloc(sizeof(int) * (n_lm ? n_lm : 1));
     g->Dk = zalloc(sizeof(double) * 6 * n_kf);
     g->Dl = zalloc(sizeof(double) * 3 * n_lm);
     g->kf_lam = zalloc(sizeof(double) * 36 * n_kf);
@@ -467,7 +471,8 @@ orc_graph* orc_create(const orc_cam* cam, const orc_params* prm,
 void orc_destroy(orc_graph* g)
 {
     if (!g) return;
-    void* ptrs[] = { g->Rref, g->cref, g->lref, g->fk, g->fm, g->z, g->anchored, g->Dk, g->Dl,
+    void* ptrs[] = { g->Rref, g->cref, g->lref, g->fk, g->fm, g->z, g->anchored, g->kf_birth, g->lm_birth,
+                     g->Dk, g->Dl,
                      g->kf_lam, g->kf_eta, g->lm_lam, g->lm_eta, g->kf_mu, g->lm_mu,
                      g->mk_lam, g->mk_eta, g->ml_lam, g->ml_eta, g->nk_lam, g->nk_eta, g->nl_lam, g->nl_eta,
                      g->linA, g->linc, g->x0, g->tlin };
@@ -638,3 +643,148 @@ int orc_huber_count(const orc_graph* g)
 }
 
 long orc_relinearisations(const orc_graph* g) { return g->n_relin; }
+
+/* ------------------------------------------------------------------------
+ * incremental SLAM (Sec. 9.2)
+ * ---------------------------------------------------------------------- */
+
+static void* grow(void* p, size_t old_bytes, size_t new_bytes)
+{
+    void* q = realloc(p, new_bytes ? new_bytes : 1);
+    if (q && new_bytes > old_bytes) memset((char*)q + old_bytes, 0, new_bytes - old_bytes);
+    return q;
+}
+
+int orc_sizes(const orc_graph* g, int* n_kf, int* n_lm, int* n_obs)
+{
+    if (n_kf) *n_kf = g->n_kf;
+    if (n_lm) *n_lm = g->n_lm;
+    if (n_obs) *n_obs = g->n_f;
+    return 0;
+}
+
+int orc_add_keyframe(orc_graph* g, const double* kf_Rt_init, int n_new_lm, const double* new_lm_xyz,
+                     int n_obs, const int* obs_lm, const double* obs_uv)
+{
+    const int K0 = g->n_kf, L0 = g->n_lm, F0 = g->n_f;
+    const int K1 = K0 + 1, L1 = L0 + n_new_lm, F1 = F0 + n_obs;
+    if (n_new_lm < 0 || n_obs < 0) return -1;
+    if (!kf_Rt_init && K0 == 0) return -1;
+    for (int i = 0; i < n_obs; ++i)
+        if (obs_lm[i] < 0 || obs_lm[i] >= L1) return -1;
+    for (int j = L0; j < L1; ++j) {
+        int seen = 0;
+        for (int i = 0; i < n_obs && !seen; ++i) seen = obs_lm[i] == j;
+        if (!seen && !new_lm_xyz) return -1;
+    }
+
+    /* pose of the new keyframe: given, or the latest keyframe's current estimate */
+    double Rt[12];
+    if (kf_Rt_init) {
+        memcpy(Rt, kf_Rt_init, sizeof Rt);
+    } else {
+        double dR[9], R[9], c[3];
+        orc_so3_exp(g->kf_mu + 6 * (K0 - 1) + 3, dR);
+        matmul3(dR, g->Rref + 9 * (K0 - 1), R);
+        for (int i = 0; i < 3; ++i) c[i] = g->cref[3 * (K0 - 1) + i] + g->kf_mu[6 * (K0 - 1) + i];
+        for (int i = 0; i < 9; ++i) Rt[i] = R[i];
+        for (int i = 0; i < 3; ++i) Rt[9 + i] = -(R[i * 3] * c[0] + R[i * 3 + 1] * c[1] + R[i * 3 + 2] * c[2]);
+    }
+
+    size_t d = sizeof(double);
+#define GROW(ptr, per, oldn, newn) ptr = grow(ptr, (size_t)(per) * (oldn), (size_t)(per) * (newn))
+    GROW(g->Rref, 9 * d, K0, K1); GROW(g->cref, 3 * d, K0, K1); GROW(g->anchored, 1, K0, K1);
+    GROW(g->kf_birth, sizeof(int), K0, K1); GROW(g->Dk, 6 * d, K0, K1); GROW(g->kf_lam, 36 * d, K0, K1);
+    GROW(g->kf_eta, 6 * d, K0, K1); GROW(g->kf_mu, 6 * d, K0, K1);
+    GROW(g->lref, 3 * d, L0, L1); GROW(g->lm_birth, sizeof(int), L0, L1); GROW(g->Dl, 3 * d, L0, L1);
+    GROW(g->lm_lam, 9 * d, L0, L1); GROW(g->lm_eta, 3 * d, L0, L1); GROW(g->lm_mu, 3 * d, L0, L1);
+    GROW(g->fk, sizeof(int), F0, F1); GROW(g->fm, sizeof(int), F0, F1); GROW(g->z, 2 * d, F0, F1);
+    GROW(g->mk_lam, 36 * d, F0, F1); GROW(g->mk_eta, 6 * d, F0, F1); GROW(g->ml_lam, 9 * d, F0, F1);
+    GROW(g->ml_eta, 3 * d, F0, F1); GROW(g->nk_lam, 36 * d, F0, F1); GROW(g->nk_eta, 6 * d, F0, F1);
+    GROW(g->nl_lam, 9 * d, F0, F1); GROW(g->nl_eta, 3 * d, F0, F1); GROW(g->linA, 81 * d, F0, F1);
+    GROW(g->linc, 9 * d, F0, F1); GROW(g->x0, 9 * d, F0, F1); GROW(g->tlin, sizeof(int), F0, F1);
+#undef GROW
+
+    /* references of the new variables = their initial values */
+    for (int i = 0; i < 9; ++i) g->Rref[9 * K0 + i] = Rt[i];
+    for (int i = 0; i < 3; ++i)
+        g->cref[3 * K0 + i] = -(Rt[0 * 3 + i] * Rt[9] + Rt[1 * 3 + i] * Rt[10] + Rt[2 * 3 + i] * Rt[11]);
+    g->kf_birth[K0] = g->t;
+    for (int j = L0; j < L1; ++j) {
+        g->lm_birth[j] = g->t;
+        if (new_lm_xyz) {
+            for (int i = 0; i < 3; ++i) g->lref[3 * j + i] = new_lm_xyz[3 * (j - L0) + i];
+        } else {
+            /* Sec. 9.2: 1 m depth along the first ray that observes it */
+            int o = 0;
+            while (obs_lm[o] != j) ++o;
+            double pc[3] = { (obs_uv[2 * o] - g->cam.cx) / g->cam.fx, (obs_uv[2 * o + 1] - g->cam.cy) / g->cam.fy, 1.0 };
+            for (int i = 0; i < 3; ++i)
+                g->lref[3 * j + i] = g->cref[3 * K0 + i] + Rt[0 * 3 + i] * pc[0] + Rt[1 * 3 + i] * pc[1] + Rt[2 * 3 + i] * pc[2];
+        }
+    }
+    g->n_kf = K1;
+    g->n_lm = L1;
+    g->n_f = F1;
+
+    /* new factors: linearised at the current means (new variables at their
+     * chart origin), zero messages, (re)linearised now */
+    orc_params p1 = g->prm;
+    p1.huber_nsigma = 0.0;
+    double J[18], r[2], k, A[81], c[9];
+    int* deg_l = zalloc(sizeof(int) * (n_new_lm ? n_new_lm : 1));
+    int deg_k = 0;
+    for (int i = 0; i < n_obs; ++i) {
+        int f = F0 + i, m = obs_lm[i];
+        g->fk[f] = K0;
+        g->fm[f] = m;
+        g->z[2 * f] = obs_uv[2 * i];
+        g->z[2 * f + 1] = obs_uv[2 * i + 1];
+        double* x0 = g->x0 + 9 * f;
+        for (int q = 0; q < 6; ++q) x0[q] = g->kf_mu[6 * K0 + q];
+        for (int q = 0; q < 3; ++q) x0[6 + q] = g->lm_mu[3 * m + q];
+        g->tlin[f] = g->t;
+        orc_linearise(&g->cam, &g->prm, g->Rref + 9 * K0, g->cref + 3 * K0, g->lref + 3 * m, x0, x0 + 6,
+                      g->z + 2 * f, J, r, &k, g->linA + 81 * f, g->linc + 9 * f);
+        /* prior of the new variables (Sec. 4 / Sec. 8), from these factors
+         * at this point with Huber weight 1 */
+        orc_linearise(&g->cam, &p1, g->Rref + 9 * K0, g->cref + 3 * K0, g->lref + 3 * m, x0, x0 + 6,
+                      g->z + 2 * f, J, r, &k, A, c);
+        for (int q = 0; q < 6; ++q) g->Dk[6 * K0 + q] += A[q * 9 + q];
+        deg_k++;
+        if (m >= L0) {
+            for (int q = 0; q < 3; ++q) g->Dl[3 * m + q] += A[(6 + q) * 9 + 6 + q];
+            deg_l[m - L0]++;
+        }
+    }
+    {
+        double mx = 0.0;
+        for (int q = 0; q < 6; ++q) {
+            if (deg_k) g->Dk[6 * K0 + q] /= deg_k;
+            if (g->Dk[6 * K0 + q] > mx) mx = g->Dk[6 * K0 + q];
+        }
+        for (int q = 0; q < 6; ++q) {
+            if (mx <= 0.0) g->Dk[6 * K0 + q] = 1.0;
+            else if (g->Dk[6 * K0 + q] < 1e-9 * mx) g->Dk[6 * K0 + q] = 1e-9 * mx;
+        }
+    }
+    for (int j = L0; j < L1; ++j) {
+        double mx = 0.0;
+        for (int q = 0; q < 3; ++q) {
+            if (deg_l[j - L0]) g->Dl[3 * j + q] /= deg_l[j - L0];
+            if (g->Dl[3 * j + q] > mx) mx = g->Dl[3 * j + q];
+        }
+        for (int q = 0; q < 3; ++q) {
+            if (mx <= 0.0) g->Dl[3 * j + q] = 1.0;
+            else if (g->Dl[3 * j + q] < 1e-9 * mx) g->Dl[3 * j + q] = 1e-9 * mx;
+        }
+    }
+    free(deg_l);
+
+    /* beliefs of the new variables: their prior at scale s(0), mean 0 */
+    double s0 = orc_prior_scale(&g->prm, 0);
+    for (int i = 0; i < 6; ++i) g->kf_lam[36 * K0 + i * 6 + i] = s0 * g->Dk[6 * K0 + i];
+    for (int j = L0; j < L1; ++j)
+        for (int i = 0; i < 3; ++i) g->lm_lam[9 * j + i * 3 + i] = s0 * g->Dl[3 * j + i];
+    return K0;
+}

@@ -58,6 +58,18 @@ orc_graph* orc_create(const orc_cam* cam, const orc_params* prm,
                       int n_anchor, const int* anchor_kf);
 void orc_destroy(orc_graph* g);
 
+/* Incremental SLAM (Sec. 9.2): add one keyframe observing n_obs points.
+ * kf_Rt_init (12) or NULL: the latest keyframe's current world pose.
+ * New points get indices n_lm .. n_lm + n_new_lm - 1; new_lm_xyz (n_new_lm x
+ * 3) or NULL: 1 m depth along the first observation of each in this call.
+ * New variables take their initial value as chart origin and a prior built
+ * like the others' (from their factors' Jacobians there), annealed from
+ * this iteration on; new factors are linearised at the current means and
+ * start with zero messages.  Returns the new keyframe's index, or -1. */
+int orc_add_keyframe(orc_graph* g, const double* kf_Rt_init, int n_new_lm, const double* new_lm_xyz,
+                     int n_obs, const int* obs_lm, const double* obs_uv);
+int orc_sizes(const orc_graph* g, int* n_kf, int* n_lm, int* n_obs);
+
 /* Run n synchronous iterations.  Returns 0, or -1 if a belief stopped being
  * positive definite.  *max_dmu (nullable) = max_v |mu_v^{t+1} - mu_v^t|_inf of
  * the last iteration. */

@@ -47,6 +47,8 @@ struct DevState {
     int32_t* tile_start = nullptr;
     int32_t* big_lm = nullptr;
     int32_t* orphan = nullptr;
+    int32_t* kf_birth = nullptr;
+    int32_t* lm_birth = nullptr;
     R* kf_D = nullptr;
     R* kf_A = nullptr;
     R* lm_D = nullptr;
@@ -61,7 +63,7 @@ struct DevState {
     R* prior_s = nullptr;      // prior scale table, prior_anneal_iters + 1 entries
 
     void release() {
-        void* ptrs[] = {z, fk, fm, kf_R, kf_c, lm_ref, kf_off, kf_list, kpos, lm_off, tile_start, big_lm, orphan, kf_D, kf_A, lm_D,
+        void* ptrs[] = {z, fk, fm, kf_R, kf_c, lm_ref, kf_off, kf_list, kpos, lm_off, tile_start, big_lm, orphan, kf_birth, lm_birth, kf_D, kf_A, lm_D,
                         uv_ref, x0, tlin, mk, mk2, ml, kf_bel, lm_bel, prior_s};
         for (void* p : ptrs)
             if (p) cudaFree(p);
@@ -103,6 +105,7 @@ struct gbp_graph {
     std::vector<int32_t> fk, fm, obs_index;     // obs_index[f] = caller's observation index
     std::vector<double> z;
     std::vector<uint8_t> anchored;
+    std::vector<int32_t> kf_birth, lm_birth;    // iteration each variable was added at (prior anneal start)
     std::vector<int32_t> prob_kf0, prob_lm0;    // problem table (n_problems + 1 entries, last = totals)
     std::vector<int32_t> prob_f0;               // first internal factor of each problem (+ total)
     int32_t* d_prob_f0 = nullptr;               // device copy for the per-problem metrics
@@ -204,7 +207,7 @@ gbp_status upload_prior_table(gbp_graph* g) {
 // Upload the problem into freshly allocated device buffers of type R and
 // generate the priors; leaves the dynamic state uninitialised.
 template <typename R>
-gbp_status build_device(gbp_graph* g) {
+gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
     DevState<R>& s = state<R>(g);
     s.release();
     const int nk = g->n_kf, nl = g->n_lm, nf = g->n_f;
@@ -284,6 +287,8 @@ gbp_status build_device(gbp_graph* g) {
     CK(dev_alloc(&s.tile_start, tiles.size()));
     CK(dev_alloc(&s.big_lm, big.size()));
     CK(dev_alloc(&s.orphan, orphan.size()));
+    CK(dev_alloc(&s.kf_birth, nk));
+    CK(dev_alloc(&s.lm_birth, nl));
     CK(dev_alloc(&s.kf_D, 6 * (size_t)nk));
     CK(dev_alloc(&s.kf_A, 6 * (size_t)nk));
     CK(dev_alloc(&s.lm_D, 3 * (size_t)nl));
@@ -310,6 +315,13 @@ gbp_status build_device(gbp_graph* g) {
         CK(cudaMemcpyAsync(s.orphan, orphan.data(), sizeof(int32_t) * orphan.size(), cudaMemcpyHostToDevice, st));
     if (!big.empty())
         CK(cudaMemcpyAsync(s.big_lm, big.data(), sizeof(int32_t) * big.size(), cudaMemcpyHostToDevice, st));
+    if (nk) CK(cudaMemcpyAsync(s.kf_birth, g->kf_birth.data(), sizeof(int32_t) * nk, cudaMemcpyHostToDevice, st));
+    if (nl) CK(cudaMemcpyAsync(s.lm_birth, g->lm_birth.data(), sizeof(int32_t) * nl, cudaMemcpyHostToDevice, st));
+    // linearisation points (the references at creation) for the prior pass
+    if (x0_init && nf)
+        CK(cudaMemcpyAsync(s.x0, x0_init->data(), sizeof(R) * 9 * (size_t)nf, cudaMemcpyHostToDevice, st));
+    else if (nf)
+        CK(cudaMemsetAsync(s.x0, 0, sizeof(R) * 9 * (size_t)nf, st));
 
     DevGraph<R>& d = s.g;
     d.n_kf = nk;
@@ -328,6 +340,8 @@ gbp_status build_device(gbp_graph* g) {
     d.tile_start = s.tile_start;
     d.big_lm = s.big_lm;
     d.orphan = s.orphan;
+    d.kf_birth = s.kf_birth;
+    d.lm_birth = s.lm_birth;
     d.n_tiles = n_tiles;
     d.n_big = (int32_t)big.size();
     d.n_orphan = (int32_t)orphan.size();
@@ -645,6 +659,178 @@ std::vector<std::pair<void*, size_t>> state_buffers(gbp_graph* g) {
             {g->ctl, sizeof(int32_t) * CTL_N}};
 }
 
+// Slot of every factor's keyframe message: its position in the keyframe's
+// CSR list (factors of a keyframe in internal order).
+std::vector<int32_t> keyframe_slots(const std::vector<int32_t>& fk, int n_kf) {
+    std::vector<int32_t> off(n_kf + 1, 0), kpos(fk.size());
+    for (int32_t k : fk) off[k + 1]++;
+    for (int v = 0; v < n_kf; ++v) off[v + 1] += off[v];
+    for (size_t f = 0; f < fk.size(); ++f) kpos[f] = off[fk[f]]++;
+    return kpos;
+}
+
+// Incremental SLAM (Sec. 9.2).  The iteration state is carried over factor
+// by factor and variable by variable into the rebuilt layout; new variables
+// take their prior from their own factors at those factors' linearisation
+// points, annealed from this iteration on; new factors are linearised at the
+// current means with zero messages.
+template <typename R>
+gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_lm, const double* new_lm_xyz,
+                             int n_obs, const int32_t* obs_lm, const double* obs_uv) {
+    cudaStream_t st = g->stream;
+    const int K0 = g->n_kf, L0 = g->n_lm, F0 = g->n_f;
+    const int K1 = K0 + 1, L1 = L0 + n_new_lm, F1 = F0 + n_obs;
+    std::vector<int32_t> ctl(CTL_N), tlin(F0);
+    std::vector<R> x0(9 * (size_t)F0), mk((size_t)KREC * F0), ml(9 * (size_t)F0), kb((size_t)KBEL * K0),
+        lb((size_t)LBEL * L0), kD(6 * (size_t)K0), kA(6 * (size_t)K0), lD(3 * (size_t)L0);
+    {
+        DevState<R>& s = state<R>(g);
+        CK(cudaMemcpyAsync(ctl.data(), g->ctl, sizeof(int32_t) * CTL_N, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const R* mk_cur = (ctl[CTL_ITER] & 1) ? s.mk2 : s.mk;
+        CK(cudaMemcpyAsync(x0.data(), s.x0, sizeof(R) * x0.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(tlin.data(), s.tlin, sizeof(int32_t) * tlin.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(mk.data(), mk_cur, sizeof(R) * mk.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ml.data(), s.ml, sizeof(R) * ml.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(kb.data(), s.kf_bel, sizeof(R) * kb.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(lb.data(), s.lm_bel, sizeof(R) * lb.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(kD.data(), s.kf_D, sizeof(R) * kD.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(kA.data(), s.kf_A, sizeof(R) * kA.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(lD.data(), s.lm_D, sizeof(R) * lD.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    const int t = ctl[CTL_ITER];
+    if (ctl[CTL_ERR]) return fail(g, GBP_ESTATE, "graph is in an error state");
+
+    // pose of the new keyframe: given, or the latest keyframe's current estimate
+    double Rt[12];
+    if (kf_Rt_init) {
+        std::copy(kf_Rt_init, kf_Rt_init + 12, Rt);
+    } else {
+        const R* mu = &kb[(size_t)KBEL * (K0 - 1) + 27];
+        double w[3] = {double(mu[3]), double(mu[4]), double(mu[5])}, E[9];
+        so3_exp_host(w, E);
+        const double* Rr = &g->kf_R[9 * (size_t)(K0 - 1)];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) Rt[3 * i + j] = E[3 * i] * Rr[j] + E[3 * i + 1] * Rr[3 + j] + E[3 * i + 2] * Rr[6 + j];
+        double c[3];
+        for (int i = 0; i < 3; ++i) c[i] = g->kf_c[3 * (K0 - 1) + i] + double(mu[i]);
+        for (int i = 0; i < 3; ++i) Rt[9 + i] = -(Rt[3 * i] * c[0] + Rt[3 * i + 1] * c[1] + Rt[3 * i + 2] * c[2]);
+    }
+    double cnew[3];
+    for (int i = 0; i < 3; ++i) cnew[i] = -(Rt[i] * Rt[9] + Rt[3 + i] * Rt[10] + Rt[6 + i] * Rt[11]);
+
+    // state of the old factors by caller observation index
+    std::vector<int32_t> old_index = g->obs_index;
+    std::vector<int32_t> old_kpos = keyframe_slots(g->fk, K0);
+    std::vector<int32_t> ok(F1), ol(F1), idx(F1);
+    std::vector<double> uv(2 * (size_t)F1);
+    std::vector<int32_t> where(F1, -1);   // caller index -> old internal factor
+    for (int f = 0; f < F0; ++f) {
+        const int ci = old_index[f];
+        ok[ci] = g->fk[f];
+        ol[ci] = g->fm[f];
+        uv[2 * ci] = g->z[2 * f];
+        uv[2 * ci + 1] = g->z[2 * f + 1];
+        where[ci] = f;
+    }
+    for (int i = 0; i < n_obs; ++i) {
+        ok[F0 + i] = K0;
+        ol[F0 + i] = obs_lm[i];
+        uv[2 * (F0 + i)] = obs_uv[2 * i];
+        uv[2 * (F0 + i) + 1] = obs_uv[2 * i + 1];
+    }
+    std::iota(idx.begin(), idx.end(), 0);
+
+    // new variables
+    for (int i = 0; i < 9; ++i) g->kf_R.push_back(Rt[i]);
+    for (int i = 0; i < 3; ++i) g->kf_c.push_back(cnew[i]);
+    g->anchored.push_back(0);
+    g->kf_birth.push_back(t);
+    for (int j = L0; j < L1; ++j) {
+        double X[3];
+        if (new_lm_xyz) {
+            for (int i = 0; i < 3; ++i) X[i] = new_lm_xyz[3 * (j - L0) + i];
+        } else {
+            // Sec. 9.2: 1 m depth along the first ray that observes the point
+            int o = 0;
+            while (obs_lm[o] != j) ++o;
+            double pc[3] = {(obs_uv[2 * o] - g->intr.cx) / g->intr.fx, (obs_uv[2 * o + 1] - g->intr.cy) / g->intr.fy, 1.0};
+            for (int i = 0; i < 3; ++i) X[i] = cnew[i] + Rt[i] * pc[0] + Rt[3 + i] * pc[1] + Rt[6 + i] * pc[2];
+        }
+        for (int i = 0; i < 3; ++i) g->lm_ref.push_back(X[i]);
+        g->lm_birth.push_back(t);
+    }
+    g->n_kf = K1;
+    g->n_lm = L1;
+    order_factors(g, ok, ol, uv, idx);
+    g->prob_kf0 = {0, K1};
+    g->prob_lm0 = {0, L1};
+    g->prob_f0 = {0, F1};
+    CK(cudaMemcpy(g->d_prob_f0, g->prob_f0.data(), sizeof(int32_t) * 2, cudaMemcpyHostToDevice));
+    g->uv_ref.clear();   // the reference projections no longer cover every factor
+
+    // linearisation points in the new order: old factors keep theirs, new
+    // ones take the current means (a new variable's mean is 0 in its chart)
+    std::vector<R> x0n(9 * (size_t)F1), mln(9 * (size_t)F1, R(0)), mkn((size_t)KREC * F1, R(0));
+    std::vector<int32_t> tlinn(F1);
+    std::vector<int32_t> kpos = keyframe_slots(g->fk, K1);
+    for (int f = 0; f < F1; ++f) {
+        const int ci = g->obs_index[f];
+        const int of = ci < F0 ? where[ci] : -1;
+        if (of >= 0) {
+            for (int i = 0; i < 9; ++i) {
+                x0n[(size_t)i * F1 + f] = x0[(size_t)i * F0 + of];
+                mln[(size_t)i * F1 + f] = ml[(size_t)i * F0 + of];
+            }
+            tlinn[f] = tlin[of];
+            std::copy(&mk[(size_t)KREC * old_kpos[of]], &mk[(size_t)KREC * old_kpos[of]] + KREC,
+                      &mkn[(size_t)KREC * kpos[f]]);
+        } else {
+            const int m = g->fm[f];
+            for (int i = 0; i < 6; ++i) x0n[(size_t)i * F1 + f] = R(0);
+            for (int i = 0; i < 3; ++i) x0n[(size_t)(6 + i) * F1 + f] = m < L0 ? lb[(size_t)LBEL * m + 9 + i] : R(0);
+            tlinn[f] = t;
+        }
+    }
+    destroy_exec(g);
+    gbp_status bst = build_device<R>(g, &x0n);
+    if (bst != GBP_OK) return bst;
+
+    // priors: old variables keep theirs, new ones take the pass just run
+    DevState<R>& s = state<R>(g);
+    std::vector<R> kDn(6 * (size_t)K1), lDn(3 * (size_t)L1), kAn(6 * (size_t)K1, R(0));
+    CK(cudaMemcpyAsync(kDn.data(), s.kf_D, sizeof(R) * kDn.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(lDn.data(), s.lm_D, sizeof(R) * lDn.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::copy(kD.begin(), kD.end(), kDn.begin());
+    std::copy(lD.begin(), lD.end(), lDn.begin());
+    std::copy(kA.begin(), kA.end(), kAn.begin());
+    // beliefs: old carried over, new = their prior at scale s(0), mean 0
+    const R s0 = g->prm.prior_anneal_iters > 0 ? R(1) : R(g->prm.prior_final_scale);
+    const R isig2 = R(1.0 / (double(g->prm.sigma_px) * double(g->prm.sigma_px)));
+    std::vector<R> kbn((size_t)KBEL * K1, R(0)), lbn((size_t)LBEL * L1, R(0));
+    std::copy(kb.begin(), kb.end(), kbn.begin());
+    std::copy(lb.begin(), lb.end(), lbn.begin());
+    for (int i = 0; i < 6; ++i) kbn[(size_t)KBEL * K0 + i * (i + 1) / 2 + i] = s0 * kDn[6 * (size_t)K0 + i] * isig2;
+    for (int j = L0; j < L1; ++j)
+        for (int i = 0; i < 3; ++i) lbn[(size_t)LBEL * j + i * (i + 1) / 2 + i] = s0 * lDn[3 * (size_t)j + i] * isig2;
+    R* mk_cur = (t & 1) ? s.mk2 : s.mk;
+    R* mk_other = (t & 1) ? s.mk : s.mk2;
+    CK(cudaMemcpyAsync(s.kf_D, kDn.data(), sizeof(R) * kDn.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.lm_D, lDn.data(), sizeof(R) * lDn.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.kf_A, kAn.data(), sizeof(R) * kAn.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.tlin, tlinn.data(), sizeof(int32_t) * tlinn.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.ml, mln.data(), sizeof(R) * mln.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(mk_cur, mkn.data(), sizeof(R) * mkn.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(mk_other, 0, sizeof(R) * mkn.size(), st));
+    CK(cudaMemcpyAsync(s.kf_bel, kbn.data(), sizeof(R) * kbn.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.lm_bel, lbn.data(), sizeof(R) * lbn.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(g->ctl, ctl.data(), sizeof(int32_t) * CTL_N, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return GBP_OK;
+}
+
 // ==========================================================================
 // C ABI
 
@@ -714,6 +900,7 @@ gbp_status create_impl(const gbp_intrinsics* intr, int32_t n_kf, const double* k
 
     gbp_graph* g = new (std::nothrow) gbp_graph();
     if (!g) return GBP_ENOMEM;
+    (void)cudaGetLastError();   // an error left by an unrelated earlier call is not ours to report
     g->intr = *intr;
     gbp_default_params(&g->prm);
     g->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
@@ -730,6 +917,8 @@ gbp_status create_impl(const gbp_intrinsics* intr, int32_t n_kf, const double* k
         for (int i = 0; i < 3; ++i) g->kf_c[3 * v + i] = -(Rt[i] * Rt[9] + Rt[3 + i] * Rt[10] + Rt[6 + i] * Rt[11]);
     }
     g->lm_ref.assign(lm_xyz, lm_xyz + 3 * (size_t)n_lm);
+    g->kf_birth.assign(n_kf, 0);
+    g->lm_birth.assign(n_lm, 0);
     g->anchored.assign(n_kf, 0);
     for (int i = 0; i < n_anchor; ++i) g->anchored[anchor_kf[i]] = 1;
     // every observed point must be in front of its camera at the initial values
@@ -895,6 +1084,16 @@ gbp_status gbp_reset(gbp_graph* g) {
     if (!g) return GBP_EINVAL;
     gbp_status st = ensure_built(g);
     if (st != GBP_OK) return st;
+    // back to iteration 0: every variable counts as present from the start
+    if (std::any_of(g->kf_birth.begin(), g->kf_birth.end(), [](int32_t b) { return b != 0; }) ||
+        std::any_of(g->lm_birth.begin(), g->lm_birth.end(), [](int32_t b) { return b != 0; })) {
+        std::fill(g->kf_birth.begin(), g->kf_birth.end(), 0);
+        std::fill(g->lm_birth.begin(), g->lm_birth.end(), 0);
+        int32_t* kb = g->storage ? g->sd.kf_birth : g->sf.kf_birth;
+        int32_t* lb = g->storage ? g->sd.lm_birth : g->sf.lm_birth;
+        if (g->n_kf) CK(cudaMemcpy(kb, g->kf_birth.data(), sizeof(int32_t) * g->n_kf, cudaMemcpyHostToDevice));
+        if (g->n_lm) CK(cudaMemcpy(lb, g->lm_birth.data(), sizeof(int32_t) * g->n_lm, cudaMemcpyHostToDevice));
+    }
     return g->storage ? reset_state<double>(g) : reset_state<float>(g);
 }
 
@@ -1167,9 +1366,29 @@ gbp_status gbp_autotune(gbp_graph* g, int32_t n_trial, int32_t* chosen, double* 
 
 gbp_status gbp_add_keyframe(gbp_graph* g, const double* kf_Rt_init, int32_t n_new_lm, const double* new_lm_xyz,
                             int32_t n_obs, const int32_t* obs_lm, const double* obs_uv, int32_t* new_kf_index) {
-    (void)kf_Rt_init; (void)n_new_lm; (void)new_lm_xyz; (void)n_obs; (void)obs_lm; (void)obs_uv; (void)new_kf_index;
     if (!g) return GBP_EINVAL;
-    return fail(g, GBP_ESTATE, "gbp_add_keyframe is not available in this build");
+    if (new_kf_index) *new_kf_index = -1;
+    if (n_new_lm < 0 || n_obs < 0 || (n_obs && (!obs_lm || !obs_uv))) return fail(g, GBP_EINVAL, "bad counts");
+    if (g->prob_kf0.size() != 2) return fail(g, GBP_ESTATE, "gbp_add_keyframe needs a single-problem graph");
+    if (!kf_Rt_init && g->n_kf == 0) return fail(g, GBP_EINVAL, "no keyframe to copy the initial pose from");
+    if (kf_Rt_init && !finite_all(kf_Rt_init, 12)) return fail(g, GBP_EINVAL, "initial pose not finite");
+    if (new_lm_xyz && !finite_all(new_lm_xyz, 3 * (size_t)n_new_lm)) return fail(g, GBP_EINVAL, "points not finite");
+    if (!finite_all(obs_uv, 2 * (size_t)n_obs)) return fail(g, GBP_EINVAL, "pixels not finite");
+    const int L1 = g->n_lm + n_new_lm;
+    std::vector<char> seen(n_new_lm, 0);
+    for (int i = 0; i < n_obs; ++i) {
+        if (obs_lm[i] < 0 || obs_lm[i] >= L1) return fail(g, GBP_EINVAL, "observation index out of range");
+        if (obs_lm[i] >= g->n_lm) seen[obs_lm[i] - g->n_lm] = 1;
+    }
+    if (!new_lm_xyz)
+        for (char c : seen)
+            if (!c) return fail(g, GBP_EINVAL, "a new point without observation needs an initial position");
+    gbp_status st = ensure_built(g);
+    if (st != GBP_OK) return st;
+    st = g->storage ? add_keyframe_impl<double>(g, kf_Rt_init, n_new_lm, new_lm_xyz, n_obs, obs_lm, obs_uv)
+                    : add_keyframe_impl<float>(g, kf_Rt_init, n_new_lm, new_lm_xyz, n_obs, obs_lm, obs_uv);
+    if (st == GBP_OK && new_kf_index) *new_kf_index = g->n_kf - 1;
+    return st;
 }
 
 void gbp_destroy_graph(gbp_graph* g) {

@@ -70,6 +70,8 @@ struct DevGraph {
     const int32_t* big_lm;    // landmarks split across tiles (more than 32 factors)
     const int32_t* orphan;    // variables without factors: keyframe v, or n_kf + landmark
     int32_t n_tiles, n_big, n_orphan;
+    const int32_t* kf_birth;  // n_kf: iteration at which the keyframe was added (prior anneal start)
+    const int32_t* lm_birth;  // n_lm
     const R* kf_D;            // n_kf x 6, prior diagonal at sigma = 1
     const R* kf_A;            // n_kf x 6, anchor diagonal at sigma = 1 (0 = not anchored)
     const R* lm_D;            // n_lm x 3

@@ -401,7 +401,20 @@ __device__ __forceinline__ void raise_error(int32_t* ctl, int where) {
 // tabulated on the host.
 template <typename R>
 __device__ __forceinline__ R prior_scale(const KParams<R>& P, int t) {
+    t = t < 0 ? 0 : t;
     return P.prior_s[t < P.prior_T ? t : P.prior_T];
+}
+
+// A variable's prior anneals from the iteration it was added at (Sec. 9.2:
+// keyframes and points added during incremental SLAM start at measurement
+// scale like the initial ones).
+template <typename R>
+__device__ __forceinline__ R kf_prior_scale(const DevGraph<R>& g, const KParams<R>& P, int k, int t) {
+    return prior_scale(P, t - g.kf_birth[k]);
+}
+template <typename R>
+__device__ __forceinline__ R lm_prior_scale(const DevGraph<R>& g, const KParams<R>& P, int m, int t) {
+    return prior_scale(P, t - g.lm_birth[m]);
 }
 
 template <typename R, int n>
@@ -569,8 +582,7 @@ __device__ __forceinline__ void dmu_atomic_max_slot(int32_t* ctl, int slot, floa
 // other warp).  Returns this lane's max |dmu|.
 
 template <typename R>
-__device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R>& P, int tile, int t, R s_next,
-                                           int lane) {
+__device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R>& P, int tile, int t, int lane) {
     const int n_f = g.n_f;
     const int ts = g.tile_start[tile], te = g.tile_start[tile + 1];
     const int f = ts + lane;
@@ -675,7 +687,7 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
         {
             R Pm[6], qm[3];
             if (whole) {
-                const R sp = prior_scale(P, t) * P.inv_sigma2;
+                const R sp = lm_prior_scale(g, P, m, t) * P.inv_sigma2;
 #pragma unroll
                 for (int i = 0; i < 6; ++i) Pm[i] = cav[i];
 #pragma unroll
@@ -782,7 +794,8 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
         }
     }
     float dmu = 0.0f;
-    if (whole && lane == hi - ts - 1) dmu = finish_landmark<R>(g, P, m, s_next, sum, mu_m_old, g.lm_bel_out);
+    if (whole && lane == hi - ts - 1)
+        dmu = finish_landmark<R>(g, P, m, lm_prior_scale(g, P, m, t + 1), sum, mu_m_old, g.lm_bel_out);
     return dmu;
 }
 
@@ -796,8 +809,7 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
 // orphan groups.  Returns max |dmu| in lane 0.
 
 template <typename R>
-__device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParams<R>& P, int w, int t, R s_next,
-                                              int lane) {
+__device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParams<R>& P, int w, int t, int lane) {
     float dmu = 0.0f;
     if (w < g.n_kf) {
         const int k = w;
@@ -820,7 +832,7 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
             R mu_old[6];
 #pragma unroll
             for (int i = 0; i < 6; ++i) mu_old[i] = __ldcg(old + 27 + i);
-            dmu = finish_keyframe<R>(g, P, k, s_next, acc, mu_old, g.kf_bel_out);
+            dmu = finish_keyframe<R>(g, P, k, kf_prior_scale(g, P, k, t + 1), acc, mu_old, g.kf_bel_out);
         }
     } else if (w < g.n_kf + g.n_big) {
         const int m = g.big_lm[w - g.n_kf];
@@ -837,7 +849,7 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
         if (lane == 0) {
             const R* old = g.lm_bel + (size_t)m * LBEL;
             R mu_old[3] = {__ldcg(old + 9), __ldcg(old + 10), __ldcg(old + 11)};
-            dmu = finish_landmark<R>(g, P, m, s_next, acc, mu_old, g.lm_bel_out);
+            dmu = finish_landmark<R>(g, P, m, lm_prior_scale(g, P, m, t + 1), acc, mu_old, g.lm_bel_out);
         }
     } else {
         // variables without factors: prior-only beliefs, mean 0
@@ -851,7 +863,8 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
                 for (int j = 0; j < KBEL; ++j) out[j] = R(0);
 #pragma unroll
                 for (int q = 0; q < 6; ++q)
-                    out[pk(q, q)] = (s_next * g.kf_D[v * 6 + q] + P.anchor_scale * g.kf_A[v * 6 + q]) * isig2;
+                    out[pk(q, q)] = (kf_prior_scale(g, P, v, t + 1) * g.kf_D[v * 6 + q] +
+                                     P.anchor_scale * g.kf_A[v * 6 + q]) * isig2;
                 store_rec<R, KBEL>(g.kf_bel_out + (size_t)v * KBEL, out);
             } else {
                 const int mm = v - g.n_kf;
@@ -859,7 +872,7 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
 #pragma unroll
                 for (int j = 0; j < LBEL; ++j) out[j] = R(0);
 #pragma unroll
-                for (int q = 0; q < 3; ++q) out[pk(q, q)] = s_next * g.lm_D[mm * 3 + q] * isig2;
+                for (int q = 0; q < 3; ++q) out[pk(q, q)] = lm_prior_scale(g, P, mm, t + 1) * g.lm_D[mm * 3 + q] * isig2;
                 store_rec<R, LBEL>(g.lm_bel_out + (size_t)mm * LBEL, out);
             }
         }
@@ -881,7 +894,7 @@ __global__ void __launch_bounds__(FACTOR_BLOCK) factor_kernel(DevGraph<R> g, KPa
     const int tile = blockIdx.x * (FACTOR_BLOCK / 32) + (threadIdx.x >> 5);
     if (tile >= g.n_tiles) return;   // uniform per warp
     const int t = g.ctl[CTL_ITER];
-    float dmu = tile_work<R>(g, P, tile, t, prior_scale(P, t + 1), lane);
+    float dmu = tile_work<R>(g, P, tile, t, lane);
     dmu = warp_max(dmu);
     if (lane == 0 && dmu > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), dmu);
 }
@@ -893,7 +906,7 @@ __global__ void __launch_bounds__(FACTOR_BLOCK) belief_kernel(DevGraph<R> g, KPa
     const int w = blockIdx.x * (FACTOR_BLOCK / 32) + (threadIdx.x >> 5);
     const int t = g.ctl[CTL_ITER];
     float dmu = 0.0f;
-    if (w < phase_b_items(g)) dmu = phase_b_item<R>(g, P, w, t, prior_scale(P, t + 1), lane);
+    if (w < phase_b_items(g)) dmu = phase_b_item<R>(g, P, w, t, lane);
     // the last block to finish closes the iteration (max is order
     // independent, so the atomic on non-negative float bits is deterministic)
     dmu = warp_max(dmu);
@@ -968,18 +981,17 @@ __global__ void __launch_bounds__(FACTOR_BLOCK) persistent_kernel(DevGraph<R> g,
     float last = 0.0f;
     for (int it = 0; it < n_iters; ++it) {
         const int t = t0 + it;
-        const R s_next = prior_scale(P, t + 1);
         // phase A: factors and landmarks wholly inside a tile
         float dmu = 0.0f;
         for (int tile = gwarp; tile < g.n_tiles; tile += nwarps)
-            dmu = fmaxf(dmu, tile_work<R>(g, P, tile, t, s_next, lane));
+            dmu = fmaxf(dmu, tile_work<R>(g, P, tile, t, lane));
         dmu = warp_max(dmu);
         if (lane == 0 && dmu > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), dmu);
         if (!grid_barrier(g.ctl, nb, &flag_sh)) break;
         // phase B: keyframes, split landmarks, orphans
         if (blockIdx.x == 0 && threadIdx.x == 0) g.ctl[dmu_slot(t + 1)] = 0;   // every block has read it
         float d2 = 0.0f;
-        for (int w = gwarp; w < items; w += nwarps) d2 = fmaxf(d2, phase_b_item<R>(g, P, w, t, s_next, lane));
+        for (int w = gwarp; w < items; w += nwarps) d2 = fmaxf(d2, phase_b_item<R>(g, P, w, t, lane));
         d2 = warp_max(d2);
         if (lane == 0 && d2 > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), d2);
         if (!grid_barrier(g.ctl, nb, &flag_sh)) break;
@@ -998,9 +1010,9 @@ __global__ void __launch_bounds__(FACTOR_BLOCK) persistent_kernel(DevGraph<R> g,
 template <typename R>
 __global__ void init_beliefs_kernel(DevGraph<R> g, KParams<R> P) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    const R s = prior_scale(P, 0);
     const R isig2 = P.inv_sigma2;
     if (v < g.n_kf) {
+        const R s = kf_prior_scale(g, P, v, g.kf_birth[v]);
         R out[KBEL];
 #pragma unroll
         for (int j = 0; j < KBEL; ++j) out[j] = R(0);
@@ -1010,6 +1022,7 @@ __global__ void init_beliefs_kernel(DevGraph<R> g, KParams<R> P) {
         store_rec<R, KBEL>(g.kf_bel + (size_t)v * KBEL, out);
     } else if (v < g.n_kf + g.n_lm) {
         const int m = v - g.n_kf;
+        const R s = lm_prior_scale(g, P, m, g.lm_birth[m]);
         R out[LBEL];
 #pragma unroll
         for (int j = 0; j < LBEL; ++j) out[j] = R(0);
@@ -1021,7 +1034,8 @@ __global__ void init_beliefs_kernel(DevGraph<R> g, KParams<R> P) {
 
 // ------------------------------------------------------------------------
 // prior generation (Sec. 4 / Sec. 8): per-variable mean over its factors of
-// diag(J_v^T J_v) at the reference point with Huber weight 1 and sigma = 1.
+// diag(J_v^T J_v) at the factors' linearisation points (the references, at
+// creation) with Huber weight 1 and sigma = 1.
 
 template <typename R>
 __global__ void __launch_bounds__(FACTOR_BLOCK) prior_factor_kernel(DevGraph<R> g, KParams<R> P, R* tmp_k, R* tmp_l) {
@@ -1034,7 +1048,7 @@ __global__ void __launch_bounds__(FACTOR_BLOCK) prior_factor_kernel(DevGraph<R> 
     Q.inv_sigma = R(1);
     R x0[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) x0[i] = R(0);
+    for (int i = 0; i < 9; ++i) x0[i] = g.x0[(size_t)i * g.n_f + f];
     Lin<R> L;
     linearise<R>(Q, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3, g.lm_ref + (size_t)m * 3, x0,
                  g.z[2 * (size_t)f], g.z[2 * (size_t)f + 1], L);

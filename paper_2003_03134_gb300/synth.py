@@ -22,8 +22,8 @@ from dataclasses import dataclass, field
 import numpy as np
 from scipy.spatial.transform import Rotation
 
-__all__ = ["Problem", "make_circle", "make_walk", "make_loop", "make_batch",
-           "make_chain", "make_stream", "concat", "workload"]
+__all__ = ["Problem", "StreamStep", "make_circle", "make_walk", "make_loop", "make_batch",
+           "make_chain", "make_stream", "stream_plan", "concat", "workload"]
 
 
 @dataclass
@@ -360,19 +360,48 @@ def make_chain(n_kf: int = 3, seed: int = 0, noise_px: float = 1.0) -> Problem:
                    obs_kf, obs_lm, uv, np.zeros(obs_kf.size, bool), (), params)
 
 
-def make_stream(seed: int = 0, n_kf: int = 500, n_lm: int = 8000, start_kf: int = 10):
-    """Incremental-SLAM stream over one walk problem.  Returns the problem and
-    a list of steps; step s adds keyframe ``start_kf + s`` with its
-    observations.  New keyframes start at the latest keyframe's initial pose
-    and new points at 1 m depth along their first observing ray (Sec. 9.2)."""
-    p = make_walk(seed=seed, n_kf=n_kf, n_lm=n_lm, obs_range=(4, 15), name=f"stream{n_kf}x{n_lm}")
-    first_kf = np.full(p.n_lm, p.n_kf, dtype=np.int64)
-    np.minimum.at(first_kf, p.obs_lm, p.obs_kf)
+@dataclass
+class StreamStep:
+    kf: int                    # keyframe index in the growing graph
+    obs_lm: np.ndarray         # (n,) int32 landmark indices in the growing graph
+    obs_uv: np.ndarray         # (n, 2) pixels
+    n_new_lm: int              # landmarks first seen by this keyframe (the last n_new_lm indices)
+    kf_Rt_true: np.ndarray     # (12,) ground truth pose of the new keyframe
+    new_lm_true: np.ndarray    # (n_new_lm, 3) ground truth of the new landmarks
+
+
+def stream_plan(p: Problem, start_kf: int):
+    """Split a problem into an initial graph (keyframes < start_kf and the
+    points they see) and one step per later keyframe, landmarks renumbered in
+    order of first appearance (Sec. 9.2 incremental SLAM)."""
+    first = np.full(p.n_lm, p.n_kf, dtype=np.int64)
+    np.minimum.at(first, p.obs_lm, p.obs_kf)
+    order = np.lexsort((np.arange(p.n_lm), first))            # by first observing keyframe
+    order = order[first[order] < p.n_kf]
+    new_id = np.full(p.n_lm, -1, dtype=np.int64)
+    new_id[order] = np.arange(order.size)
+    init_lm = order[first[order] < start_kf]
+    sel = p.obs_kf < start_kf
+    init = Problem(name=p.name + f"_first{start_kf}", seed=p.seed, fx=p.fx, fy=p.fy, cx=p.cx, cy=p.cy,
+                   width=p.width, height=p.height, kf_Rt_true=p.kf_Rt_true[:start_kf],
+                   kf_Rt_init=p.kf_Rt_init[:start_kf], lm_true=p.lm_true[init_lm], lm_init=p.lm_init[init_lm],
+                   obs_kf=p.obs_kf[sel].astype(np.int32), obs_lm=new_id[p.obs_lm[sel]].astype(np.int32),
+                   obs_uv=p.obs_uv[sel], obs_outlier=p.obs_outlier[sel],
+                   anchor_kf=p.anchor_kf[p.anchor_kf < start_kf], params=dict(p.params))
     steps = []
     for k in range(start_kf, p.n_kf):
-        sel = np.nonzero(p.obs_kf == k)[0]
-        steps.append(dict(kf=k, obs=sel, new_lm=np.nonzero(first_kf == k)[0]))
-    return p, first_kf, steps
+        idx = np.nonzero(p.obs_kf == k)[0]
+        lm_new = order[first[order] == k]
+        steps.append(StreamStep(kf=k, obs_lm=new_id[p.obs_lm[idx]].astype(np.int32), obs_uv=p.obs_uv[idx],
+                                n_new_lm=int(lm_new.size), kf_Rt_true=p.kf_Rt_true[k], new_lm_true=p.lm_true[lm_new]))
+    return init, steps
+
+
+def make_stream(seed: int = 0, n_kf: int = 500, n_lm: int = 8000, start_kf: int = 10):
+    """Incremental-SLAM stream over one walk problem: the initial graph and
+    the steps that add one keyframe each (see stream_plan)."""
+    p = make_walk(seed=seed, n_kf=n_kf, n_lm=n_lm, obs_range=(4, 15), name=f"stream{n_kf}x{n_lm}")
+    return stream_plan(p, start_kf)
 
 
 def concat(problems: list[Problem], name: str | None = None) -> Problem:

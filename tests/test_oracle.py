@@ -413,3 +413,78 @@ def test_relinearisation_threshold_never_met_equals_linear_mode():
     b.iterate(60)
     for x, y in zip(a.means(), b.means()):
         np.testing.assert_array_equal(x, y)
+
+
+# ------------------------------------------------------- incremental (Sec. 9.2)
+
+def test_added_keyframe_and_points_start_where_the_paper_puts_them():
+    p = synth.make_walk(2, n_kf=14, n_lm=150)
+    init, steps = synth.stream_plan(p, 8)
+    o = oracle.Oracle(init)
+    o.iterate(25)
+    kf_before, _ = o.world()
+    st = steps[0]
+    k = o.add_keyframe(st.obs_lm, st.obs_uv, n_new_lm=st.n_new_lm)
+    assert k == init.n_kf
+    kf, lm = o.world()
+    # new keyframe = the latest keyframe's current estimate
+    np.testing.assert_allclose(kf[k], kf_before[k - 1], atol=1e-12)
+    np.testing.assert_allclose(kf[:k], kf_before, atol=0)
+    # a new point sits 1 m in front of the new keyframe on its observed ray
+    R, t = kf[k, :9].reshape(3, 3), kf[k, 9:]
+    for j in range(init.n_lm, init.n_lm + st.n_new_lm):
+        i = int(np.nonzero(st.obs_lm == j)[0][0])
+        pc = R @ lm[j] + t
+        assert pc[2] == pytest.approx(1.0, abs=1e-12)
+        uv = np.array([p.fx * pc[0] / pc[2] + p.cx, p.fy * pc[1] / pc[2] + p.cy])
+        np.testing.assert_allclose(uv, st.obs_uv[i], atol=1e-9)
+
+
+def test_incremental_fixed_point_is_gauss_newton_stationary():
+    """After keyframes are added and the graph converges, the means satisfy
+    the Gauss-Newton stationarity of the grown problem (objective of Sec. 4
+    with the priors at their final scale)."""
+    p = synth.make_circle(5, n_kf=7, n_lm=30)
+    init, steps = synth.stream_plan(p, 4)
+    o = oracle.Oracle(init, relin_beta=0.0, relin_interval=10)
+    o.iterate(20)
+    for st in steps:
+        o.add_keyframe(st.obs_lm, st.obs_uv, n_new_lm=st.n_new_lm,
+                       new_lm_xyz=st.new_lm_true + 0.05 if st.n_new_lm else None)
+        o.iterate(15)
+    it, d = o.run_to_convergence(1e-14, 60000, chunk=10)
+    assert d < 1e-12
+    kf, lm = o.means()
+    nk, nl, nf = o.sizes()
+    # the grown graph's observations in the order the oracle stores them
+    obs_kf = np.concatenate([init.obs_kf] + [np.full(st.obs_lm.size, init.n_kf + i) for i, st in enumerate(steps)])
+    obs_lm = np.concatenate([init.obs_lm] + [st.obs_lm for st in steps])
+    obs_uv = np.concatenate([init.obs_uv] + [st.obs_uv for st in steps])
+    assert obs_kf.size == nf
+    # references = initial values the oracle used
+    Rw, lw = o.world()
+    mu_k, mu_l = o.means()
+    refs = []
+    for v in range(nk):
+        w = mu_k[v, 3:]
+        Rv = Rw[v, :9].reshape(3, 3)
+        Rref = Rotation.from_rotvec(w).as_matrix().T @ Rv
+        cref = -Rv.T @ Rw[v, 9:] - mu_k[v, :3]
+        refs.append((Rref, cref))
+    lref = lw - mu_l
+    Dk, Dl = o.prior_diag()
+    x = np.concatenate([kf.ravel(), lm.ravel()])
+    P = 0.01 * np.concatenate([Dk.ravel(), Dl.ravel()])
+    for a in init.anchor_kf:
+        P[6 * a:6 * a + 6] += 1e3 * Dk[a]
+    H = np.diag(P)
+    gvec = -P * x
+    cam = _cam(p)
+    for f in range(nf):
+        k, m = obs_kf[f], obs_lm[f]
+        lin = oracle.linearise(cam, refs[k][0].ravel(), refs[k][1], lref[m], kf[k], lm[m], obs_uv[f])
+        idx = np.r_[6 * k:6 * k + 6, 6 * nk + 3 * m:6 * nk + 3 * m + 3]
+        H[np.ix_(idx, idx)] += lin["A"]
+        gvec[idx] += lin["k"] * lin["J"].T @ lin["r"]
+    step = np.linalg.solve(H, gvec)
+    assert np.abs(step).max() < 1e-7
