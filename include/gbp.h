@@ -79,6 +79,8 @@ typedef struct {
                                    gbp_iterate call with a grid barrier between phases, 2: one launch
                                    per phase (factor kernel, belief kernel) replayed as a CUDA graph.
                                    All modes give bitwise identical results.                        */
+    int32_t damping_mode;       /* 0: the fixed d above (Sec. 5, Sec. 8); 1: per-factor d predicted by
+                                   the damping network given to gbp_set_damping_model (see below)   */
 } gbp_params;
 
 typedef struct {
@@ -259,6 +261,96 @@ gbp_status gbp_reprojection_error_noalloc(const gbp_intrinsics* intr, double z_m
                                           const double* lm_xyz, int32_t n_obs, const int32_t* obs_kf,
                                           const int32_t* obs_lm, const double* obs_uv, double* out,
                                           void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Learned damping network.  The paper damps every message with one fixed d
+ * (Sec. 5, d = 0.4 in Sec. 8); this extension predicts a per-factor d in
+ * (0, 0.9) from 16 features of the factor's recent messages with a small
+ * MLP (16 -> 64 -> 64 -> 1, ReLU hidden layers, output 0.9 * sigmoid), and
+ * trains it on targets recorded from GBP runs.  It has no counterpart in the
+ * paper.  Damping never changes GBP's fixed point, so the learned path ends
+ * at the same beliefs as fixed damping.
+ *
+ * Parameters: one flat float32 vector of GBP_MLP_NPARAM values, in order
+ * W1 [16][64] (row = input feature), b1 [64], W2 [64][64] (row = input
+ * unit), b2 [64], W3 [64], b3 [1]; layer l computes h_l = relu(h_{l-1} W_l +
+ * b_l).  Arithmetic: weights and activations rounded to BF16, products on
+ * tensor cores (mma.sync m16n8k16) accumulated in FP32; master weights, Adam
+ * moments and gradients in FP32.
+ * ------------------------------------------------------------------------ */
+#define GBP_MLP_NFEAT 16
+#define GBP_MLP_NPARAM 5313
+
+typedef struct gbp_mlp gbp_mlp;
+
+/* Create a network with the given host parameters (GBP_MLP_NPARAM floats,
+ * all finite, else GBP_EINVAL); Adam moments start at zero.  All device
+ * memory is owned by the network; work goes on cuda_stream (NULL = legacy
+ * default stream). */
+gbp_status gbp_mlp_create(const float* params, void* cuda_stream, gbp_mlp** out);
+/* Replace the parameters (host, GBP_MLP_NPARAM floats) and zero the Adam
+ * state and step count. */
+gbp_status gbp_mlp_set_params(gbp_mlp* net, const float* params);
+/* Copy the FP32 master parameters to the host.  Synchronises the stream. */
+gbp_status gbp_mlp_get_params(const gbp_mlp* net, float* params);
+/* Predictions for count rows of DEVICE features X (count x 16 floats,
+ * row-major) into DEVICE y (count floats).  Asynchronous on the stream. */
+gbp_status gbp_mlp_forward(gbp_mlp* net, const float* X, int32_t count, float* y);
+/* Mean-squared-error loss over count rows of DEVICE X (count x 16) against
+ * DEVICE targets (count floats), and its gradient with respect to the flat
+ * parameters, written to HOST grad (GBP_MLP_NPARAM floats) and *loss
+ * (nullable).  Partial sums are added in a fixed order, so the result is
+ * reproducible.  Synchronises the stream. */
+gbp_status gbp_mlp_gradient(gbp_mlp* net, const float* X, const float* target, int32_t count, float* grad,
+                            double* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected; Kingma
+ * and Ba 2015) at learning rate lr on the mean-squared-error loss of a
+ * minibatch: rows idx[0..count) (DEVICE int32, nullable = rows 0..count) of
+ * DEVICE X and target.  *loss_out (nullable, host) receives the minibatch
+ * loss before the step and then the call synchronises; with loss_out NULL
+ * the call is asynchronous. */
+gbp_status gbp_mlp_train_step(gbp_mlp* net, const float* X, const float* target, const int32_t* idx,
+                              int32_t count, float lr, float* loss_out);
+void gbp_mlp_destroy(gbp_mlp* net);
+
+/* Give graph g its own copy of the network's current weights (later
+ * training of net does not affect g until the next call); NULL removes it.
+ * With damping_mode = 1 each factor's eta messages are damped by the
+ * network's prediction d_f in place of d:
+ *   eta_{f->v} = (1 - d_f) eta_new + d_f eta_old,  Lambda undamped (Sec. 5),
+ * from the second iteration after the factor's (re)linearisation on (the
+ * first message after a relinearisation stays undamped; the fixed schedule's
+ * hold of undamped_iters does not apply).  d_f comes from 16 features of the
+ * factor: its Mahalanobis residual and Huber weight (Sec. 6), how much of
+ * each variable's incoming precision it supplies, the relative change of
+ * each of its two messages over the last 4 iterations, the two variables'
+ * degrees, and the iterations since its linearisation and since its
+ * landmark appeared.  Iterating with damping_mode = 1 and no network gives
+ * GBP_ESTATE. */
+gbp_status gbp_set_damping_model(gbp_graph* g, const gbp_mlp* net);
+
+/* Training data for the network.  gbp_capture_messages stores the graph's
+ * current messages as the reference (normally after running to
+ * convergence); gbp_record_iterations then runs n_iters iterations from the
+ * current state with the fixed damping schedule and writes, per iteration i
+ * and factor f (the library's internal factor order, row i * n_obs + f):
+ *   X[row * 16 + j]  the 16 features above (DEVICE, 16-byte aligned,
+ *                    n_iters * n_obs * 16 floats)
+ *   target[row]      the damping that brings the undamped new eta closest
+ *                    to the reference message, per message side
+ *                    clip(<eta_old - eta_new, eta_ref - eta_new> /
+ *                    |eta_old - eta_new|^2, 0, 0.9), averaged over the two
+ *                    sides; -1 where the learned schedule never damps (the
+ *                    iteration of a relinearisation, a factor behind the
+ *                    camera) or where eta_old = eta_new on both sides
+ *                    (DEVICE, n_iters * n_obs floats).
+ * GBP_ESTATE without a captured reference (also after gbp_add_keyframe,
+ * which drops it).  Synchronises the stream. */
+gbp_status gbp_capture_messages(gbp_graph* g);
+/* The caller's observation index of each of the library's internal factors
+ * (n_obs int32, host): the row order of gbp_record_iterations. */
+gbp_status gbp_get_factor_order(const gbp_graph* g, int32_t* obs_index);
+gbp_status gbp_record_iterations(gbp_graph* g, int32_t n_iters, float* X, float* target);
 
 const char* gbp_status_string(gbp_status s);
 const char* gbp_last_error(const gbp_graph* g);

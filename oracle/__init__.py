@@ -83,6 +83,12 @@ def lib():
         L.orc_linearise.argtypes = [C.POINTER(_Cam), C.POINTER(_Params), _D, _D, _D, _D, _D, _D,
                                     _D, _D, _D, _D, _D]
         L.orc_factor_message.argtypes = [_D, _D, C.c_int, _D, _D, _D, _D]
+        L.orc_net_forward.restype = C.c_double
+        L.orc_net_forward.argtypes = [_D, _D]
+        L.orc_set_damping_net.argtypes = [C.c_void_p, _D]
+        L.orc_set_reference_messages.argtypes = [C.c_void_p, _D]
+        L.orc_set_reference_messages.restype = None
+        L.orc_iterate_record.argtypes = [C.c_void_p, C.c_int, _D, _D]
         _lib = L
     return _lib
 
@@ -172,6 +178,16 @@ def factor_message(A, c, target, lam_in, eta_in):
     if rc != 0:
         raise np.linalg.LinAlgError("matrix to invert is not positive definite")
     return lam_out.reshape(na, na), eta_out
+
+
+N_FEAT, N_NET_PARAMS = 16, 5313
+
+
+def net_forward(params, x) -> float:
+    """The damping network's output for one feature row (FP64, in C)."""
+    p, xv = _f64(params), _f64(x)
+    assert p.size == N_NET_PARAMS and xv.size == N_FEAT
+    return lib().orc_net_forward(_dp(p), _dp(xv))
 
 
 # ---------------------------------------------------------------------------
@@ -294,3 +310,37 @@ class Oracle:
 
     def relinearisations(self) -> int:
         return lib().orc_relinearisations(self._h)
+
+    # learned damping
+    def set_damping_net(self, params):
+        """Learned schedule with these network parameters; None: fixed schedule."""
+        if params is None:
+            lib().orc_set_damping_net(self._h, None)
+            return
+        self._net = _f64(params)
+        if self._net.size != N_NET_PARAMS or lib().orc_set_damping_net(self._h, _dp(self._net)) != 0:
+            raise ValueError("bad network parameters")
+
+    def set_reference_messages(self, mk_eta, ml_eta):
+        """Reference eta of the damping targets: (n_obs, 6) messages to the
+        keyframes and (n_obs, 3) to the landmarks."""
+        self._ref = np.ascontiguousarray(np.concatenate([_f64(mk_eta).reshape(-1, 6), _f64(ml_eta).reshape(-1, 3)],
+                                                        axis=1))
+        lib().orc_set_reference_messages(self._h, _dp(self._ref))
+
+    def capture_messages(self):
+        """The current messages become the reference."""
+        _, mk_eta, _, ml_eta = self.messages()
+        self.set_reference_messages(mk_eta, ml_eta)
+
+    def iterate_record(self, n: int):
+        """n iterations of the fixed schedule; returns features (n, n_obs, 16)
+        and damping targets (n, n_obs) in observation order."""
+        nf = self.sizes()[2]
+        X, T = np.zeros((n, nf, N_FEAT)), np.zeros((n, nf))
+        rc = lib().orc_iterate_record(self._h, int(n), _dp(X), _dp(T))
+        if rc == -2:
+            raise RuntimeError("no reference messages set")
+        if rc != 0:
+            raise FloatingPointError("a belief stopped being positive definite")
+        return X, T

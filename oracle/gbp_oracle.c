@@ -291,6 +291,12 @@ struct orc_graph {
     double *x0;                          /* its linearisation point [xk; xl]     */
     int *tlin;                           /* iteration at which it was taken      */
     long n_relin;                        /* relinearisations since creation      */
+    double *lin_r2, *lin_k;              /* |r|^2 and Huber weight at the linearisation (0, 0 if inactive) */
+    /* learned damping (no counterpart in the paper) */
+    double *hist;                        /* per factor: relative message changes of the last 3 iterations,
+                                            keyframe side [0..2], landmark side [3..5], most recent first */
+    double *net;                         /* damping network parameters (ORC_NET_NPARAM) or NULL         */
+    double *eta_ref;                     /* per factor: reference eta (keyframe 6, landmark 3) or NULL   */
 };
 
 static void* zalloc(size_t n) { return calloc(n ? n : 1, 1); }
@@ -455,10 +461,15 @@ orc_graph* orc_create(const orc_cam* cam, const orc_params* prm,
     g->linc = zalloc(sizeof(double) * 9 * F);
     g->x0 = zalloc(sizeof(double) * 9 * F);
     g->tlin = zalloc(sizeof(int) * F);
+    g->lin_r2 = zalloc(sizeof(double) * F);
+    g->lin_k = zalloc(sizeof(double) * F);
+    g->hist = zalloc(sizeof(double) * 6 * F);
     for (int f = 0; f < n_obs; ++f) {
         int kk = g->fk[f], m = g->fm[f];
-        orc_linearise(cam, prm, g->Rref + 9 * kk, g->cref + 3 * kk, g->lref + 3 * m, zero6, zero6,
-                      g->z + 2 * f, J, r, &k, g->linA + 81 * f, g->linc + 9 * f);
+        int active = orc_linearise(cam, prm, g->Rref + 9 * kk, g->cref + 3 * kk, g->lref + 3 * m, zero6, zero6,
+                                   g->z + 2 * f, J, r, &k, g->linA + 81 * f, g->linc + 9 * f);
+        g->lin_r2[f] = active ? r[0] * r[0] + r[1] * r[1] : 0.0;
+        g->lin_k[f] = active ? k : 0.0;
     }
     /* b^0 = prior(0), messages zero */
     if (update_beliefs(g, NULL) != 0) {
@@ -475,16 +486,141 @@ void orc_destroy(orc_graph* g)
                      g->Dk, g->Dl,
                      g->kf_lam, g->kf_eta, g->lm_lam, g->lm_eta, g->kf_mu, g->lm_mu,
                      g->mk_lam, g->mk_eta, g->ml_lam, g->ml_eta, g->nk_lam, g->nk_eta, g->nl_lam, g->nl_eta,
-                     g->linA, g->linc, g->x0, g->tlin };
+                     g->linA, g->linc, g->x0, g->tlin, g->lin_r2, g->lin_k, g->hist, g->net, g->eta_ref };
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(g);
 }
 
-int orc_iterate(orc_graph* g, int n, double* max_dmu)
+/* ------------------------------------------------------------------------
+ * learned damping (no counterpart in the paper: it replaces the fixed d of
+ * Sec. 5 / Sec. 8 by a per-factor prediction)
+ * ---------------------------------------------------------------------- */
+
+double orc_net_forward(const double* P, const double x[ORC_NET_NFEAT])
+{
+    const double *W1 = P, *b1 = P + 1024, *W2 = P + 1088, *b2 = P + 5184, *W3 = P + 5248, b3 = P[5312];
+    double h1[64], h2[64];
+    for (int j = 0; j < 64; ++j) {
+        double s = b1[j];
+        for (int i = 0; i < ORC_NET_NFEAT; ++i) s += x[i] * W1[i * 64 + j];
+        h1[j] = s > 0.0 ? s : 0.0;
+    }
+    for (int j = 0; j < 64; ++j) {
+        double s = b2[j];
+        for (int i = 0; i < 64; ++i) s += h1[i] * W2[i * 64 + j];
+        h2[j] = s > 0.0 ? s : 0.0;
+    }
+    double z = b3;
+    for (int j = 0; j < 64; ++j) z += h2[j] * W3[j];
+    return 0.9 / (1.0 + exp(-z));
+}
+
+static double norm_n(const double* a, int n)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += a[i] * a[i];
+    return sqrt(s);
+}
+
+/* |new - old| / (|new| + |old|): 0 for an unchanged message, 1 for a new one */
+static double rel_change(const double* nw, const double* old, int n)
+{
+    double d[6];
+    for (int i = 0; i < n; ++i) d[i] = nw[i] - old[i];
+    return norm_n(d, n) / (norm_n(nw, n) + norm_n(old, n) + 1e-30);
+}
+
+/* The damping d in [0, 0.9] that brings (1 - d) new + d old closest to ref:
+ * the least-squares step along old - new, clipped.  *valid = 0 when
+ * old = new (up to 1e-10 of their squared norms), where d is arbitrary. */
+static double best_damping(const double* nw, const double* old, const double* ref, int n, int* valid)
+{
+    double uu = 0.0, uv = 0.0, nn = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double u = old[i] - nw[i];
+        uu += u * u;
+        uv += u * (ref[i] - nw[i]);
+        nn += nw[i] * nw[i] + old[i] * old[i];
+    }
+    *valid = uu > 1e-10 * nn && uu > 0.0;
+    if (!*valid) return 0.0;
+    double d = uv / uu;
+    return d < 0.0 ? 0.0 : (d > 0.9 ? 0.9 : d);
+}
+
+static double trace_n(const double* A, int n)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += A[i * n + i];
+    return s;
+}
+
+/* The 16 features of factor f, from this iteration's undamped new messages
+ * (nk_*, nl_*), the previous messages (mk_*, ml_*), the beliefs b^t and the
+ * stored history; then the history moves one step. */
+static void factor_features(orc_graph* g, int f, const int* deg_k, const int* deg_l, double* x)
+{
+    int kk = g->fk[f], m = g->fm[f];
+    double Pk[36], Pm[9];
+    for (int i = 0; i < 36; ++i) Pk[i] = g->kf_lam[36 * kk + i] - g->mk_lam[36 * f + i];
+    for (int i = 0; i < 9; ++i) Pm[i] = g->lm_lam[9 * m + i] - g->ml_lam[9 * f + i];
+    double tlk = trace_n(g->nk_lam + 36 * f, 6), tlm = trace_n(g->nl_lam + 9 * f, 3);
+    double M = sqrt(g->lin_r2[f]) / g->prm.sigma_px;
+    double ck = rel_change(g->nk_eta + 6 * f, g->mk_eta + 6 * f, 6);
+    double cm = rel_change(g->nl_eta + 3 * f, g->ml_eta + 3 * f, 3);
+    double* h = g->hist + 6 * f;
+    int dt_lin = g->t - g->tlin[f], dt_birth = g->t - g->lm_birth[m];
+    x[0] = log1p(M) / 3.0;
+    x[1] = g->lin_k[f];
+    x[2] = tlk / (tlk + trace_n(Pk, 6) + 1e-30);
+    x[3] = tlm / (tlm + trace_n(Pm, 3) + 1e-30);
+    x[4] = ck;   x[5] = h[0];  x[6] = h[1];  x[7] = h[2];
+    x[8] = cm;   x[9] = h[3];  x[10] = h[4]; x[11] = h[5];
+    x[12] = log1p((double)deg_k[kk]) / 5.0;
+    x[13] = log1p((double)deg_l[m]) / 3.0;
+    x[14] = (dt_lin < 50 ? dt_lin : 50) / 50.0;
+    x[15] = (dt_birth < 50 ? dt_birth : 50) / 50.0;
+    h[2] = h[1]; h[1] = h[0]; h[0] = ck;
+    h[5] = h[4]; h[4] = h[3]; h[3] = cm;
+}
+
+int orc_set_damping_net(orc_graph* g, const double* params)
+{
+    free(g->net);
+    g->net = NULL;
+    if (!params) return 0;
+    for (int i = 0; i < ORC_NET_NPARAM; ++i)
+        if (!isfinite(params[i])) return -1;
+    g->net = malloc(sizeof(double) * ORC_NET_NPARAM);
+    memcpy(g->net, params, sizeof(double) * ORC_NET_NPARAM);
+    return 0;
+}
+
+void orc_set_reference_messages(orc_graph* g, const double* eta_ref)
+{
+    free(g->eta_ref);
+    g->eta_ref = NULL;
+    if (!eta_ref) return;
+    g->eta_ref = zalloc(sizeof(double) * 9 * (size_t)g->n_f);
+    memcpy(g->eta_ref, eta_ref, sizeof(double) * 9 * (size_t)g->n_f);
+}
+
+/* mode 0: the fixed schedule; 1: learned d_f (needs a network); 2: fixed
+ * schedule, recording features into X (n x n_f x 16) and damping targets
+ * toward eta_ref into T (n x n_f; -1 where the learned schedule does not
+ * damp or the message did not change). */
+static int iterate_impl(orc_graph* g, int n, double* max_dmu, int mode, double* X, double* T)
 {
     double J[18], r[2], k;
     double lam_in[36], eta_in[6];
-    for (int it = 0; it < n; ++it) {
+    int *deg_k = NULL, *deg_l = NULL;
+    if (mode != 0) {
+        deg_k = zalloc(sizeof(int) * (size_t)g->n_kf);
+        deg_l = zalloc(sizeof(int) * (size_t)g->n_lm);
+        for (int f = 0; f < g->n_f; ++f) { deg_k[g->fk[f]]++; deg_l[g->fm[f]]++; }
+    }
+    int status = 0;
+    for (int it = 0; it < n && status == 0; ++it) {
         for (int f = 0; f < g->n_f; ++f) {
             int kk = g->fk[f], m = g->fm[f];
             double* x0 = g->x0 + 9 * f;
@@ -496,9 +632,11 @@ int orc_iterate(orc_graph* g, int n, double* max_dmu)
                 for (int i = 0; i < 6; ++i) dist2 += (g->kf_mu[6 * kk + i] - x0[i]) * (g->kf_mu[6 * kk + i] - x0[i]);
                 for (int i = 0; i < 3; ++i) dist2 += (g->lm_mu[3 * m + i] - x0[6 + i]) * (g->lm_mu[3 * m + i] - x0[6 + i]);
                 if (sqrt(dist2) > g->prm.relin_beta) {
-                    orc_linearise(&g->cam, &g->prm, g->Rref + 9 * kk, g->cref + 3 * kk, g->lref + 3 * m,
-                                  g->kf_mu + 6 * kk, g->lm_mu + 3 * m, g->z + 2 * f, J, r, &k,
-                                  g->linA + 81 * f, g->linc + 9 * f);
+                    int active = orc_linearise(&g->cam, &g->prm, g->Rref + 9 * kk, g->cref + 3 * kk, g->lref + 3 * m,
+                                               g->kf_mu + 6 * kk, g->lm_mu + 3 * m, g->z + 2 * f, J, r, &k,
+                                               g->linA + 81 * f, g->linc + 9 * f);
+                    g->lin_r2[f] = active ? r[0] * r[0] + r[1] * r[1] : 0.0;
+                    g->lin_k[f] = active ? k : 0.0;
                     for (int i = 0; i < 6; ++i) x0[i] = g->kf_mu[6 * kk + i];
                     for (int i = 0; i < 3; ++i) x0[6 + i] = g->lm_mu[3 * m + i];
                     g->tlin[f] = g->t;
@@ -511,22 +649,42 @@ int orc_iterate(orc_graph* g, int n, double* max_dmu)
              * previous message to it is the variable-to-factor message */
             for (int i = 0; i < 9; ++i) lam_in[i] = g->lm_lam[9 * m + i] - g->ml_lam[9 * f + i];
             for (int i = 0; i < 3; ++i) eta_in[i] = g->lm_eta[3 * m + i] - g->ml_eta[3 * f + i];
-            if (orc_factor_message(A, c, 0, lam_in, eta_in, g->nk_lam + 36 * f, g->nk_eta + 6 * f) != 0) return -1;
+            if (orc_factor_message(A, c, 0, lam_in, eta_in, g->nk_lam + 36 * f, g->nk_eta + 6 * f) != 0) { status = -1; break; }
             /* to the landmark */
             for (int i = 0; i < 36; ++i) lam_in[i] = g->kf_lam[36 * kk + i] - g->mk_lam[36 * f + i];
             for (int i = 0; i < 6; ++i) eta_in[i] = g->kf_eta[6 * kk + i] - g->mk_eta[6 * f + i];
-            if (orc_factor_message(A, c, 1, lam_in, eta_in, g->nl_lam + 9 * f, g->nl_eta + 3 * f) != 0) return -1;
-            /* damping of the eta update (Sec. 5).  Messages stay undamped for
-             * undamped_iters iterations after a (re)linearisation (Sec. 8);
-             * the message sent in the iteration of a (re)linearisation --
-             * including a factor's first message -- is never damped. */
-            int hold = g->prm.undamped_iters > 1 ? g->prm.undamped_iters : 1;
-            if (g->t - g->tlin[f] >= hold) {
-                double d = g->prm.damping;
+            if (orc_factor_message(A, c, 1, lam_in, eta_in, g->nl_lam + 9 * f, g->nl_eta + 3 * f) != 0) { status = -1; break; }
+            /* damping of the eta update (Sec. 5).  Fixed schedule: messages
+             * stay undamped for undamped_iters iterations after a
+             * (re)linearisation (Sec. 8); the message sent in the iteration of
+             * a (re)linearisation -- including a factor's first message -- is
+             * never damped.  Learned schedule: d_f from the network whenever
+             * t > t_lin. */
+            double feat[ORC_NET_NFEAT];
+            if (mode != 0) factor_features(g, f, deg_k, deg_l, feat);
+            if (mode == 2) {
+                double* xo = X + ((size_t)it * g->n_f + f) * ORC_NET_NFEAT;
+                for (int j = 0; j < ORC_NET_NFEAT; ++j) xo[j] = feat[j];
+                int vk, vm;
+                double dk = best_damping(g->nk_eta + 6 * f, g->mk_eta + 6 * f, g->eta_ref + 9 * f, 6, &vk);
+                double dm = best_damping(g->nl_eta + 3 * f, g->ml_eta + 3 * f, g->eta_ref + 9 * f + 6, 3, &vm);
+                double target = (vk || vm) ? (vk * dk + vm * dm) / (vk + vm) : -1.0;
+                if (g->t == g->tlin[f] || !(g->lin_k[f] > 0.0)) target = -1.0;
+                T[(size_t)it * g->n_f + f] = target;
+            }
+            double d = -1.0;
+            if (mode == 1) {
+                if (g->t > g->tlin[f]) d = orc_net_forward(g->net, feat);
+            } else {
+                int hold = g->prm.undamped_iters > 1 ? g->prm.undamped_iters : 1;
+                if (g->t - g->tlin[f] >= hold) d = g->prm.damping;
+            }
+            if (d >= 0.0) {
                 for (int i = 0; i < 6; ++i) g->nk_eta[6 * f + i] = (1.0 - d) * g->nk_eta[6 * f + i] + d * g->mk_eta[6 * f + i];
                 for (int i = 0; i < 3; ++i) g->nl_eta[3 * f + i] = (1.0 - d) * g->nl_eta[3 * f + i] + d * g->ml_eta[3 * f + i];
             }
         }
+        if (status != 0) break;
         /* synchronous schedule: every factor used m^t; now m^{t+1} replaces it */
         double* tmp;
         tmp = g->mk_lam; g->mk_lam = g->nk_lam; g->nk_lam = tmp;
@@ -534,9 +692,23 @@ int orc_iterate(orc_graph* g, int n, double* max_dmu)
         tmp = g->ml_lam; g->ml_lam = g->nl_lam; g->nl_lam = tmp;
         tmp = g->ml_eta; g->ml_eta = g->nl_eta; g->nl_eta = tmp;
         g->t += 1;
-        if (update_beliefs(g, max_dmu) != 0) return -1;
+        if (update_beliefs(g, max_dmu) != 0) status = -1;
     }
-    return 0;
+    free(deg_k);
+    free(deg_l);
+    return status;
+}
+
+int orc_iterate(orc_graph* g, int n, double* max_dmu)
+{
+    if (g->net) return iterate_impl(g, n, max_dmu, 1, NULL, NULL);
+    return iterate_impl(g, n, max_dmu, 0, NULL, NULL);
+}
+
+int orc_iterate_record(orc_graph* g, int n, double* X, double* T)
+{
+    if (!g->eta_ref || !X || !T) return -2;
+    return iterate_impl(g, n, NULL, 2, X, T);
 }
 
 int orc_iterations_done(const orc_graph* g) { return g->t; }
@@ -703,7 +875,10 @@ int orc_add_keyframe(orc_graph* g, const double* kf_Rt_init, int n_new_lm, const
     GROW(g->ml_eta, 3 * d, F0, F1); GROW(g->nk_lam, 36 * d, F0, F1); GROW(g->nk_eta, 6 * d, F0, F1);
     GROW(g->nl_lam, 9 * d, F0, F1); GROW(g->nl_eta, 3 * d, F0, F1); GROW(g->linA, 81 * d, F0, F1);
     GROW(g->linc, 9 * d, F0, F1); GROW(g->x0, 9 * d, F0, F1); GROW(g->tlin, sizeof(int), F0, F1);
+    GROW(g->lin_r2, d, F0, F1); GROW(g->lin_k, d, F0, F1); GROW(g->hist, 6 * d, F0, F1);
 #undef GROW
+    free(g->eta_ref);   /* the reference covered the old factors only */
+    g->eta_ref = NULL;
 
     /* references of the new variables = their initial values */
     for (int i = 0; i < 9; ++i) g->Rref[9 * K0 + i] = Rt[i];
@@ -744,8 +919,10 @@ int orc_add_keyframe(orc_graph* g, const double* kf_Rt_init, int n_new_lm, const
         for (int q = 0; q < 6; ++q) x0[q] = g->kf_mu[6 * K0 + q];
         for (int q = 0; q < 3; ++q) x0[6 + q] = g->lm_mu[3 * m + q];
         g->tlin[f] = g->t;
-        orc_linearise(&g->cam, &g->prm, g->Rref + 9 * K0, g->cref + 3 * K0, g->lref + 3 * m, x0, x0 + 6,
-                      g->z + 2 * f, J, r, &k, g->linA + 81 * f, g->linc + 9 * f);
+        int active = orc_linearise(&g->cam, &g->prm, g->Rref + 9 * K0, g->cref + 3 * K0, g->lref + 3 * m, x0,
+                                   x0 + 6, g->z + 2 * f, J, r, &k, g->linA + 81 * f, g->linc + 9 * f);
+        g->lin_r2[f] = active ? r[0] * r[0] + r[1] * r[1] : 0.0;
+        g->lin_k[f] = active ? k : 0.0;
         /* prior of the new variables (Sec. 4 / Sec. 8), from these factors
          * at this point with Huber weight 1 */
         orc_linearise(&g->cam, &p1, g->Rref + 9 * K0, g->cref + 3 * K0, g->lref + 3 * m, x0, x0 + 6,

@@ -6,6 +6,7 @@
 // iteration loop as a CUDA graph, and converts chart means to world poses
 // at the boundary.
 #include "gbp_internal.h"
+#include "gbp_mlp.cuh"
 #include "../../include/gbp.h"
 
 #include <algorithm>
@@ -61,10 +62,12 @@ struct DevState {
     R* kf_bel = nullptr;
     R* lm_bel = nullptr;
     R* prior_s = nullptr;      // prior scale table, prior_anneal_iters + 1 entries
+    float* hist = nullptr;     // learned damping: 6 x n_f message-change history
+    R* eta_inf = nullptr;      // record schedule: 9 x n_f reference messages (gbp_capture_messages)
 
     void release() {
         void* ptrs[] = {z, fk, fm, kf_R, kf_c, lm_ref, kf_off, kf_list, kpos, lm_off, tile_start, big_lm, orphan, kf_birth, lm_birth, kf_D, kf_A, lm_D,
-                        uv_ref, x0, tlin, mk, mk2, ml, kf_bel, lm_bel, prior_s};
+                        uv_ref, x0, tlin, mk, mk2, ml, kf_bel, lm_bel, prior_s, hist, eta_inf};
         for (void* p : ptrs)
             if (p) cudaFree(p);
         *this = DevState<R>();
@@ -125,6 +128,10 @@ struct gbp_graph {
     int tuned_mode = 0;                         // autotuner's choice (1 or 2), 0 = not tuned
     int last_mode = 0;                          // launch mode of the last gbp_iterate()
     int64_t launches = 0;                       // kernels launched (graph replays count their kernels)
+    // learned damping: the graph's own copy of a network's packed weights
+    uint32_t* mlp_frag = nullptr;
+    float* mlp_bias = nullptr;
+    bool has_model = false;
 };
 
 namespace {
@@ -170,6 +177,8 @@ KParams<R> make_kparams(gbp_graph* g) {
     k.damp_hold = std::max(p.undamped_iters, 1);
     k.linear = p.linear;
     k.fallback = p.precision_mode == 0 ? 1 : 0;
+    k.mlp_frag = g->mlp_frag;
+    k.mlp_bias = g->mlp_bias;
     return k;
 }
 
@@ -299,6 +308,7 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
     CK(dev_alloc(&s.ml, 9 * (size_t)nf));
     CK(dev_alloc(&s.kf_bel, (size_t)KBEL * nk));
     CK(dev_alloc(&s.lm_bel, (size_t)LBEL * nl));
+    CK(dev_alloc(&s.hist, 6 * (size_t)std::max(nf, 1)));
     cudaStream_t st = g->stream;
     CK(cudaMemcpyAsync(s.z, zr.data(), sizeof(R) * zr.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.fk, g->fk.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice, st));
@@ -360,6 +370,10 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
     d.lm_bel = s.lm_bel;
     d.kf_bel_out = s.kf_bel;
     d.lm_bel_out = s.lm_bel;
+    d.hist = s.hist;
+    d.eta_inf = nullptr;
+    d.rec_X = nullptr;
+    d.rec_T = nullptr;
     d.ctl = g->ctl;
 
     // priors: per-factor diagonal information at the reference (temporary
@@ -403,6 +417,7 @@ gbp_status reset_state(gbp_graph* g) {
     CK(cudaMemsetAsync(s.ml, 0, sizeof(R) * 9 * nf, st));
     CK(cudaMemsetAsync(s.kf_bel, 0, sizeof(R) * KBEL * g->n_kf, st));
     CK(cudaMemsetAsync(s.lm_bel, 0, sizeof(R) * LBEL * g->n_lm, st));
+    CK(cudaMemsetAsync(s.hist, 0, sizeof(float) * 6 * nf, st));
     int32_t c0[CTL_N] = {0};
     CK(cudaMemcpyAsync(g->ctl, c0, sizeof(c0), cudaMemcpyHostToDevice, st));
     CK(launch_init<R>(s.g, make_kparams<R>(g), st));
@@ -430,7 +445,7 @@ cudaError_t enqueue_iterations(gbp_graph* g, int n, cudaStream_t st) {
     const DevGraph<R>& d = state<R>(g).g;
     KParams<R> kp = make_kparams<R>(g);
     for (int i = 0; i < n; ++i) {
-        cudaError_t e = launch_factor<R>(d, kp, st);
+        cudaError_t e = launch_factor<R>(d, kp, st, g->prm.damping_mode);
         if (e != cudaSuccess) return e;
         e = launch_belief<R>(d, kp, st);
         if (e != cudaSuccess) return e;
@@ -493,6 +508,7 @@ gbp_status check_params(const gbp_params* p, std::string& why) {
     if (p->check_every < 1) { why = "check_every must be >= 1"; return GBP_EINVAL; }
     if (p->precision_mode < 0 || p->precision_mode > 2) { why = "precision_mode must be 0, 1 or 2"; return GBP_EINVAL; }
     if (p->launch_mode < 0 || p->launch_mode > 2) { why = "launch_mode must be 0, 1 or 2"; return GBP_EINVAL; }
+    if (p->damping_mode < 0 || p->damping_mode > 1) { why = "damping_mode must be 0 or 1"; return GBP_EINVAL; }
     if (!(p->conv_tol >= 0.0f)) { why = "conv_tol must be >= 0"; return GBP_EINVAL; }
     return GBP_OK;
 }
@@ -632,11 +648,12 @@ gbp_status iterate_phases(gbp_graph* g, int n, float conv_tol, int* done_out) {
 // One cooperative launch for all n iterations; the convergence test (same
 // cadence as above) runs on the device.
 gbp_status iterate_persistent(gbp_graph* g, int n, float conv_tol, int* done_out) {
-    const int grid = g->storage ? persistent_grid<double>(g->sd.g) : persistent_grid<float>(g->sf.g);
+    const int dm = g->prm.damping_mode;
+    const int grid = g->storage ? persistent_grid<double>(g->sd.g, dm) : persistent_grid<float>(g->sf.g, dm);
     if (grid <= 0) return fail(g, GBP_ECUDA, "persistent launch: occupancy query failed");
     cudaError_t e = g->storage
-        ? launch_persistent<double>(g->sd.g, make_kparams<double>(g), n, conv_tol, g->prm.check_every, grid, g->stream)
-        : launch_persistent<float>(g->sf.g, make_kparams<float>(g), n, conv_tol, g->prm.check_every, grid, g->stream);
+        ? launch_persistent<double>(g->sd.g, make_kparams<double>(g), n, conv_tol, g->prm.check_every, grid, g->stream, dm)
+        : launch_persistent<float>(g->sf.g, make_kparams<float>(g), n, conv_tol, g->prm.check_every, grid, g->stream, dm);
     if (e != cudaSuccess) return cuda_fail(g, e, "cooperative launch");
     g->launches += 1;
     if (conv_tol > 0.0f) {
@@ -656,7 +673,7 @@ std::vector<std::pair<void*, size_t>> state_buffers(gbp_graph* g) {
     return {{s.x0, sizeof(R) * 9 * nf},        {s.tlin, sizeof(int32_t) * nf},   {s.mk, sizeof(R) * KREC * nf},
             {s.mk2, sizeof(R) * KREC * nf},
             {s.ml, sizeof(R) * 9 * nf},        {s.kf_bel, sizeof(R) * KBEL * nk}, {s.lm_bel, sizeof(R) * LBEL * nl},
-            {g->ctl, sizeof(int32_t) * CTL_N}};
+            {s.hist, sizeof(float) * 6 * nf}, {g->ctl, sizeof(int32_t) * CTL_N}};
 }
 
 // Slot of every factor's keyframe message: its position in the keyframe's
@@ -683,6 +700,7 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
     std::vector<int32_t> ctl(CTL_N), tlin(F0);
     std::vector<R> x0(9 * (size_t)F0), mk((size_t)KREC * F0), ml(9 * (size_t)F0), kb((size_t)KBEL * K0),
         lb((size_t)LBEL * L0), kD(6 * (size_t)K0), kA(6 * (size_t)K0), lD(3 * (size_t)L0);
+    std::vector<float> hist(6 * (size_t)F0);
     {
         DevState<R>& s = state<R>(g);
         CK(cudaMemcpyAsync(ctl.data(), g->ctl, sizeof(int32_t) * CTL_N, cudaMemcpyDeviceToHost, st));
@@ -692,6 +710,7 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
         CK(cudaMemcpyAsync(tlin.data(), s.tlin, sizeof(int32_t) * tlin.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(mk.data(), mk_cur, sizeof(R) * mk.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(ml.data(), s.ml, sizeof(R) * ml.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hist.data(), s.hist, sizeof(float) * hist.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(kb.data(), s.kf_bel, sizeof(R) * kb.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(lb.data(), s.lm_bel, sizeof(R) * lb.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(kD.data(), s.kf_D, sizeof(R) * kD.size(), cudaMemcpyDeviceToHost, st));
@@ -773,6 +792,7 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
     // linearisation points in the new order: old factors keep theirs, new
     // ones take the current means (a new variable's mean is 0 in its chart)
     std::vector<R> x0n(9 * (size_t)F1), mln(9 * (size_t)F1, R(0)), mkn((size_t)KREC * F1, R(0));
+    std::vector<float> histn(6 * (size_t)F1, 0.0f);
     std::vector<int32_t> tlinn(F1);
     std::vector<int32_t> kpos = keyframe_slots(g->fk, K1);
     for (int f = 0; f < F1; ++f) {
@@ -784,6 +804,7 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
                 mln[(size_t)i * F1 + f] = ml[(size_t)i * F0 + of];
             }
             tlinn[f] = tlin[of];
+            for (int j = 0; j < 6; ++j) histn[(size_t)j * F1 + f] = hist[(size_t)j * F0 + of];
             std::copy(&mk[(size_t)KREC * old_kpos[of]], &mk[(size_t)KREC * old_kpos[of]] + KREC,
                       &mkn[(size_t)KREC * kpos[f]]);
         } else {
@@ -822,12 +843,31 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
     CK(cudaMemcpyAsync(s.kf_A, kAn.data(), sizeof(R) * kAn.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.tlin, tlinn.data(), sizeof(int32_t) * tlinn.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.ml, mln.data(), sizeof(R) * mln.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.hist, histn.data(), sizeof(float) * histn.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(mk_cur, mkn.data(), sizeof(R) * mkn.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(mk_other, 0, sizeof(R) * mkn.size(), st));
     CK(cudaMemcpyAsync(s.kf_bel, kbn.data(), sizeof(R) * kbn.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.lm_bel, lbn.data(), sizeof(R) * lbn.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(g->ctl, ctl.data(), sizeof(int32_t) * CTL_N, cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
+    return GBP_OK;
+}
+
+// Record schedule: n iterations with the fixed damping schedule, one launch
+// per phase, each writing its n_f feature rows and damping targets.
+template <typename R>
+gbp_status record_iterations(gbp_graph* g, int n, float* X, float* T) {
+    DevState<R>& s = state<R>(g);
+    DevGraph<R> d = s.g;
+    d.eta_inf = s.eta_inf;
+    const KParams<R> kp = make_kparams<R>(g);
+    for (int i = 0; i < n; ++i) {
+        d.rec_X = X + (size_t)i * g->n_f * N_FEAT;
+        d.rec_T = T + (size_t)i * g->n_f;
+        CK(launch_factor<R>(d, kp, g->stream, DAMP_RECORD));
+        CK(launch_belief<R>(d, kp, g->stream));
+    }
+    g->launches += 2 * (int64_t)n;
     return GBP_OK;
 }
 
@@ -855,6 +895,7 @@ void gbp_default_params(gbp_params* p) {
     p->precision_mode = 0;
     p->linear = 0;
     p->launch_mode = 0;
+    p->damping_mode = 0;
 }
 
 const char* gbp_status_string(gbp_status s) {
@@ -1065,7 +1106,7 @@ gbp_status gbp_set_params(gbp_graph* g, const gbp_params* p) {
     std::string why;
     if (check_params(p, why) != GBP_OK) return fail(g, GBP_EINVAL, why);
     bool sigma_changed = p->sigma_px != g->prm.sigma_px;
-    if (p->precision_mode != g->prm.precision_mode) g->tuned_mode = 0;
+    if (p->precision_mode != g->prm.precision_mode || p->damping_mode != g->prm.damping_mode) g->tuned_mode = 0;
     g->prm = *p;
     destroy_exec(g);
     (void)sigma_changed;   // priors are stored at sigma = 1 and scaled in the kernels
@@ -1104,6 +1145,8 @@ gbp_status gbp_iterate(gbp_graph* g, int32_t n_iters, int32_t* iters_done) {
     if (st != GBP_OK) return st;
     int n = n_iters > 0 ? n_iters : g->prm.iterations;
     if (g->n_f == 0 && g->n_kf == 0 && g->n_lm == 0) return GBP_OK;
+    if (g->prm.damping_mode == 1 && !g->has_model)
+        return fail(g, GBP_ESTATE, "damping_mode 1 needs a network (gbp_set_damping_model)");
     int mode = g->prm.launch_mode;
     if (mode == 0) {
         if (!g->tuned_mode) {
@@ -1233,6 +1276,8 @@ gbp_status gbp_profile_iterations(gbp_graph* g, int32_t n_iters, double* ms_out)
     if (!g || !ms_out || n_iters <= 0) return GBP_EINVAL;
     gbp_status st = ensure_built(g);
     if (st != GBP_OK) return st;
+    if (g->prm.damping_mode == 1 && !g->has_model)
+        return fail(g, GBP_ESTATE, "damping_mode 1 needs a network (gbp_set_damping_model)");
     int mode = g->prm.launch_mode ? g->prm.launch_mode : (g->tuned_mode ? g->tuned_mode : 2);
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaError_t e = cudaSuccess;
@@ -1276,7 +1321,8 @@ gbp_status gbp_profile_iterations(gbp_graph* g, int32_t n_iters, double* ms_out)
         if (e == cudaSuccess) {
             cudaError_t le = cudaSuccess;
             for (int i = 0; i < n_iters && le == cudaSuccess; ++i)
-                le = g->storage ? launch_factor<double>(pd, kd_, g->capture) : launch_factor<float>(pf, kf_, g->capture);
+                le = g->storage ? launch_factor<double>(pd, kd_, g->capture, g->prm.damping_mode)
+                                : launch_factor<float>(pf, kf_, g->capture, g->prm.damping_mode);
             e = cudaStreamEndCapture(g->capture, &graph);
             if (le != cudaSuccess) e = le;
         }
@@ -1309,6 +1355,8 @@ gbp_status gbp_autotune(gbp_graph* g, int32_t n_trial, int32_t* chosen, double* 
     if (!g || n_trial <= 0) return GBP_EINVAL;
     gbp_status st = ensure_built(g);
     if (st != GBP_OK) return st;
+    if (g->prm.damping_mode == 1 && !g->has_model)
+        return fail(g, GBP_ESTATE, "damping_mode 1 needs a network (gbp_set_damping_model)");
     auto bufs = g->storage ? state_buffers<double>(g) : state_buffers<float>(g);
     std::vector<void*> snap(bufs.size(), nullptr);
     cudaError_t e = cudaSuccess;
@@ -1403,7 +1451,65 @@ void gbp_destroy_graph(gbp_graph* g) {
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
     if (g->h_met) cudaFreeHost(g->h_met);
     if (g->capture) cudaStreamDestroy(g->capture);
+    if (g->mlp_frag) cudaFree(g->mlp_frag);
+    if (g->mlp_bias) cudaFree(g->mlp_bias);
     delete g;
+}
+
+gbp_status gbp_set_damping_model(gbp_graph* g, const gbp_mlp* net) {
+    if (!g) return GBP_EINVAL;
+    if (!net) {
+        g->has_model = false;
+        return GBP_OK;
+    }
+    if (!g->mlp_frag) {
+        destroy_exec(g);   // captured launches hold the (so far null) weight pointers
+        CK(dev_alloc(&g->mlp_frag, FWD_FRAG_WORDS));
+        CK(dev_alloc(&g->mlp_bias, MLP_BIAS_WORDS));
+    }
+    CK(mlp_copy_packed(net, g->mlp_frag, g->mlp_bias, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    g->has_model = true;
+    return GBP_OK;
+}
+
+gbp_status gbp_get_factor_order(const gbp_graph* g, int32_t* obs_index) {
+    if (!g || (g->n_f && !obs_index)) return GBP_EINVAL;
+    std::copy(g->obs_index.begin(), g->obs_index.end(), obs_index);
+    return GBP_OK;
+}
+
+gbp_status gbp_capture_messages(gbp_graph* g) {
+    if (!g) return GBP_EINVAL;
+    gbp_status st = ensure_built(g);
+    if (st != GBP_OK) return st;
+    st = read_ctl(g);
+    if (st != GBP_OK) return st;
+    const int t = g->h_ctl[CTL_ITER];
+    const size_t n = 9 * (size_t)std::max(g->n_f, 1);
+    if (g->storage) {
+        if (!g->sd.eta_inf) CK(dev_alloc(&g->sd.eta_inf, n));
+        CK(launch_capture_messages<double>(g->sd.g, t, g->sd.eta_inf, g->stream));
+    } else {
+        if (!g->sf.eta_inf) CK(dev_alloc(&g->sf.eta_inf, n));
+        CK(launch_capture_messages<float>(g->sf.g, t, g->sf.eta_inf, g->stream));
+    }
+    g->launches += 1;
+    CK(cudaStreamSynchronize(g->stream));
+    return GBP_OK;
+}
+
+gbp_status gbp_record_iterations(gbp_graph* g, int32_t n_iters, float* X, float* target) {
+    if (!g || n_iters < 0) return GBP_EINVAL;
+    if (n_iters > 0 && g->n_f > 0 && (!X || !target)) return GBP_EINVAL;
+    if (reinterpret_cast<uintptr_t>(X) % 16 != 0) return fail(g, GBP_EINVAL, "X must be 16-byte aligned");
+    gbp_status st = ensure_built(g);
+    if (st != GBP_OK) return st;
+    if (!(g->storage ? (void*)g->sd.eta_inf : (void*)g->sf.eta_inf))
+        return fail(g, GBP_ESTATE, "no reference messages: call gbp_capture_messages first");
+    st = g->storage ? record_iterations<double>(g, n_iters, X, target) : record_iterations<float>(g, n_iters, X, target);
+    if (st != GBP_OK) return st;
+    return read_ctl(g);
 }
 
 }  // extern "C"

@@ -17,6 +17,8 @@
 //                                Lambda (21), eta (6), mu (6), pad
 //   per landmark:         lref (3 double), prior diagonal (3), belief record
 //                         LBEL Real: Lambda (6), eta (3), mu (3)
+//   per factor, learned damping: hist -- relative message changes of the
+//                                last 3 iterations, float SoA (6 x n_f)
 //   CSR keyframe -> factor list (kf_off, kf_list); landmark -> contiguous
 //   factor range (lm_off), since factors are sorted by landmark; warp tiles
 //   of whole landmarks (tile_start); per-variable arrival counters.
@@ -24,6 +26,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+struct gbp_mlp;
 
 namespace gbp {
 
@@ -50,7 +54,18 @@ struct KParams {
     int32_t damp_hold;        // damping applies when t - tlin >= damp_hold (>= 1)
     int32_t linear;
     int32_t fallback;         // FP32 path: redo ill-conditioned factorisations in FP64
+    // learned damping (network weights packed by gbp_mlp.cu)
+    const uint32_t* mlp_frag; // BF16 B-operand fragments of layers 1-3
+    const float* mlp_bias;    // b1 (64), b2 (64), b3, pad, W3 (64)
 };
+
+// Damping schedules (kernel template argument).
+enum DampMode : int {
+    DAMP_FIXED = 0,    // d of Sec. 5 after the undamped hold of Sec. 8
+    DAMP_LEARNED = 1,  // per-factor d from the network, from the second iteration after a (re)linearisation
+    DAMP_RECORD = 2    // fixed schedule; features and damping targets written to rec_X / rec_T
+};
+constexpr int N_FEAT = 16;
 
 template <typename R>
 struct DevGraph {
@@ -88,6 +103,11 @@ struct DevGraph {
     R* lm_bel;                // n_lm x LBEL  (read as b^t)
     R* kf_bel_out;            // where b^{t+1} is written (normally == kf_bel)
     R* lm_bel_out;            // (normally == lm_bel)
+    // learned damping
+    float* hist;              // 6 x n_f: relative message change of the last 3 iterations (kf side, lm side)
+    const R* eta_inf;         // record: 9 x n_f reference messages eta (kf side 6, lm side 3)
+    float* rec_X;             // record: n_f x 16 features of the current iteration
+    float* rec_T;             // record: n_f damping targets (-1: a sample the learned schedule never uses)
     // control block
     int32_t* ctl;             // see Ctl
 };
@@ -116,12 +136,15 @@ constexpr int FACTOR_BLOCK = 128;   // 4 warps per block (every kernel of the it
 constexpr int METRIC_BLOCK = 256;
 
 // kernel launchers (gbp_kernels.cu)
-template <typename R> cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s);
+template <typename R> cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s,
+                                                int mode = DAMP_FIXED);
 template <typename R> cudaError_t launch_init(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s);
 template <typename R> cudaError_t launch_belief(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s);
-template <typename R> int persistent_grid(const DevGraph<R>& g);   // co-resident blocks to use; 0 on error
+template <typename R> int persistent_grid(const DevGraph<R>& g, int mode);   // co-resident blocks; 0 on error
 template <typename R> cudaError_t launch_persistent(const DevGraph<R>& g, const KParams<R>& p, int n_iters,
-                                                    float conv_tol, int check_every, int grid, cudaStream_t s);
+                                                    float conv_tol, int check_every, int grid, cudaStream_t s,
+                                                    int mode);
+template <typename R> cudaError_t launch_capture_messages(const DevGraph<R>& g, int t, R* eta_inf, cudaStream_t s);
 template <typename R> cudaError_t launch_prior(const DevGraph<R>& g, const KParams<R>& p, R* tmp_k, R* tmp_l,
                                                R* kf_D, R* lm_D, cudaStream_t s);
 template <typename R> cudaError_t launch_metrics(const DevGraph<R>& g, const KParams<R>& p, double* partials,
@@ -130,5 +153,10 @@ template <typename R> cudaError_t launch_problem_metrics(const DevGraph<R>& g, c
                                                          const int32_t* prob_f0, int n_problems, double* out,
                                                          cudaStream_t s);
 int metrics_blocks(int n_f);
+
+// damping network (gbp_mlp.cu): device-to-device copy of a network's packed
+// forward weights (FWD_FRAG_WORDS words, MLP_BIAS_WORDS floats), ordered
+// after the network's pending work
+cudaError_t mlp_copy_packed(const gbp_mlp* net, uint32_t* frag, float* bias, cudaStream_t s);
 
 }  // namespace gbp

@@ -28,6 +28,7 @@
 // but never subtracts two large matrices, and Q = V^T V with
 // V = L_b^-1 J_b^T (Cholesky P_b = L_b L_b^T) is PSD by construction.
 #include "gbp_internal.h"
+#include "gbp_mlp.cuh"
 
 #include <math.h>
 
@@ -573,6 +574,71 @@ __device__ __forceinline__ void dmu_atomic_max_slot(int32_t* ctl, int slot, floa
 }
 
 // ------------------------------------------------------------------------
+// Learned damping.  Features of factor f at iteration t (all O(1)):
+//   0  log(1 + M) / 3, M = |r| / sigma (Mahalanobis residual, Sec. 6)
+//   1  Huber weight k (Sec. 6; 0 for a factor behind the camera)
+//   2  tr Lambda_{f->k} / (tr Lambda_{f->k} + tr P_k), P_k the keyframe's incoming precision
+//   3  the same for the landmark
+//   4  |eta_new - eta_old| / (|eta_new| + |eta_old|) of the message to the keyframe, this iteration
+//   5-7  the same, the three previous iterations (most recent first)
+//   8-11 the same for the message to the landmark
+//   12 log(1 + deg k) / 5,  13 log(1 + deg m) / 3
+//   14 min(t - t_lin, 50) / 50,  15 min(t - t_birth(m), 50) / 50
+// Target (record mode), per side: the damping that moves the new message
+// closest to a reference message eta_inf (the run's converged message),
+//   d* = clip(<eta_old - eta_new, eta_inf - eta_new> / |eta_old - eta_new|^2, 0, 0.9),
+// averaged over the sides where eta_old != eta_new.
+
+template <typename R, int n>
+__device__ __forceinline__ float rel_change(const R* nw, const R* old) {
+    R dd = R(0), a = R(0), b = R(0);
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        dd += (nw[i] - old[i]) * (nw[i] - old[i]);
+        a += nw[i] * nw[i];
+        b += old[i] * old[i];
+    }
+    return float(sqrt(dd) / (sqrt(a) + sqrt(b) + R(1e-30)));
+}
+
+template <typename R, int n>
+__device__ __forceinline__ float best_damping(const R* nw, const R* old, const R* inf, bool& valid) {
+    R uu = R(0), uv = R(0), nn = R(0);
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        const R u = old[i] - nw[i];
+        uu += u * u;
+        uv += u * (inf[i] - nw[i]);
+        nn += nw[i] * nw[i] + old[i] * old[i];
+    }
+    valid = uu > R(1e-10) * nn && uu > R(0);
+    return valid ? fminf(fmaxf(float(uv / uu), 0.0f), MLP_DMAX) : 0.0f;
+}
+
+// Shared memory of the learned schedule: the network's packed weights and
+// per-warp activation tiles (BF16 bits).
+template <int MODE>
+struct MlpSmem {
+    int unused;
+};
+template <>
+struct MlpSmem<DAMP_LEARNED> {
+    uint32_t frag[FWD_FRAG_WORDS];
+    float bias[MLP_BIAS_WORDS];
+    alignas(16) uint16_t x[FACTOR_BLOCK / 32][32 * XS];
+    alignas(16) uint16_t h[FACTOR_BLOCK / 32][32 * HS];
+};
+
+template <int MODE, typename R>
+__device__ __forceinline__ void mlp_load(const KParams<R>& P, MlpSmem<MODE>& S) {
+    if constexpr (MODE == DAMP_LEARNED) {
+        for (int i = threadIdx.x; i < FWD_FRAG_WORDS; i += blockDim.x) S.frag[i] = P.mlp_frag[i];
+        for (int i = threadIdx.x; i < MLP_BIAS_WORDS; i += blockDim.x) S.bias[i] = P.mlp_bias[i];
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------
 // Phase A: one warp, one tile of whole landmarks (at most 32 factors,
 // consecutive in landmark order), one lane per factor -- relinearisation
 // test, Jacobian, Huber weight, both messages, damping (Sec. 4-6, 8); then
@@ -580,9 +646,13 @@ __device__ __forceinline__ void dmu_atomic_max_slot(int32_t* ctl, int slot, floa
 // warp scan (fixed lane order) and each landmark's last lane forms its
 // belief b^{t+1} and mean (a landmark wholly inside a tile is read by no
 // other warp).  Returns this lane's max |dmu|.
+// MODE selects the damping schedule (DampMode); the learned schedule
+// evaluates the network for the warp's 32 factors at once on the tensor
+// cores, between forming the messages and damping them.
 
-template <typename R>
-__device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R>& P, int tile, int t, int lane) {
+template <typename R, int MODE>
+__device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R>& P, int tile, int t, int lane,
+                                           MlpSmem<MODE>& S) {
     const int n_f = g.n_f;
     const int ts = g.tile_start[tile], te = g.tile_start[tile + 1];
     const int f = ts + lane;
@@ -591,6 +661,15 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
     R sum[9];           // this lane's new landmark message (Lambda 6, eta 3)
     R mu_m_old[3] = {R(0), R(0), R(0)};
     int m = -1, lo = 0, hi = 0;
+    // learned / record schedules: undamped new and previous eta of both
+    // messages, and the features
+    constexpr bool FEAT = MODE != DAMP_FIXED;
+    R ek_new[6], ek_old[6], em_new[3], em_old[3];
+    float feat[N_FEAT];
+#pragma unroll
+    for (int i = 0; i < N_FEAT; ++i) feat[i] = 0.0f;
+    size_t ks_f = 0;
+    int tl_f = 0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) sum[i] = R(0);
 
@@ -679,8 +758,11 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
         Lin<R> L;
         linearise<R>(P, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3, g.lm_ref + (size_t)m * 3, x0,
                      g.z[2 * (size_t)f], g.z[2 * (size_t)f + 1], L);
-        const bool damp = t - tl >= P.damp_hold;
+        const bool damp = MODE != DAMP_LEARNED && t - tl >= P.damp_hold;
         const R d = P.damping;
+        ks_f = ks;
+        tl_f = tl;
+        float tr_pk = 0.0f, tr_pm = 0.0f, tr_lk = 0.0f;
 
         // ---- message to the keyframe: marginalise the landmark ----
         // incoming = landmark belief / this factor's previous message to it
@@ -701,6 +783,7 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
 #pragma unroll
                 for (int i = 0; i < 3; ++i) qm[i] = lb[6 + i] - ml[6 + i];
             }
+            if constexpr (FEAT) tr_pm = float(Pm[0] + Pm[2] + Pm[5]);
             R lam_k[21], eta_k[6], ratio_m;
             bool ok_m = message<R, 6, 3>(Pm, qm, L.Jl, L.Jk, L.y, L.W, lam_k, eta_k, ratio_m);
             if (sizeof(R) == 4 && P.fallback && !ok_m) {
@@ -730,6 +813,15 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
                 for (int i = 0; i < 21; ++i) Pk[i] = kb[i] - mk[i];
 #pragma unroll
                 for (int i = 0; i < 6; ++i) qk[i] = kb[21 + i] - mk[21 + i];
+                if constexpr (FEAT) {
+                    tr_pk = float(Pk[0] + Pk[2] + Pk[5] + Pk[9] + Pk[14] + Pk[20]);
+                    tr_lk = float(lam_k[0] + lam_k[2] + lam_k[5] + lam_k[9] + lam_k[14] + lam_k[20]);
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        ek_new[i] = eta_k[i];
+                        ek_old[i] = mk[21 + i];
+                    }
+                }
                 // damping of eta (Sec. 5); undamped in the iteration of a
                 // (re)linearisation and for the next damp_hold - 1
                 // iterations (Sec. 8)
@@ -766,6 +858,56 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
                 atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
             }
             if (!ok_k) raise_error(g.ctl, -1 - f);
+            if constexpr (FEAT) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    em_new[i] = eta_m[i];
+                    em_old[i] = ml[6 + i];
+                }
+                const float tr_lm = float(lam_m[0] + lam_m[2] + lam_m[5]);
+                const float M = float(sqrt(L.r2) * P.inv_sigma);
+                const float ck = rel_change<R, 6>(ek_new, ek_old);
+                const float cm = rel_change<R, 3>(em_new, em_old);
+                float h[6];
+#pragma unroll
+                for (int j = 0; j < 6; ++j) h[j] = g.hist[(size_t)j * n_f + f];
+                feat[0] = log1pf(M) * (1.0f / 3.0f);
+                feat[1] = float(L.W / P.inv_sigma2);
+                feat[2] = tr_lk / (tr_lk + tr_pk + 1e-30f);
+                feat[3] = tr_lm / (tr_lm + tr_pm + 1e-30f);
+                feat[4] = ck;
+                feat[5] = h[0];
+                feat[6] = h[1];
+                feat[7] = h[2];
+                feat[8] = cm;
+                feat[9] = h[3];
+                feat[10] = h[4];
+                feat[11] = h[5];
+                feat[12] = log1pf(float(g.kf_off[k + 1] - g.kf_off[k])) * 0.2f;
+                feat[13] = log1pf(float(hi - lo)) * (1.0f / 3.0f);
+                feat[14] = float(min(t - tl, 50)) * 0.02f;
+                feat[15] = float(min(t - g.lm_birth[m], 50)) * 0.02f;
+                const float hn[6] = {ck, h[0], h[1], cm, h[3], h[4]};
+#pragma unroll
+                for (int j = 0; j < 6; ++j) g.hist[(size_t)j * n_f + f] = hn[j];
+                if constexpr (MODE == DAMP_RECORD) {
+                    R ik[6], im[3];
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) ik[i] = g.eta_inf[(size_t)i * n_f + f];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) im[i] = g.eta_inf[(size_t)(6 + i) * n_f + f];
+                    bool vk, vm;
+                    const float dk = best_damping<R, 6>(ek_new, ek_old, ik, vk);
+                    const float dm = best_damping<R, 3>(em_new, em_old, im, vm);
+                    float target = (vk || vm) ? (dk * float(vk) + dm * float(vm)) / float(int(vk) + int(vm)) : -1.0f;
+                    if (t == tl || !(L.W > R(0))) target = -1.0f;   // never damped by the learned schedule
+                    float4* xo = reinterpret_cast<float4*>(g.rec_X + (size_t)f * N_FEAT);
+#pragma unroll
+                    for (int j = 0; j < N_FEAT / 4; ++j)
+                        xo[j] = make_float4(feat[4 * j], feat[4 * j + 1], feat[4 * j + 2], feat[4 * j + 3]);
+                    g.rec_T[f] = target;
+                }
+            }
             if (damp) {
 #pragma unroll
                 for (int i = 0; i < 3; ++i) eta_m[i] = (R(1) - d) * eta_m[i] + d * ml[6 + i];
@@ -779,6 +921,35 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
             for (int i = 0; i < 3; ++i) {
                 g.ml_out[(size_t)(6 + i) * n_f + f] = eta_m[i];
                 sum[6 + i] = eta_m[i];
+            }
+        }
+    }
+
+    if constexpr (MODE == DAMP_LEARNED) {
+        // the network for the warp's 32 factors (inactive lanes: zero rows),
+        // then eta damped by each factor's own d; a factor's first message
+        // after a (re)linearisation stays undamped
+        const int w = threadIdx.x >> 5;
+        __nv_bfloat16* xt = reinterpret_cast<__nv_bfloat16*>(S.x[w]);
+        __nv_bfloat16* ht = reinterpret_cast<__nv_bfloat16*>(S.h[w]);
+#pragma unroll
+        for (int j = 0; j < N_FEAT; j += 2) {
+            *reinterpret_cast<uint32_t*>(xt + lane * XS + j) = pack_bf16(feat[j], feat[j + 1]);
+        }
+        __syncwarp();
+        const float z3 = mlp_forward_warp(S.frag, S.bias, xt, ht, nullptr, lane);
+        float dl = mlp_output(z3);
+        if (!(dl >= 0.0f && dl <= MLP_DMAX)) dl = float(P.damping);
+        if (active && t > tl_f) {
+            const R dd = R(dl);
+            R* o = mk_write(g, t) + ks_f;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) o[21 + i] = (R(1) - dd) * ek_new[i] + dd * ek_old[i];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const R e = (R(1) - dd) * em_new[i] + dd * em_old[i];
+                g.ml_out[(size_t)(6 + i) * n_f + f] = e;
+                sum[6 + i] = e;
             }
         }
     }
@@ -888,13 +1059,15 @@ __host__ __device__ inline int phase_b_items(const DevGraph<R>& g) {
 // ------------------------------------------------------------------------
 // Two-kernel iteration (the launch-per-phase path).
 
-template <typename R>
+template <typename R, int MODE>
 __global__ void __launch_bounds__(FACTOR_BLOCK) factor_kernel(DevGraph<R> g, KParams<R> P) {
+    __shared__ __align__(16) MlpSmem<MODE> S;
+    mlp_load<MODE>(P, S);
     const int lane = threadIdx.x & 31;
     const int tile = blockIdx.x * (FACTOR_BLOCK / 32) + (threadIdx.x >> 5);
     if (tile >= g.n_tiles) return;   // uniform per warp
     const int t = g.ctl[CTL_ITER];
-    float dmu = tile_work<R>(g, P, tile, t, lane);
+    float dmu = tile_work<R, MODE>(g, P, tile, t, lane, S);
     dmu = warp_max(dmu);
     if (lane == 0 && dmu > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), dmu);
 }
@@ -966,10 +1139,12 @@ __device__ __forceinline__ bool grid_barrier(int32_t* ctl, int nblocks, int* fla
     return *flag_sh;
 }
 
-template <typename R>
+template <typename R, int MODE>
 __global__ void __launch_bounds__(FACTOR_BLOCK) persistent_kernel(DevGraph<R> g, KParams<R> P, int n_iters,
                                                                     float conv_tol, int check_every) {
     __shared__ int flag_sh;
+    __shared__ __align__(16) MlpSmem<MODE> S;
+    mlp_load<MODE>(P, S);
     constexpr int WPB = FACTOR_BLOCK / 32;
     const int lane = threadIdx.x & 31;
     const int gwarp = blockIdx.x * WPB + (threadIdx.x >> 5);
@@ -984,7 +1159,7 @@ __global__ void __launch_bounds__(FACTOR_BLOCK) persistent_kernel(DevGraph<R> g,
         // phase A: factors and landmarks wholly inside a tile
         float dmu = 0.0f;
         for (int tile = gwarp; tile < g.n_tiles; tile += nwarps)
-            dmu = fmaxf(dmu, tile_work<R>(g, P, tile, t, lane));
+            dmu = fmaxf(dmu, tile_work<R, MODE>(g, P, tile, t, lane, S));
         dmu = warp_max(dmu);
         if (lane == 0 && dmu > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), dmu);
         if (!grid_barrier(g.ctl, nb, &flag_sh)) break;
@@ -1239,10 +1414,16 @@ int metrics_blocks(int n_f) {
 }
 
 template <typename R>
-cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s) {
+cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s, int mode) {
     if (g.n_tiles == 0) return cudaSuccess;
     constexpr int wpb = FACTOR_BLOCK / 32;
-    factor_kernel<R><<<(g.n_tiles + wpb - 1) / wpb, FACTOR_BLOCK, 0, s>>>(g, p);
+    const int blocks = (g.n_tiles + wpb - 1) / wpb;
+    if (mode == DAMP_LEARNED)
+        factor_kernel<R, DAMP_LEARNED><<<blocks, FACTOR_BLOCK, 0, s>>>(g, p);
+    else if (mode == DAMP_RECORD)
+        factor_kernel<R, DAMP_RECORD><<<blocks, FACTOR_BLOCK, 0, s>>>(g, p);
+    else
+        factor_kernel<R, DAMP_FIXED><<<blocks, FACTOR_BLOCK, 0, s>>>(g, p);
     return cudaGetLastError();
 }
 
@@ -1256,12 +1437,14 @@ cudaError_t launch_belief(const DevGraph<R>& g, const KParams<R>& p, cudaStream_
 }
 
 template <typename R>
-int persistent_grid(const DevGraph<R>& g) {
+int persistent_grid(const DevGraph<R>& g, int mode) {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<R>, FACTOR_BLOCK, 0) != cudaSuccess)
-        return 0;
+    cudaError_t e = mode == DAMP_LEARNED
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<R, DAMP_LEARNED>, FACTOR_BLOCK, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<R, DAMP_FIXED>, FACTOR_BLOCK, 0);
+    if (e != cudaSuccess || per_sm <= 0) return 0;
     constexpr int wpb = FACTOR_BLOCK / 32;
     const int cap = sms * per_sm;
     const int want = (std::max(g.n_tiles, phase_b_items(g)) + wpb - 1) / wpb;
@@ -1270,12 +1453,36 @@ int persistent_grid(const DevGraph<R>& g) {
 
 template <typename R>
 cudaError_t launch_persistent(const DevGraph<R>& g, const KParams<R>& p, int n_iters, float conv_tol,
-                              int check_every, int grid, cudaStream_t s) {
+                              int check_every, int grid, cudaStream_t s, int mode) {
     DevGraph<R> gg = g;
     KParams<R> pp = p;
     void* args[] = {&gg, &pp, &n_iters, &conv_tol, &check_every};
-    return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(persistent_kernel<R>), dim3(grid), dim3(FACTOR_BLOCK),
-                                       args, 0, s);
+    void* fn = mode == DAMP_LEARNED ? reinterpret_cast<void*>(persistent_kernel<R, DAMP_LEARNED>)
+                                    : reinterpret_cast<void*>(persistent_kernel<R, DAMP_FIXED>);
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(FACTOR_BLOCK), args, 0, s);
+}
+
+// The current messages' eta in factor order (keyframe side 6, landmark side
+// 3; SoA 9 x n_f): the reference of the record schedule's damping targets.
+template <typename R>
+__global__ void capture_messages_kernel(DevGraph<R> g, const R* __restrict__ mk_cur, R* __restrict__ eta_inf) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= g.n_f) return;
+    const size_t n_f = g.n_f;
+    const R* rec = mk_cur + (size_t)g.kpos[f] * KREC;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) eta_inf[i * n_f + f] = rec[21 + i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) eta_inf[(6 + i) * n_f + f] = g.ml[(6 + i) * n_f + f];
+}
+
+template <typename R>
+cudaError_t launch_capture_messages(const DevGraph<R>& g, int t, R* eta_inf, cudaStream_t s) {
+    if (g.n_f == 0) return cudaSuccess;
+    // after t completed iterations the current messages m^t are in buffer t & 1
+    const R* mk_cur = (t & 1) ? g.mk2 : g.mk;
+    capture_messages_kernel<R><<<(g.n_f + 255) / 256, 256, 0, s>>>(g, mk_cur, eta_inf);
+    return cudaGetLastError();
 }
 
 template <typename R>
@@ -1311,12 +1518,13 @@ cudaError_t launch_problem_metrics(const DevGraph<R>& g, const KParams<R>& p, co
 }
 
 #define GBP_INSTANTIATE(R)                                                                                 \
-    template cudaError_t launch_factor<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t);            \
+    template cudaError_t launch_factor<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t, int);       \
+    template cudaError_t launch_capture_messages<R>(const DevGraph<R>&, int, R*, cudaStream_t);            \
     template cudaError_t launch_init<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t);              \
     template cudaError_t launch_belief<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t);            \
     template cudaError_t launch_problem_metrics<R>(const DevGraph<R>&, const KParams<R>&, const int32_t*, int, double*, cudaStream_t); \
-    template int persistent_grid<R>(const DevGraph<R>&);                                                   \
-    template cudaError_t launch_persistent<R>(const DevGraph<R>&, const KParams<R>&, int, float, int, int, cudaStream_t); \
+    template int persistent_grid<R>(const DevGraph<R>&, int);                                              \
+    template cudaError_t launch_persistent<R>(const DevGraph<R>&, const KParams<R>&, int, float, int, int, cudaStream_t, int); \
     template cudaError_t launch_prior<R>(const DevGraph<R>&, const KParams<R>&, R*, R*, R*, R*, cudaStream_t); \
     template cudaError_t launch_metrics<R>(const DevGraph<R>&, const KParams<R>&, double*, int, double*, cudaStream_t);
 

@@ -41,7 +41,7 @@ class gbp_params(C.Structure):
                 ("anchor_scale", C.c_float), ("z_min", C.c_float), ("relin_beta", C.c_float),
                 ("relin_interval", C.c_int32), ("undamped_iters", C.c_int32),
                 ("fp64_pivot_ratio", C.c_float), ("precision_mode", C.c_int32), ("linear", C.c_int32),
-                ("launch_mode", C.c_int32)]
+                ("launch_mode", C.c_int32), ("damping_mode", C.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -73,7 +73,11 @@ EXPORTS = ["gbp_default_params", "gbp_create_graph", "gbp_set_params", "gbp_get_
            "gbp_reset", "gbp_get_beliefs", "gbp_get_means", "gbp_set_reference", "gbp_add_keyframe",
            "gbp_get_stats", "gbp_get_sizes", "gbp_profile_iterations", "gbp_destroy_graph", "gbp_status_string",
            "gbp_last_error", "gbp_reprojection_error_noalloc", "gbp_autotune", "gbp_create_batch",
-           "gbp_get_batch_info", "gbp_get_problem_are"]
+           "gbp_get_batch_info", "gbp_get_problem_are", "gbp_mlp_create", "gbp_mlp_set_params",
+           "gbp_mlp_get_params", "gbp_mlp_forward", "gbp_mlp_gradient", "gbp_mlp_train_step", "gbp_mlp_destroy",
+           "gbp_set_damping_model", "gbp_capture_messages", "gbp_get_factor_order", "gbp_record_iterations"]
+GBP_MLP_NFEAT = 16
+GBP_MLP_NPARAM = 5313
 GBP_NOALLOC_MAX_OBS = 1 << 20
 
 
@@ -115,6 +119,19 @@ def lib() -> C.CDLL:
     L.gbp_last_error.restype = C.c_char_p
     L.gbp_reprojection_error_noalloc.argtypes = [C.POINTER(gbp_intrinsics), C.c_double, vp, vp, C.c_int32, vp, vp,
                                                  vp, vp, vp]
+    _F = C.POINTER(C.c_float)
+    L.gbp_mlp_create.argtypes = [_F, vp, C.POINTER(vp)]
+    L.gbp_mlp_set_params.argtypes = [vp, _F]
+    L.gbp_mlp_get_params.argtypes = [vp, _F]
+    L.gbp_mlp_forward.argtypes = [vp, vp, C.c_int32, vp]
+    L.gbp_mlp_gradient.argtypes = [vp, vp, vp, C.c_int32, _F, _D]
+    L.gbp_mlp_train_step.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_float, _F]
+    L.gbp_mlp_destroy.argtypes = [vp]
+    L.gbp_mlp_destroy.restype = None
+    L.gbp_set_damping_model.argtypes = [vp, vp]
+    L.gbp_capture_messages.argtypes = [vp]
+    L.gbp_record_iterations.argtypes = [vp, C.c_int32, vp, vp]
+    L.gbp_get_factor_order.argtypes = [vp, _I]
     _lib = L
     return L
 
@@ -309,6 +326,89 @@ def gbp_destroy_graph(g: int) -> None:
         lib().gbp_destroy_graph(g)
 
 
+# --- learned damping network (device arrays are passed as raw pointers) ---
+
+def _f32(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float32).reshape(-1)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def gbp_mlp_create(params, stream=None) -> int:
+    w = _f32(params, GBP_MLP_NPARAM)
+    out = C.c_void_p()
+    _check(lib().gbp_mlp_create(w.ctypes.data_as(C.POINTER(C.c_float)), C.c_void_p(stream or 0), C.byref(out)))
+    return out.value
+
+
+def gbp_mlp_set_params(net: int, params) -> None:
+    w = _f32(params, GBP_MLP_NPARAM)
+    _check(lib().gbp_mlp_set_params(net, w.ctypes.data_as(C.POINTER(C.c_float))))
+
+
+def gbp_mlp_get_params(net: int) -> np.ndarray:
+    w = np.empty(GBP_MLP_NPARAM, dtype=np.float32)
+    _check(lib().gbp_mlp_get_params(net, w.ctypes.data_as(C.POINTER(C.c_float))))
+    return w
+
+
+def gbp_mlp_forward(net: int, X_ptr: int, count: int, y_ptr: int) -> None:
+    """Predictions for ``count`` rows of device features (count x 16 float32)
+    into device ``y`` (count float32); asynchronous."""
+    _check(lib().gbp_mlp_forward(net, X_ptr, int(count), y_ptr))
+
+
+def gbp_mlp_gradient(net: int, X_ptr: int, target_ptr: int, count: int):
+    """(loss, gradient as a float32 vector of GBP_MLP_NPARAM) of the mean
+    squared error over ``count`` device rows."""
+    g = np.empty(GBP_MLP_NPARAM, dtype=np.float32)
+    loss = C.c_double()
+    _check(lib().gbp_mlp_gradient(net, X_ptr, target_ptr, int(count), g.ctypes.data_as(C.POINTER(C.c_float)),
+                                  C.byref(loss)))
+    return loss.value, g
+
+
+def gbp_mlp_train_step(net: int, X_ptr: int, target_ptr: int, idx_ptr, count: int, lr: float,
+                       want_loss: bool = False):
+    """One Adam step on rows ``idx`` (device int32 pointer, or None for rows
+    0..count) of device X / target.  Returns the minibatch loss when
+    ``want_loss`` (synchronising), else None (asynchronous)."""
+    loss = C.c_float()
+    _check(lib().gbp_mlp_train_step(net, X_ptr, target_ptr, idx_ptr or None, int(count), float(lr),
+                                    C.byref(loss) if want_loss else None))
+    return float(loss.value) if want_loss else None
+
+
+def gbp_mlp_destroy(net: int) -> None:
+    if net:
+        lib().gbp_mlp_destroy(net)
+
+
+def gbp_set_damping_model(g: int, net) -> None:
+    """Copy the network's weights into graph ``g`` (``net`` None removes them)."""
+    _check(lib().gbp_set_damping_model(g, net or None), g)
+
+
+def gbp_capture_messages(g: int) -> None:
+    _check(lib().gbp_capture_messages(g), g)
+
+
+def gbp_get_factor_order(g: int) -> np.ndarray:
+    """Caller observation index of each internal factor (the record rows)."""
+    n = gbp_get_sizes(g)[2]
+    out = np.zeros(n, dtype=np.int32)
+    _check(lib().gbp_get_factor_order(g, _ip(out)), g)
+    return out
+
+
+def gbp_record_iterations(g: int, n_iters: int, X_ptr: int, target_ptr: int) -> None:
+    """Run ``n_iters`` iterations with the fixed schedule, writing n_iters x
+    n_obs feature rows (16 float32 each) to device ``X`` and damping targets
+    to device ``target``."""
+    _check(lib().gbp_record_iterations(g, int(n_iters), X_ptr, target_ptr), g)
+
+
 # ---------------------------------------------------------------------------
 
 class Graph:
@@ -370,6 +470,19 @@ class Graph:
     def add_keyframe(self, obs_lm, obs_uv, kf_Rt_init=None, n_new_lm=0, new_lm_xyz=None) -> int:
         return gbp_add_keyframe(self.h, kf_Rt_init, new_lm_xyz, n_new_lm, obs_lm, obs_uv)
 
+    def set_damping_model(self, net):
+        """``net``: a DampingNet (its current weights are copied) or None."""
+        gbp_set_damping_model(self.h, net.h if net is not None else None)
+
+    def capture_messages(self):
+        gbp_capture_messages(self.h)
+
+    def record(self, n_iters: int, X_ptr: int, target_ptr: int):
+        gbp_record_iterations(self.h, n_iters, X_ptr, target_ptr)
+
+    def factor_order(self) -> np.ndarray:
+        return gbp_get_factor_order(self.h)
+
     def close(self):
         if getattr(self, "h", None):
             gbp_destroy_graph(self.h)
@@ -386,3 +499,37 @@ class Graph:
 
     def __exit__(self, *a):
         self.close()
+
+
+class DampingNet:
+    """Owning wrapper around one gbp_mlp handle."""
+
+    def __init__(self, params, stream=None):
+        self.h = gbp_mlp_create(params, stream)
+
+    @property
+    def params(self) -> np.ndarray:
+        return gbp_mlp_get_params(self.h)
+
+    def set_params(self, params):
+        gbp_mlp_set_params(self.h, params)
+
+    def forward(self, X_ptr: int, count: int, y_ptr: int):
+        gbp_mlp_forward(self.h, X_ptr, count, y_ptr)
+
+    def gradient(self, X_ptr: int, target_ptr: int, count: int):
+        return gbp_mlp_gradient(self.h, X_ptr, target_ptr, count)
+
+    def train_step(self, X_ptr: int, target_ptr: int, count: int, lr: float, idx_ptr=None, want_loss=False):
+        return gbp_mlp_train_step(self.h, X_ptr, target_ptr, idx_ptr, count, lr, want_loss)
+
+    def close(self):
+        if getattr(self, "h", None):
+            gbp_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
