@@ -369,6 +369,17 @@ def run_gpu(args, rank, world, local):
             ms_1px = float(np.median(ts))
         g.set_params(conv_tol=CONV_TOL)
 
+        # learned per-factor damping (the shipped network) against fixed d = 0.4
+        from paper_2003_03134_gb300 import learned
+        net = gbp.DampingNet(learned.trained_params(), stream=stream.cuda_stream)
+        cmp = learned.compare(torch, p, net, reference=(kf_ref, lm_ref), stream=stream.cuda_stream,
+                              conv_tol=CONV_TOL)
+        net.close()
+        learned_line = {"weights": "paper_2003_03134_gb300/damping_net.npy (1000 training problems, seeds 10000-10999)",
+                        "reference": "ARE vs the oracle's converged solution", "thresholds_px": [1.0, 0.1, 0.01],
+                        **{k: {"iters": v["iters"], "ms": v["ms"], "final_are": v["final"]["are"]}
+                           for k, v in cmp.items()}}
+
         # end to end through the C ABI with host buffers: create (H2D), solve, read beliefs (D2H)
         e2e_t, e2e_updates = [], 0.0
         h2d = p.n_kf * 96 + p.n_lm * 24 + p.n_obs * (4 + 4 + 16) + 4 * len(p.anchor_kf)
@@ -392,7 +403,7 @@ def run_gpu(args, rank, world, local):
             "config": {"workload": workload_name(p), "l2": "flushed between steps (256 MiB write, untimed)",
                        "parallelism": f"independent problems, one per GPU ({world})",
                        "iters_per_step": float(np.mean(iters))},
-            "ms_to_1px_vs_oracle": ms_1px, "iters_to_1px_vs_oracle": t_1px,
+            "ms_to_1px_vs_oracle": ms_1px, "iters_to_1px_vs_oracle": t_1px, "learned_damping": learned_line,
             "roofline": roof, "at_scale": at_scale, "cpu_baseline": cpu,
             "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s},

@@ -318,15 +318,17 @@ void gbp_mlp_destroy(gbp_mlp* net);
  * With damping_mode = 1 each factor's eta messages are damped by the
  * network's prediction d_f in place of d:
  *   eta_{f->v} = (1 - d_f) eta_new + d_f eta_old,  Lambda undamped (Sec. 5),
- * from the second iteration after the factor's (re)linearisation on (the
- * first message after a relinearisation stays undamped; the fixed schedule's
- * hold of undamped_iters does not apply).  d_f comes from 16 features of the
+ * wherever the fixed schedule damps (after the undamped_iters hold that
+ * follows a (re)linearisation, Sec. 8).  d_f comes from 16 features of the
  * factor: its Mahalanobis residual and Huber weight (Sec. 6), how much of
- * each variable's incoming precision it supplies, the relative change of
- * each of its two messages over the last 4 iterations, the two variables'
- * degrees, and the iterations since its linearisation and since its
- * landmark appeared.  Iterating with damping_mode = 1 and no network gives
- * GBP_ESTATE. */
+ * each variable's incoming precision it supplies, for each of its two
+ * messages the relative change over the last 3 iterations and the cosine
+ * between the proposed and the previous step (oscillation or steady
+ * progress), the two variables' degrees, and the iterations since its
+ * linearisation and since its landmark appeared.  The per-factor history
+ * behind these features is kept only while damping_mode = 1 or while
+ * recording, and restarts from zero on gbp_reset.  Iterating with
+ * damping_mode = 1 and no network gives GBP_ESTATE. */
 gbp_status gbp_set_damping_model(gbp_graph* g, const gbp_mlp* net);
 
 /* Training data for the network.  gbp_capture_messages stores the graph's
@@ -336,14 +338,15 @@ gbp_status gbp_set_damping_model(gbp_graph* g, const gbp_mlp* net);
  * and factor f (the library's internal factor order, row i * n_obs + f):
  *   X[row * 16 + j]  the 16 features above (DEVICE, 16-byte aligned,
  *                    n_iters * n_obs * 16 floats)
- *   target[row]      the damping that brings the undamped new eta closest
- *                    to the reference message, per message side
- *                    clip(<eta_old - eta_new, eta_ref - eta_new> /
- *                    |eta_old - eta_new|^2, 0, 0.9), averaged over the two
- *                    sides; -1 where the learned schedule never damps (the
- *                    iteration of a relinearisation, a factor behind the
- *                    camera) or where eta_old = eta_new on both sides
- *                    (DEVICE, n_iters * n_obs floats).
+ *   target[row]      the d in [0, 0.9] minimising, over the message sides
+ *                    s whose eta changed,
+ *                    sum_s |(1 - d) eta_new,s + d eta_old,s - eta_ref,s|^2
+ *                          / |eta_old,s - eta_new,s|^2
+ *                    (eta_new undamped, eta_old the previous message,
+ *                    eta_ref the captured reference); -1 where the schedule
+ *                    does not damp (the hold after a relinearisation), for
+ *                    a factor behind the camera, or where neither message
+ *                    changed (DEVICE, n_iters * n_obs floats).
  * GBP_ESTATE without a captured reference (also after gbp_add_keyframe,
  * which drops it).  Synchronises the stream. */
 gbp_status gbp_capture_messages(gbp_graph* g);

@@ -293,13 +293,17 @@ struct orc_graph {
     long n_relin;                        /* relinearisations since creation      */
     double *lin_r2, *lin_k;              /* |r|^2 and Huber weight at the linearisation (0, 0 if inactive) */
     /* learned damping (no counterpart in the paper) */
-    double *hist;                        /* per factor: relative message changes of the last 3 iterations,
-                                            keyframe side [0..2], landmark side [3..5], most recent first */
+    double *hist;                        /* per factor (ORC_HIST): relative message changes at t-1 and t-2,
+                                            keyframe side [0..1], landmark side [2..3]; the landmark
+                                            message eta of t-1 [4..6]; kept while features are computed */
+    double *pk_eta;                      /* per factor: eta of the message to the keyframe at t-1        */
     double *net;                         /* damping network parameters (ORC_NET_NPARAM) or NULL         */
     double *eta_ref;                     /* per factor: reference eta (keyframe 6, landmark 3) or NULL   */
 };
 
 static void* zalloc(size_t n) { return calloc(n ? n : 1, 1); }
+
+enum { ORC_HIST = 8 };
 
 /* Belief b^t of every variable: prior(t) + sum of the current messages
  * (Sec. 5, belief equations); then its mean by a Cholesky solve. */
@@ -463,7 +467,8 @@ orc_graph* orc_create(const orc_cam* cam, const orc_params* prm,
     g->tlin = zalloc(sizeof(int) * F);
     g->lin_r2 = zalloc(sizeof(double) * F);
     g->lin_k = zalloc(sizeof(double) * F);
-    g->hist = zalloc(sizeof(double) * 6 * F);
+    g->hist = zalloc(sizeof(double) * ORC_HIST * F);
+    g->pk_eta = zalloc(sizeof(double) * 6 * F);
     for (int f = 0; f < n_obs; ++f) {
         int kk = g->fk[f], m = g->fm[f];
         int active = orc_linearise(cam, prm, g->Rref + 9 * kk, g->cref + 3 * kk, g->lref + 3 * m, zero6, zero6,
@@ -486,7 +491,8 @@ void orc_destroy(orc_graph* g)
                      g->Dk, g->Dl,
                      g->kf_lam, g->kf_eta, g->lm_lam, g->lm_eta, g->kf_mu, g->lm_mu,
                      g->mk_lam, g->mk_eta, g->ml_lam, g->ml_eta, g->nk_lam, g->nk_eta, g->nl_lam, g->nl_eta,
-                     g->linA, g->linc, g->x0, g->tlin, g->lin_r2, g->lin_k, g->hist, g->net, g->eta_ref };
+                     g->linA, g->linc, g->x0, g->tlin, g->lin_r2, g->lin_k, g->hist, g->pk_eta, g->net,
+                     g->eta_ref };
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(g);
 }
@@ -530,10 +536,10 @@ static double rel_change(const double* nw, const double* old, int n)
     return norm_n(d, n) / (norm_n(nw, n) + norm_n(old, n) + 1e-30);
 }
 
-/* The damping d in [0, 0.9] that brings (1 - d) new + d old closest to ref:
- * the least-squares step along old - new, clipped.  *valid = 0 when
- * old = new (up to 1e-10 of their squared norms), where d is arbitrary. */
-static double best_damping(const double* nw, const double* old, const double* ref, int n, int* valid)
+/* |(1 - d) new + d old - ref|^2 is a parabola in d; returns its vertex
+ * <old - new, ref - new> / |old - new|^2.  *valid = 0 when old = new (up to
+ * 1e-10 of their squared norms), where every d is equally good. */
+static double damping_vertex(const double* nw, const double* old, const double* ref, int n, int* valid)
 {
     double uu = 0.0, uv = 0.0, nn = 0.0;
     for (int i = 0; i < n; ++i) {
@@ -543,9 +549,19 @@ static double best_damping(const double* nw, const double* old, const double* re
         nn += nw[i] * nw[i] + old[i] * old[i];
     }
     *valid = uu > 1e-10 * nn && uu > 0.0;
-    if (!*valid) return 0.0;
-    double d = uv / uu;
-    return d < 0.0 ? 0.0 : (d > 0.9 ? 0.9 : d);
+    return *valid ? uv / uu : 0.0;
+}
+
+/* cosine between the proposed step new - old and the previous step old - prev */
+static double step_cosine(const double* nw, const double* old, const double* prev, int n)
+{
+    double a[6], b[6], ab = 0.0;
+    for (int i = 0; i < n; ++i) {
+        a[i] = nw[i] - old[i];
+        b[i] = old[i] - prev[i];
+        ab += a[i] * b[i];
+    }
+    return ab / (norm_n(a, n) * norm_n(b, n) + 1e-30);
 }
 
 static double trace_n(const double* A, int n)
@@ -556,8 +572,9 @@ static double trace_n(const double* A, int n)
 }
 
 /* The 16 features of factor f, from this iteration's undamped new messages
- * (nk_*, nl_*), the previous messages (mk_*, ml_*), the beliefs b^t and the
- * stored history; then the history moves one step. */
+ * (nk_*, nl_*), the messages m^t (mk_*, ml_*) and m^{t-1} (pk_eta, stored
+ * landmark eta), the beliefs b^t and the stored history; then the history
+ * moves one step. */
 static void factor_features(orc_graph* g, int f, const int* deg_k, const int* deg_l, double* x)
 {
     int kk = g->fk[f], m = g->fm[f];
@@ -568,20 +585,27 @@ static void factor_features(orc_graph* g, int f, const int* deg_k, const int* de
     double M = sqrt(g->lin_r2[f]) / g->prm.sigma_px;
     double ck = rel_change(g->nk_eta + 6 * f, g->mk_eta + 6 * f, 6);
     double cm = rel_change(g->nl_eta + 3 * f, g->ml_eta + 3 * f, 3);
-    double* h = g->hist + 6 * f;
+    double* h = g->hist + ORC_HIST * f;
     int dt_lin = g->t - g->tlin[f], dt_birth = g->t - g->lm_birth[m];
     x[0] = log1p(M) / 3.0;
     x[1] = g->lin_k[f];
     x[2] = tlk / (tlk + trace_n(Pk, 6) + 1e-30);
     x[3] = tlm / (tlm + trace_n(Pm, 3) + 1e-30);
-    x[4] = ck;   x[5] = h[0];  x[6] = h[1];  x[7] = h[2];
-    x[8] = cm;   x[9] = h[3];  x[10] = h[4]; x[11] = h[5];
+    x[4] = ck;
+    x[5] = h[0];
+    x[6] = h[1];
+    x[7] = step_cosine(g->nk_eta + 6 * f, g->mk_eta + 6 * f, g->pk_eta + 6 * f, 6);
+    x[8] = cm;
+    x[9] = h[2];
+    x[10] = h[3];
+    x[11] = step_cosine(g->nl_eta + 3 * f, g->ml_eta + 3 * f, h + 4, 3);
     x[12] = log1p((double)deg_k[kk]) / 5.0;
     x[13] = log1p((double)deg_l[m]) / 3.0;
     x[14] = (dt_lin < 50 ? dt_lin : 50) / 50.0;
     x[15] = (dt_birth < 50 ? dt_birth : 50) / 50.0;
-    h[2] = h[1]; h[1] = h[0]; h[0] = ck;
-    h[5] = h[4]; h[4] = h[3]; h[3] = cm;
+    h[1] = h[0]; h[0] = ck;
+    h[3] = h[2]; h[2] = cm;
+    for (int i = 0; i < 3; ++i) h[4 + i] = g->ml_eta[3 * f + i];
 }
 
 int orc_set_damping_net(orc_graph* g, const double* params)
@@ -607,8 +631,9 @@ void orc_set_reference_messages(orc_graph* g, const double* eta_ref)
 
 /* mode 0: the fixed schedule; 1: learned d_f (needs a network); 2: fixed
  * schedule, recording features into X (n x n_f x 16) and damping targets
- * toward eta_ref into T (n x n_f; -1 where the learned schedule does not
- * damp or the message did not change). */
+ * toward eta_ref into T (n x n_f; -1 where the schedule does not damp or
+ * neither message changed).  Both schedules damp only after the undamped
+ * hold of Sec. 8; the learned one with d_f in place of d. */
 static int iterate_impl(orc_graph* g, int n, double* max_dmu, int mode, double* X, double* T)
 {
     double J[18], r[2], k;
@@ -654,31 +679,34 @@ static int iterate_impl(orc_graph* g, int n, double* max_dmu, int mode, double* 
             for (int i = 0; i < 36; ++i) lam_in[i] = g->kf_lam[36 * kk + i] - g->mk_lam[36 * f + i];
             for (int i = 0; i < 6; ++i) eta_in[i] = g->kf_eta[6 * kk + i] - g->mk_eta[6 * f + i];
             if (orc_factor_message(A, c, 1, lam_in, eta_in, g->nl_lam + 9 * f, g->nl_eta + 3 * f) != 0) { status = -1; break; }
-            /* damping of the eta update (Sec. 5).  Fixed schedule: messages
-             * stay undamped for undamped_iters iterations after a
-             * (re)linearisation (Sec. 8); the message sent in the iteration of
-             * a (re)linearisation -- including a factor's first message -- is
-             * never damped.  Learned schedule: d_f from the network whenever
-             * t > t_lin. */
+            /* damping of the eta update (Sec. 5): messages stay undamped for
+             * undamped_iters iterations after a (re)linearisation (Sec. 8); the
+             * message sent in the iteration of a (re)linearisation -- including
+             * a factor's first message -- is never damped.  Then d, or the
+             * network's d_f in the learned schedule. */
+            const int hold = g->prm.undamped_iters > 1 ? g->prm.undamped_iters : 1;
             double feat[ORC_NET_NFEAT];
             if (mode != 0) factor_features(g, f, deg_k, deg_l, feat);
             if (mode == 2) {
                 double* xo = X + ((size_t)it * g->n_f + f) * ORC_NET_NFEAT;
                 for (int j = 0; j < ORC_NET_NFEAT; ++j) xo[j] = feat[j];
+                /* the d in [0, 0.9] minimising the sum over the changed sides of
+                 * |(1 - d) new + d old - ref|^2 / |old - new|^2: each term is a
+                 * unit-curvature parabola around its vertex, so the minimiser
+                 * is the clipped mean of the vertices */
                 int vk, vm;
-                double dk = best_damping(g->nk_eta + 6 * f, g->mk_eta + 6 * f, g->eta_ref + 9 * f, 6, &vk);
-                double dm = best_damping(g->nl_eta + 3 * f, g->ml_eta + 3 * f, g->eta_ref + 9 * f + 6, 3, &vm);
-                double target = (vk || vm) ? (vk * dk + vm * dm) / (vk + vm) : -1.0;
-                if (g->t == g->tlin[f] || !(g->lin_k[f] > 0.0)) target = -1.0;
+                double dk = damping_vertex(g->nk_eta + 6 * f, g->mk_eta + 6 * f, g->eta_ref + 9 * f, 6, &vk);
+                double dm = damping_vertex(g->nl_eta + 3 * f, g->ml_eta + 3 * f, g->eta_ref + 9 * f + 6, 3, &vm);
+                double target = -1.0;
+                if (vk || vm) {
+                    target = (vk * dk + vm * dm) / (vk + vm);
+                    target = target < 0.0 ? 0.0 : (target > 0.9 ? 0.9 : target);
+                }
+                if (g->t - g->tlin[f] < hold || !(g->lin_k[f] > 0.0)) target = -1.0;
                 T[(size_t)it * g->n_f + f] = target;
             }
             double d = -1.0;
-            if (mode == 1) {
-                if (g->t > g->tlin[f]) d = orc_net_forward(g->net, feat);
-            } else {
-                int hold = g->prm.undamped_iters > 1 ? g->prm.undamped_iters : 1;
-                if (g->t - g->tlin[f] >= hold) d = g->prm.damping;
-            }
+            if (g->t - g->tlin[f] >= hold) d = mode == 1 ? orc_net_forward(g->net, feat) : g->prm.damping;
             if (d >= 0.0) {
                 for (int i = 0; i < 6; ++i) g->nk_eta[6 * f + i] = (1.0 - d) * g->nk_eta[6 * f + i] + d * g->mk_eta[6 * f + i];
                 for (int i = 0; i < 3; ++i) g->nl_eta[3 * f + i] = (1.0 - d) * g->nl_eta[3 * f + i] + d * g->ml_eta[3 * f + i];
@@ -686,6 +714,7 @@ static int iterate_impl(orc_graph* g, int n, double* max_dmu, int mode, double* 
         }
         if (status != 0) break;
         /* synchronous schedule: every factor used m^t; now m^{t+1} replaces it */
+        memcpy(g->pk_eta, g->mk_eta, sizeof(double) * 6 * (size_t)g->n_f);
         double* tmp;
         tmp = g->mk_lam; g->mk_lam = g->nk_lam; g->nk_lam = tmp;
         tmp = g->mk_eta; g->mk_eta = g->nk_eta; g->nk_eta = tmp;
@@ -875,7 +904,8 @@ int orc_add_keyframe(orc_graph* g, const double* kf_Rt_init, int n_new_lm, const
     GROW(g->ml_eta, 3 * d, F0, F1); GROW(g->nk_lam, 36 * d, F0, F1); GROW(g->nk_eta, 6 * d, F0, F1);
     GROW(g->nl_lam, 9 * d, F0, F1); GROW(g->nl_eta, 3 * d, F0, F1); GROW(g->linA, 81 * d, F0, F1);
     GROW(g->linc, 9 * d, F0, F1); GROW(g->x0, 9 * d, F0, F1); GROW(g->tlin, sizeof(int), F0, F1);
-    GROW(g->lin_r2, d, F0, F1); GROW(g->lin_k, d, F0, F1); GROW(g->hist, 6 * d, F0, F1);
+    GROW(g->lin_r2, d, F0, F1); GROW(g->lin_k, d, F0, F1); GROW(g->hist, ORC_HIST * d, F0, F1);
+    GROW(g->pk_eta, 6 * d, F0, F1);
 #undef GROW
     free(g->eta_ref);   /* the reference covered the old factors only */
     g->eta_ref = NULL;

@@ -106,20 +106,23 @@ long orc_relinearisations(const orc_graph* g);
  * Network: 16 features -> 64 -> 64 -> 1, ReLU hidden layers, output
  * 0.9 * sigmoid; ORC_NET_NPARAM parameters in the order W1 (16 x 64, row =
  * input), b1, W2 (64 x 64), b2, W3 (64), b3.  Features of factor f at
- * iteration t:
+ * iteration t, with eta_new this iteration's undamped message, eta_old =
+ * m^t and eta_prev = m^{t-1} on each side:
  *   0  log(1 + M) / 3 with M = |r| / sigma at the factor's linearisation
  *   1  its Huber weight (0 if the point is behind z_min)
  *   2  tr Lambda_new(f->k) / (tr Lambda_new(f->k) + tr P_k), P_k = the
  *      keyframe belief's precision minus the factor's previous message
  *   3  the same for the landmark
  *   4  |eta_new - eta_old| / (|eta_new| + |eta_old|) of the message to the
- *      keyframe (eta_new undamped); 5-7 its values at t-1, t-2, t-3
- *   8-11 the same for the message to the landmark
+ *      keyframe; 5, 6 its values at t-1 and t-2
+ *   7  cosine between eta_new - eta_old and eta_old - eta_prev (keyframe side)
+ *   8-11 the same four for the message to the landmark (its eta_prev is
+ *      remembered only while features are computed: learned or record runs)
  *   12 log(1 + deg k) / 5;  13 log(1 + deg m) / 3
  *   14 min(t - t_lin, 50) / 50;  15 min(t - t_birth(m), 50) / 50
  * Learned schedule: with a network set, orc_iterate damps both eta messages
- * of factor f by d_f = net(features) whenever t > t_lin (the first message
- * after a (re)linearisation stays undamped; undamped_iters is ignored). */
+ * of factor f by d_f = net(features) wherever the fixed schedule damps
+ * (after the undamped hold of Sec. 8). */
 #define ORC_NET_NFEAT 16
 #define ORC_NET_NPARAM 5313
 double orc_net_forward(const double* params, const double x[ORC_NET_NFEAT]);
@@ -131,11 +134,11 @@ int orc_set_damping_net(orc_graph* g, const double* params);
 void orc_set_reference_messages(orc_graph* g, const double* eta_ref /* n_f x 9 */);
 /* n iterations of the fixed schedule writing, for iteration i and factor f
  * (caller order), X[(i n_f + f) 16 + j] = feature j and T[i n_f + f] = the
- * damping target: per message side, the d in [0, 0.9] minimising
- * |(1 - d) eta_new + d eta_old - eta_ref| (the clipped least-squares step),
- * averaged over the sides where eta_old != eta_new; -1 where no side
- * qualifies, in the iteration of a (re)linearisation, or for a factor
- * behind z_min.  Returns 0, -1 (belief not positive definite) or -2 (no
+ * damping target: the d in [0, 0.9] minimising the sum over the message
+ * sides where eta_old != eta_new of
+ * |(1 - d) eta_new + d eta_old - eta_ref|^2 / |eta_old - eta_new|^2;
+ * -1 where neither side changed, where the schedule does not damp (the
+ * undamped hold after a (re)linearisation), or for a factor behind z_min.  Returns 0, -1 (belief not positive definite) or -2 (no
  * reference set). */
 int orc_iterate_record(orc_graph* g, int n, double* X, double* T);
 

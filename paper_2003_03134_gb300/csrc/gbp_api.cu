@@ -62,7 +62,7 @@ struct DevState {
     R* kf_bel = nullptr;
     R* lm_bel = nullptr;
     R* prior_s = nullptr;      // prior scale table, prior_anneal_iters + 1 entries
-    float* hist = nullptr;     // learned damping: 6 x n_f message-change history
+    float* hist = nullptr;     // learned damping: HIST x n_f message-change history
     R* eta_inf = nullptr;      // record schedule: 9 x n_f reference messages (gbp_capture_messages)
 
     void release() {
@@ -308,7 +308,7 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
     CK(dev_alloc(&s.ml, 9 * (size_t)nf));
     CK(dev_alloc(&s.kf_bel, (size_t)KBEL * nk));
     CK(dev_alloc(&s.lm_bel, (size_t)LBEL * nl));
-    CK(dev_alloc(&s.hist, 6 * (size_t)std::max(nf, 1)));
+    CK(dev_alloc(&s.hist, HIST * (size_t)std::max(nf, 1)));
     cudaStream_t st = g->stream;
     CK(cudaMemcpyAsync(s.z, zr.data(), sizeof(R) * zr.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.fk, g->fk.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice, st));
@@ -417,7 +417,7 @@ gbp_status reset_state(gbp_graph* g) {
     CK(cudaMemsetAsync(s.ml, 0, sizeof(R) * 9 * nf, st));
     CK(cudaMemsetAsync(s.kf_bel, 0, sizeof(R) * KBEL * g->n_kf, st));
     CK(cudaMemsetAsync(s.lm_bel, 0, sizeof(R) * LBEL * g->n_lm, st));
-    CK(cudaMemsetAsync(s.hist, 0, sizeof(float) * 6 * nf, st));
+    CK(cudaMemsetAsync(s.hist, 0, sizeof(float) * HIST * nf, st));
     int32_t c0[CTL_N] = {0};
     CK(cudaMemcpyAsync(g->ctl, c0, sizeof(c0), cudaMemcpyHostToDevice, st));
     CK(launch_init<R>(s.g, make_kparams<R>(g), st));
@@ -673,7 +673,7 @@ std::vector<std::pair<void*, size_t>> state_buffers(gbp_graph* g) {
     return {{s.x0, sizeof(R) * 9 * nf},        {s.tlin, sizeof(int32_t) * nf},   {s.mk, sizeof(R) * KREC * nf},
             {s.mk2, sizeof(R) * KREC * nf},
             {s.ml, sizeof(R) * 9 * nf},        {s.kf_bel, sizeof(R) * KBEL * nk}, {s.lm_bel, sizeof(R) * LBEL * nl},
-            {s.hist, sizeof(float) * 6 * nf}, {g->ctl, sizeof(int32_t) * CTL_N}};
+            {s.hist, sizeof(float) * HIST * nf}, {g->ctl, sizeof(int32_t) * CTL_N}};
 }
 
 // Slot of every factor's keyframe message: its position in the keyframe's
@@ -698,17 +698,19 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
     const int K0 = g->n_kf, L0 = g->n_lm, F0 = g->n_f;
     const int K1 = K0 + 1, L1 = L0 + n_new_lm, F1 = F0 + n_obs;
     std::vector<int32_t> ctl(CTL_N), tlin(F0);
-    std::vector<R> x0(9 * (size_t)F0), mk((size_t)KREC * F0), ml(9 * (size_t)F0), kb((size_t)KBEL * K0),
+    std::vector<R> x0(9 * (size_t)F0), mk((size_t)KREC * F0), mkp((size_t)KREC * F0), ml(9 * (size_t)F0), kb((size_t)KBEL * K0),
         lb((size_t)LBEL * L0), kD(6 * (size_t)K0), kA(6 * (size_t)K0), lD(3 * (size_t)L0);
-    std::vector<float> hist(6 * (size_t)F0);
+    std::vector<float> hist(HIST * (size_t)F0);
     {
         DevState<R>& s = state<R>(g);
         CK(cudaMemcpyAsync(ctl.data(), g->ctl, sizeof(int32_t) * CTL_N, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         const R* mk_cur = (ctl[CTL_ITER] & 1) ? s.mk2 : s.mk;
+        const R* mk_prev = (ctl[CTL_ITER] & 1) ? s.mk : s.mk2;   // m^{t-1}, read by the learned schedule
         CK(cudaMemcpyAsync(x0.data(), s.x0, sizeof(R) * x0.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(tlin.data(), s.tlin, sizeof(int32_t) * tlin.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(mk.data(), mk_cur, sizeof(R) * mk.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(mkp.data(), mk_prev, sizeof(R) * mkp.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(ml.data(), s.ml, sizeof(R) * ml.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(hist.data(), s.hist, sizeof(float) * hist.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(kb.data(), s.kf_bel, sizeof(R) * kb.size(), cudaMemcpyDeviceToHost, st));
@@ -791,8 +793,9 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
 
     // linearisation points in the new order: old factors keep theirs, new
     // ones take the current means (a new variable's mean is 0 in its chart)
-    std::vector<R> x0n(9 * (size_t)F1), mln(9 * (size_t)F1, R(0)), mkn((size_t)KREC * F1, R(0));
-    std::vector<float> histn(6 * (size_t)F1, 0.0f);
+    std::vector<R> x0n(9 * (size_t)F1), mln(9 * (size_t)F1, R(0)), mkn((size_t)KREC * F1, R(0)),
+        mkpn((size_t)KREC * F1, R(0));
+    std::vector<float> histn(HIST * (size_t)F1, 0.0f);
     std::vector<int32_t> tlinn(F1);
     std::vector<int32_t> kpos = keyframe_slots(g->fk, K1);
     for (int f = 0; f < F1; ++f) {
@@ -804,9 +807,11 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
                 mln[(size_t)i * F1 + f] = ml[(size_t)i * F0 + of];
             }
             tlinn[f] = tlin[of];
-            for (int j = 0; j < 6; ++j) histn[(size_t)j * F1 + f] = hist[(size_t)j * F0 + of];
+            for (int j = 0; j < HIST; ++j) histn[(size_t)j * F1 + f] = hist[(size_t)j * F0 + of];
             std::copy(&mk[(size_t)KREC * old_kpos[of]], &mk[(size_t)KREC * old_kpos[of]] + KREC,
                       &mkn[(size_t)KREC * kpos[f]]);
+            std::copy(&mkp[(size_t)KREC * old_kpos[of]], &mkp[(size_t)KREC * old_kpos[of]] + KREC,
+                      &mkpn[(size_t)KREC * kpos[f]]);
         } else {
             const int m = g->fm[f];
             for (int i = 0; i < 6; ++i) x0n[(size_t)i * F1 + f] = R(0);
@@ -845,7 +850,7 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
     CK(cudaMemcpyAsync(s.ml, mln.data(), sizeof(R) * mln.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.hist, histn.data(), sizeof(float) * histn.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(mk_cur, mkn.data(), sizeof(R) * mkn.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(mk_other, 0, sizeof(R) * mkn.size(), st));
+    CK(cudaMemcpyAsync(mk_other, mkpn.data(), sizeof(R) * mkpn.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.kf_bel, kbn.data(), sizeof(R) * kbn.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.lm_bel, lbn.data(), sizeof(R) * lbn.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(g->ctl, ctl.data(), sizeof(int32_t) * CTL_N, cudaMemcpyHostToDevice, st));

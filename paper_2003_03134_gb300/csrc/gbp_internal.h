@@ -18,7 +18,8 @@
 //   per landmark:         lref (3 double), prior diagonal (3), belief record
 //                         LBEL Real: Lambda (6), eta (3), mu (3)
 //   per factor, learned damping: hist -- relative message changes of the
-//                                last 3 iterations, float SoA (6 x n_f)
+//                                last 2 iterations and the previous landmark
+//                                message eta, float SoA (HIST x n_f)
 //   CSR keyframe -> factor list (kf_off, kf_list); landmark -> contiguous
 //   factor range (lm_off), since factors are sorted by landmark; warp tiles
 //   of whole landmarks (tile_start); per-variable arrival counters.
@@ -66,6 +67,7 @@ enum DampMode : int {
     DAMP_RECORD = 2    // fixed schedule; features and damping targets written to rec_X / rec_T
 };
 constexpr int N_FEAT = 16;
+constexpr int HIST = 8;   // per-factor history floats: |d eta| at t-1, t-2 (kf, lm), landmark eta of t-1, pad
 
 template <typename R>
 struct DevGraph {
@@ -104,7 +106,7 @@ struct DevGraph {
     R* kf_bel_out;            // where b^{t+1} is written (normally == kf_bel)
     R* lm_bel_out;            // (normally == lm_bel)
     // learned damping
-    float* hist;              // 6 x n_f: relative message change of the last 3 iterations (kf side, lm side)
+    float* hist;              // HIST x n_f: message-change history of the learned schedule
     const R* eta_inf;         // record: 9 x n_f reference messages eta (kf side 6, lm side 3)
     float* rec_X;             // record: n_f x 16 features of the current iteration
     float* rec_T;             // record: n_f damping targets (-1: a sample the learned schedule never uses)

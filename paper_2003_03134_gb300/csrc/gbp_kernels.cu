@@ -574,20 +574,26 @@ __device__ __forceinline__ void dmu_atomic_max_slot(int32_t* ctl, int slot, floa
 }
 
 // ------------------------------------------------------------------------
-// Learned damping.  Features of factor f at iteration t (all O(1)):
+// Learned damping.  Features of factor f at iteration t (all O(1)); for each
+// message side, eta_new is this iteration's undamped message, eta_old = m^t
+// and eta_prev = m^{t-1}:
 //   0  log(1 + M) / 3, M = |r| / sigma (Mahalanobis residual, Sec. 6)
 //   1  Huber weight k (Sec. 6; 0 for a factor behind the camera)
 //   2  tr Lambda_{f->k} / (tr Lambda_{f->k} + tr P_k), P_k the keyframe's incoming precision
 //   3  the same for the landmark
-//   4  |eta_new - eta_old| / (|eta_new| + |eta_old|) of the message to the keyframe, this iteration
-//   5-7  the same, the three previous iterations (most recent first)
-//   8-11 the same for the message to the landmark
+//   4  |eta_new - eta_old| / (|eta_new| + |eta_old|) of the message to the keyframe
+//   5, 6  its values at iterations t - 1 and t - 2
+//   7  cosine between eta_new - eta_old and eta_old - eta_prev (0 if either is 0):
+//      negative when the message oscillates, positive when it moves steadily
+//   8-11 the same four for the message to the landmark
 //   12 log(1 + deg k) / 5,  13 log(1 + deg m) / 3
 //   14 min(t - t_lin, 50) / 50,  15 min(t - t_birth(m), 50) / 50
-// Target (record mode), per side: the damping that moves the new message
-// closest to a reference message eta_inf (the run's converged message),
-//   d* = clip(<eta_old - eta_new, eta_inf - eta_new> / |eta_old - eta_new|^2, 0, 0.9),
-// averaged over the sides where eta_old != eta_new.
+// Target (record mode): the damping d in [0, 0.9] minimising
+//   sum_s |(1 - d) eta_new,s + d eta_old,s - eta_inf,s|^2 / |eta_old,s - eta_new,s|^2
+// over the sides s where eta_old != eta_new, eta_inf the reference (the
+// run's converged message): each term is |u_s|^-2 times a parabola in d with
+// vertex d_s = <u_s, eta_inf,s - eta_new,s> / |u_s|^2 (u_s = eta_old,s -
+// eta_new,s), so the minimiser is clip(mean_s d_s, 0, 0.9).
 
 template <typename R, int n>
 __device__ __forceinline__ float rel_change(const R* nw, const R* old) {
@@ -602,7 +608,21 @@ __device__ __forceinline__ float rel_change(const R* nw, const R* old) {
 }
 
 template <typename R, int n>
-__device__ __forceinline__ float best_damping(const R* nw, const R* old, const R* inf, bool& valid) {
+__device__ __forceinline__ float step_cosine(const R* nw, const R* old, const R* prev) {
+    R ab = R(0), aa = R(0), bb = R(0);
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        const R a = nw[i] - old[i], b = old[i] - prev[i];
+        ab += a * b;
+        aa += a * a;
+        bb += b * b;
+    }
+    return float(ab / (sqrt(aa) * sqrt(bb) + R(1e-30)));
+}
+
+// Vertex of one side's parabola (unclipped); valid = the side's message changed.
+template <typename R, int n>
+__device__ __forceinline__ float damping_vertex(const R* nw, const R* old, const R* inf, bool& valid) {
     R uu = R(0), uv = R(0), nn = R(0);
 #pragma unroll
     for (int i = 0; i < n; ++i) {
@@ -612,7 +632,7 @@ __device__ __forceinline__ float best_damping(const R* nw, const R* old, const R
         nn += nw[i] * nw[i] + old[i] * old[i];
     }
     valid = uu > R(1e-10) * nn && uu > R(0);
-    return valid ? fminf(fmaxf(float(uv / uu), 0.0f), MLP_DMAX) : 0.0f;
+    return valid ? float(uv / uu) : 0.0f;
 }
 
 // Shared memory of the learned schedule: the network's packed weights and
@@ -626,7 +646,6 @@ struct MlpSmem<DAMP_LEARNED> {
     uint32_t frag[FWD_FRAG_WORDS];
     float bias[MLP_BIAS_WORDS];
     alignas(16) uint16_t x[FACTOR_BLOCK / 32][32 * XS];
-    alignas(16) uint16_t h[FACTOR_BLOCK / 32][32 * HS];
 };
 
 template <int MODE, typename R>
@@ -664,12 +683,16 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
     // learned / record schedules: undamped new and previous eta of both
     // messages, and the features
     constexpr bool FEAT = MODE != DAMP_FIXED;
-    R ek_new[6], ek_old[6], em_new[3], em_old[3];
+    R ek_new[6], ek_old[6], em_new[3], em_old[3], ek_prev[6];
     float feat[N_FEAT];
 #pragma unroll
     for (int i = 0; i < N_FEAT; ++i) feat[i] = 0.0f;
     size_t ks_f = 0;
     int tl_f = 0;
+    // feature inputs that do not depend on this iteration's messages, loaded
+    // first so that their latency overlaps the message arithmetic
+    float h[HIST];
+    int deg_k = 0, birth_m = 0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) sum[i] = R(0);
 
@@ -681,6 +704,13 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
         hi = g.lm_off[m + 1];
 #pragma unroll
         for (int i = 0; i < 9; ++i) ml[i] = g.ml[(size_t)i * n_f + f];
+        if constexpr (FEAT) {
+#pragma unroll
+            for (int j = 0; j < HIST; ++j) h[j] = g.hist[(size_t)j * n_f + f];
+            const int k = g.fk[f];
+            deg_k = g.kf_off[k + 1] - g.kf_off[k];
+            birth_m = g.lm_birth[m];
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < 9; ++i) ml[i] = R(0);
@@ -758,10 +788,16 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
         Lin<R> L;
         linearise<R>(P, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3, g.lm_ref + (size_t)m * 3, x0,
                      g.z[2 * (size_t)f], g.z[2 * (size_t)f + 1], L);
-        const bool damp = MODE != DAMP_LEARNED && t - tl >= P.damp_hold;
+        const bool damp = MODE != DAMP_LEARNED && t - tl >= P.damp_hold;   // learned: after the network
         const R d = P.damping;
         ks_f = ks;
         tl_f = tl;
+        if constexpr (FEAT) {
+            // m^{t-1} to the keyframe: still in the buffer this iteration writes
+            const R* pw = mk_write(g, t) + ks;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) ek_prev[i] = pw[21 + i];
+        }
         float tr_pk = 0.0f, tr_pm = 0.0f, tr_lk = 0.0f;
 
         // ---- message to the keyframe: marginalise the landmark ----
@@ -868,9 +904,7 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
                 const float M = float(sqrt(L.r2) * P.inv_sigma);
                 const float ck = rel_change<R, 6>(ek_new, ek_old);
                 const float cm = rel_change<R, 3>(em_new, em_old);
-                float h[6];
-#pragma unroll
-                for (int j = 0; j < 6; ++j) h[j] = g.hist[(size_t)j * n_f + f];
+                const R em_prev[3] = {R(h[4]), R(h[5]), R(h[6])};
                 feat[0] = log1pf(M) * (1.0f / 3.0f);
                 feat[1] = float(L.W / P.inv_sigma2);
                 feat[2] = tr_lk / (tr_lk + tr_pk + 1e-30f);
@@ -878,18 +912,18 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
                 feat[4] = ck;
                 feat[5] = h[0];
                 feat[6] = h[1];
-                feat[7] = h[2];
+                feat[7] = step_cosine<R, 6>(ek_new, ek_old, ek_prev);
                 feat[8] = cm;
-                feat[9] = h[3];
-                feat[10] = h[4];
-                feat[11] = h[5];
-                feat[12] = log1pf(float(g.kf_off[k + 1] - g.kf_off[k])) * 0.2f;
+                feat[9] = h[2];
+                feat[10] = h[3];
+                feat[11] = step_cosine<R, 3>(em_new, em_old, em_prev);
+                feat[12] = log1pf(float(deg_k)) * 0.2f;
                 feat[13] = log1pf(float(hi - lo)) * (1.0f / 3.0f);
                 feat[14] = float(min(t - tl, 50)) * 0.02f;
-                feat[15] = float(min(t - g.lm_birth[m], 50)) * 0.02f;
-                const float hn[6] = {ck, h[0], h[1], cm, h[3], h[4]};
+                feat[15] = float(min(t - birth_m, 50)) * 0.02f;
+                const float hn[HIST] = {ck, h[0], cm, h[2], float(em_old[0]), float(em_old[1]), float(em_old[2]), 0.0f};
 #pragma unroll
-                for (int j = 0; j < 6; ++j) g.hist[(size_t)j * n_f + f] = hn[j];
+                for (int j = 0; j < HIST; ++j) g.hist[(size_t)j * n_f + f] = hn[j];
                 if constexpr (MODE == DAMP_RECORD) {
                     R ik[6], im[3];
 #pragma unroll
@@ -897,10 +931,14 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
 #pragma unroll
                     for (int i = 0; i < 3; ++i) im[i] = g.eta_inf[(size_t)(6 + i) * n_f + f];
                     bool vk, vm;
-                    const float dk = best_damping<R, 6>(ek_new, ek_old, ik, vk);
-                    const float dm = best_damping<R, 3>(em_new, em_old, im, vm);
-                    float target = (vk || vm) ? (dk * float(vk) + dm * float(vm)) / float(int(vk) + int(vm)) : -1.0f;
-                    if (t == tl || !(L.W > R(0))) target = -1.0f;   // never damped by the learned schedule
+                    const float dk = damping_vertex<R, 6>(ek_new, ek_old, ik, vk);
+                    const float dm = damping_vertex<R, 3>(em_new, em_old, im, vm);
+                    float target = (vk || vm) ? fminf(fmaxf((dk * float(vk) + dm * float(vm)) /
+                                                            float(int(vk) + int(vm)), 0.0f), MLP_DMAX)
+                                              : -1.0f;
+                    // samples the learned schedule never damps: the hold after
+                    // a (re)linearisation, a factor behind the camera
+                    if (t - tl < P.damp_hold || !(L.W > R(0))) target = -1.0f;
                     float4* xo = reinterpret_cast<float4*>(g.rec_X + (size_t)f * N_FEAT);
 #pragma unroll
                     for (int j = 0; j < N_FEAT / 4; ++j)
@@ -927,29 +965,31 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
 
     if constexpr (MODE == DAMP_LEARNED) {
         // the network for the warp's 32 factors (inactive lanes: zero rows),
-        // then eta damped by each factor's own d; a factor's first message
-        // after a (re)linearisation stays undamped
+        // then eta damped by each factor's own d wherever the fixed schedule
+        // would damp (after the undamped hold of Sec. 8)
         const int w = threadIdx.x >> 5;
-        __nv_bfloat16* xt = reinterpret_cast<__nv_bfloat16*>(S.x[w]);
-        __nv_bfloat16* ht = reinterpret_cast<__nv_bfloat16*>(S.h[w]);
+        const bool damp_f = active && t - tl_f >= P.damp_hold;
+        if (__any_sync(0xffffffffu, damp_f)) {   // uniform per warp: skipped while every lane is in its hold
+            __nv_bfloat16* xt = reinterpret_cast<__nv_bfloat16*>(S.x[w]);
 #pragma unroll
-        for (int j = 0; j < N_FEAT; j += 2) {
-            *reinterpret_cast<uint32_t*>(xt + lane * XS + j) = pack_bf16(feat[j], feat[j + 1]);
-        }
-        __syncwarp();
-        const float z3 = mlp_forward_warp(S.frag, S.bias, xt, ht, nullptr, lane);
-        float dl = mlp_output(z3);
-        if (!(dl >= 0.0f && dl <= MLP_DMAX)) dl = float(P.damping);
-        if (active && t > tl_f) {
-            const R dd = R(dl);
-            R* o = mk_write(g, t) + ks_f;
+            for (int j = 0; j < N_FEAT; j += 2)
+                *reinterpret_cast<uint32_t*>(xt + lane * XS + j) = pack_bf16(feat[j], feat[j + 1]);
+            __syncwarp();
+            const float z3 = mlp_forward_regs(S.frag, S.bias, xt, lane);
+            __syncwarp();   // the tile is rewritten by the warp's next tile
+            float dl = mlp_output(z3);
+            if (!(dl >= 0.0f && dl <= MLP_DMAX)) dl = float(P.damping);
+            if (damp_f) {
+                const R dd = R(dl);
+                R* o = mk_write(g, t) + ks_f;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) o[21 + i] = (R(1) - dd) * ek_new[i] + dd * ek_old[i];
+                for (int i = 0; i < 6; ++i) o[21 + i] = (R(1) - dd) * ek_new[i] + dd * ek_old[i];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const R e = (R(1) - dd) * em_new[i] + dd * em_old[i];
-                g.ml_out[(size_t)(6 + i) * n_f + f] = e;
-                sum[6 + i] = e;
+                for (int i = 0; i < 3; ++i) {
+                    const R e = (R(1) - dd) * em_new[i] + dd * em_old[i];
+                    g.ml_out[(size_t)(6 + i) * n_f + f] = e;
+                    sum[6 + i] = e;
+                }
             }
         }
     }

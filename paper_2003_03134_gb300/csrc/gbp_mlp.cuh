@@ -153,4 +153,74 @@ __device__ __forceinline__ float mlp_forward_warp(const uint32_t* frag, const fl
 
 __device__ __forceinline__ float mlp_output(float z3) { return MLP_DMAX / (1.0f + __expf(-z3)); }
 
+// Register-resident forward pass for inference: the D fragments of one
+// layer (16 x 8 tiles, FP32) are exactly the A fragments of the next layer
+// (16 x 16, BF16 pairs) once packed -- tile 2j supplies columns 0-7 and tile
+// 2j+1 columns 8-15 of k-step j -- so activations never leave registers.
+// Bitwise equal to mlp_forward_warp (same roundings, same mma order).
+// X: the warp's 32 x 16 input tile (BF16, stride XS) in shared memory;
+// frag/bias as for mlp_forward_warp.  Returns z3 of row `lane`.
+__device__ __forceinline__ float mlp_forward_regs(const uint32_t* frag, const float* bias, const __nv_bfloat16* X,
+                                                  int lane) {
+    const int g = lane >> 2, q = lane & 3;
+    float z[2][2];   // [m-tile][row g / g + 8] of output column 0 (lanes with q == 0)
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        // layer 1: h1 = relu(X W1 + b1) -> A fragments of layer 2
+        uint32_t x0, x1, x2, x3;
+        load_a(X, XS, 16 * mt, 0, lane, x0, x1, x2, x3);
+        uint32_t a1[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+            uint32_t b0, b1;
+            load_b(frag, FT_L1 + nt, lane, b0, b1);
+            mma_bf16(d, x0, x1, x2, x3, b0, b1);
+            const int c = 8 * nt + 2 * q;
+            const float bc0 = bias[c], bc1 = bias[c + 1];
+            const uint32_t lo = pack_bf16(fmaxf(d[0] + bc0, 0.f), fmaxf(d[1] + bc1, 0.f));
+            const uint32_t hi = pack_bf16(fmaxf(d[2] + bc0, 0.f), fmaxf(d[3] + bc1, 0.f));
+            a1[nt >> 1][(nt & 1) ? 2 : 0] = lo;
+            a1[nt >> 1][(nt & 1) ? 3 : 1] = hi;
+        }
+        // layer 2: h2 = relu(h1 W2 + b2) -> A fragments of layer 3
+        uint32_t a2[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                uint32_t b0, b1;
+                load_b(frag, FT_L2 + ks * 8 + nt, lane, b0, b1);
+                mma_bf16(d, a1[ks][0], a1[ks][1], a1[ks][2], a1[ks][3], b0, b1);
+            }
+            const int c = 8 * nt + 2 * q;
+            const float bc0 = bias[MLP_H + c], bc1 = bias[MLP_H + c + 1];
+            const uint32_t lo = pack_bf16(fmaxf(d[0] + bc0, 0.f), fmaxf(d[1] + bc1, 0.f));
+            const uint32_t hi = pack_bf16(fmaxf(d[2] + bc0, 0.f), fmaxf(d[3] + bc1, 0.f));
+            a2[nt >> 1][(nt & 1) ? 2 : 0] = lo;
+            a2[nt >> 1][(nt & 1) ? 3 : 1] = hi;
+        }
+        // layer 3: z3 = h2 W3 (column 0 of the output tile)
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+            uint32_t b0, b1;
+            load_b(frag, FT_L3 + ks, lane, b0, b1);
+            mma_bf16(d, a2[ks][0], a2[ks][1], a2[ks][2], a2[ks][3], b0, b1);
+        }
+        z[mt][0] = d[0];
+        z[mt][1] = d[2];
+    }
+    // row r = lane: m-tile r / 16, held by lane 4 (r % 8) as row g (r % 16 < 8) or g + 8
+    const int src = (lane & 7) << 2;
+    const float v00 = __shfl_sync(0xffffffffu, z[0][0], src);
+    const float v01 = __shfl_sync(0xffffffffu, z[0][1], src);
+    const float v10 = __shfl_sync(0xffffffffu, z[1][0], src);
+    const float v11 = __shfl_sync(0xffffffffu, z[1][1], src);
+    const float v = (lane < 16) ? ((lane & 8) ? v01 : v00) : ((lane & 8) ? v11 : v10);
+    (void)g;
+    return v + bias[2 * MLP_H];
+}
+
 }  // namespace gbp

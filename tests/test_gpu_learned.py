@@ -2,9 +2,9 @@
 record schedule's features and targets) against the FP64 oracle.
 
 Parity has three parts.  (1) A constant network (W3 = 0) turns the learned
-schedule into the fixed schedule with d = its output and no hold after a
-relinearisation, which the oracle computes exactly: FP32 tolerance as for
-fixed damping, TOL32 = 1e-5 relative per variable.  (2) The features and
+schedule into the fixed schedule with d = its output, which the oracle
+computes exactly: FP32 tolerance as for fixed damping, TOL32 = 1e-5
+relative per variable.  (2) The features and
 targets recorded on the GPU against the oracle's, row by row: features to
 2e-4 absolute (FP32 messages), targets to 0.02 where both messages clearly
 changed (a target is a ratio of differences of messages, so FP32 rounding
@@ -17,7 +17,7 @@ import pytest
 
 import oracle
 from oracle import mlp
-from paper_2003_03134_gb300 import build, gbp, synth
+from paper_2003_03134_gb300 import build, gbp, learned, synth
 
 pytestmark = pytest.mark.gpu
 
@@ -92,7 +92,7 @@ def test_constant_network_matches_oracle(torch, mode):
     g.iterate(80)
     kf, lm = g.beliefs()
     st = g.stats()
-    o = oracle.Oracle(p, huber_nsigma=2.0, undamped_iters=1, damping=d, **DET)
+    o = oracle.Oracle(p, huber_nsigma=2.0, damping=d, **DET)
     o.iterate(80)
     okf, olm = o.world()
     e = rel_err(kf, lm, okf, olm)
@@ -110,7 +110,7 @@ def test_constant_network_fp64_matches_oracle_tightly(torch):
     g.set_damping_model(net)
     g.iterate(100)
     kf, lm = g.beliefs()
-    o = oracle.Oracle(p, huber_nsigma=2.0, undamped_iters=1, damping=d)
+    o = oracle.Oracle(p, huber_nsigma=2.0, damping=d)
     o.iterate(100)
     okf, olm = o.world()
     assert rel_err(kf, lm, okf, olm).max() < 1e-8
@@ -182,17 +182,32 @@ def _record_pair(torch, p, n_conv, n_rec, prm):
 
 def test_recorded_features_and_targets_match_oracle(torch):
     p = synth.make_walk(5, n_kf=20, n_lm=250)
-    gX, gT, oX, oT, gw, ow = _record_pair(torch, p, 150, 15, dict(huber_nsigma=2.0, **DET))
+    gX, gT, oX, oT, gw, ow = _record_pair(torch, p, 150, 20, dict(huber_nsigma=2.0, **DET))
     assert (gX != -7.0).all() and (gT != -7.0).all()
     err = np.abs(gX - oX)
-    assert err.max() <= 2e-4, np.unravel_index(err.argmax(), err.shape)
-    # recording runs the fixed schedule: the beliefs still match the oracle
-    assert rel_err(*gw, *ow).max() <= TOL32
+    # every feature but the step cosines (7, 11) is compared everywhere.  A
+    # cosine's error is about the messages' FP32 trajectory error (~1e-5 of
+    # |eta|, the parity tolerance) over the step lengths: with both steps
+    # above 1e-2 of |eta| it stays below ~2e-3
+    plain = [j for j in range(16) if j not in (7, 11)]
+    assert err[..., plain].max() <= 2e-4, np.unravel_index(err[..., plain].argmax(), err[..., plain].shape)
+    for j, a, b in ((7, 4, 5), (11, 8, 9)):
+        big = (oX[..., a] > 1e-2) & (oX[..., b] > 1e-2)
+        assert big.sum() > 1000
+        assert err[..., j][big].max() <= 5e-3, err[..., j][big].max()
+        assert np.median(err[..., j][big]) <= 1e-4
+    # recording runs the fixed schedule unchanged: bitwise the plain run's beliefs
+    g = gbp.Graph(p, huber_nsigma=2.0, **DET)
+    g.iterate(20)
+    for a, b in zip(g.beliefs(), gw):
+        np.testing.assert_array_equal(a, b)
+    g.close()
     # targets never used by the learned schedule are flagged on both sides
-    never = (oX[..., 14] == 0.0) | (oX[..., 1] == 0.0)
+    hold = oracle.DEFAULTS["undamped_iters"]
+    never = (oX[..., 14] < hold / 50.0 - 1e-9) | (oX[..., 1] == 0.0)
     assert (oT[never] == -1.0).all() and (gT[never] == -1.0).all()
     clear = (oT >= 0) & (oX[..., 4] > 1e-2) & (oX[..., 8] > 1e-2)
-    assert clear.sum() > 2000
+    assert clear.sum() > 1000
     dT = np.abs(gT[clear] - oT[clear])
     assert dT.max() <= 0.02, dT.max()
     assert np.median(dT) <= 1e-3
@@ -213,3 +228,49 @@ def test_record_arguments(torch):
     g.record(2, X.data_ptr(), T.data_ptr())
     assert g.stats()["iterations"] == 2
     g.close()
+
+
+@pytest.mark.parametrize("seed", [0, 2])
+def test_trained_network_gain(torch, seed):
+    """What the shipped network (trained on problems with seeds 10000-10999)
+    gains on held-out paper-scale problems: fewer iterations to 0.01 px of
+    average reprojection error against the converged solution, no more
+    iterations to 0.1 px or 1 px, and the same final error."""
+    net = gbp.DampingNet(learned.trained_params())
+    r = learned.compare(torch, synth.make_walk(seed=seed), net)
+    fx, lr = r["fixed"], r["learned"]
+    print(seed, {k: (fx[k], lr[k]) for k in ("iters", "ms")})
+    assert lr["iters"]["0.01"] <= 0.85 * fx["iters"]["0.01"]
+    assert lr["iters"]["0.1"] <= fx["iters"]["0.1"]
+    assert lr["iters"]["1.0"] <= fx["iters"]["1.0"]
+    assert abs(lr["final"]["are"] - fx["final"]["are"]) <= 1e-2
+    net.close()
+
+
+def test_trained_network_reaches_the_fixed_damping_beliefs(torch):
+    """Damping does not move the fixed point.  With relinearisation at every
+    10th iteration (no threshold) the FP32 iteration ends in a small limit
+    cycle -- relinearising at rounded means perturbs the weakly constrained
+    points by ~1e-5 each period -- so the comparison is made at the same
+    phase of that cycle and against its own amplitude: the learned end state
+    lies within twice the fixed schedule's half-period drift (and at least
+    within TOL32) of the fixed end state, with the same ARE to 1e-3 px.
+    Priors end at 1/10 of a measurement (not 1/100) so that the weakly
+    observed directions converge within the 4000 iterations."""
+    p = synth.make_walk(1, n_kf=40, n_lm=600)
+    net = gbp.DampingNet(learned.trained_params())
+    fixed = gbp.Graph(p, huber_nsigma=2.0, prior_final_scale=0.1, **DET)
+    fixed.iterate(4000)
+    f_end = fixed.beliefs()
+    f_are = fixed.stats()["are"]
+    fixed.iterate(5)
+    drift = rel_err(*fixed.beliefs(), *f_end).max()
+    fixed.close()
+    g = gbp.Graph(p, huber_nsigma=2.0, prior_final_scale=0.1, damping_mode=1, **DET)
+    g.set_damping_model(net)
+    g.iterate(4000)
+    e = rel_err(*g.beliefs(), *f_end)
+    assert e.max() <= max(TOL32, 2.0 * drift), (e.max(), drift)
+    assert abs(g.stats()["are"] - f_are) <= 1e-3
+    g.close()
+    net.close()

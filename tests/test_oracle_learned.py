@@ -41,13 +41,13 @@ def _constant_net(d):
 
 def test_constant_network_is_the_fixed_schedule():
     """W3 = 0 makes every d_f = 0.9 sigmoid(b3); the learned schedule then
-    is the fixed one with that d and no undamped hold beyond t = t_lin."""
+    is the fixed one with that d (same undamped hold after relinearising)."""
     p = synth.make_walk(3, n_kf=15, n_lm=150)
     net = _constant_net(0.3)
     d = oracle.net_forward(net, np.zeros(16))
     assert abs(d - 0.3) < 1e-12
-    a = oracle.Oracle(p, huber_nsigma=2.0, undamped_iters=1, damping=d)
-    b = oracle.Oracle(p, huber_nsigma=2.0, undamped_iters=1, damping=d)
+    a = oracle.Oracle(p, huber_nsigma=2.0, damping=d)
+    b = oracle.Oracle(p, huber_nsigma=2.0, damping=d)
     b.set_damping_net(net)
     a.iterate(60)
     b.iterate(60)
@@ -87,11 +87,15 @@ def test_record_needs_a_reference():
         o.iterate_record(1)
 
 
-def _brute_force_damping(nw, old, ref):
-    """argmin over a fine grid of d in [0, 0.9] of |(1-d) nw + d old - ref|."""
+def _brute_force_damping(sides):
+    """argmin over a fine grid of d in [0, 0.9] of the sum over the sides
+    (nw, old, ref) of |(1-d) nw + d old - ref|^2 / |old - nw|^2."""
     grid = np.linspace(0.0, 0.9, 9001)
-    cand = (1.0 - grid)[:, None] * nw[None, :] + grid[:, None] * old[None, :]
-    return grid[np.argmin(((cand - ref[None, :]) ** 2).sum(axis=1))]
+    total = np.zeros_like(grid)
+    for nw, old, ref in sides:
+        cand = (1.0 - grid)[:, None] * nw[None, :] + grid[:, None] * old[None, :]
+        total += ((cand - ref[None, :]) ** 2).sum(axis=1) / ((old - nw) @ (old - nw))
+    return grid[np.argmin(total)]
 
 
 def test_features_and_targets_from_public_pieces():
@@ -128,7 +132,11 @@ def test_features_and_targets_from_public_pieces():
     def rel(a, b):
         return np.linalg.norm(a - b, axis=1) / (np.linalg.norm(a, axis=1) + np.linalg.norm(b, axis=1) + 1e-30)
 
-    hist = np.zeros((nf, 6))
+    def cos(a, b):
+        return (a * b).sum(axis=1) / (np.linalg.norm(a, axis=1) * np.linalg.norm(b, axis=1) + 1e-30)
+
+    hist = np.zeros((nf, 4))
+    ek_prev, el_prev = np.zeros((nf, 6)), np.zeros((nf, 3))
     n_checked = 0
     for t in range(12):
         lk0, ek0, ll0, el0 = o.messages()
@@ -149,14 +157,15 @@ def test_features_and_targets_from_public_pieces():
         want[:, 1] = k
         want[:, 2] = tr_lk / (tr_lk + tr_pk + 1e-30)
         want[:, 3] = tr_ll / (tr_ll + tr_pl + 1e-30)
-        want[:, 4], want[:, 5:8] = ck, hist[:, 0:3]
-        want[:, 8], want[:, 9:12] = cm, hist[:, 3:6]
+        want[:, 4], want[:, 5:7], want[:, 7] = ck, hist[:, 0:2], cos(nk - ek0, ek0 - ek_prev)
+        want[:, 8], want[:, 9:11], want[:, 11] = cm, hist[:, 2:4], cos(nl - el0, el0 - el_prev)
         want[:, 12] = np.log1p(deg_k) / 5.0
         want[:, 13] = np.log1p(deg_l) / 3.0
         want[:, 14] = min(t, 50) / 50.0
         want[:, 15] = min(t, 50) / 50.0
         np.testing.assert_allclose(X, want, rtol=0, atol=1e-7)
-        hist = np.concatenate([ck[:, None], hist[:, 0:2], cm[:, None], hist[:, 3:5]], axis=1)
+        hist = np.stack([ck, hist[:, 0], cm, hist[:, 2]], axis=1)
+        ek_prev, el_prev = ek0, el0
 
         for f in range(nf):
             if t == 0 or k[f] == 0.0:
@@ -166,8 +175,8 @@ def test_features_and_targets_from_public_pieces():
             for nw, old, r in ((nk[f], ek0[f], rk[f]), (nl[f], el0[f], rl[f])):
                 u = old - nw
                 if u @ u > 1e-10 * (nw @ nw + old @ old):
-                    sides.append(_brute_force_damping(nw, old, r))
-            expect = np.mean(sides) if sides else -1.0
+                    sides.append((nw, old, r))
+            expect = _brute_force_damping(sides) if sides else -1.0
             assert abs(T[f] - expect) <= 2e-4, (t, f, T[f], expect)
             n_checked += 1
     assert n_checked > 1000
