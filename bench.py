@@ -79,18 +79,20 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(n_f):
-    """DRAM bytes per factor-kernel launch from the committed ncu summary,
-    scaled to this launch's factor count; None if the kernel changed since."""
+def ncu_traffic(n_f, regime):
+    """DRAM bytes per factor-kernel launch from the committed ncu capture of
+    the same regime ("l2_resident" for the paper-scale problem, "hbm" for
+    the batched workload), scaled to this launch's factor count; None if
+    the kernel changed since the capture."""
     path = os.path.join(ROOT, "profiles", "factor_kernel_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
     except Exception:
         return None
-    if d.get("kernel_source_hash") != kernel_source_hash():
+    if d.get("kernel_source_hash") != kernel_source_hash() or regime not in d:
         return None
-    return float(d["dram_bytes_per_factor"]) * n_f
+    return float(d[regime]["dram_bytes_per_factor"]) * n_f
 
 
 class ClockSampler:
@@ -225,31 +227,34 @@ def oracle_solution(p, max_iters, tol):
     return kf, lm, it, dt, t_1px
 
 
-def roofline(p, iter_ms, fac_ms, mode):
+def roofline(p, iter_ms, fac_ms, mode, regime="l2_resident"):
     bytes_iter = BYTES_PER_FACTOR * p.n_obs + BYTES_PER_KF * p.n_kf + BYTES_PER_LM * p.n_lm
     peak, peak_kind = peaks()
     achieved = bytes_iter / (iter_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": ncu_traffic(p.n_obs),
+            "traffic": ncu_traffic(p.n_obs, regime),
             "kernel": "persistent_kernel<float>" if mode == 1 else "factor_kernel<float> + belief_kernel<float>",
             "launch_mode": mode, "bytes_per_iteration": bytes_iter, "ms_per_iteration": iter_ms,
             "factor_kernel_ms": fac_ms, "peak_source": f"{peak_kind} HBM copy bandwidth"}
 
 
+def _batch_counts(seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return int(rng.integers(10, 201)), int(rng.integers(100, 5001))
+
+
 def _make_batch_problem(seed):
     from paper_2003_03134_gb300 import synth
-    rng = np.random.Generator(np.random.PCG64(seed))
-    n_kf = int(rng.integers(10, 201))
-    n_lm = int(rng.integers(100, 5001))
+    n_kf, n_lm = _batch_counts(seed)
     return synth.make_walk(seed=seed, n_kf=n_kf, n_lm=n_lm, name=f"batch{seed}")
 
 
-def batch_problems(n, first_seed=0):
-    """The batched workload: n independent walk problems, problem i seeded by
+def batch_problems(seeds):
+    """Problems of the batched workload: problem i is a walk problem seeded by
     i with U{10..200} keyframes and U{100..5000} points (generated in a
     spawn-context process pool)."""
     import multiprocessing as mp
-    seeds = list(range(first_seed, first_seed + n))
+    seeds = list(seeds)
     try:
         with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
             return pool.map(_make_batch_problem, seeds)
@@ -257,27 +262,41 @@ def batch_problems(n, first_seed=0):
         return [_make_batch_problem(s) for s in seeds]
 
 
-def measure_at_scale(gbp, stream, n_problems=256, iters=20):
+def measure_at_scale(gbp, stream, rank=0, world=1, n_problems=256, iters=20, launch_mode=0, device=None):
     """Throughput and HBM roofline on the batched workload: n_problems
-    independent problems of uneven size in one graph (one persistent launch
-    per gbp_iterate), state far larger than L2."""
-    probs = batch_problems(n_problems)
-    g = gbp.Graph(probs, stream=stream.cuda_stream, huber_nsigma=HUBER)
+    independent problems of uneven size, shared out over the ranks by size
+    (their point counts, which set the factor counts) and solved as one
+    graph per rank (one persistent launch per gbp_iterate), state far larger
+    than L2.  Whole-job figures: total factors over the slowest rank's time."""
+    from paper_2003_03134_gb300 import shard
+    sizes = [_batch_counts(s)[1] for s in range(n_problems)]
+    mine = shard.partition(sizes, world)[rank]
+    probs = batch_problems(mine)
+    g = gbp.Graph(probs if len(probs) > 1 else probs[0], stream=stream.cuda_stream, huber_nsigma=HUBER)
     n_kf, n_lm, n_f = gbp.gbp_get_sizes(g.h)
-    mode, ms1, ms2 = g.autotune(8)
+    if launch_mode:
+        g.set_params(launch_mode=launch_mode)
+        mode, ms1, ms2 = launch_mode, None, None
+    else:
+        mode, ms1, ms2 = g.autotune(8)
+    import torch
+    torch.cuda.nvtx.range_push("bench_scale")
     iter_ms, fac_ms = g.profile(iters)
+    torch.cuda.nvtx.range_pop()
     st = g.stats()
     g.close()
+    job_ms, job_f = shard.reduce_timing(iter_ms, n_f, device=device)
 
     class _Size:
         pass
     sz = _Size()
     sz.n_obs, sz.n_kf, sz.n_lm = n_f, n_kf, n_lm
-    return {"workload": f"{n_problems} independent walk problems of uneven size in one graph "
-                        f"({n_kf} keyframes, {n_lm} points, {n_f} factors)",
-            "value": n_f / (iter_ms * 1e-3), "unit": UNIT, "ms_per_iteration": iter_ms,
+    return {"workload": f"{n_problems} independent walk problems of uneven size, {len(mine)} on this rank in one "
+                        f"graph ({n_kf} keyframes, {n_lm} points, {n_f} factors)",
+            "value": job_f / (job_ms * 1e-3), "unit": UNIT, "ms_per_iteration": job_ms,
+            "ranks": world, "partition": "size-balanced (largest first to the least-loaded rank)",
             "autotune_ms_per_iteration": {"persistent": ms1, "per_phase": ms2},
-            "roofline": roofline(sz, iter_ms, fac_ms, mode), "fp64_fallbacks": st["fp64_fallbacks"]}
+            "roofline": roofline(sz, iter_ms, fac_ms, mode, "hbm"), "fp64_fallbacks": st["fp64_fallbacks"]}
 
 
 def run_gpu(args, rank, world, local):
@@ -310,12 +329,14 @@ def run_gpu(args, rank, world, local):
     iters = []
     launches0 = g.stats()["kernel_launches"]
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("bench_timed")   # profilers select the timed launches by this range
         for i in range(args.steps):
             flush.fill_(i & 0xFF)   # evict L2 between steps (untimed)
             starts[i].record(stream)
             g.reset()
             iters.append(g.iterate(0))
             ends[i].record(stream)
+        torch.cuda.nvtx.range_pop()
         barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = float(sum(step_ms))
@@ -335,7 +356,8 @@ def run_gpu(args, rank, world, local):
     g.reset()
     iter_ms, fac_ms = g.profile(64)
     roof = roofline(p, iter_ms, fac_ms, st_timed["launch_mode"])
-    at_scale = measure_at_scale(gbp, stream) if (rank == 0 and not args.no_scale) else None
+    at_scale = None if args.no_scale else measure_at_scale(gbp, stream, rank, world, args.scale_problems,
+                                                             device=dev)
 
     line = None
     if rank == 0:
@@ -418,6 +440,24 @@ def run_gpu(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_scale_only(args, rank, world, local):
+    import torch
+    from paper_2003_03134_gb300 import build, gbp
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    r = measure_at_scale(gbp, torch.cuda.current_stream(dev), rank, world, args.scale_problems,
+                         launch_mode=args.launch_mode, device=dev)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps({"at_scale": r}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -427,9 +467,15 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=20, help="oracle iterations per reference step")
     ap.add_argument("--oracle-iters", type=int, default=1000, help="cap of the oracle solve (CPU baseline)")
     ap.add_argument("--no-scale", action="store_true", help="skip the batched at-scale measurement")
+    ap.add_argument("--scale-problems", type=int, default=256, help="problems in the batched measurement")
+    ap.add_argument("--scale-only", action="store_true",
+                    help="only the batched measurement (profiling runs); prints its own JSON line")
+    ap.add_argument("--launch-mode", type=int, default=0, help="with --scale-only: 1 persistent, 2 per phase")
     args = ap.parse_args()
     rank, world, local = dist_env()
-    if args.impl == "reference":
+    if args.scale_only:
+        run_scale_only(args, rank, world, local)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_gpu(args, rank, world, local)
