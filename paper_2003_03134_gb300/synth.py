@@ -23,7 +23,7 @@ import numpy as np
 from scipy.spatial.transform import Rotation
 
 __all__ = ["Problem", "StreamStep", "make_circle", "make_walk", "make_loop", "make_batch",
-           "make_chain", "make_stream", "stream_plan", "concat", "workload"]
+           "make_chain", "make_stream", "stream_plan", "concat", "subgraph", "workload"]
 
 
 @dataclass
@@ -420,6 +420,26 @@ def concat(problems: list[Problem], name: str | None = None) -> Problem:
                    obs_uv=cat("obs_uv"), obs_outlier=cat("obs_outlier"),
                    anchor_kf=np.concatenate([p.anchor_kf + kf_off[i] for i, p in enumerate(problems)]).astype(np.int32),
                    params=dict(p0.params))
+
+
+def subgraph(p: Problem, n_kf: int, min_obs: int = 2) -> Problem:
+    """The part of ``p`` seen by its first ``n_kf`` keyframes: those
+    keyframes, every point observed at least ``min_obs`` times by them, and
+    those observations, re-indexed (anchors among the kept keyframes stay
+    anchored)."""
+    m = p.obs_kf < n_kf
+    cnt = np.bincount(p.obs_lm[m], minlength=p.n_lm)
+    keep_lm = np.flatnonzero(cnt >= min_obs)
+    remap = np.full(p.n_lm, -1, dtype=np.int64)
+    remap[keep_lm] = np.arange(keep_lm.size)
+    keep = m & (remap[p.obs_lm] >= 0)
+    return Problem(name=f"{p.name}_kf{n_kf}", seed=p.seed, fx=p.fx, fy=p.fy, cx=p.cx, cy=p.cy,
+                   width=p.width, height=p.height, kf_Rt_true=p.kf_Rt_true[:n_kf].copy(),
+                   kf_Rt_init=p.kf_Rt_init[:n_kf].copy(), lm_true=p.lm_true[keep_lm].copy(),
+                   lm_init=p.lm_init[keep_lm].copy(), obs_kf=p.obs_kf[keep].astype(np.int32),
+                   obs_lm=remap[p.obs_lm[keep]].astype(np.int32), obs_uv=p.obs_uv[keep].copy(),
+                   obs_outlier=p.obs_outlier[keep].copy(),
+                   anchor_kf=p.anchor_kf[p.anchor_kf < n_kf].astype(np.int32), params=dict(p.params))
 
 
 def workload(name: str, seed: int = 0) -> Problem:
