@@ -48,7 +48,7 @@ typedef enum {
     GBP_EINVAL = 1,     /* invalid argument (index out of range, non-finite value, bad size)   */
     GBP_ENOMEM = 2,     /* host or device allocation failed                                    */
     GBP_ECUDA = 3,      /* a CUDA call failed (no device, launch error, ...)                   */
-    GBP_EDIVERGED = 4,  /* a belief stopped being positive definite or became non-finite       */
+    GBP_EDIVERGED = 4,  /* a belief stopped being positive definite or its mean became non-finite */
     GBP_ETIMEOUT = 5,   /* a bounded device-side wait gave up                                   */
     GBP_ESTATE = 6      /* call not valid in the graph's current state                          */
 } gbp_status;
@@ -95,6 +95,11 @@ typedef struct {
     int32_t launch_mode;        /* launch mode gbp_iterate() used last (1 persistent, 2 per phase) */
     int64_t kernel_launches;    /* kernels this graph has launched since creation (graph replays
                                    count each kernel they contain)                                 */
+    int32_t held_messages;      /* messages left at their previous value since creation / reset:
+                                   the incoming precision (belief / previous message of the
+                                   marginalised variable) was not positive definite even after the
+                                   FP64 redo -- in FP32 mode, rounding of the stored messages in a
+                                   direction that only the weak prior constrains                    */
 } gbp_stats;
 
 /* Fill *out with the defaults listed above. */

@@ -72,6 +72,8 @@ def lib():
         L.orc_add_keyframe.argtypes = [C.c_void_p, _D, C.c_int, _D, C.c_int, _I, _D]
         L.orc_sizes.argtypes = [C.c_void_p, _I, _I, _I]
         L.orc_relinearisations.restype = C.c_long
+        L.orc_held_messages.argtypes = [C.c_void_p]
+        L.orc_held_messages.restype = C.c_long
         L.orc_so3_exp.argtypes = [_D, _D]
         L.orc_so3_left_jacobian.argtypes = [_D, _D]
         L.orc_huber_weight.restype = C.c_double
@@ -310,6 +312,9 @@ class Oracle:
 
     def relinearisations(self) -> int:
         return lib().orc_relinearisations(self._h)
+
+    def held_messages(self) -> int:
+        return lib().orc_held_messages(self._h)
 
     # learned damping
     def set_damping_net(self, params):

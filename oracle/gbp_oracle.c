@@ -291,6 +291,7 @@ struct orc_graph {
     double *x0;                          /* its linearisation point [xk; xl]     */
     int *tlin;                           /* iteration at which it was taken      */
     long n_relin;                        /* relinearisations since creation      */
+    long n_held;                         /* messages held at their previous value */
     double *lin_r2, *lin_k;              /* |r|^2 and Huber weight at the linearisation (0, 0 if inactive) */
     /* learned damping (no counterpart in the paper) */
     double *hist;                        /* per factor (ORC_HIST): relative message changes at t-1 and t-2,
@@ -674,11 +675,21 @@ static int iterate_impl(orc_graph* g, int n, double* max_dmu, int mode, double* 
              * previous message to it is the variable-to-factor message */
             for (int i = 0; i < 9; ++i) lam_in[i] = g->lm_lam[9 * m + i] - g->ml_lam[9 * f + i];
             for (int i = 0; i < 3; ++i) eta_in[i] = g->lm_eta[3 * m + i] - g->ml_eta[3 * f + i];
-            if (orc_factor_message(A, c, 0, lam_in, eta_in, g->nk_lam + 36 * f, g->nk_eta + 6 * f) != 0) { status = -1; break; }
+            /* a message whose incoming precision is not positive definite
+             * cannot be formed; it keeps its previous value */
+            if (orc_factor_message(A, c, 0, lam_in, eta_in, g->nk_lam + 36 * f, g->nk_eta + 6 * f) != 0) {
+                memcpy(g->nk_lam + 36 * f, g->mk_lam + 36 * f, sizeof(double) * 36);
+                memcpy(g->nk_eta + 6 * f, g->mk_eta + 6 * f, sizeof(double) * 6);
+                g->n_held += 1;
+            }
             /* to the landmark */
             for (int i = 0; i < 36; ++i) lam_in[i] = g->kf_lam[36 * kk + i] - g->mk_lam[36 * f + i];
             for (int i = 0; i < 6; ++i) eta_in[i] = g->kf_eta[6 * kk + i] - g->mk_eta[6 * f + i];
-            if (orc_factor_message(A, c, 1, lam_in, eta_in, g->nl_lam + 9 * f, g->nl_eta + 3 * f) != 0) { status = -1; break; }
+            if (orc_factor_message(A, c, 1, lam_in, eta_in, g->nl_lam + 9 * f, g->nl_eta + 3 * f) != 0) {
+                memcpy(g->nl_lam + 9 * f, g->ml_lam + 9 * f, sizeof(double) * 9);
+                memcpy(g->nl_eta + 3 * f, g->ml_eta + 3 * f, sizeof(double) * 3);
+                g->n_held += 1;
+            }
             /* damping of the eta update (Sec. 5): messages stay undamped for
              * undamped_iters iterations after a (re)linearisation (Sec. 8); the
              * message sent in the iteration of a (re)linearisation -- including
@@ -844,6 +855,8 @@ int orc_huber_count(const orc_graph* g)
 }
 
 long orc_relinearisations(const orc_graph* g) { return g->n_relin; }
+
+long orc_held_messages(const orc_graph* g) { return g->n_held; }
 
 /* ------------------------------------------------------------------------
  * incremental SLAM (Sec. 9.2)

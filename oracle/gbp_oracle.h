@@ -71,7 +71,8 @@ int orc_add_keyframe(orc_graph* g, const double* kf_Rt_init, int n_new_lm, const
 int orc_sizes(const orc_graph* g, int* n_kf, int* n_lm, int* n_obs);
 
 /* Run n synchronous iterations.  Returns 0, or -1 if a belief stopped being
- * positive definite.  *max_dmu (nullable) = max_v |mu_v^{t+1} - mu_v^t|_inf of
+ * positive definite (a message whose incoming precision is not positive
+ * definite keeps its previous value instead).  *max_dmu (nullable) = max_v |mu_v^{t+1} - mu_v^t|_inf of
  * the last iteration. */
 int orc_iterate(orc_graph* g, int n, double* max_dmu);
 int orc_iterations_done(const orc_graph* g);
@@ -100,6 +101,10 @@ double orc_are_vs(const orc_graph* g, const double* ref_kf_Rt, const double* ref
 int orc_huber_count(const orc_graph* g);
 /* Relinearisations performed since creation (all factors). */
 long orc_relinearisations(const orc_graph* g);
+/* Messages left at their previous value because their incoming precision
+ * (the marginalised variable's belief divided by the previous message) was
+ * not positive definite, so the Schur complement of Sec. 5 does not exist. */
+long orc_held_messages(const orc_graph* g);
 
 /* ---- learned damping (no counterpart in the paper: a per-factor d in place
  * of the fixed d of Sec. 5 / Sec. 8) ----

@@ -479,10 +479,7 @@ gbp_status read_ctl(gbp_graph* g) {
     if (g->h_ctl[CTL_ERR]) {
         int w = g->h_ctl[CTL_ERR_WHERE];
         char buf[160];
-        if (w < 0)
-            snprintf(buf, sizeof buf, "factor %d: an incoming precision was not positive definite", -1 - w);
-        else
-            snprintf(buf, sizeof buf, "variable %d: belief not positive definite or mean not finite", w);
+        snprintf(buf, sizeof buf, "variable %d: belief not positive definite or mean not finite", w);
         return fail(g, GBP_EDIVERGED, buf);
     }
     return GBP_OK;
@@ -1264,6 +1261,7 @@ gbp_status gbp_get_stats(const gbp_graph* cg, gbp_stats* out) {
     out->huber_count = (int32_t)g->h_met[MET_HUBER];
     out->fp64_fallbacks = g->h_ctl[CTL_FALLBACKS];
     out->relinearisations = g->h_ctl[CTL_RELINS];
+    out->held_messages = g->h_ctl[CTL_HELD];
     out->launch_mode = g->last_mode;
     out->kernel_launches = g->launches;
     return st;

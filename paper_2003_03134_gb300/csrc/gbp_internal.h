@@ -128,6 +128,7 @@ enum Ctl : int {
     CTL_BAR_COUNT = 9,     // grid barrier arrivals
     CTL_BAR_GEN = 10,      // grid barrier generation
     CTL_ITERS_RUN = 11,    // iterations run by the last persistent launch
+    CTL_HELD = 12,         // messages left at their previous value (incoming precision not positive definite)
     CTL_N = 16
 };
 

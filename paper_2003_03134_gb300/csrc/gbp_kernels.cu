@@ -329,35 +329,78 @@ __device__ __forceinline__ bool message(C* Pb, const C* qb, const C Jb[2][nb], c
     return ok;
 }
 
+// The keyframe's incoming message for the FP64 fallback, summed from its
+// parts: the keyframe's prior at iteration t (as the belief b^t added it)
+// plus every OTHER factor's current message to it -- b^t - m^t without the
+// rounding of the FP32 belief, whose sum over ~100 messages can leave the
+// difference indefinite when this factor's message dominates a direction.
+// A keyframe's messages m^t sit contiguously in its CSR slots [i0, i1) of
+// the buffer this iteration only reads.
+template <typename R>
+struct KfCavity {
+    const R* msgs;          // m^t in keyframe CSR order
+    const int32_t* kf_off;  // CSR offsets
+    const R* D;             // the keyframe's prior diagonal (6) and anchor diagonal (6), sigma = 1
+    const R* A;
+    int k, self;
+    R s, anchor_scale, inv_sigma2;   // prior scale s(t), anchor factor, 1 / sigma^2
+};
+
 // FP64 redo of one message of factor f from FP32 state (the fallback for an
 // ill-conditioned FP32 factorisation).  It re-reads its inputs -- the
-// factor's linearisation point, the adjacent belief and the factor's
-// previous message, none of which the calling thread has overwritten yet --
-// and writes the undamped message to out (element i at out[i * out_stride]),
-// so that the FP32 path keeps all of its operands in registers.
+// factor's linearisation point and the incoming message's parts, none of
+// which the calling thread has overwritten yet -- and writes the undamped
+// message to out (element i at out[i * out_stride]), so that the FP32 path
+// keeps all of its operands in registers.  Message to the keyframe: the
+// landmark's incoming message is b^t - m^t from bel_other and msg_other.
+// Message to the landmark: the keyframe's b^t - m^t first; if that is not
+// positive definite, summed exactly from its parts (KfCavity, a loop over
+// the keyframe's messages) and tried again.  All reads go through L2: in
+// the persistent kernel other SMs write these between iterations.
 template <typename R, bool to_landmark>
-__device__ __noinline__ bool message_fp64(const R* __restrict__ x0s, int n_f, int f, const double* __restrict__ Rref,
+__device__ __noinline__ bool message_fp64(const R* x0s, int n_f, int f, const double* __restrict__ Rref,
                                           const double* __restrict__ cref, const double* __restrict__ lref,
-                                          const R* __restrict__ zf, const R* __restrict__ bel_other,
-                                          const R* __restrict__ msg_other, int stride_other, R* out, int out_stride,
+                                          const R* zf, const R* bel_other, const R* msg_other, int stride_other,
+                                          KfCavity<R> kc, R* out, int out_stride,
                                           double fx, double fy, double cx, double cy, double inv_sigma2,
                                           double inv_sigma, double huber_n, double z_min) {
     KParams<double> P{};
     P.fx = fx; P.fy = fy; P.cx = cx; P.cy = cy;
     P.inv_sigma2 = inv_sigma2; P.inv_sigma = inv_sigma; P.huber_n = huber_n; P.z_min = z_min;
     double x0[9];
-    for (int i = 0; i < 9; ++i) x0[i] = double(x0s[(size_t)i * n_f + f]);
+    for (int i = 0; i < 9; ++i) x0[i] = double(__ldcg(x0s + (size_t)i * n_f + f));
     Lin<double> L;
-    linearise<double>(P, Rref, cref, lref, x0, double(zf[0]), double(zf[1]), L);
+    linearise<double>(P, Rref, cref, lref, x0, double(__ldcg(zf)), double(__ldcg(zf + 1)), L);
     constexpr int na = to_landmark ? 3 : 6, nb = to_landmark ? 6 : 3;
     constexpr int pa = na * (na + 1) / 2, pb = nb * (nb + 1) / 2;
     double Pb[pb], q[nb], lam[pa], eta[na], ratio;
     // incoming = belief of the marginalised variable / previous message to it
-    for (int i = 0; i < pb; ++i) Pb[i] = double(bel_other[i]) - double(msg_other[(size_t)i * stride_other]);
-    for (int i = 0; i < nb; ++i) q[i] = double(bel_other[pb + i]) - double(msg_other[(size_t)(pb + i) * stride_other]);
+    for (int i = 0; i < pb; ++i)
+        Pb[i] = double(__ldcg(bel_other + i)) - double(__ldcg(msg_other + (size_t)i * stride_other));
+    for (int i = 0; i < nb; ++i)
+        q[i] = double(__ldcg(bel_other + pb + i)) - double(__ldcg(msg_other + (size_t)(pb + i) * stride_other));
     bool ok;
-    if constexpr (to_landmark) ok = message<double, 3, 6>(Pb, q, L.Jk, L.Jl, L.y, L.W, lam, eta, ratio);
-    else ok = message<double, 6, 3>(Pb, q, L.Jl, L.Jk, L.y, L.W, lam, eta, ratio);
+    if constexpr (to_landmark) {
+        ok = message<double, 3, 6>(Pb, q, L.Jk, L.Jl, L.y, L.W, lam, eta, ratio);
+        if (!ok) {
+            for (int i = 0; i < pb; ++i) Pb[i] = 0.0;
+            for (int i = 0; i < nb; ++i) {
+                // as b^t added it, in the kernel's precision
+                Pb[pk(i, i)] = double((kc.s * kc.D[i] + kc.anchor_scale * kc.A[i]) * kc.inv_sigma2);
+                q[i] = 0.0;   // the prior mean is the chart origin
+            }
+            const int i0 = kc.kf_off[kc.k], i1 = kc.kf_off[kc.k + 1];
+            for (int j = i0; j < i1; ++j) {
+                if (j == kc.self) continue;
+                const R* r = kc.msgs + (size_t)j * KREC;
+                for (int i = 0; i < pb; ++i) Pb[i] += double(__ldcg(r + i));
+                for (int i = 0; i < nb; ++i) q[i] += double(__ldcg(r + pb + i));
+            }
+            ok = message<double, 3, 6>(Pb, q, L.Jk, L.Jl, L.y, L.W, lam, eta, ratio);
+        }
+    } else {
+        ok = message<double, 6, 3>(Pb, q, L.Jl, L.Jk, L.y, L.W, lam, eta, ratio);
+    }
     for (int i = 0; i < pa; ++i) out[(size_t)i * out_stride] = R(lam[i]);
     for (int i = 0; i < na; ++i) out[(size_t)(pa + i) * out_stride] = R(eta[i]);
     return ok;
@@ -826,7 +869,7 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
                 R* o = mk_write(g, t) + ks;
                 ok_m = message_fp64<R, false>(g.x0, n_f, f, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3,
                                               g.lm_ref + (size_t)m * 3, g.z + 2 * (size_t)f,
-                                              g.lm_bel + (size_t)m * LBEL, g.ml + f, n_f, o, 1,
+                                              g.lm_bel + (size_t)m * LBEL, g.ml + f, n_f, KfCavity<R>{}, o, 1,
                                               double(P.fx), double(P.fy), double(P.cx), double(P.cy),
                                               double(P.inv_sigma2), double(P.inv_sigma), double(P.huber_n),
                                               double(P.z_min));
@@ -836,7 +879,10 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
                 for (int i = 0; i < 6; ++i) eta_k[i] = o[21 + i];
                 atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
             }
-            if (!ok_m) raise_error(g.ctl, -1 - f);
+            // an incoming precision that is not positive definite even in
+            // FP64 (rounding of stored FP32 messages in a direction the prior
+            // barely constrains) leaves the message at its previous value
+            if (!ok_m) atomicAdd(&g.ctl[CTL_HELD], 1);
             // incoming for the landmark side: keyframe belief / this
             // factor's previous message to the keyframe (read before the new
             // message overwrites it)
@@ -849,6 +895,12 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
                 for (int i = 0; i < 21; ++i) Pk[i] = kb[i] - mk[i];
 #pragma unroll
                 for (int i = 0; i < 6; ++i) qk[i] = kb[21 + i] - mk[21 + i];
+                if (!ok_m) {   // held
+#pragma unroll
+                    for (int i = 0; i < 21; ++i) lam_k[i] = mk[i];
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) eta_k[i] = mk[21 + i];
+                }
                 if constexpr (FEAT) {
                     tr_pk = float(Pk[0] + Pk[2] + Pk[5] + Pk[9] + Pk[14] + Pk[20]);
                     tr_lk = float(lam_k[0] + lam_k[2] + lam_k[5] + lam_k[9] + lam_k[14] + lam_k[20]);
@@ -881,9 +933,11 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
             bool ok_k = message<R, 3, 6>(Pk, qk, L.Jk, L.Jl, L.y, L.W, lam_m, eta_m, ratio_k);
             if (sizeof(R) == 4 && P.fallback && (!ok_k || ratio_k < P.pivot_ratio)) {
                 R* o = g.ml_out + f;
+                const KfCavity<R> kc{mk_read(g, t), g.kf_off, g.kf_D + (size_t)k * 6, g.kf_A + (size_t)k * 6, k,
+                                     int(ks / KREC), kf_prior_scale(g, P, k, t), P.anchor_scale, P.inv_sigma2};
                 ok_k = message_fp64<R, true>(g.x0, n_f, f, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3,
                                              g.lm_ref + (size_t)m * 3, g.z + 2 * (size_t)f,
-                                             g.kf_bel + (size_t)k * KBEL, mk_read(g, t) + ks, 1, o, n_f,
+                                             g.kf_bel + (size_t)k * KBEL, mk_read(g, t) + ks, 1, kc, o, n_f,
                                              double(P.fx), double(P.fy), double(P.cx), double(P.cy),
                                              double(P.inv_sigma2), double(P.inv_sigma), double(P.huber_n),
                                              double(P.z_min));
@@ -893,7 +947,13 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
                 for (int i = 0; i < 3; ++i) eta_m[i] = o[(size_t)(6 + i) * n_f];
                 atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
             }
-            if (!ok_k) raise_error(g.ctl, -1 - f);
+            if (!ok_k) {   // held, as above
+                atomicAdd(&g.ctl[CTL_HELD], 1);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) lam_m[i] = ml[i];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) eta_m[i] = ml[6 + i];
+            }
             if constexpr (FEAT) {
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
@@ -1179,9 +1239,10 @@ __device__ __forceinline__ bool grid_barrier(int32_t* ctl, int nblocks, int* fla
     return *flag_sh;
 }
 
+// The FP32 fixed schedule is held to 3 blocks per SM (<= 168 registers).
 template <typename R, int MODE>
-__global__ void __launch_bounds__(FACTOR_BLOCK) persistent_kernel(DevGraph<R> g, KParams<R> P, int n_iters,
-                                                                    float conv_tol, int check_every) {
+__global__ void __launch_bounds__(FACTOR_BLOCK, (MODE == DAMP_FIXED && sizeof(R) == 4) ? 3 : 1)
+    persistent_kernel(DevGraph<R> g, KParams<R> P, int n_iters, float conv_tol, int check_every) {
     __shared__ int flag_sh;
     __shared__ __align__(16) MlpSmem<MODE> S;
     mlp_load<MODE>(P, S);

@@ -200,3 +200,35 @@ def compare(torch, problem, net: gbp.DampingNet, thresholds=(1.0, 0.1, 0.01), ma
         res[name] = r
         g.close()
     return res
+
+
+def stream_compare(torch, net: gbp.DampingNet, init, steps, per_step: int = 20, stream=None, **solver):
+    """The incremental stream of Sec. 9.2 (one keyframe added every
+    ``per_step`` iterations) with fixed d = 0.4 and with the learned
+    schedule: per step the ARE of the current graph after its iterations,
+    and the device time of all iterations (CUDA events around each step's
+    gbp_iterate; gbp_add_keyframe's host re-layout is the same for both and
+    not included)."""
+    prm = dict(SOLVER, **solver)
+    out = {}
+    cur = torch.cuda.current_stream()
+    for name, mode in (("fixed", 0), ("learned", 1)):
+        g = gbp.Graph(init, stream=stream, damping_mode=mode, **prm)
+        if mode:
+            g.set_damping_model(net)
+        ares, ms = [], 0.0
+        for i in range(len(steps) + 1):
+            if i:
+                st = steps[i - 1]
+                g.add_keyframe(st.obs_lm, st.obs_uv, n_new_lm=st.n_new_lm)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(cur)
+            g.iterate(per_step)
+            b.record(cur)
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+            ares.append(g.stats()["are"])
+        out[name] = {"are_per_step": ares, "mean_are": float(np.mean(ares)), "final_are": ares[-1],
+                     "device_ms": ms, "iterations": per_step * (len(steps) + 1)}
+        g.close()
+    return out

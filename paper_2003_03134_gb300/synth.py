@@ -200,35 +200,65 @@ def make_circle(seed: int = 0, n_kf: int = 10, n_lm: int = 100, radius: float = 
                    obs_kf, obs_lm, uv, outlier, anchors, params)
 
 
+def _smooth_track(rng, n_kf, step=0.08, turn_sigma_deg=1.0, max_turn_deg=8.0):
+    """Camera centres and headings of a video-like track: constant step,
+    heading driven by an AR(1) turn rate capped at max_turn_deg per keyframe,
+    steered back toward the middle of [2, 8]^2 near its edges."""
+    pos = rng.uniform(3.0, 7.0, 2)
+    theta = rng.uniform(0, 2 * np.pi)
+    omega = 0.0
+    out = []
+    for _ in range(n_kf):
+        out.append((pos.copy(), theta))
+        omega = 0.9 * omega + rng.normal(0.0, np.radians(turn_sigma_deg))
+        edge = min(pos[0] - 2.0, 8.0 - pos[0], pos[1] - 2.0, 8.0 - pos[1])
+        if edge < 1.5:
+            to_c = np.arctan2(5.0 - pos[1], 5.0 - pos[0])
+            err = (to_c - theta + np.pi) % (2 * np.pi) - np.pi
+            omega += 0.15 * err
+        omega = float(np.clip(omega, -np.radians(max_turn_deg), np.radians(max_turn_deg)))
+        theta += omega
+        pos = np.clip(pos + step * np.array([np.cos(theta), np.sin(theta)]), 2.0, 8.0)
+    return out
+
+
 def make_walk(seed: int = 0, n_kf: int = 125, n_lm: int = 1919, obs_range=(4, 15),
               outlier_frac: float = 0.02, noise_px: float = 1.0, rot_sigma: float = 0.05,
               pos_sigma: float = 0.1, lm_sigma: float = 0.1, anchors=(0,),
-              name: str | None = None) -> Problem:
+              name: str | None = None, smooth: bool = False) -> Problem:
     """Keyframes on a smooth random walk (height 1.5 m, AR(1) velocity,
     heading along the velocity, horizontal optical axis) inside a
     10 x 10 x 3 m volume of points; each point seen by 4-15 keyframes drawn
-    with visibility weight exp(-depth / 3 m); 2% outlier pixels."""
+    with visibility weight exp(-depth / 3 m); 2% outlier pixels.  With
+    ``smooth`` the keyframes follow a video-like track instead (8 cm steps,
+    a few degrees of turn per keyframe; see _smooth_track), as a SLAM front
+    end would select them."""
     rng = np.random.Generator(np.random.PCG64(seed))
     fx, fy, cx, cy, w, h = CAMERA
-    pos = rng.uniform(2.0, 8.0, 2)
-    ang = rng.uniform(0, 2 * np.pi)
-    v = 0.1 * np.array([np.cos(ang), np.sin(ang)])
     kf = []
-    for _ in range(n_kf):
-        heading = np.array([v[0], v[1], 0.0])
-        R = _look_rotation(heading, np.array([0.0, 0.0, 1.0]))
-        kf.append(_pack(R, np.array([pos[0], pos[1], 1.5])))
-        v = 0.9 * v + rng.normal(0.0, 0.05, 2)
-        if np.linalg.norm(v) < 1e-3:
-            v = v + 1e-3
-        pos = pos + v
-        for d in range(2):
-            if pos[d] < 2.0:
-                pos[d] = 4.0 - pos[d]
-                v[d] = abs(v[d])
-            elif pos[d] > 8.0:
-                pos[d] = 16.0 - pos[d]
-                v[d] = -abs(v[d])
+    if smooth:
+        for pos, theta in _smooth_track(rng, n_kf):
+            R = _look_rotation(np.array([np.cos(theta), np.sin(theta), 0.0]), np.array([0.0, 0.0, 1.0]))
+            kf.append(_pack(R, np.array([pos[0], pos[1], 1.5])))
+    else:
+        pos = rng.uniform(2.0, 8.0, 2)
+        ang = rng.uniform(0, 2 * np.pi)
+        v = 0.1 * np.array([np.cos(ang), np.sin(ang)])
+        for _ in range(n_kf):
+            heading = np.array([v[0], v[1], 0.0])
+            R = _look_rotation(heading, np.array([0.0, 0.0, 1.0]))
+            kf.append(_pack(R, np.array([pos[0], pos[1], 1.5])))
+            v = 0.9 * v + rng.normal(0.0, 0.05, 2)
+            if np.linalg.norm(v) < 1e-3:
+                v = v + 1e-3
+            pos = pos + v
+            for d in range(2):
+                if pos[d] < 2.0:
+                    pos[d] = 4.0 - pos[d]
+                    v[d] = abs(v[d])
+                elif pos[d] > 8.0:
+                    pos[d] = 16.0 - pos[d]
+                    v[d] = -abs(v[d])
     kf_true = np.array(kf)
     lo = np.array([0.0, 0.0, 0.0])
     hi = np.array([10.0, 10.0, 3.0])
@@ -398,9 +428,10 @@ def stream_plan(p: Problem, start_kf: int):
 
 
 def make_stream(seed: int = 0, n_kf: int = 500, n_lm: int = 8000, start_kf: int = 10):
-    """Incremental-SLAM stream over one walk problem: the initial graph and
-    the steps that add one keyframe each (see stream_plan)."""
-    p = make_walk(seed=seed, n_kf=n_kf, n_lm=n_lm, obs_range=(4, 15), name=f"stream{n_kf}x{n_lm}")
+    """Incremental-SLAM stream over one video-like walk (smooth track, a few
+    degrees and 8 cm between keyframes): the initial graph and the steps
+    that add one keyframe each (see stream_plan)."""
+    p = make_walk(seed=seed, n_kf=n_kf, n_lm=n_lm, obs_range=(4, 15), name=f"stream{n_kf}x{n_lm}", smooth=True)
     return stream_plan(p, start_kf)
 
 

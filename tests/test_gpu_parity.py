@@ -115,6 +115,21 @@ def test_fp32_paper_schedule_properties(seed):
     assert np.mean(e <= TOL32) >= 0.9
 
 
+@pytest.mark.parametrize("mode", [1, 2])
+def test_forced_fp64_fallback_matches_oracle(mode):
+    """fp64_pivot_ratio = 1 sends every message to the landmarks through the
+    FP64 fallback: the result still meets the FP32 bar (the fallback reads
+    FP32 state) and every such message is counted."""
+    p = synth.make_walk(2, n_kf=25, n_lm=300)
+    n = 60
+    kf, lm, st, okf, olm, o = run_pair(p, n, dict(huber_nsigma=2.0, fp64_pivot_ratio=1.0, launch_mode=mode, **DET),
+                                       dict(huber_nsigma=2.0, **DET))
+    e = rel_err(kf, lm, okf, olm)
+    assert e.max() <= TOL32, (e.max(), np.median(e))
+    # every active factor's keyframe marginal, every iteration (plus belief redos)
+    assert st["fp64_fallbacks"] >= n * int((p.obs_kf >= 0).sum()) * 0.9
+
+
 def test_linear_mode_matches_oracle():
     p = synth.make_circle(3, n_kf=6, n_lm=40)
     kf, lm, st, okf, olm, o = run_pair(p, 300, dict(linear=1, precision_mode=2), dict(linear=1))
@@ -360,3 +375,4 @@ def test_add_keyframe_rejects_bad_input():
     assert g.add_keyframe(st.obs_lm, st.obs_uv, n_new_lm=st.n_new_lm) == init.n_kf
     g.iterate(5)
     g.close()
+
