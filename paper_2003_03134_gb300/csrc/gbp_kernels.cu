@@ -198,26 +198,23 @@ struct Lin {
     R r2;   // |r|^2 (pixels^2)
 };
 
+// Rr: the keyframe's reference rotation in R; dlc = lref - cref, subtracted
+// in double before rounding to R (the large world coordinates cancel there).
 template <typename R>
-__device__ __forceinline__ void linearise(const KParams<R>& P, const double* __restrict__ Rref,
-                                          const double* __restrict__ cref, const double* __restrict__ lref,
-                                          const R x0[9], R zu, R zv, Lin<R>& L) {
+__device__ __forceinline__ void linearise_ref(const KParams<R>& P, const R Rr[9], const R dlc[3], const R x0[9],
+                                              R zu, R zv, Lin<R>& L) {
     R w[3] = {x0[3], x0[4], x0[5]};
     R E[9], Jw[9];
     so3_exp_jl(w, E, Jw);
-    R Rr[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) Rr[i] = R(Rref[i]);
     R Rm[9];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j)
             Rm[i * 3 + j] = E[i * 3 + 0] * Rr[0 * 3 + j] + E[i * 3 + 1] * Rr[1 * 3 + j] + E[i * 3 + 2] * Rr[2 * 3 + j];
-    // the large world coordinates cancel in double before rounding to R
     R d[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) d[i] = R(lref[i] - cref[i]) + (x0[6 + i] - x0[i]);
+    for (int i = 0; i < 3; ++i) d[i] = dlc[i] + (x0[6 + i] - x0[i]);
     R p[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) p[i] = Rm[i * 3 + 0] * d[0] + Rm[i * 3 + 1] * d[1] + Rm[i * 3 + 2] * d[2];
@@ -279,6 +276,24 @@ __device__ __forceinline__ void linearise(const KParams<R>& P, const double* __r
         for (int j = 0; j < 3; ++j) s += L.Jk[a][j] * (x0[j] - x0[6 + j]) + L.Jk[a][3 + j] * x0[3 + j];
         L.y[a] = s;
     }
+}
+
+template <typename R>
+__device__ __forceinline__ void load_refs(const double* __restrict__ Rref, const double* __restrict__ cref,
+                                          const double* __restrict__ lref, R Rr[9], R dlc[3]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Rr[i] = R(Rref[i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dlc[i] = R(lref[i] - cref[i]);
+}
+
+template <typename R>
+__device__ __forceinline__ void linearise(const KParams<R>& P, const double* __restrict__ Rref,
+                                          const double* __restrict__ cref, const double* __restrict__ lref,
+                                          const R x0[9], R zu, R zv, Lin<R>& L) {
+    R Rr[9], dlc[3];
+    load_refs<R>(Rref, cref, lref, Rr, dlc);
+    linearise_ref<R>(P, Rr, dlc, x0, zu, zv, L);
 }
 
 // ------------------------------------------------------------------------
@@ -793,6 +808,11 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
         const int k = g.fk[f];
         const size_t ks = (size_t)g.kpos[f] * KREC;   // this factor's keyframe-message slot
         const R* kbp = g.kf_bel + (size_t)k * KBEL;
+        // static geometry first: its loads need not wait for the
+        // relinearisation decision below (which may store to x0)
+        R Rr[9], dlc[3];
+        load_refs<R>(g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3, g.lm_ref + (size_t)m * 3, Rr, dlc);
+        const R zu = g.z[2 * (size_t)f], zv = g.z[2 * (size_t)f + 1];
         R lb[LBEL];
         load_rec_cg<R, LBEL>(g.lm_bel + (size_t)m * LBEL, lb);
         mu_m_old[0] = lb[9];
@@ -829,8 +849,7 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
         }
 
         Lin<R> L;
-        linearise<R>(P, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3, g.lm_ref + (size_t)m * 3, x0,
-                     g.z[2 * (size_t)f], g.z[2 * (size_t)f + 1], L);
+        linearise_ref<R>(P, Rr, dlc, x0, zu, zv, L);
         const bool damp = MODE != DAMP_LEARNED && t - tl >= P.damp_hold;   // learned: after the network
         const R d = P.damping;
         ks_f = ks;
