@@ -128,6 +128,7 @@ struct gbp_graph {
     int tuned_mode = 0;                         // autotuner's choice (1 or 2), 0 = not tuned
     int last_mode = 0;                          // launch mode of the last gbp_iterate()
     int64_t launches = 0;                       // kernels launched (graph replays count their kernels)
+    bool pdl = true;                            // programmatic dependent launch between the per-phase kernels
     // learned damping: the graph's own copy of a network's packed weights
     uint32_t* mlp_frag = nullptr;
     float* mlp_bias = nullptr;
@@ -445,30 +446,51 @@ cudaError_t enqueue_iterations(gbp_graph* g, int n, cudaStream_t st) {
     const DevGraph<R>& d = state<R>(g).g;
     KParams<R> kp = make_kparams<R>(g);
     for (int i = 0; i < n; ++i) {
-        cudaError_t e = launch_factor<R>(d, kp, st, g->prm.damping_mode);
+        cudaError_t e = launch_factor<R>(d, kp, st, g->prm.damping_mode, g->pdl);
         if (e != cudaSuccess) return e;
-        e = launch_belief<R>(d, kp, st);
+        e = launch_belief<R>(d, kp, st, g->pdl);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
+// Record GRAPH_CHUNK iterations as a CUDA graph.  With programmatic
+// dependent launch between the kernels if the capture accepts it, else
+// (and from then on) with plain stream order.
 gbp_status ensure_exec(gbp_graph* g) {
     if (g->exec) return GBP_OK;
-    cudaGraph_t graph = nullptr;
-    CK(cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = g->storage ? enqueue_iterations<double>(g, GRAPH_CHUNK, g->capture)
-                               : enqueue_iterations<float>(g, GRAPH_CHUNK, g->capture);
-    cudaError_t e2 = cudaStreamEndCapture(g->capture, &graph);
-    if (e != cudaSuccess) return cuda_fail(g, e, "capture");
-    if (e2 != cudaSuccess) return cuda_fail(g, e2, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&g->exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) {
-        g->exec = nullptr;
-        return cuda_fail(g, e, "cudaGraphInstantiate");
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = g->storage ? enqueue_iterations<double>(g, GRAPH_CHUNK, g->capture)
+                                   : enqueue_iterations<float>(g, GRAPH_CHUNK, g->capture);
+        cudaError_t e2 = cudaStreamEndCapture(g->capture, &graph);
+        if (e == cudaSuccess && e2 == cudaSuccess) {
+            e = cudaGraphInstantiate(&g->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e == cudaSuccess) return GBP_OK;
+            g->exec = nullptr;
+        } else if (graph) {
+            cudaGraphDestroy(graph);
+        }
+        if (!g->pdl) {
+            if (e == cudaSuccess) e = e2;
+            return cuda_fail(g, e, "capture");
+        }
+        cudaGetLastError();
+        g->pdl = false;
     }
-    return GBP_OK;
+    return fail(g, GBP_ECUDA, "capture");
+}
+
+// max |dmu| of the last completed iteration, from the mirrored control
+// block: both launch modes leave it in the parity slot of that iteration.
+float last_dmu(const gbp_graph* g) {
+    const int t = g->h_ctl[CTL_ITER];
+    if (t <= 0) return 0.0f;
+    float v;
+    std::memcpy(&v, &g->h_ctl[((t - 1) & 1) ? CTL_DMU_ACC1 : CTL_DMU_ACC], sizeof v);
+    return v;
 }
 
 gbp_status read_ctl(gbp_graph* g) {
@@ -635,7 +657,7 @@ gbp_status iterate_phases(gbp_graph* g, int n, float conv_tol, int* done_out) {
             st = read_ctl(g);
             if (st != GBP_OK) return st;
             float dmu;
-            std::memcpy(&dmu, &g->h_ctl[CTL_DMU_LAST], sizeof dmu);
+            dmu = last_dmu(g);
             if (dmu < conv_tol) break;
         }
     }
@@ -866,8 +888,8 @@ gbp_status record_iterations(gbp_graph* g, int n, float* X, float* T) {
     for (int i = 0; i < n; ++i) {
         d.rec_X = X + (size_t)i * g->n_f * N_FEAT;
         d.rec_T = T + (size_t)i * g->n_f;
-        CK(launch_factor<R>(d, kp, g->stream, DAMP_RECORD));
-        CK(launch_belief<R>(d, kp, g->stream));
+        CK(launch_factor<R>(d, kp, g->stream, DAMP_RECORD, g->pdl));
+        CK(launch_belief<R>(d, kp, g->stream, g->pdl));
     }
     g->launches += 2 * (int64_t)n;
     return GBP_OK;
@@ -1254,7 +1276,7 @@ gbp_status gbp_get_stats(const gbp_graph* cg, gbp_stats* out) {
     CK(cudaMemcpyAsync(g->h_met, g->met, sizeof(double) * MET_N, cudaMemcpyDeviceToHost, g->stream));
     gbp_status st = read_ctl(g);   // synchronises
     out->iterations = g->h_ctl[CTL_ITER];
-    std::memcpy(&out->max_dmu, &g->h_ctl[CTL_DMU_LAST], sizeof(float));
+    out->max_dmu = last_dmu(g);
     out->are = g->h_met[MET_ARE];
     out->are_ref = g->h_met[MET_ARE_REF];
     out->n_are = (int32_t)g->h_met[MET_N_ARE];

@@ -117,9 +117,9 @@ struct DevGraph {
 // int32 slots of the device control block
 enum Ctl : int {
     CTL_ITER = 0,          // completed iterations
-    CTL_DONE = 1,          // blocks finished in the current belief launch
+    CTL_DONE = 1,          // (unused)
     CTL_DMU_ACC = 2,       // running max |dmu| (float bits) of even iterations
-    CTL_DMU_LAST = 3,      // max |dmu| of the last completed iteration (float bits)
+    CTL_DMU_LAST = 3,      // persistent kernel: max |dmu| of the last iteration it ran (float bits)
     CTL_FALLBACKS = 4,     // FP64 redo count
     CTL_RELINS = 5,        // relinearisation count
     CTL_ERR = 6,           // 1: a belief lost positive definiteness / became non-finite; 2: barrier timeout
@@ -129,6 +129,7 @@ enum Ctl : int {
     CTL_BAR_GEN = 10,      // grid barrier generation
     CTL_ITERS_RUN = 11,    // iterations run by the last persistent launch
     CTL_HELD = 12,         // messages left at their previous value (incoming precision not positive definite)
+    CTL_ITER_B = 13,       // per-phase launches: the iteration the belief kernel closes (set by the factor kernel)
     CTL_N = 16
 };
 
@@ -139,10 +140,13 @@ constexpr int FACTOR_BLOCK = 128;   // 4 warps per block (every kernel of the it
 constexpr int METRIC_BLOCK = 256;
 
 // kernel launchers (gbp_kernels.cu)
+// pdl: programmatic dependent launch (the kernel may start while the
+// previous kernel in the stream finishes; it waits for that kernel's writes)
 template <typename R> cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s,
-                                                int mode = DAMP_FIXED);
+                                                int mode = DAMP_FIXED, bool pdl = false);
 template <typename R> cudaError_t launch_init(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s);
-template <typename R> cudaError_t launch_belief(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s);
+template <typename R> cudaError_t launch_belief(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s,
+                                                bool pdl = false);
 template <typename R> int persistent_grid(const DevGraph<R>& g, int mode);   // co-resident blocks; 0 on error
 template <typename R> cudaError_t launch_persistent(const DevGraph<R>& g, const KParams<R>& p, int n_iters,
                                                     float conv_tol, int check_every, int grid, cudaStream_t s,

@@ -33,6 +33,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <utility>
 
 namespace gbp {
 
@@ -548,17 +549,17 @@ __device__ __forceinline__ float finish_landmark(const DevGraph<R>& g, const KPa
 // Keyframe belief b^{t+1} = s(t+1) D + anchor + sum of messages and its
 // mean from the (already reduced) sums; writes the record to out and
 // returns |dmu|_inf against mu_old.
+// prior[i] = (s(t+1) D_i + anchor_scale A_i) / sigma^2, formed by the caller.
 template <typename R>
-__device__ __forceinline__ float finish_keyframe(const DevGraph<R>& g, const KParams<R>& P, int k, R s,
+__device__ __forceinline__ float finish_keyframe(const DevGraph<R>& g, const KParams<R>& P, int k, const R* prior,
                                                  const R* sum, const R* mu_old, R* out_bel) {
     R lam[21], eta[6], mu[6], work[21], ratio;
-    const R isig2 = P.inv_sigma2;
 #pragma unroll
     for (int j = 0; j < 21; ++j) lam[j] = sum[j];
 #pragma unroll
     for (int j = 0; j < 6; ++j) eta[j] = sum[21 + j];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) lam[pk(i, i)] += (s * g.kf_D[k * 6 + i] + P.anchor_scale * g.kf_A[k * 6 + i]) * isig2;
+    for (int i = 0; i < 6; ++i) lam[pk(i, i)] += prior[i];
 #pragma unroll
     for (int j = 0; j < 21; ++j) work[j] = lam[j];
     bool ok = solve_mean<R, 6>(work, eta, mu, ratio);
@@ -1104,6 +1105,17 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
     if (w < g.n_kf) {
         const int k = w;
         const R* msgs = mk_write(g, t);
+        // the keyframe's own inputs first, so their loads overlap the reduction
+        R prior[6], mu_old[6];
+        {
+            const R sp = kf_prior_scale(g, P, k, t + 1);
+            const R* old = g.kf_bel + (size_t)k * KBEL;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                prior[i] = (sp * g.kf_D[k * 6 + i] + P.anchor_scale * g.kf_A[k * 6 + i]) * P.inv_sigma2;
+                mu_old[i] = __ldcg(old + 27 + i);
+            }
+        }
         R acc[27];
 #pragma unroll
         for (int j = 0; j < 27; ++j) acc[j] = R(0);
@@ -1117,13 +1129,7 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
         }
 #pragma unroll
         for (int j = 0; j < 27; ++j) acc[j] = warp_sum(acc[j]);
-        if (lane == 0) {
-            const R* old = g.kf_bel + (size_t)k * KBEL;
-            R mu_old[6];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) mu_old[i] = __ldcg(old + 27 + i);
-            dmu = finish_keyframe<R>(g, P, k, kf_prior_scale(g, P, k, t + 1), acc, mu_old, g.kf_bel_out);
-        }
+        if (lane == 0) dmu = finish_keyframe<R>(g, P, k, prior, acc, mu_old, g.kf_bel_out);
     } else if (w < g.n_kf + g.n_big) {
         const int m = g.big_lm[w - g.n_kf];
         R acc[9];
@@ -1178,45 +1184,51 @@ __host__ __device__ inline int phase_b_items(const DevGraph<R>& g) {
 // ------------------------------------------------------------------------
 // Two-kernel iteration (the launch-per-phase path).
 
+// Programmatic dependent launch: the per-phase kernels let the next kernel
+// in the stream launch once all of their blocks are past their main work
+// (so only one kernel waits ahead), and wait for the previous kernel's
+// completion (and its memory) before they read anything it writes.  Without
+// the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_allow_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <typename R, int MODE>
 __global__ void __launch_bounds__(FACTOR_BLOCK) factor_kernel(DevGraph<R> g, KParams<R> P) {
     __shared__ __align__(16) MlpSmem<MODE> S;
-    mlp_load<MODE>(P, S);
+    mlp_load<MODE>(P, S);   // network weights do not change between iterations
+    pdl_wait_prev();
     const int lane = threadIdx.x & 31;
     const int tile = blockIdx.x * (FACTOR_BLOCK / 32) + (threadIdx.x >> 5);
-    if (tile >= g.n_tiles) return;   // uniform per warp
     const int t = g.ctl[CTL_ITER];
-    float dmu = tile_work<R, MODE>(g, P, tile, t, lane, S);
+    float dmu = 0.0f;
+    if (tile < g.n_tiles) dmu = tile_work<R, MODE>(g, P, tile, t, lane, S);   // uniform per warp
+    pdl_allow_next();
     dmu = warp_max(dmu);
     if (lane == 0 && dmu > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), dmu);
+    // the belief kernel of this iteration reads t from CTL_ITER_B: the belief
+    // kernel of t - 1 has finished and that of t starts after this kernel
+    if (blockIdx.x == 0 && threadIdx.x == 0) g.ctl[CTL_ITER_B] = t;
 }
 
 template <typename R>
 __global__ void __launch_bounds__(FACTOR_BLOCK) belief_kernel(DevGraph<R> g, KParams<R> P) {
-    __shared__ int is_last;
+    pdl_wait_prev();
     const int lane = threadIdx.x & 31;
     const int w = blockIdx.x * (FACTOR_BLOCK / 32) + (threadIdx.x >> 5);
-    const int t = g.ctl[CTL_ITER];
+    const int t = g.ctl[CTL_ITER_B];
+    // close the iteration from one thread: the factor kernel of t has
+    // finished and that of t + 1 starts only after this kernel, so the
+    // counter it reads and the |dmu| slot it fills are free to set now
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        g.ctl[CTL_ITER] = t + 1;
+        g.ctl[dmu_slot(t + 1)] = 0;
+    }
     float dmu = 0.0f;
     if (w < phase_b_items(g)) dmu = phase_b_item<R>(g, P, w, t, lane);
-    // the last block to finish closes the iteration (max is order
-    // independent, so the atomic on non-negative float bits is deterministic)
+    pdl_allow_next();
+    // max is order independent: the atomic on non-negative float bits is deterministic
     dmu = warp_max(dmu);
     if (lane == 0 && dmu > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), dmu);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        int ticket = atomicAdd(&g.ctl[CTL_DONE], 1);
-        is_last = (ticket == (int)gridDim.x - 1);
-    }
-    __syncthreads();
-    if (is_last && threadIdx.x == 0) {
-        __threadfence();
-        g.ctl[CTL_DMU_LAST] = atomicAdd(&g.ctl[dmu_slot(t)], 0);
-        g.ctl[dmu_slot(t + 1)] = 0;   // slot of the next iteration starts empty
-        g.ctl[CTL_DONE] = 0;
-        g.ctl[CTL_ITER] = t + 1;
-    }
 }
 
 // ------------------------------------------------------------------------
@@ -1533,27 +1545,37 @@ int metrics_blocks(int n_f) {
     return b;
 }
 
-template <typename R>
-cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s, int mode) {
-    if (g.n_tiles == 0) return cudaSuccess;
-    constexpr int wpb = FACTOR_BLOCK / 32;
-    const int blocks = (g.n_tiles + wpb - 1) / wpb;
-    if (mode == DAMP_LEARNED)
-        factor_kernel<R, DAMP_LEARNED><<<blocks, FACTOR_BLOCK, 0, s>>>(g, p);
-    else if (mode == DAMP_RECORD)
-        factor_kernel<R, DAMP_RECORD><<<blocks, FACTOR_BLOCK, 0, s>>>(g, p);
-    else
-        factor_kernel<R, DAMP_FIXED><<<blocks, FACTOR_BLOCK, 0, s>>>(g, p);
-    return cudaGetLastError();
+// One launch, with programmatic stream serialisation when pdl is set.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_ex(void (*kernel)(KArgs...), int blocks, cudaStream_t s, bool pdl, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(FACTOR_BLOCK);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 template <typename R>
-cudaError_t launch_belief(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s) {
+cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s, int mode, bool pdl) {
+    constexpr int wpb = FACTOR_BLOCK / 32;
+    const int blocks = std::max(1, (g.n_tiles + wpb - 1) / wpb);   // >= 1: it also publishes the iteration index
+    if (mode == DAMP_LEARNED) return launch_ex(factor_kernel<R, DAMP_LEARNED>, blocks, s, pdl, g, p);
+    if (mode == DAMP_RECORD) return launch_ex(factor_kernel<R, DAMP_RECORD>, blocks, s, pdl, g, p);
+    return launch_ex(factor_kernel<R, DAMP_FIXED>, blocks, s, pdl, g, p);
+}
+
+template <typename R>
+cudaError_t launch_belief(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s, bool pdl) {
     constexpr int wpb = FACTOR_BLOCK / 32;
     int blocks = (phase_b_items(g) + wpb - 1) / wpb;
     if (blocks < 1) blocks = 1;
-    belief_kernel<R><<<blocks, FACTOR_BLOCK, 0, s>>>(g, p);
-    return cudaGetLastError();
+    return launch_ex(belief_kernel<R>, blocks, s, pdl, g, p);
 }
 
 template <typename R>
@@ -1638,10 +1660,10 @@ cudaError_t launch_problem_metrics(const DevGraph<R>& g, const KParams<R>& p, co
 }
 
 #define GBP_INSTANTIATE(R)                                                                                 \
-    template cudaError_t launch_factor<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t, int);       \
+    template cudaError_t launch_factor<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t, int, bool); \
     template cudaError_t launch_capture_messages<R>(const DevGraph<R>&, int, R*, cudaStream_t);            \
     template cudaError_t launch_init<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t);              \
-    template cudaError_t launch_belief<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t);            \
+    template cudaError_t launch_belief<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t, bool);      \
     template cudaError_t launch_problem_metrics<R>(const DevGraph<R>&, const KParams<R>&, const int32_t*, int, double*, cudaStream_t); \
     template int persistent_grid<R>(const DevGraph<R>&, int);                                              \
     template cudaError_t launch_persistent<R>(const DevGraph<R>&, const KParams<R>&, int, float, int, int, cudaStream_t, int); \
