@@ -716,6 +716,30 @@ __device__ __forceinline__ void mlp_load(const KParams<R>& P, MlpSmem<MODE>& S) 
     }
 }
 
+// 16-byte asynchronous global-to-shared copies (cp.async, through L2).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// The per-phase factor kernel starts the weight copy at launch and waits for
+// it (every warp of the block, once) just before the network, so the copy
+// overlaps the message arithmetic instead of preceding it.
+template <int MODE, typename R>
+__device__ __forceinline__ void mlp_load_async(const KParams<R>& P, MlpSmem<MODE>& S) {
+    if constexpr (MODE == DAMP_LEARNED) {
+        for (int c = threadIdx.x; c < FWD_FRAG_WORDS / 4; c += blockDim.x) cp_async16(S.frag + 4 * c, P.mlp_frag + 4 * c);
+        for (int c = threadIdx.x; c < MLP_BIAS_WORDS / 4; c += blockDim.x) cp_async16(S.bias + 4 * c, P.mlp_bias + 4 * c);
+        cp_async_commit();
+    }
+}
+__device__ __forceinline__ void mlp_load_wait() {
+    cp_async_wait_all();
+    __syncthreads();
+}
+
 // ------------------------------------------------------------------------
 // Phase A: one warp, one tile of whole landmarks (at most 32 factors,
 // consecutive in landmark order), one lane per factor -- relinearisation
@@ -730,7 +754,7 @@ __device__ __forceinline__ void mlp_load(const KParams<R>& P, MlpSmem<MODE>& S) 
 
 template <typename R, int MODE>
 __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R>& P, int tile, int t, int lane,
-                                           MlpSmem<MODE>& S) {
+                                           MlpSmem<MODE>& S, bool weights_pending = false) {
     const int n_f = g.n_f;
     const int ts = g.tile_start[tile], te = g.tile_start[tile + 1];
     const int f = ts + lane;
@@ -1049,6 +1073,7 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
         // would damp (after the undamped hold of Sec. 8)
         const int w = threadIdx.x >> 5;
         const bool damp_f = active && t - tl_f >= P.damp_hold;
+        if (weights_pending) mlp_load_wait();   // uniform per block: every warp of the block passes here once
         if (__any_sync(0xffffffffu, damp_f)) {   // uniform per warp: skipped while every lane is in its hold
             __nv_bfloat16* xt = reinterpret_cast<__nv_bfloat16*>(S.x[w]);
 #pragma unroll
@@ -1195,13 +1220,14 @@ __device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.w
 template <typename R, int MODE>
 __global__ void __launch_bounds__(FACTOR_BLOCK) factor_kernel(DevGraph<R> g, KParams<R> P) {
     __shared__ __align__(16) MlpSmem<MODE> S;
-    mlp_load<MODE>(P, S);   // network weights do not change between iterations
+    mlp_load_async<MODE>(P, S);   // network weights do not change between iterations
     pdl_wait_prev();
     const int lane = threadIdx.x & 31;
     const int tile = blockIdx.x * (FACTOR_BLOCK / 32) + (threadIdx.x >> 5);
     const int t = g.ctl[CTL_ITER];
     float dmu = 0.0f;
-    if (tile < g.n_tiles) dmu = tile_work<R, MODE>(g, P, tile, t, lane, S);   // uniform per warp
+    if (tile < g.n_tiles) dmu = tile_work<R, MODE>(g, P, tile, t, lane, S, MODE == DAMP_LEARNED);   // uniform per warp
+    else if constexpr (MODE == DAMP_LEARNED) mlp_load_wait();   // the block's barrier, for warps without a tile
     pdl_allow_next();
     dmu = warp_max(dmu);
     if (lane == 0 && dmu > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), dmu);

@@ -28,8 +28,9 @@ constexpr float MLP_DMAX = 0.9f;
 constexpr int FT_L1 = 0, FT_L2 = 8, FT_L3 = 40, FT_W2T = 44, FT_N = 76;
 constexpr int FRAG_WORDS = FT_N * 32 * 2;        // uint32 words
 constexpr int FWD_FRAG_WORDS = FT_W2T * 32 * 2;  // words the forward pass needs
-// FP32 side buffer: b1 [64], b2 [64], b3, pad, W3 [64] (W3 for the backward pass)
-constexpr int MLP_BIAS_WORDS = 2 * MLP_H + 2 + MLP_H;
+// FP32 side buffer: b1 [64], b2 [64], b3, pad, W3 [64] (W3 for the backward
+// pass), pad to a multiple of 16 bytes (copied in 16-byte pieces)
+constexpr int MLP_BIAS_WORDS = 2 * MLP_H + 2 + MLP_H + 2;
 
 // shared-memory row strides (BF16 elements), chosen so that the 8 rows a
 // fragment load touches fall in distinct banks
