@@ -37,9 +37,17 @@ constexpr int MLP_BIAS_WORDS = 2 * MLP_H + 2 + MLP_H + 2;
 constexpr int XS = 24;   // 16-wide input tile
 constexpr int HS = 72;   // 64-wide hidden tile
 
+// two FP32 values -> a BF16 pair (lo in bits 0-15), round to nearest even,
+// one conversion instruction; the _relu form also clamps negatives to 0
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    __nv_bfloat16 a = __float2bfloat16_rn(lo), b = __float2bfloat16_rn(hi);
-    return uint32_t(__bfloat16_as_ushort(a)) | (uint32_t(__bfloat16_as_ushort(b)) << 16);
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+__device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
 }
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
@@ -179,8 +187,8 @@ __device__ __forceinline__ float mlp_forward_regs(const uint32_t* frag, const fl
             mma_bf16(d, x0, x1, x2, x3, b0, b1);
             const int c = 8 * nt + 2 * q;
             const float bc0 = bias[c], bc1 = bias[c + 1];
-            const uint32_t lo = pack_bf16(fmaxf(d[0] + bc0, 0.f), fmaxf(d[1] + bc1, 0.f));
-            const uint32_t hi = pack_bf16(fmaxf(d[2] + bc0, 0.f), fmaxf(d[3] + bc1, 0.f));
+            const uint32_t lo = pack_bf16_relu(d[0] + bc0, d[1] + bc1);
+            const uint32_t hi = pack_bf16_relu(d[2] + bc0, d[3] + bc1);
             a1[nt >> 1][(nt & 1) ? 2 : 0] = lo;
             a1[nt >> 1][(nt & 1) ? 3 : 1] = hi;
         }
@@ -197,8 +205,8 @@ __device__ __forceinline__ float mlp_forward_regs(const uint32_t* frag, const fl
             }
             const int c = 8 * nt + 2 * q;
             const float bc0 = bias[MLP_H + c], bc1 = bias[MLP_H + c + 1];
-            const uint32_t lo = pack_bf16(fmaxf(d[0] + bc0, 0.f), fmaxf(d[1] + bc1, 0.f));
-            const uint32_t hi = pack_bf16(fmaxf(d[2] + bc0, 0.f), fmaxf(d[3] + bc1, 0.f));
+            const uint32_t lo = pack_bf16_relu(d[0] + bc0, d[1] + bc1);
+            const uint32_t hi = pack_bf16_relu(d[2] + bc0, d[3] + bc1);
             a2[nt >> 1][(nt & 1) ? 2 : 0] = lo;
             a2[nt >> 1][(nt & 1) ? 3 : 1] = hi;
         }
