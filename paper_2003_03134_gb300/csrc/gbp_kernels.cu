@@ -625,6 +625,56 @@ __device__ __forceinline__ R warp_sum(R v) {
     return v;
 }
 
+// Compensated summation (Knuth's TwoSum): hi + lo carries a running sum
+// with the rounding error of every addition kept in lo, so a sum of many
+// FP32 terms comes out within about one rounding of its exact value, in
+// whatever order the terms are added.
+template <typename R>
+__device__ __forceinline__ void two_sum_add(R& hi, R& lo, R x) {
+    const R s = hi + x;
+    const R bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
+}
+
+// Sum NV (a power of two, <= 32) values over the 32 lanes of a warp, as
+// (hi, lo) pairs.  Offsets 16 .. NV exchange every value (butterfly); the
+// remaining levels halve: at offset h a lane keeps the upper or the lower
+// half of its values (by lane bit h), sends the other half to its partner
+// and adds the partner's copy of the half it keeps -- 31 shuffle pairs in
+// all for 32 values.  On return lane l holds the total of value l % NV in
+// hi[0], lo[0].  Every total is formed by one fixed tree, so the result
+// does not depend on the lane that holds it.
+template <typename R, int NV>
+__device__ __forceinline__ void warp_transpose_sum(R (&hi)[NV], R (&lo)[NV], int lane) {
+    static_assert(NV >= 1 && NV <= 32 && (NV & (NV - 1)) == 0, "NV");
+#pragma unroll
+    for (int o = 16; o >= NV; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const R rh = __shfl_xor_sync(0xffffffffu, hi[i], o);
+            const R rl = __shfl_xor_sync(0xffffffffu, lo[i], o);
+            two_sum_add(hi[i], lo[i], rh);
+            lo[i] += rl;
+        }
+    }
+#pragma unroll
+    for (int h = NV / 2; h >= 1; h >>= 1) {
+        const bool up = (lane & h) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            R kh = up ? hi[h + i] : hi[i], kl = up ? lo[h + i] : lo[i];
+            const R sh = up ? hi[i] : hi[h + i], sl = up ? lo[i] : lo[h + i];
+            const R rh = __shfl_xor_sync(0xffffffffu, sh, h);
+            const R rl = __shfl_xor_sync(0xffffffffu, sl, h);
+            two_sum_add(kh, kl, rh);
+            kl += rl;
+            hi[i] = kh;
+            lo[i] = kl;
+        }
+    }
+}
+
 __device__ __forceinline__ int dmu_slot(int t) { return (t & 1) ? CTL_DMU_ACC1 : CTL_DMU_ACC; }
 
 __device__ __forceinline__ void dmu_atomic_max_slot(int32_t* ctl, int slot, float v) {
@@ -1116,23 +1166,31 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
 }
 
 // ------------------------------------------------------------------------
-// Phase B: one warp per keyframe (a fixed-order reduction of its messages,
-// which are stored contiguously in the keyframe's CSR order: lane l takes
-// entries l, l + 32, ...; then a fixed shuffle tree; lane 0 forms the
-// belief), one warp per landmark split
-// across tiles, and prior-only beliefs for variables without factors (32
-// per warp).  Work item w: [0, n_kf) keyframes, then split landmarks, then
-// orphan groups.  Returns max |dmu| in lane 0.
+// Phase B: one block (FACTOR_BLOCK threads) per work item.  Item b in
+// [0, n_kf): keyframe b -- a fixed-order reduction of its messages, which
+// are stored contiguously in the keyframe's CSR order: thread i takes
+// entries i, i + FACTOR_BLOCK, ...; a transposing shuffle tree per warp;
+// the warps' partial sums added in warp order; thread 0 forms the belief.
+// Every addition is compensated, so an FP32 belief is its messages' sum
+// rounded about once, however the entries fall across the threads.  Then one
+// item per landmark split across tiles (the same scheme over its factors'
+// landmark messages), then groups of FACTOR_BLOCK variables without factors
+// (prior-only beliefs).  Every thread of the block calls it with the same
+// item; returns max |dmu| in thread 0.
 
 template <typename R>
-__device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParams<R>& P, int w, int t, int lane) {
+__device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParams<R>& P, int item, int t) {
+    constexpr int NW = FACTOR_BLOCK / 32;
+    __shared__ R part_hi[NW][27], part_lo[NW][27];   // the warps' (hi, lo) sums
+    __shared__ R total[27];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float dmu = 0.0f;
-    if (w < g.n_kf) {
-        const int k = w;
+    if (item < g.n_kf) {
+        const int k = item;
         const R* msgs = mk_write(g, t);
-        // the keyframe's own inputs first, so their loads overlap the reduction
+        // thread 0's own inputs first, so their loads overlap the reduction
         R prior[6], mu_old[6];
-        {
+        if (tid == 0) {
             const R sp = kf_prior_scale(g, P, k, t + 1);
             const R* old = g.kf_bel + (size_t)k * KBEL;
 #pragma unroll
@@ -1141,40 +1199,78 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
                 mu_old[i] = __ldcg(old + 27 + i);
             }
         }
-        R acc[27];
+        R hi[32], lo[32];
 #pragma unroll
-        for (int j = 0; j < 27; ++j) acc[j] = R(0);
+        for (int j = 0; j < 32; ++j) hi[j] = lo[j] = R(0);
         const int b0 = g.kf_off[k], b1 = g.kf_off[k + 1];
-#pragma unroll 4
-        for (int i = b0 + lane; i < b1; i += 32) {
+#pragma unroll 2
+        for (int i = b0 + tid; i < b1; i += FACTOR_BLOCK) {
             R rec[KREC];
             load_rec_cg<R, KREC>(msgs + (size_t)i * KREC, rec);
 #pragma unroll
-            for (int j = 0; j < 27; ++j) acc[j] += rec[j];
+            for (int j = 0; j < 27; ++j) two_sum_add(hi[j], lo[j], rec[j]);
         }
+        warp_transpose_sum<R, 32>(hi, lo, lane);
+        if (lane < 27) {
+            part_hi[warp][lane] = hi[0];
+            part_lo[warp][lane] = lo[0];
+        }
+        __syncthreads();
+        if (tid < 27) {
+            R h = part_hi[0][tid], l = part_lo[0][tid];
 #pragma unroll
-        for (int j = 0; j < 27; ++j) acc[j] = warp_sum(acc[j]);
-        if (lane == 0) dmu = finish_keyframe<R>(g, P, k, prior, acc, mu_old, g.kf_bel_out);
-    } else if (w < g.n_kf + g.n_big) {
-        const int m = g.big_lm[w - g.n_kf];
-        R acc[9];
+            for (int w = 1; w < NW; ++w) {
+                two_sum_add(h, l, part_hi[w][tid]);
+                l += part_lo[w][tid];
+            }
+            total[tid] = h + l;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            R acc[27];
 #pragma unroll
-        for (int j = 0; j < 9; ++j) acc[j] = R(0);
+            for (int j = 0; j < 27; ++j) acc[j] = total[j];
+            dmu = finish_keyframe<R>(g, P, k, prior, acc, mu_old, g.kf_bel_out);
+        }
+        __syncthreads();   // part is reused by the block's next item
+    } else if (item < g.n_kf + g.n_big) {
+        const int m = g.big_lm[item - g.n_kf];
+        R hi[16], lo[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) hi[j] = lo[j] = R(0);
         const int b0 = g.lm_off[m], b1 = g.lm_off[m + 1];
-        for (int f = b0 + lane; f < b1; f += 32) {
+        for (int f = b0 + tid; f < b1; f += FACTOR_BLOCK) {
 #pragma unroll
-            for (int j = 0; j < 9; ++j) acc[j] += __ldcg(g.ml_out + (size_t)j * g.n_f + f);
+            for (int j = 0; j < 9; ++j) two_sum_add(hi[j], lo[j], __ldcg(g.ml_out + (size_t)j * g.n_f + f));
         }
+        warp_transpose_sum<R, 16>(hi, lo, lane);
+        if (lane < 9) {
+            part_hi[warp][lane] = hi[0];
+            part_lo[warp][lane] = lo[0];
+        }
+        __syncthreads();
+        if (tid < 9) {
+            R h = part_hi[0][tid], l = part_lo[0][tid];
 #pragma unroll
-        for (int j = 0; j < 9; ++j) acc[j] = warp_sum(acc[j]);
-        if (lane == 0) {
+            for (int w = 1; w < NW; ++w) {
+                two_sum_add(h, l, part_hi[w][tid]);
+                l += part_lo[w][tid];
+            }
+            total[tid] = h + l;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            R acc[9];
+#pragma unroll
+            for (int j = 0; j < 9; ++j) acc[j] = total[j];
             const R* old = g.lm_bel + (size_t)m * LBEL;
             R mu_old[3] = {__ldcg(old + 9), __ldcg(old + 10), __ldcg(old + 11)};
             dmu = finish_landmark<R>(g, P, m, lm_prior_scale(g, P, m, t + 1), acc, mu_old, g.lm_bel_out);
         }
+        __syncthreads();
     } else {
         // variables without factors: prior-only beliefs, mean 0
-        const int i = (w - g.n_kf - g.n_big) * 32 + lane;
+        const int i = (item - g.n_kf - g.n_big) * FACTOR_BLOCK + tid;
         if (i < g.n_orphan) {
             const int v = g.orphan[i];
             const R isig2 = P.inv_sigma2;
@@ -1201,9 +1297,10 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
     return dmu;
 }
 
+// phase-B work items (blocks)
 template <typename R>
 __host__ __device__ inline int phase_b_items(const DevGraph<R>& g) {
-    return g.n_kf + g.n_big + (g.n_orphan + 31) / 32;
+    return g.n_kf + g.n_big + (g.n_orphan + FACTOR_BLOCK - 1) / FACTOR_BLOCK;
 }
 
 // ------------------------------------------------------------------------
@@ -1239,8 +1336,6 @@ __global__ void __launch_bounds__(FACTOR_BLOCK) factor_kernel(DevGraph<R> g, KPa
 template <typename R>
 __global__ void __launch_bounds__(FACTOR_BLOCK) belief_kernel(DevGraph<R> g, KParams<R> P) {
     pdl_wait_prev();
-    const int lane = threadIdx.x & 31;
-    const int w = blockIdx.x * (FACTOR_BLOCK / 32) + (threadIdx.x >> 5);
     const int t = g.ctl[CTL_ITER_B];
     // close the iteration from one thread: the factor kernel of t has
     // finished and that of t + 1 starts only after this kernel, so the
@@ -1250,11 +1345,10 @@ __global__ void __launch_bounds__(FACTOR_BLOCK) belief_kernel(DevGraph<R> g, KPa
         g.ctl[dmu_slot(t + 1)] = 0;
     }
     float dmu = 0.0f;
-    if (w < phase_b_items(g)) dmu = phase_b_item<R>(g, P, w, t, lane);
+    if (blockIdx.x < phase_b_items(g)) dmu = phase_b_item<R>(g, P, blockIdx.x, t);   // uniform per block
     pdl_allow_next();
     // max is order independent: the atomic on non-negative float bits is deterministic
-    dmu = warp_max(dmu);
-    if (lane == 0 && dmu > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), dmu);
+    if (threadIdx.x == 0 && dmu > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), dmu);
 }
 
 // ------------------------------------------------------------------------
@@ -1324,9 +1418,8 @@ __global__ void __launch_bounds__(FACTOR_BLOCK, (MODE == DAMP_FIXED && sizeof(R)
         // phase B: keyframes, split landmarks, orphans
         if (blockIdx.x == 0 && threadIdx.x == 0) g.ctl[dmu_slot(t + 1)] = 0;   // every block has read it
         float d2 = 0.0f;
-        for (int w = gwarp; w < items; w += nwarps) d2 = fmaxf(d2, phase_b_item<R>(g, P, w, t, lane));
-        d2 = warp_max(d2);
-        if (lane == 0 && d2 > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), d2);
+        for (int item = blockIdx.x; item < items; item += nb) d2 = fmaxf(d2, phase_b_item<R>(g, P, item, t));
+        if (threadIdx.x == 0 && d2 > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), d2);
         if (!grid_barrier(g.ctl, nb, &flag_sh)) break;
         done = it + 1;
         last = __int_as_float(__ldcg(&g.ctl[dmu_slot(t)]));
@@ -1598,8 +1691,7 @@ cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_
 
 template <typename R>
 cudaError_t launch_belief(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s, bool pdl) {
-    constexpr int wpb = FACTOR_BLOCK / 32;
-    int blocks = (phase_b_items(g) + wpb - 1) / wpb;
+    int blocks = phase_b_items(g);
     if (blocks < 1) blocks = 1;
     return launch_ex(belief_kernel<R>, blocks, s, pdl, g, p);
 }
@@ -1615,7 +1707,7 @@ int persistent_grid(const DevGraph<R>& g, int mode) {
     if (e != cudaSuccess || per_sm <= 0) return 0;
     constexpr int wpb = FACTOR_BLOCK / 32;
     const int cap = sms * per_sm;
-    const int want = (std::max(g.n_tiles, phase_b_items(g)) + wpb - 1) / wpb;
+    const int want = std::max((g.n_tiles + wpb - 1) / wpb, phase_b_items(g));
     return std::max(1, std::min(cap, want));
 }
 
