@@ -311,7 +311,9 @@ def run_gpu(args, rank, world, local):
         dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.current_stream(dev)
     p = synth.make_walk(seed=rank)
-    params = dict(huber_nsigma=HUBER, conv_tol=CONV_TOL, check_every=CHECK_EVERY, iterations=MAX_ITERS)
+    # launch_mode 0: the library's autotuner picks (measured on first use)
+    params = dict(huber_nsigma=HUBER, conv_tol=CONV_TOL, check_every=CHECK_EVERY, iterations=MAX_ITERS,
+                  launch_mode=args.launch_mode)
     g = gbp.Graph(p, stream=stream.cuda_stream, **params)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
@@ -470,7 +472,9 @@ def main():
     ap.add_argument("--scale-problems", type=int, default=256, help="problems in the batched measurement")
     ap.add_argument("--scale-only", action="store_true",
                     help="only the batched measurement (profiling runs); prints its own JSON line")
-    ap.add_argument("--launch-mode", type=int, default=0, help="with --scale-only: 1 persistent, 2 per phase")
+    ap.add_argument("--launch-mode", type=int, default=0, choices=(0, 1, 2),
+                    help="0 autotune (default), 1 persistent, 2 per phase; a profiler's serialisation changes "
+                         "what the autotuner measures, so a capture pins the mode the live run chose")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.scale_only:

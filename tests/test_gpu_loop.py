@@ -17,7 +17,17 @@ oracle's only in summation order, departs from it by up to 6e-7 on those
 points after 60 iterations (4e-5 after 300) while its 99th percentile stays
 at 1e-9.  The bar is therefore: 99th percentile and every keyframe within
 the 1e-5 tolerance, at most 0.1% of the beliefs beyond it, and the average
-reprojection error within 1e-3 px."""
+reprojection error within 1e-3 px.
+
+The average reprojection error counts only measurements whose point is at
+least z_min in front of its camera (Sec. 9.1 read that way), so it jumps
+where a point crosses that depth: one weakly observed point of the
+subgraph drifts to within a few cm of a camera centre, where FP32 and FP64
+land on opposite sides of z_min and that single ~2500 px residual moves the
+average by 0.013 px.  Both runs are therefore compared over the measurements
+that both count, with at most a handful (1e-4 of them) counted by one run
+only; the library's own figure is checked against the same definition
+evaluated here."""
 import os
 import time
 
@@ -51,6 +61,35 @@ def per_belief(kf, lm, okf, olm):
                    kf_max=float(ek.max()), lm_max=float(el.max()), frac_over=float((e > TOL32).mean()))
 
 
+Z_MIN = 0.05   # the depth cut of the average reprojection error (library default)
+
+
+def residuals(p, kf, lm):
+    """Pixel residual and depth of every measurement for poses kf (rows:
+    world-to-camera rotation, 9, then translation, 3) and points lm."""
+    fx, fy, cx, cy = p.intrinsics()[:4]
+    k, m = np.asarray(p.obs_kf), np.asarray(p.obs_lm)
+    R = kf[:, :9].reshape(-1, 3, 3)
+    pc = np.einsum("nij,nj->ni", R[k], lm[m]) + kf[k, 9:]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        uv = np.stack([fx * pc[:, 0] / pc[:, 2] + cx, fy * pc[:, 1] / pc[:, 2] + cy], axis=-1)
+    return np.linalg.norm(uv - np.asarray(p.obs_uv), axis=1), pc[:, 2]
+
+
+def compare_are(p, lib_are, kf, lm, okf, olm):
+    """The library's ARE equals the definition evaluated on its beliefs; the
+    two solutions' ARE over the measurements both count agree to 1e-3 px."""
+    r, z = residuals(p, kf, lm)
+    ro, zo = residuals(p, okf, olm)
+    own, other = z >= Z_MIN, zo >= Z_MIN
+    assert abs(lib_are - r[own].mean()) <= 1e-5
+    both = own & other
+    split = int((own != other).sum())
+    print("ARE over common measurements", r[both].mean(), ro[both].mean(), "counted by one side only", split)
+    assert split <= max(1, 1e-4 * len(r))
+    assert abs(r[both].mean() - ro[both].mean()) <= 1e-3
+
+
 def check(s):
     assert s["p99"] <= TOL32, s
     assert s["kf_max"] <= TOL32, s
@@ -75,7 +114,7 @@ def test_loop_subgraph_fp32_against_oracle(loop):
     print("subgraph", q.n_kf, q.n_lm, q.n_obs, s, "ARE", st["are"], o.are()[0],
           "oracle factor-updates/s", q.n_obs * n / dt, "fp64 fallbacks", st["fp64_fallbacks"])
     check(s)
-    assert abs(st["are"] - o.are()[0]) <= 1e-3
+    compare_are(q, st["are"], kf, lm, okf, olm)
 
 
 def test_loop_full_graph_fp32_against_fp64(loop):
@@ -94,4 +133,4 @@ def test_loop_full_graph_fp32_against_fp64(loop):
     print("full graph", loop.n_kf, loop.n_lm, loop.n_obs, s)
     assert np.isfinite(kf).all() and np.isfinite(lm).all()
     check(s)
-    assert abs(st32["are"] - st64["are"]) <= 1e-3
+    compare_are(loop, st32["are"], kf, lm, dkf, dlm)
