@@ -356,6 +356,16 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
     d.n_tiles = n_tiles;
     d.n_big = (int32_t)big.size();
     d.n_orphan = (int32_t)orphan.size();
+    {
+        // a block per belief item while a warp per item would leave SMs
+        // idle (at most one block of FACTOR_BLOCK / 32 items per SM), else
+        // a warp per item, so that the single-thread solves of many
+        // keyframes run side by side
+        int dev = 0, sms = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        d.b_warps = (nk + d.n_big) <= sms * (FACTOR_BLOCK / 32) ? FACTOR_BLOCK / 32 : 1;
+    }
     d.kf_D = s.kf_D;
     d.kf_A = s.kf_A;
     d.lm_D = s.lm_D;

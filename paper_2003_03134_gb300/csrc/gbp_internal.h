@@ -87,6 +87,7 @@ struct DevGraph {
     const int32_t* big_lm;    // landmarks split across tiles (more than 32 factors)
     const int32_t* orphan;    // variables without factors: keyframe v, or n_kf + landmark
     int32_t n_tiles, n_big, n_orphan;
+    int32_t b_warps;          // warps per belief-phase item: 4 (a block) for small graphs, else 1
     const int32_t* kf_birth;  // n_kf: iteration at which the keyframe was added (prior anneal start)
     const int32_t* lm_birth;  // n_lm
     const R* kf_D;            // n_kf x 6, prior diagonal at sigma = 1

@@ -675,6 +675,28 @@ __device__ __forceinline__ void warp_transpose_sum(R (&hi)[NV], R (&lo)[NV], int
     }
 }
 
+// The same transposing reduction without compensation (one shuffle and
+// one addition per step): lane l receives the total of value l % NV.
+template <typename R, int NV>
+__device__ __forceinline__ R warp_transpose_sum_plain(R (&v)[NV], int lane) {
+#pragma unroll
+    for (int o = 16; o >= NV; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+#pragma unroll
+    for (int h = NV / 2; h >= 1; h >>= 1) {
+        const bool up = (lane & h) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const R keep = up ? v[h + i] : v[i];
+            const R send = up ? v[i] : v[h + i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+        }
+    }
+    return v[0];
+}
+
 __device__ __forceinline__ int dmu_slot(int t) { return (t & 1) ? CTL_DMU_ACC1 : CTL_DMU_ACC; }
 
 __device__ __forceinline__ void dmu_atomic_max_slot(int32_t* ctl, int slot, float v) {
@@ -1166,31 +1188,76 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
 }
 
 // ------------------------------------------------------------------------
-// Phase B: one block (FACTOR_BLOCK threads) per work item.  Item b in
-// [0, n_kf): keyframe b -- a fixed-order reduction of its messages, which
-// are stored contiguously in the keyframe's CSR order: thread i takes
-// entries i, i + FACTOR_BLOCK, ...; a transposing shuffle tree per warp;
-// the warps' partial sums added in warp order; thread 0 forms the belief.
-// Every addition is compensated, so an FP32 belief is its messages' sum
-// rounded about once, however the entries fall across the threads.  Then one
-// item per landmark split across tiles (the same scheme over its factors'
-// landmark messages), then groups of FACTOR_BLOCK variables without factors
-// (prior-only beliefs).  Every thread of the block calls it with the same
-// item; returns max |dmu| in thread 0.
+// Phase B: one group of threads per work item -- one warp, or the whole
+// block for small graphs (g.b_warps = FACTOR_BLOCK / 32), where a warp per
+// item would leave SMs idle.  Item b in [0, n_kf): keyframe b -- a
+// fixed-order reduction of its messages, stored contiguously in the
+// keyframe's CSR order: thread i of the group takes entries i, i + group
+// size, ...; then the group's sums (group_total) reach the group's first
+// thread, which forms the belief.  In the block mapping (small graphs) only
+// a thread's own one or two additions round plainly and every addition
+// after them is compensated, so an FP32 belief is its messages' sum to
+// within about one rounding more; the warp mapping (large graphs, where a
+// lane adds ~5-10 entries itself) keeps a plain tree.  Then one item per landmark
+// split across tiles (the same over its factors' landmark messages), then
+// groups of variables without factors (prior-only beliefs).  Every thread
+// of the group calls it with the same item; returns max |dmu| in the
+// group's first thread.
 
-template <typename R>
-__device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParams<R>& P, int item, int t) {
+// Totals of NVAL values (NV >= NVAL, a power of two) over the group, into
+// out[] of the group's first thread.  A warp: a plain transposing tree.  A
+// block: a compensated transposing tree per warp, then NVAL threads add the
+// warps' (hi, lo) sums, compensated, in warp order.
+template <typename R, int NV, int NVAL, int W>
+__device__ __forceinline__ void group_total(R (&v)[NV], R (&out)[NVAL]) {
     constexpr int NW = FACTOR_BLOCK / 32;
-    __shared__ R part_hi[NW][27], part_lo[NW][27];   // the warps' (hi, lo) sums
-    __shared__ R total[27];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ R part_hi[NW][32], part_lo[NW][32], total[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (W == 1) {
+        // many items: a plain tree (the warp's own few entries per lane
+        // dominate the rounding anyway), kept cheap for large graphs
+        const R t = warp_transpose_sum_plain<R, NV>(v, lane);
+#pragma unroll
+        for (int j = 0; j < NVAL; ++j) out[j] = __shfl_sync(0xffffffffu, t, j);
+    } else {
+        R lo[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) lo[j] = R(0);
+        warp_transpose_sum<R, NV>(v, lo, lane);
+        if (lane < NVAL) {
+            part_hi[warp][lane] = v[0];
+            part_lo[warp][lane] = lo[0];
+        }
+        __syncthreads();
+        if (threadIdx.x < NVAL) {
+            R h = part_hi[0][threadIdx.x], l = part_lo[0][threadIdx.x];
+#pragma unroll
+            for (int w = 1; w < NW; ++w) {
+                two_sum_add(h, l, part_hi[w][threadIdx.x]);
+                l += part_lo[w][threadIdx.x];
+            }
+            total[threadIdx.x] = h + l;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int j = 0; j < NVAL; ++j) out[j] = total[j];
+        }
+    }
+}
+
+// W: warps per item (g.b_warps)
+template <typename R, int W>
+__device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParams<R>& P, int item, int t) {
+    const int gsize = 32 * W;
+    const int tg = threadIdx.x & (gsize - 1);   // thread within the group
     float dmu = 0.0f;
     if (item < g.n_kf) {
         const int k = item;
         const R* msgs = mk_write(g, t);
-        // thread 0's own inputs first, so their loads overlap the reduction
+        // the first thread's own inputs first, so their loads overlap the reduction
         R prior[6], mu_old[6];
-        if (tid == 0) {
+        if (tg == 0) {
             const R sp = kf_prior_scale(g, P, k, t + 1);
             const R* old = g.kf_bel + (size_t)k * KBEL;
 #pragma unroll
@@ -1199,78 +1266,40 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
                 mu_old[i] = __ldcg(old + 27 + i);
             }
         }
-        R hi[32], lo[32];
+        R hi[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) hi[j] = lo[j] = R(0);
+        for (int j = 0; j < 32; ++j) hi[j] = R(0);
         const int b0 = g.kf_off[k], b1 = g.kf_off[k + 1];
-#pragma unroll 2
-        for (int i = b0 + tid; i < b1; i += FACTOR_BLOCK) {
+#pragma unroll 4
+        for (int i = b0 + tg; i < b1; i += gsize) {
             R rec[KREC];
             load_rec_cg<R, KREC>(msgs + (size_t)i * KREC, rec);
 #pragma unroll
-            for (int j = 0; j < 27; ++j) two_sum_add(hi[j], lo[j], rec[j]);
+            for (int j = 0; j < 27; ++j) hi[j] += rec[j];
         }
-        warp_transpose_sum<R, 32>(hi, lo, lane);
-        if (lane < 27) {
-            part_hi[warp][lane] = hi[0];
-            part_lo[warp][lane] = lo[0];
-        }
-        __syncthreads();
-        if (tid < 27) {
-            R h = part_hi[0][tid], l = part_lo[0][tid];
-#pragma unroll
-            for (int w = 1; w < NW; ++w) {
-                two_sum_add(h, l, part_hi[w][tid]);
-                l += part_lo[w][tid];
-            }
-            total[tid] = h + l;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            R acc[27];
-#pragma unroll
-            for (int j = 0; j < 27; ++j) acc[j] = total[j];
-            dmu = finish_keyframe<R>(g, P, k, prior, acc, mu_old, g.kf_bel_out);
-        }
-        __syncthreads();   // part is reused by the block's next item
+        R acc[27];
+        group_total<R, 32, 27, W>(hi, acc);
+        if (tg == 0) dmu = finish_keyframe<R>(g, P, k, prior, acc, mu_old, g.kf_bel_out);
     } else if (item < g.n_kf + g.n_big) {
         const int m = g.big_lm[item - g.n_kf];
-        R hi[16], lo[16];
+        R hi[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) hi[j] = lo[j] = R(0);
+        for (int j = 0; j < 16; ++j) hi[j] = R(0);
         const int b0 = g.lm_off[m], b1 = g.lm_off[m + 1];
-        for (int f = b0 + tid; f < b1; f += FACTOR_BLOCK) {
+        for (int f = b0 + tg; f < b1; f += gsize) {
 #pragma unroll
-            for (int j = 0; j < 9; ++j) two_sum_add(hi[j], lo[j], __ldcg(g.ml_out + (size_t)j * g.n_f + f));
+            for (int j = 0; j < 9; ++j) hi[j] += __ldcg(g.ml_out + (size_t)j * g.n_f + f);
         }
-        warp_transpose_sum<R, 16>(hi, lo, lane);
-        if (lane < 9) {
-            part_hi[warp][lane] = hi[0];
-            part_lo[warp][lane] = lo[0];
-        }
-        __syncthreads();
-        if (tid < 9) {
-            R h = part_hi[0][tid], l = part_lo[0][tid];
-#pragma unroll
-            for (int w = 1; w < NW; ++w) {
-                two_sum_add(h, l, part_hi[w][tid]);
-                l += part_lo[w][tid];
-            }
-            total[tid] = h + l;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            R acc[9];
-#pragma unroll
-            for (int j = 0; j < 9; ++j) acc[j] = total[j];
+        R acc[9];
+        group_total<R, 16, 9, W>(hi, acc);
+        if (tg == 0) {
             const R* old = g.lm_bel + (size_t)m * LBEL;
             R mu_old[3] = {__ldcg(old + 9), __ldcg(old + 10), __ldcg(old + 11)};
             dmu = finish_landmark<R>(g, P, m, lm_prior_scale(g, P, m, t + 1), acc, mu_old, g.lm_bel_out);
         }
-        __syncthreads();
     } else {
         // variables without factors: prior-only beliefs, mean 0
-        const int i = (item - g.n_kf - g.n_big) * FACTOR_BLOCK + tid;
+        const int i = (item - g.n_kf - g.n_big) * gsize + tg;
         if (i < g.n_orphan) {
             const int v = g.orphan[i];
             const R isig2 = P.inv_sigma2;
@@ -1297,10 +1326,19 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
     return dmu;
 }
 
-// phase-B work items (blocks)
+// phase-B work items, and the blocks that hold them at one item per group
 template <typename R>
 __host__ __device__ inline int phase_b_items(const DevGraph<R>& g) {
-    return g.n_kf + g.n_big + (g.n_orphan + FACTOR_BLOCK - 1) / FACTOR_BLOCK;
+    return g.n_kf + g.n_big + (g.n_orphan + 32 * g.b_warps - 1) / (32 * g.b_warps);
+}
+template <typename R>
+__host__ __device__ inline int phase_b_blocks(const DevGraph<R>& g) {
+    constexpr int WPB = FACTOR_BLOCK / 32;
+    return (phase_b_items(g) * g.b_warps + WPB - 1) / WPB;
+}
+// the item of this thread's group when block b holds items from b * items-per-block
+__device__ __forceinline__ int phase_b_item_of(int W, int block) {
+    return W == FACTOR_BLOCK / 32 ? block : block * (FACTOR_BLOCK / 32) + (int(threadIdx.x) >> 5);
 }
 
 // ------------------------------------------------------------------------
@@ -1333,7 +1371,8 @@ __global__ void __launch_bounds__(FACTOR_BLOCK) factor_kernel(DevGraph<R> g, KPa
     if (blockIdx.x == 0 && threadIdx.x == 0) g.ctl[CTL_ITER_B] = t;
 }
 
-template <typename R>
+// BW = g.b_warps (warps per belief item), one instantiation per mapping
+template <typename R, int BW>
 __global__ void __launch_bounds__(FACTOR_BLOCK) belief_kernel(DevGraph<R> g, KParams<R> P) {
     pdl_wait_prev();
     const int t = g.ctl[CTL_ITER_B];
@@ -1345,10 +1384,11 @@ __global__ void __launch_bounds__(FACTOR_BLOCK) belief_kernel(DevGraph<R> g, KPa
         g.ctl[dmu_slot(t + 1)] = 0;
     }
     float dmu = 0.0f;
-    if (blockIdx.x < phase_b_items(g)) dmu = phase_b_item<R>(g, P, blockIdx.x, t);   // uniform per block
+    const int item = phase_b_item_of(BW, blockIdx.x);
+    if (item < phase_b_items(g)) dmu = phase_b_item<R, BW>(g, P, item, t);   // uniform per group
     pdl_allow_next();
     // max is order independent: the atomic on non-negative float bits is deterministic
-    if (threadIdx.x == 0 && dmu > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), dmu);
+    if (dmu > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), dmu);
 }
 
 // ------------------------------------------------------------------------
@@ -1391,7 +1431,10 @@ __device__ __forceinline__ bool grid_barrier(int32_t* ctl, int nblocks, int* fla
 }
 
 // The FP32 fixed schedule is held to 3 blocks per SM (<= 168 registers).
-template <typename R, int MODE>
+// BW = g.b_warps (warps per belief item): a separate instantiation per
+// mapping, so that the block mapping's barriers and shared-memory reduction
+// do not weigh on the register allocation of the warp mapping's kernel.
+template <typename R, int MODE, int BW>
 __global__ void __launch_bounds__(FACTOR_BLOCK, (MODE == DAMP_FIXED && sizeof(R) == 4) ? 3 : 1)
     persistent_kernel(DevGraph<R> g, KParams<R> P, int n_iters, float conv_tol, int check_every) {
     __shared__ int flag_sh;
@@ -1418,8 +1461,12 @@ __global__ void __launch_bounds__(FACTOR_BLOCK, (MODE == DAMP_FIXED && sizeof(R)
         // phase B: keyframes, split landmarks, orphans
         if (blockIdx.x == 0 && threadIdx.x == 0) g.ctl[dmu_slot(t + 1)] = 0;   // every block has read it
         float d2 = 0.0f;
-        for (int item = blockIdx.x; item < items; item += nb) d2 = fmaxf(d2, phase_b_item<R>(g, P, item, t));
-        if (threadIdx.x == 0 && d2 > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), d2);
+        // a block per item, or a warp per item (see phase_b_item)
+        constexpr bool per_block = BW == WPB;
+        const int stride = per_block ? nb : nwarps;
+        for (int item = per_block ? int(blockIdx.x) : gwarp; item < items; item += stride)
+            d2 = fmaxf(d2, phase_b_item<R, BW>(g, P, item, t));
+        if (d2 > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), d2);   // groups' first threads
         if (!grid_barrier(g.ctl, nb, &flag_sh)) break;
         done = it + 1;
         last = __int_as_float(__ldcg(&g.ctl[dmu_slot(t)]));
@@ -1691,9 +1738,21 @@ cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_
 
 template <typename R>
 cudaError_t launch_belief(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s, bool pdl) {
-    int blocks = phase_b_items(g);
+    int blocks = phase_b_blocks(g);
     if (blocks < 1) blocks = 1;
-    return launch_ex(belief_kernel<R>, blocks, s, pdl, g, p);
+    if (g.b_warps == FACTOR_BLOCK / 32) return launch_ex(belief_kernel<R, FACTOR_BLOCK / 32>, blocks, s, pdl, g, p);
+    return launch_ex(belief_kernel<R, 1>, blocks, s, pdl, g, p);
+}
+
+// the persistent kernel for this graph's belief mapping and damping schedule
+template <typename R>
+const void* persistent_fn(const DevGraph<R>& g, int mode) {
+    constexpr int WPB = FACTOR_BLOCK / 32;
+    if (g.b_warps == WPB)
+        return mode == DAMP_LEARNED ? reinterpret_cast<const void*>(persistent_kernel<R, DAMP_LEARNED, WPB>)
+                                    : reinterpret_cast<const void*>(persistent_kernel<R, DAMP_FIXED, WPB>);
+    return mode == DAMP_LEARNED ? reinterpret_cast<const void*>(persistent_kernel<R, DAMP_LEARNED, 1>)
+                                : reinterpret_cast<const void*>(persistent_kernel<R, DAMP_FIXED, 1>);
 }
 
 template <typename R>
@@ -1701,13 +1760,11 @@ int persistent_grid(const DevGraph<R>& g, int mode) {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    cudaError_t e = mode == DAMP_LEARNED
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<R, DAMP_LEARNED>, FACTOR_BLOCK, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<R, DAMP_FIXED>, FACTOR_BLOCK, 0);
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_fn(g, mode), FACTOR_BLOCK, 0);
     if (e != cudaSuccess || per_sm <= 0) return 0;
     constexpr int wpb = FACTOR_BLOCK / 32;
     const int cap = sms * per_sm;
-    const int want = std::max((g.n_tiles + wpb - 1) / wpb, phase_b_items(g));
+    const int want = std::max((g.n_tiles + wpb - 1) / wpb, phase_b_blocks(g));
     return std::max(1, std::min(cap, want));
 }
 
@@ -1717,9 +1774,7 @@ cudaError_t launch_persistent(const DevGraph<R>& g, const KParams<R>& p, int n_i
     DevGraph<R> gg = g;
     KParams<R> pp = p;
     void* args[] = {&gg, &pp, &n_iters, &conv_tol, &check_every};
-    void* fn = mode == DAMP_LEARNED ? reinterpret_cast<void*>(persistent_kernel<R, DAMP_LEARNED>)
-                                    : reinterpret_cast<void*>(persistent_kernel<R, DAMP_FIXED>);
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(FACTOR_BLOCK), args, 0, s);
+    return cudaLaunchCooperativeKernel(persistent_fn(g, mode), dim3(grid), dim3(FACTOR_BLOCK), args, 0, s);
 }
 
 // The current messages' eta in factor order (keyframe side 6, landmark side
