@@ -1353,7 +1353,7 @@ __device__ __forceinline__ void pdl_allow_next() { asm volatile("griddepcontrol.
 __device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename R, int MODE>
-__global__ void __launch_bounds__(FACTOR_BLOCK) factor_kernel(DevGraph<R> g, KParams<R> P) {
+__device__ __forceinline__ void factor_body(const DevGraph<R>& g, const KParams<R>& P) {
     __shared__ __align__(16) MlpSmem<MODE> S;
     mlp_load_async<MODE>(P, S);   // network weights do not change between iterations
     pdl_wait_prev();
@@ -1369,6 +1369,19 @@ __global__ void __launch_bounds__(FACTOR_BLOCK) factor_kernel(DevGraph<R> g, KPa
     // the belief kernel of this iteration reads t from CTL_ITER_B: the belief
     // kernel of t - 1 has finished and that of t starts after this kernel
     if (blockIdx.x == 0 && threadIdx.x == 0) g.ctl[CTL_ITER_B] = t;
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(FACTOR_BLOCK) factor_kernel(DevGraph<R> g, KParams<R> P) {
+    factor_body<R, MODE>(g, P);
+}
+
+// The FP32 fixed schedule on large graphs (a warp per belief item): at
+// least 4 blocks per SM (<= 128 registers), trading spills for the
+// occupancy that hides HBM latency; small graphs keep factor_kernel.
+template <typename R, int MODE>
+__global__ void __launch_bounds__(FACTOR_BLOCK, 4) factor_kernel_lg(DevGraph<R> g, KParams<R> P) {
+    factor_body<R, MODE>(g, P);
 }
 
 // BW = g.b_warps (warps per belief item), one instantiation per mapping
@@ -1430,12 +1443,13 @@ __device__ __forceinline__ bool grid_barrier(int32_t* ctl, int nblocks, int* fla
     return *flag_sh;
 }
 
-// The FP32 fixed schedule is held to 3 blocks per SM (<= 168 registers).
+// The FP32 fixed schedule is held to 3 blocks per SM (<= 168 registers), 4
+// (<= 128) with the warp belief mapping (large graphs).
 // BW = g.b_warps (warps per belief item): a separate instantiation per
 // mapping, so that the block mapping's barriers and shared-memory reduction
 // do not weigh on the register allocation of the warp mapping's kernel.
 template <typename R, int MODE, int BW>
-__global__ void __launch_bounds__(FACTOR_BLOCK, (MODE == DAMP_FIXED && sizeof(R) == 4) ? 3 : 1)
+__global__ void __launch_bounds__(FACTOR_BLOCK, (MODE == DAMP_FIXED && sizeof(R) == 4) ? (BW == 1 ? 4 : 3) : 1)
     persistent_kernel(DevGraph<R> g, KParams<R> P, int n_iters, float conv_tol, int check_every) {
     __shared__ int flag_sh;
     __shared__ __align__(16) MlpSmem<MODE> S;
@@ -1733,6 +1747,7 @@ cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_
     const int blocks = std::max(1, (g.n_tiles + wpb - 1) / wpb);   // >= 1: it also publishes the iteration index
     if (mode == DAMP_LEARNED) return launch_ex(factor_kernel<R, DAMP_LEARNED>, blocks, s, pdl, g, p);
     if (mode == DAMP_RECORD) return launch_ex(factor_kernel<R, DAMP_RECORD>, blocks, s, pdl, g, p);
+    if (sizeof(R) == 4 && g.b_warps == 1) return launch_ex(factor_kernel_lg<R, DAMP_FIXED>, blocks, s, pdl, g, p);
     return launch_ex(factor_kernel<R, DAMP_FIXED>, blocks, s, pdl, g, p);
 }
 
