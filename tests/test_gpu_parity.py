@@ -239,6 +239,22 @@ def test_launch_modes_are_bitwise_identical():
         np.testing.assert_array_equal(x, y)
 
 
+def test_launch_modes_are_bitwise_identical_on_a_large_graph():
+    """Graphs with more keyframes than 4 per SM take the warp-per-item belief
+    mapping and the large-graph kernels (4 blocks per SM): both launch modes
+    still run the same arithmetic in the same order."""
+    probs = synth.make_batch(6, kf_range=(150, 200), lm_range=(500, 800))
+    res = []
+    for mode in (1, 2):
+        g = gbp.Graph(probs, huber_nsigma=2.0, launch_mode=mode)
+        assert gbp.gbp_get_sizes(g.h)[0] > 4 * 152
+        g.iterate(25)
+        res.append(g.means())
+        g.close()
+    for x, y in zip(*res):
+        np.testing.assert_array_equal(x, y)
+
+
 def test_convergence_stops_at_the_same_iteration_in_both_modes():
     p = synth.make_circle(2)
     done = []
