@@ -214,6 +214,12 @@ gbp_status gbp_get_stats(const gbp_graph* g, gbp_stats* out);
 
 gbp_status gbp_get_sizes(const gbp_graph* g, int32_t* n_kf, int32_t* n_lm, int32_t* n_obs);
 
+/* Iteration at which each observation's factor was last (re)linearised
+ * (t_lin of the lazy schedule of Sec. 5 / Sec. 8; 0 = still at its first
+ * linearisation), n_obs int32 in the caller's observation order (host).
+ * Synchronises the stream. */
+gbp_status gbp_get_relin_iters(const gbp_graph* g, int32_t* tlin);
+
 /* Kernel timing.  ms_out[0]: mean device time per iteration in the current
  * launch mode (n_iters iterations from reset, CUDA events on the graph's
  * stream).  ms_out[1]: mean device time of one factor-kernel launch (phase
@@ -244,9 +250,11 @@ void gbp_destroy_graph(gbp_graph* g);
  *   intr      pinhole intrinsics (host pointer)
  *   z_min     observations whose point lies closer than z_min to the camera
  *             are left out of the average
- *   kf_Rt     device, n_kf x 12 doubles (R row-major, t; world to camera)
- *   lm_xyz    device, n_lm x 3 doubles
- *   obs_kf, obs_lm  device, n_obs int32 indices (not range-checked here)
+ *   n_kf, kf_Rt   device, n_kf x 12 doubles (R row-major, t; world to camera)
+ *   n_lm, lm_xyz  device, n_lm x 3 doubles
+ *   obs_kf, obs_lm  device, n_obs int32 indices; an observation whose
+ *             keyframe or landmark index is out of range is left out of the
+ *             average (its arrays are never read through it)
  *   obs_uv    device, n_obs x 2 doubles (pixels)
  *   out       device, 2 doubles: out[0] = mean |z - pi(R l + t)| in pixels,
  *             out[1] = number of observations averaged
@@ -255,15 +263,18 @@ void gbp_destroy_graph(gbp_graph* g);
  * Scratch: a fixed 64 KiB array in the library's device memory, present on
  * every GPU that loads the library until the process exits; no cudaMalloc,
  * cudaFree or allocating library routine is called.  The first call on a
- * device looks up that array's device address (make it before any stream
- * capture).  All calls share the array and it keeps the last call's partial
- * sums, so calls whose kernels overlap on the GPU (different streams, or
- * several host threads) race and must be serialised by the caller.
- * GBP_EINVAL: n_obs < 0, n_obs > GBP_NOALLOC_MAX_OBS (the scratch array's
- * capacity), or a required pointer is NULL.  GBP_ECUDA: no device or a
- * launch failed. */
-gbp_status gbp_reprojection_error_noalloc(const gbp_intrinsics* intr, double z_min, const double* kf_Rt,
-                                          const double* lm_xyz, int32_t n_obs, const int32_t* obs_kf,
+ * device looks up that array's device address and caches it for the rest of
+ * the process (make that first call before any stream capture; after a
+ * cudaDeviceReset of that device the cached address is stale, so do not
+ * call this entry point on it again in the same process).  All calls share
+ * the array and it keeps the last call's partial sums, so calls whose
+ * kernels overlap on the GPU (different streams, or several host threads)
+ * race and must be serialised by the caller.
+ * GBP_EINVAL: a negative count, n_obs > GBP_NOALLOC_MAX_OBS (the scratch
+ * array's capacity), or a required pointer is NULL.  GBP_ECUDA: no device or
+ * a launch failed. */
+gbp_status gbp_reprojection_error_noalloc(const gbp_intrinsics* intr, double z_min, int32_t n_kf, const double* kf_Rt,
+                                          int32_t n_lm, const double* lm_xyz, int32_t n_obs, const int32_t* obs_kf,
                                           const int32_t* obs_lm, const double* obs_uv, double* out,
                                           void* cuda_stream);
 

@@ -91,6 +91,9 @@ def lib():
         L.orc_set_reference_messages.argtypes = [C.c_void_p, _D]
         L.orc_set_reference_messages.restype = None
         L.orc_iterate_record.argtypes = [C.c_void_p, C.c_int, _D, _D]
+        L.orc_get_relin_iters.argtypes = [C.c_void_p, _I]
+        L.orc_get_relin_iters.restype = None
+        L.orc_set_messages.argtypes = [C.c_void_p, _D, _D, _D, _D]
         _lib = L
     return _lib
 
@@ -312,6 +315,21 @@ class Oracle:
 
     def relinearisations(self) -> int:
         return lib().orc_relinearisations(self._h)
+
+    def relin_iters(self) -> np.ndarray:
+        """Iteration of each factor's last (re)linearisation, observation order."""
+        t = np.zeros(self.sizes()[2], dtype=np.int32)
+        lib().orc_get_relin_iters(self._h, _ip(t))
+        return t
+
+    def set_messages(self, mk_lam, mk_eta, ml_lam, ml_eta):
+        """Test hook: replace the current messages (the layout of messages())
+        and recompute the beliefs from them."""
+        n = self.sizes()[2]
+        a, b = _f64(mk_lam).reshape(n, 36), _f64(mk_eta).reshape(n, 6)
+        c, d = _f64(ml_lam).reshape(n, 9), _f64(ml_eta).reshape(n, 3)
+        if lib().orc_set_messages(self._h, _dp(a), _dp(b), _dp(c), _dp(d)) != 0:
+            raise FloatingPointError("a belief is not positive definite")
 
     def held_messages(self) -> int:
         return lib().orc_held_messages(self._h)

@@ -796,6 +796,22 @@ void orc_get_messages(const orc_graph* g, double* mk_lam, double* mk_eta, double
 }
 
 /* Sec. 9.1: average reprojection error over the measurements. */
+void orc_get_relin_iters(const orc_graph* g, int* tlin)
+{
+    memcpy(tlin, g->tlin, sizeof(int) * (size_t)g->n_f);
+}
+
+int orc_set_messages(orc_graph* g, const double* mk_lam, const double* mk_eta, const double* ml_lam,
+                     const double* ml_eta)
+{
+    size_t F = (size_t)g->n_f;
+    memcpy(g->mk_lam, mk_lam, sizeof(double) * 36 * F);
+    memcpy(g->mk_eta, mk_eta, sizeof(double) * 6 * F);
+    memcpy(g->ml_lam, ml_lam, sizeof(double) * 9 * F);
+    memcpy(g->ml_eta, ml_eta, sizeof(double) * 3 * F);
+    return update_beliefs(g, NULL);
+}
+
 double orc_are(const orc_graph* g, const unsigned char* mask, int* count)
 {
     double sum = 0.0;

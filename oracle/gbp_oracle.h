@@ -90,6 +90,17 @@ void orc_get_prior_diag(const orc_graph* g, double* kf_d /* n_kf x 6 */, double*
 void orc_get_messages(const orc_graph* g, double* mk_lam /* n_f x 36 */, double* mk_eta /* n_f x 6 */,
                       double* ml_lam /* n_f x 9 */, double* ml_eta /* n_f x 3 */);
 
+/* Iteration at which each factor (caller order) was last (re)linearised:
+ * t_lin of the schedule of Sec. 5 / Sec. 8 (0 = still at its first
+ * linearisation). */
+void orc_get_relin_iters(const orc_graph* g, int* tlin /* n_f */);
+/* Test hook: replace the current messages m^t (full symmetric matrices, the
+ * layout of orc_get_messages) and recompute every belief b^t = prior(t) +
+ * sum of messages and its mean.  Returns 0, or -1 if a belief is not
+ * positive definite (the graph is then unusable). */
+int orc_set_messages(orc_graph* g, const double* mk_lam, const double* mk_eta, const double* ml_lam,
+                     const double* ml_eta);
+
 /* Average reprojection error over measurements whose point lies in front of
  * the camera (depth >= z_min).  mask (nullable) selects measurements.
  * *count (nullable) receives the number averaged. */

@@ -1299,6 +1299,19 @@ gbp_status gbp_get_stats(const gbp_graph* cg, gbp_stats* out) {
     return st;
 }
 
+gbp_status gbp_get_relin_iters(const gbp_graph* cg, int32_t* tlin) {
+    gbp_graph* g = const_cast<gbp_graph*>(cg);
+    if (!g || (g->n_f && !tlin)) return GBP_EINVAL;
+    std::vector<int32_t> t(g->n_f);
+    if (g->n_f) {
+        const int32_t* d = g->storage ? g->sd.tlin : g->sf.tlin;
+        CK(cudaMemcpyAsync(t.data(), d, sizeof(int32_t) * t.size(), cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+    }
+    for (int f = 0; f < g->n_f; ++f) tlin[g->obs_index[f]] = t[f];
+    return read_ctl(g);
+}
+
 gbp_status gbp_get_sizes(const gbp_graph* g, int32_t* n_kf, int32_t* n_lm, int32_t* n_obs) {
     if (!g) return GBP_EINVAL;
     if (n_kf) *n_kf = g->n_kf;

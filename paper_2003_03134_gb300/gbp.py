@@ -105,6 +105,7 @@ def lib() -> C.CDLL:
     L.gbp_add_keyframe.argtypes = [vp, _D, C.c_int32, _D, C.c_int32, _I, _D, _I]
     L.gbp_get_stats.argtypes = [vp, C.POINTER(gbp_stats)]
     L.gbp_get_sizes.argtypes = [vp, _I, _I, _I]
+    L.gbp_get_relin_iters.argtypes = [vp, _I]
     L.gbp_profile_iterations.argtypes = [vp, C.c_int32, _D]
     L.gbp_autotune.argtypes = [vp, C.c_int32, _I, _D]
     L.gbp_create_batch.argtypes = [C.POINTER(gbp_intrinsics), C.c_int32, C.POINTER(gbp_problem_desc), vp,
@@ -117,8 +118,8 @@ def lib() -> C.CDLL:
     L.gbp_status_string.restype = C.c_char_p
     L.gbp_last_error.argtypes = [vp]
     L.gbp_last_error.restype = C.c_char_p
-    L.gbp_reprojection_error_noalloc.argtypes = [C.POINTER(gbp_intrinsics), C.c_double, vp, vp, C.c_int32, vp, vp,
-                                                 vp, vp, vp]
+    L.gbp_reprojection_error_noalloc.argtypes = [C.POINTER(gbp_intrinsics), C.c_double, C.c_int32, vp, C.c_int32, vp,
+                                                 C.c_int32, vp, vp, vp, vp, vp]
     _F = C.POINTER(C.c_float)
     L.gbp_mlp_create.argtypes = [_F, vp, C.POINTER(vp)]
     L.gbp_mlp_set_params.argtypes = [vp, _F]
@@ -288,6 +289,14 @@ def gbp_add_keyframe(g: int, kf_Rt_init, new_lm_xyz, n_new_lm: int, obs_lm, obs_
     return idx.value
 
 
+def gbp_get_relin_iters(g: int) -> np.ndarray:
+    """Iteration of each observation's last (re)linearisation (observation order)."""
+    n = gbp_get_sizes(g)[2]
+    t = np.zeros(n, dtype=np.int32)
+    _check(lib().gbp_get_relin_iters(g, _ip(t)), g)
+    return t
+
+
 def gbp_get_stats(g: int) -> gbp_stats:
     s = gbp_stats()
     _check(lib().gbp_get_stats(g, C.byref(s)), g)
@@ -309,16 +318,18 @@ def gbp_profile_iterations(g: int, n_iters: int):
     return float(out[0]), float(out[1])
 
 
-def gbp_reprojection_error_noalloc(intrinsics, z_min, kf_Rt_ptr, lm_xyz_ptr, n_obs, obs_kf_ptr, obs_lm_ptr,
-                                   obs_uv_ptr, out_ptr, stream=None) -> None:
+def gbp_reprojection_error_noalloc(intrinsics, z_min, n_kf, kf_Rt_ptr, n_lm, lm_xyz_ptr, n_obs, obs_kf_ptr,
+                                   obs_lm_ptr, obs_uv_ptr, out_ptr, stream=None) -> None:
     """Average reprojection error of caller-owned device arrays (raw device
     pointers as ints) into out_ptr[0:2] = (mean error px, count), with no
     allocation: for callers that cannot allocate device memory at that
-    point.  Asynchronous on ``stream``."""
+    point.  Observations with an out-of-range index are left out.
+    Asynchronous on ``stream``."""
     fx, fy, cx, cy, w, h = intrinsics
     intr = gbp_intrinsics(fx, fy, cx, cy, int(w), int(h))
-    _check(lib().gbp_reprojection_error_noalloc(C.byref(intr), float(z_min), kf_Rt_ptr, lm_xyz_ptr, int(n_obs),
-                                                obs_kf_ptr, obs_lm_ptr, obs_uv_ptr, out_ptr, C.c_void_p(stream or 0)))
+    _check(lib().gbp_reprojection_error_noalloc(C.byref(intr), float(z_min), int(n_kf), kf_Rt_ptr, int(n_lm),
+                                                lm_xyz_ptr, int(n_obs), obs_kf_ptr, obs_lm_ptr, obs_uv_ptr, out_ptr,
+                                                C.c_void_p(stream or 0)))
 
 
 def gbp_destroy_graph(g: int) -> None:
@@ -460,6 +471,9 @@ class Graph:
 
     def profile(self, n: int):
         return gbp_profile_iterations(self.h, n)
+
+    def relin_iters(self) -> np.ndarray:
+        return gbp_get_relin_iters(self.h)
 
     def autotune(self, n_trial: int = 8):
         return gbp_autotune(self.h, n_trial)

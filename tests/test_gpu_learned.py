@@ -283,8 +283,10 @@ def test_stream_learned_against_fixed():
     schedules keep tracking (seed 1: the error of the growing graph settles
     near the noise-and-outlier floor) the learned schedule keeps it at least
     as low as fixed d = 0.4 on most steps.  (On streams where the graph
-    drifts away from the truth the comparison goes either way; the numbers
-    for four seeds are in the design notes.)"""
+    drifts away from the truth -- new points start 1 m along their first ray
+    and are triangulated from baselines of a few centimetres -- the two
+    schedules trade places from step to step, so no ordering is asserted
+    there.)"""
     import torch
     init, steps = synth.make_stream(1)
     net = gbp.DampingNet(learned.trained_params())

@@ -101,18 +101,68 @@ def test_fp32_paper_scale_walk_matches_oracle():
     assert abs(st["are"] - o.are()[0]) <= 1e-3
 
 
+def _hops_from(p, factors):
+    """Distance of every variable (keyframes then landmarks), in factors,
+    from the variables of the given factors (0 = a variable of one of them)."""
+    nv = p.n_kf + p.n_lm
+    adj = [[] for _ in range(nv)]
+    for k, m in zip(p.obs_kf, p.obs_lm):
+        adj[k].append(p.n_kf + m)
+        adj[p.n_kf + m].append(k)
+    dist = np.full(nv, np.iinfo(np.int32).max)
+    frontier = sorted({int(p.obs_kf[f]) for f in factors} | {p.n_kf + int(p.obs_lm[f]) for f in factors})
+    for v in frontier:
+        dist[v] = 0
+    d = 0
+    while frontier:
+        d += 1
+        nxt = []
+        for v in frontier:
+            for u in adj[v]:
+                if dist[u] > d:
+                    dist[u] = d
+                    nxt.append(u)
+        frontier = nxt
+    return dist
+
+
 @pytest.mark.parametrize("seed", [0, 1])
-def test_fp32_paper_schedule_properties(seed):
-    """With the paper's beta = 0.01 compare what threshold decisions cannot
-    move: relinearisation counts, the mean reprojection error and the bulk of
-    the per-variable errors."""
+def test_fp32_paper_schedule_elementwise_outside_threshold_splits(seed):
+    """The paper's beta = 0.01 (Sec. 8).  The relinearisation test compares
+    |mu - x0| with beta, and FP32 and FP64 means differ by ~1e-7 relative,
+    so a factor whose distance lands within that of beta can relinearise in
+    a different iteration on the two sides.  Both sides report every
+    factor's t_lin after every iteration (neither sees the other's); a
+    factor whose t_lin ever differs is a threshold split.  Every belief more
+    than one factor away from all splits must meet the element-wise bar;
+    the beliefs next to a split are reported."""
     p = synth.make_walk(seed) if seed == 0 else synth.make_walk(seed, n_kf=40, n_lm=600)
-    kf, lm, st, okf, olm, o = run_pair(p, 200, dict(huber_nsigma=2.0), dict(huber_nsigma=2.0))
+    n = 200
+    g = gbp.Graph(p, huber_nsigma=2.0)
+    o = oracle.Oracle(p, huber_nsigma=2.0)
+    split = np.zeros(p.n_obs, bool)
+    for _ in range(n):
+        g.iterate(1)
+        o.iterate(1)
+        split |= g.relin_iters() != o.relin_iters()
+    kf, lm = g.beliefs()
+    st = g.stats()
+    okf, olm = o.world()
+    g.close()
     e = rel_err(kf, lm, okf, olm)
+    hops = _hops_from(p, np.flatnonzero(split))
+    far = hops >= 2
+    print(f"splits {split.sum()} of {p.n_obs} factors; beliefs next to a split {np.sum(~far)}; "
+          f"max err there {e[~far].max() if (~far).any() else 0:.3g}; elsewhere max {e[far].max():.3g} "
+          f"median {np.median(e[far]):.3g}")
+    for h in range(0, 6):
+        sel = hops == h
+        if sel.any():
+            print(f"  hop {h}: {sel.sum()} beliefs, max err {e[sel].max():.3g}")
+    assert split.mean() <= 0.01
+    assert e[far].max() <= TOL32, (e[far].max(), np.median(e[far]))
     assert abs(st["relinearisations"] - o.relinearisations()) <= max(2, 1e-3 * o.relinearisations())
     assert abs(st["are"] - o.are()[0]) <= 1e-3
-    assert np.median(e) <= 5e-6
-    assert np.mean(e <= TOL32) >= 0.9
 
 
 @pytest.mark.parametrize("mode", [1, 2])
@@ -128,6 +178,40 @@ def test_forced_fp64_fallback_matches_oracle(mode):
     assert e.max() <= TOL32, (e.max(), np.median(e))
     # every active factor's keyframe marginal, every iteration (plus belief redos)
     assert st["fp64_fallbacks"] >= n * int((p.obs_kf >= 0).sum()) * 0.9
+
+
+@pytest.mark.parametrize("hold", [0, 3, 8])
+def test_damping_starts_exactly_after_the_undamped_hold(hold):
+    """Sec. 8, as pinned on the oracle: in linear mode runs with d = 0 and
+    d = 0.4 agree bit for bit for exactly max(hold, 1) iterations and part
+    on the next, in both launch modes."""
+    p = synth.make_circle(0, n_kf=5, n_lm=30)
+    for mode in (1, 2):
+        a = gbp.Graph(p, linear=1, damping=0.0, undamped_iters=hold, launch_mode=mode)
+        b = gbp.Graph(p, linear=1, damping=0.4, undamped_iters=hold, launch_mode=mode)
+        a.iterate(max(hold, 1))
+        b.iterate(max(hold, 1))
+        for x, y in zip(a.means(), b.means()):
+            np.testing.assert_array_equal(x, y)
+        a.iterate(1)
+        b.iterate(1)
+        assert np.abs(a.means()[1] - b.means()[1]).max() > 1e-7
+        a.close()
+        b.close()
+
+
+@pytest.mark.parametrize("interval,n_iters", [(10, 10), (10, 11), (10, 35), (7, 30)])
+def test_relinearisation_count_with_beta_zero(interval, n_iters):
+    """Sec. 5 / Sec. 8 with beta = 0: n_f * floor((N - 1) / interval)
+    relinearisations after N iterations, each factor last at the largest
+    multiple of the interval below N (pinned on the oracle the same way)."""
+    p = synth.make_circle(0, n_kf=5, n_lm=30)
+    g = gbp.Graph(p, relin_beta=0.0, relin_interval=interval)
+    g.iterate(n_iters)
+    k = (n_iters - 1) // interval
+    assert g.stats()["relinearisations"] == p.n_obs * k
+    np.testing.assert_array_equal(g.relin_iters(), np.full(p.n_obs, k * interval))
+    g.close()
 
 
 def test_linear_mode_matches_oracle():

@@ -415,6 +415,128 @@ def test_relinearisation_threshold_never_met_equals_linear_mode():
         np.testing.assert_array_equal(x, y)
 
 
+# ------------------------------------------------ schedule (Sec. 5, Sec. 8)
+#
+# The relinearisation gate, the undamped hold after a (re)linearisation, the
+# damping of eta only and the held-message rule are comparisons and branches:
+# each pin below fails when one of them is flipped (< for <=), shifted by an
+# iteration, or applied to the wrong quantity.
+
+@pytest.mark.parametrize("hold", [0, 1, 3, 8])
+def test_damping_starts_exactly_after_the_undamped_hold(hold):
+    """Sec. 8: messages stay undamped for the first iterations after a
+    (re)linearisation; the first message is never damped (nothing to damp
+    towards).  In linear mode every factor is linearised at t = 0, so runs
+    with d = 0 and d = 0.4 agree bit for bit for exactly max(hold, 1)
+    iterations and part on the next."""
+    p = synth.make_circle(0, n_kf=5, n_lm=30)
+    n_same = max(hold, 1)
+    a = oracle.Oracle(p, linear=1, damping=0.0, undamped_iters=hold)
+    b = oracle.Oracle(p, linear=1, damping=0.4, undamped_iters=hold)
+    a.iterate(n_same)
+    b.iterate(n_same)
+    for x, y in zip(a.means() + a.messages(), b.means() + b.messages()):
+        np.testing.assert_array_equal(x, y)
+    a.iterate(1)
+    b.iterate(1)
+    assert np.abs(a.means()[1] - b.means()[1]).max() > 1e-9
+    # Lambda is never damped: the precision messages still agree
+    np.testing.assert_array_equal(a.messages()[0], b.messages()[0])
+    np.testing.assert_array_equal(a.messages()[2], b.messages()[2])
+
+
+@pytest.mark.parametrize("interval,n_iters", [(10, 10), (10, 11), (10, 35), (7, 29), (7, 30), (1, 5)])
+def test_relinearisation_count_with_beta_zero(interval, n_iters):
+    """Sec. 5 / Sec. 8: with beta = 0 every factor relinearises as soon as the
+    interval allows -- at t = interval, 2 interval, ... (iterations numbered
+    from 0) -- so after N iterations the count is n_f * floor((N - 1) /
+    interval) and every factor's t_lin is the last such multiple."""
+    p = synth.make_circle(0, n_kf=5, n_lm=30)
+    o = oracle.Oracle(p, relin_beta=0.0, relin_interval=interval)
+    o.iterate(n_iters)
+    k = (n_iters - 1) // interval
+    assert o.relinearisations() == p.n_obs * k
+    np.testing.assert_array_equal(o.relin_iters(), np.full(p.n_obs, k * interval))
+
+
+def test_relinearisation_needs_movement_strictly_beyond_beta():
+    """Sec. 5: a factor relinearises when its variables moved further than
+    beta.  Measurements equal to the projections at the initial estimate
+    leave every mean exactly at its chart origin, so even beta = 0 never
+    triggers a relinearisation."""
+    p = synth.make_circle(0, n_kf=5, n_lm=30)
+    R, C, _ = _refs(p)
+    q = copy.deepcopy(p)
+    q.obs_uv = np.array([oracle.project(_cam(p), R[k].ravel(), C[k], p.lm_init[m], np.zeros(6), np.zeros(3))[0]
+                         for k, m in zip(p.obs_kf, p.obs_lm)])
+    o = oracle.Oracle(q, relin_beta=0.0)
+    o.iterate(35)
+    kf, lm = o.means()
+    assert np.abs(kf).max() == 0.0 and np.abs(lm).max() == 0.0
+    assert o.relinearisations() == 0
+    np.testing.assert_array_equal(o.relin_iters(), 0)
+
+
+def test_tree_covariances_exact_while_damped_means_are_not():
+    """Sec. 5: damping acts on eta only, so on a tree the precisions still
+    become exact after a diameter's worth of iterations (Sec. 3.2) while the
+    damped means are still on their way."""
+    p = synth.make_chain(4)
+    kw = dict(linear=1, prior_anneal_iters=0, prior_final_scale=0.01, undamped_iters=1)
+    o = oracle.Oracle(p, damping=0.4, **kw)
+    o.iterate(8)
+    H, b = _dense_system(p, o, 0.01)
+    x = np.linalg.solve(H, b)
+    Sigma = np.linalg.inv(H)
+    nk = p.n_kf
+    kl, _, ll, _ = o.beliefs()
+    for v in range(nk):
+        np.testing.assert_allclose(np.linalg.inv(kl[v]), Sigma[6 * v:6 * v + 6, 6 * v:6 * v + 6], rtol=1e-7,
+                                   atol=1e-9 * np.abs(Sigma).max())
+    for v in range(p.n_lm):
+        i = 6 * nk + 3 * v
+        np.testing.assert_allclose(np.linalg.inv(ll[v]), Sigma[i:i + 3, i:i + 3], rtol=1e-7,
+                                   atol=1e-9 * np.abs(Sigma).max())
+    kf, lm = o.means()
+    err = np.abs(np.concatenate([kf.ravel(), lm.ravel()]) - x).max()
+    assert err > 1e-6 * np.abs(x).max()
+    # and undamped the means are exact by then too
+    u = oracle.Oracle(p, damping=0.0, **kw)
+    u.iterate(8)
+    kf, lm = u.means()
+    np.testing.assert_allclose(np.concatenate([kf.ravel(), lm.ravel()]), x, rtol=1e-9, atol=1e-12)
+
+
+def test_message_with_indefinite_incoming_precision_is_held():
+    """The Schur complement of Sec. 5 needs a positive definite incoming
+    precision.  A hand-built state where one factor's incoming precision
+    from its landmark is indefinite keeps that message at its previous
+    value, counts it, and sends every other message normally."""
+    p = synth.make_circle(0, n_kf=5, n_lm=30)
+    o = oracle.Oracle(p, linear=1)
+    o.iterate(3)
+    mk, ek, ml, el = (a.copy() for a in o.messages())
+    counts = np.bincount(p.obs_lm, minlength=p.n_lm)
+    m = int(np.argmax(counts >= 2))
+    f, g = np.flatnonzero(p.obs_lm == m)[:2]
+    kl, _, ll, _ = o.beliefs()
+    others = ll[m] - ml[f] - ml[g]                  # prior(t) + the remaining messages
+    big = 1e3 * np.trace(ll[m])
+    ml[f] = ml[f] + big * np.eye(3)                 # keeps the belief positive definite
+    ml[g] = -others - 1e-3 * big * np.eye(3)        # f's incoming precision: others + ml[g] < 0
+    o.set_messages(mk, ek, ml, el)
+    inc = o.beliefs()[2][m] - ml[f]
+    assert np.linalg.eigvalsh(inc)[0] < 0
+    held0 = o.held_messages()
+    o.iterate(1)
+    assert o.held_messages() - held0 == 1
+    mk1, ek1, ml1, el1 = o.messages()
+    np.testing.assert_array_equal(mk1[f], mk[f])    # kept, not zeroed or recomputed
+    np.testing.assert_array_equal(ek1[f], ek[f])
+    changed = [h for h in range(p.n_obs) if h != f and not np.array_equal(mk1[h], mk[h])]
+    assert len(changed) == p.n_obs - 1
+
+
 # ------------------------------------------------------- incremental (Sec. 9.2)
 
 def test_added_keyframe_and_points_start_where_the_paper_puts_them():
