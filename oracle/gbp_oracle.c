@@ -595,7 +595,10 @@ static void factor_features(orc_graph* g, int f, const int* deg_k, const int* de
     x[4] = ck;
     x[5] = h[0];
     x[6] = h[1];
-    x[7] = step_cosine(g->nk_eta + 6 * f, g->mk_eta + 6 * f, g->pk_eta + 6 * f, 6);
+    /* the keyframe-side step cosine compares the steps of the last two
+     * iterations only when the three messages share one linearisation
+     * (none in this iteration or the previous one); 0 otherwise */
+    x[7] = dt_lin >= 2 ? step_cosine(g->nk_eta + 6 * f, g->mk_eta + 6 * f, g->pk_eta + 6 * f, 6) : 0.0;
     x[8] = cm;
     x[9] = h[2];
     x[10] = h[3];
@@ -638,7 +641,6 @@ void orc_set_reference_messages(orc_graph* g, const double* eta_ref)
 static int iterate_impl(orc_graph* g, int n, double* max_dmu, int mode, double* X, double* T)
 {
     double J[18], r[2], k;
-    double lam_in[36], eta_in[6];
     int *deg_k = NULL, *deg_l = NULL;
     if (mode != 0) {
         deg_k = zalloc(sizeof(int) * (size_t)g->n_kf);
@@ -650,7 +652,22 @@ static int iterate_impl(orc_graph* g, int n, double* max_dmu, int mode, double* 
         for (int f = 0; f < g->n_f; ++f) {
             int kk = g->fk[f], m = g->fm[f];
             double* x0 = g->x0 + 9 * f;
-            if (!g->prm.linear && g->t - g->tlin[f] >= g->prm.relin_interval) {
+            /* the variable-to-factor messages: each variable's belief divided
+             * by this factor's previous message to it (Sec. 5); they do not
+             * depend on this iteration's linearisation */
+            double lam_inl[9], eta_inl[3], lam_ink[36], eta_ink[6], Ltmp[36];
+            for (int i = 0; i < 9; ++i) lam_inl[i] = g->lm_lam[9 * m + i] - g->ml_lam[9 * f + i];
+            for (int i = 0; i < 3; ++i) eta_inl[i] = g->lm_eta[3 * m + i] - g->ml_eta[3 * f + i];
+            for (int i = 0; i < 36; ++i) lam_ink[i] = g->kf_lam[36 * kk + i] - g->mk_lam[36 * f + i];
+            for (int i = 0; i < 6; ++i) eta_ink[i] = g->kf_eta[6 * kk + i] - g->mk_eta[6 * f + i];
+            /* a message whose incoming precision is not positive definite
+             * cannot be formed and keeps its previous value; a factor with
+             * such a message keeps its linearisation point for the iteration
+             * (a relinearisation that is due waits), so that a kept message
+             * and its factor's linearisation stay the same */
+            const int ok_l = cholesky(3, lam_inl, Ltmp) == 0;
+            const int ok_k = cholesky(6, lam_ink, Ltmp) == 0;
+            if (!g->prm.linear && ok_l && ok_k && g->t - g->tlin[f] >= g->prm.relin_interval) {
                 /* Sec. 5 / Sec. 8: relinearise when the adjacent beliefs moved
                  * more than beta from the factor's linearisation point, at
                  * most once every relin_interval iterations */
@@ -671,21 +688,14 @@ static int iterate_impl(orc_graph* g, int n, double* max_dmu, int mode, double* 
             }
             const double* A = g->linA + 81 * f;
             const double* c = g->linc + 9 * f;
-            /* to the keyframe: the landmark's belief divided by this factor's
-             * previous message to it is the variable-to-factor message */
-            for (int i = 0; i < 9; ++i) lam_in[i] = g->lm_lam[9 * m + i] - g->ml_lam[9 * f + i];
-            for (int i = 0; i < 3; ++i) eta_in[i] = g->lm_eta[3 * m + i] - g->ml_eta[3 * f + i];
-            /* a message whose incoming precision is not positive definite
-             * cannot be formed; it keeps its previous value */
-            if (orc_factor_message(A, c, 0, lam_in, eta_in, g->nk_lam + 36 * f, g->nk_eta + 6 * f) != 0) {
+            /* to the keyframe, marginalising the landmark */
+            if (!ok_l || orc_factor_message(A, c, 0, lam_inl, eta_inl, g->nk_lam + 36 * f, g->nk_eta + 6 * f) != 0) {
                 memcpy(g->nk_lam + 36 * f, g->mk_lam + 36 * f, sizeof(double) * 36);
                 memcpy(g->nk_eta + 6 * f, g->mk_eta + 6 * f, sizeof(double) * 6);
                 g->n_held += 1;
             }
-            /* to the landmark */
-            for (int i = 0; i < 36; ++i) lam_in[i] = g->kf_lam[36 * kk + i] - g->mk_lam[36 * f + i];
-            for (int i = 0; i < 6; ++i) eta_in[i] = g->kf_eta[6 * kk + i] - g->mk_eta[6 * f + i];
-            if (orc_factor_message(A, c, 1, lam_in, eta_in, g->nl_lam + 9 * f, g->nl_eta + 3 * f) != 0) {
+            /* to the landmark, marginalising the keyframe */
+            if (!ok_k || orc_factor_message(A, c, 1, lam_ink, eta_ink, g->nl_lam + 9 * f, g->nl_eta + 3 * f) != 0) {
                 memcpy(g->nl_lam + 9 * f, g->ml_lam + 9 * f, sizeof(double) * 9);
                 memcpy(g->nl_eta + 3 * f, g->ml_eta + 3 * f, sizeof(double) * 3);
                 g->n_held += 1;

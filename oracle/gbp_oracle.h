@@ -71,9 +71,10 @@ int orc_add_keyframe(orc_graph* g, const double* kf_Rt_init, int n_new_lm, const
 int orc_sizes(const orc_graph* g, int* n_kf, int* n_lm, int* n_obs);
 
 /* Run n synchronous iterations.  Returns 0, or -1 if a belief stopped being
- * positive definite (a message whose incoming precision is not positive
- * definite keeps its previous value instead).  *max_dmu (nullable) = max_v |mu_v^{t+1} - mu_v^t|_inf of
- * the last iteration. */
+ * positive definite.  A message whose incoming precision is not positive
+ * definite keeps its previous value instead, and its factor does not
+ * relinearise in that iteration.  *max_dmu (nullable) = max_v |mu_v^{t+1} -
+ * mu_v^t|_inf of the last iteration. */
 int orc_iterate(orc_graph* g, int n, double* max_dmu);
 int orc_iterations_done(const orc_graph* g);
 
@@ -131,7 +132,8 @@ long orc_held_messages(const orc_graph* g);
  *   3  the same for the landmark
  *   4  |eta_new - eta_old| / (|eta_new| + |eta_old|) of the message to the
  *      keyframe; 5, 6 its values at t-1 and t-2
- *   7  cosine between eta_new - eta_old and eta_old - eta_prev (keyframe side)
+ *   7  cosine between eta_new - eta_old and eta_old - eta_prev (keyframe side);
+ *      0 unless t - t_lin >= 2 (the three messages share one linearisation)
  *   8-11 the same four for the message to the landmark (its eta_prev is
  *      remembered only while features are computed: learned or record runs)
  *   12 log(1 + deg k) / 5;  13 log(1 + deg m) / 3

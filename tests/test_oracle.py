@@ -537,6 +537,31 @@ def test_message_with_indefinite_incoming_precision_is_held():
     assert len(changed) == p.n_obs - 1
 
 
+def test_held_message_defers_its_factors_relinearisation():
+    """A kept message is only meaningful with the linearisation it was formed
+    at, so a factor holding a message does not relinearise in that
+    iteration even when the schedule is due (beta = 0, t = interval): every
+    other factor relinearises, the held one keeps t_lin = 0 and does so in
+    the next iteration."""
+    p = synth.make_circle(0, n_kf=5, n_lm=30)
+    o = oracle.Oracle(p, relin_beta=0.0, relin_interval=10)
+    o.iterate(10)
+    mk, ek, ml, el = (a.copy() for a in o.messages())
+    m = int(np.argmax(np.bincount(p.obs_lm, minlength=p.n_lm) >= 2))
+    f, g = np.flatnonzero(p.obs_lm == m)[:2]
+    ll = o.beliefs()[2]
+    others = ll[m] - ml[f] - ml[g]
+    big = 1e3 * np.trace(ll[m])
+    ml[f] = ml[f] + big * np.eye(3)
+    ml[g] = -others - 1e-3 * big * np.eye(3)
+    o.set_messages(mk, ek, ml, el)
+    o.iterate(1)
+    tl = o.relin_iters()
+    assert o.held_messages() == 1
+    assert tl[f] == 0 and (np.delete(tl, f) == 10).all()
+    assert o.relinearisations() == p.n_obs - 1
+
+
 # ------------------------------------------------------- incremental (Sec. 9.2)
 
 def test_added_keyframe_and_points_start_where_the_paper_puts_them():

@@ -157,7 +157,10 @@ def test_features_and_targets_from_public_pieces():
         want[:, 1] = k
         want[:, 2] = tr_lk / (tr_lk + tr_pk + 1e-30)
         want[:, 3] = tr_ll / (tr_ll + tr_pl + 1e-30)
-        want[:, 4], want[:, 5:7], want[:, 7] = ck, hist[:, 0:2], cos(nk - ek0, ek0 - ek_prev)
+        # keyframe-side step cosine: only once the three messages share one
+        # linearisation (t - t_lin >= 2; linear mode: t_lin = 0)
+        want[:, 4], want[:, 5:7] = ck, hist[:, 0:2]
+        want[:, 7] = cos(nk - ek0, ek0 - ek_prev) if t >= 2 else 0.0
         want[:, 8], want[:, 9:11], want[:, 11] = cm, hist[:, 2:4], cos(nl - el0, el0 - el_prev)
         want[:, 12] = np.log1p(deg_k) / 5.0
         want[:, 13] = np.log1p(deg_l) / 3.0
