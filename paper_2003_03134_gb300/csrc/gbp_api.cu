@@ -58,7 +58,11 @@ struct DevState {
     int32_t* tlin = nullptr;
     R* mk = nullptr;
     R* mk2 = nullptr;
+    R* kj = nullptr;
+    R* kjs = nullptr;
+    R* lin = nullptr;
     R* ml = nullptr;
+    R* mlx = nullptr;
     R* kf_bel = nullptr;
     R* lm_bel = nullptr;
     R* prior_s = nullptr;      // prior scale table, prior_anneal_iters + 1 entries
@@ -67,7 +71,7 @@ struct DevState {
 
     void release() {
         void* ptrs[] = {z, fk, fm, kf_R, kf_c, lm_ref, kf_off, kf_list, kpos, lm_off, tile_start, big_lm, orphan, kf_birth, lm_birth, kf_D, kf_A, lm_D,
-                        uv_ref, x0, tlin, mk, mk2, ml, kf_bel, lm_bel, prior_s, hist, eta_inf};
+                        uv_ref, x0, tlin, mk, mk2, kj, kjs, lin, ml, mlx, kf_bel, lm_bel, prior_s, hist, eta_inf};
         for (void* p : ptrs)
             if (p) cudaFree(p);
         *this = DevState<R>();
@@ -92,6 +96,20 @@ void so3_exp_host(const double w[3], double E[9]) {
                     w[2] * w[0], w[2] * w[1], w[2] * w[2] - th2};
     for (int i = 0; i < 9; ++i) E[i] = a * W[i] + b * W2[i];
     E[0] += 1.0; E[4] += 1.0; E[8] += 1.0;
+}
+
+// The keyframe belief record of a prior-only belief (diagonal p): its
+// Cholesky factor (1/sqrt(p_i) on the diagonal), mean 0, trace, Lambda.
+template <typename R>
+void kf_prior_record_host(const R* p, R* out) {
+    std::fill(out, out + KBEL, R(0));
+    R tr = R(0);
+    for (int i = 0; i < 6; ++i) {
+        out[KB_L + i * (i + 1) / 2 + i] = R(1.0 / std::sqrt(double(p[i])));
+        out[KB_LAM + i * (i + 1) / 2 + i] = p[i];
+        tr += p[i];
+    }
+    out[KB_TR] = tr;
 }
 
 }  // namespace
@@ -172,6 +190,10 @@ KParams<R> make_kparams(gbp_graph* g) {
     k.relin_beta = R(p.relin_beta);
     k.anchor_scale = R(p.anchor_scale);
     k.pivot_ratio = R(p.fp64_pivot_ratio);
+    // a keyframe cavity keeping less than 1/1000 of its belief's precision
+    // volume amplifies FP32 rounding by up to 1000x: formed again in FP64
+    // (every one of them with fp64_pivot_ratio >= 1)
+    k.cav_ratio = R(std::max(1e-3, double(p.fp64_pivot_ratio)));
     k.prior_s = state<R>(g).prior_s;
     k.prior_T = std::max(p.prior_anneal_iters, 0);
     k.relin_interval = p.relin_interval;
@@ -306,7 +328,11 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
     CK(dev_alloc(&s.tlin, nf));
     CK(dev_alloc(&s.mk, (size_t)KREC * nf));
     CK(dev_alloc(&s.mk2, (size_t)KREC * nf));
-    CK(dev_alloc(&s.ml, 9 * (size_t)nf));
+    CK(dev_alloc(&s.kj, (size_t)KJ * nf));
+    CK(dev_alloc(&s.kjs, (size_t)KJ * nf));
+    CK(dev_alloc(&s.lin, (size_t)NLIN * nf));
+    CK(dev_alloc(&s.ml, (size_t)NML * nf));
+    CK(dev_alloc(&s.mlx, 9 * (size_t)nf));
     CK(dev_alloc(&s.kf_bel, (size_t)KBEL * nk));
     CK(dev_alloc(&s.lm_bel, (size_t)LBEL * nl));
     CK(dev_alloc(&s.hist, HIST * (size_t)std::max(nf, 1)));
@@ -375,8 +401,12 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
     d.mk = s.mk;
     d.mk2 = s.mk2;
     d.mk_redirect = nullptr;
+    d.kj = s.kj;
+    d.kjs = s.kjs;
+    d.lin = s.lin;
     d.ml = s.ml;
     d.ml_out = s.ml;
+    d.mlx = s.mlx;
     d.kf_bel = s.kf_bel;
     d.lm_bel = s.lm_bel;
     d.kf_bel_out = s.kf_bel;
@@ -425,7 +455,11 @@ gbp_status reset_state(gbp_graph* g) {
     CK(cudaMemsetAsync(s.tlin, 0, sizeof(int32_t) * nf, st));
     CK(cudaMemsetAsync(s.mk, 0, sizeof(R) * KREC * nf, st));
     CK(cudaMemsetAsync(s.mk2, 0, sizeof(R) * KREC * nf, st));
-    CK(cudaMemsetAsync(s.ml, 0, sizeof(R) * 9 * nf, st));
+    CK(cudaMemsetAsync(s.kj, 0, sizeof(R) * KJ * nf, st));
+    CK(cudaMemsetAsync(s.kjs, 0, sizeof(R) * KJ * nf, st));
+    CK(cudaMemsetAsync(s.lin, 0, sizeof(R) * NLIN * nf, st));
+    CK(cudaMemsetAsync(s.ml, 0, sizeof(R) * NML * nf, st));
+    CK(cudaMemsetAsync(s.mlx, 0, sizeof(R) * 9 * nf, st));
     CK(cudaMemsetAsync(s.kf_bel, 0, sizeof(R) * KBEL * g->n_kf, st));
     CK(cudaMemsetAsync(s.lm_bel, 0, sizeof(R) * LBEL * g->n_lm, st));
     CK(cudaMemsetAsync(s.hist, 0, sizeof(float) * HIST * nf, st));
@@ -700,8 +734,8 @@ std::vector<std::pair<void*, size_t>> state_buffers(gbp_graph* g) {
     DevState<R>& s = state<R>(g);
     const size_t nf = g->n_f, nk = g->n_kf, nl = g->n_lm;
     return {{s.x0, sizeof(R) * 9 * nf},        {s.tlin, sizeof(int32_t) * nf},   {s.mk, sizeof(R) * KREC * nf},
-            {s.mk2, sizeof(R) * KREC * nf},
-            {s.ml, sizeof(R) * 9 * nf},        {s.kf_bel, sizeof(R) * KBEL * nk}, {s.lm_bel, sizeof(R) * LBEL * nl},
+            {s.mk2, sizeof(R) * KREC * nf},    {s.kj, sizeof(R) * KJ * nf},      {s.lin, sizeof(R) * NLIN * nf},
+            {s.ml, sizeof(R) * NML * nf},      {s.kf_bel, sizeof(R) * KBEL * nk}, {s.lm_bel, sizeof(R) * LBEL * nl},
             {s.hist, sizeof(float) * HIST * nf}, {g->ctl, sizeof(int32_t) * CTL_N}};
 }
 
@@ -727,7 +761,9 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
     const int K0 = g->n_kf, L0 = g->n_lm, F0 = g->n_f;
     const int K1 = K0 + 1, L1 = L0 + n_new_lm, F1 = F0 + n_obs;
     std::vector<int32_t> ctl(CTL_N), tlin(F0);
-    std::vector<R> x0(9 * (size_t)F0), mk((size_t)KREC * F0), mkp((size_t)KREC * F0), ml(9 * (size_t)F0), kb((size_t)KBEL * K0),
+    std::vector<R> x0(9 * (size_t)F0), mk((size_t)KREC * F0), mkp((size_t)KREC * F0), kj((size_t)KJ * F0),
+        lin((size_t)NLIN * F0),
+        ml((size_t)NML * F0), kb((size_t)KBEL * K0),
         lb((size_t)LBEL * L0), kD(6 * (size_t)K0), kA(6 * (size_t)K0), lD(3 * (size_t)L0);
     std::vector<float> hist(HIST * (size_t)F0);
     {
@@ -740,6 +776,8 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
         CK(cudaMemcpyAsync(tlin.data(), s.tlin, sizeof(int32_t) * tlin.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(mk.data(), mk_cur, sizeof(R) * mk.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(mkp.data(), mk_prev, sizeof(R) * mkp.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(kj.data(), s.kj, sizeof(R) * kj.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(lin.data(), s.lin, sizeof(R) * lin.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(ml.data(), s.ml, sizeof(R) * ml.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(hist.data(), s.hist, sizeof(float) * hist.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(kb.data(), s.kf_bel, sizeof(R) * kb.size(), cudaMemcpyDeviceToHost, st));
@@ -757,7 +795,7 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
     if (kf_Rt_init) {
         std::copy(kf_Rt_init, kf_Rt_init + 12, Rt);
     } else {
-        const R* mu = &kb[(size_t)KBEL * (K0 - 1) + 27];
+        const R* mu = &kb[(size_t)KBEL * (K0 - 1) + KB_MU];
         double w[3] = {double(mu[3]), double(mu[4]), double(mu[5])}, E[9];
         so3_exp_host(w, E);
         const double* Rr = &g->kf_R[9 * (size_t)(K0 - 1)];
@@ -822,8 +860,8 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
 
     // linearisation points in the new order: old factors keep theirs, new
     // ones take the current means (a new variable's mean is 0 in its chart)
-    std::vector<R> x0n(9 * (size_t)F1), mln(9 * (size_t)F1, R(0)), mkn((size_t)KREC * F1, R(0)),
-        mkpn((size_t)KREC * F1, R(0));
+    std::vector<R> x0n(9 * (size_t)F1), mln((size_t)NML * F1, R(0)), mkn((size_t)KREC * F1, R(0)),
+        mkpn((size_t)KREC * F1, R(0)), kjn((size_t)KJ * F1, R(0)), linn((size_t)NLIN * F1, R(0));
     std::vector<float> histn(HIST * (size_t)F1, 0.0f);
     std::vector<int32_t> tlinn(F1);
     std::vector<int32_t> kpos = keyframe_slots(g->fk, K1);
@@ -831,10 +869,10 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
         const int ci = g->obs_index[f];
         const int of = ci < F0 ? where[ci] : -1;
         if (of >= 0) {
-            for (int i = 0; i < 9; ++i) {
-                x0n[(size_t)i * F1 + f] = x0[(size_t)i * F0 + of];
-                mln[(size_t)i * F1 + f] = ml[(size_t)i * F0 + of];
-            }
+            for (int i = 0; i < 9; ++i) x0n[(size_t)i * F1 + f] = x0[(size_t)i * F0 + of];
+            for (int i = 0; i < NML; ++i) mln[(size_t)i * F1 + f] = ml[(size_t)i * F0 + of];
+            for (int i = 0; i < NLIN; ++i) linn[(size_t)i * F1 + f] = lin[(size_t)i * F0 + of];
+            std::copy(&kj[(size_t)KJ * old_kpos[of]], &kj[(size_t)KJ * old_kpos[of]] + KJ, &kjn[(size_t)KJ * kpos[f]]);
             tlinn[f] = tlin[of];
             for (int j = 0; j < HIST; ++j) histn[(size_t)j * F1 + f] = hist[(size_t)j * F0 + of];
             std::copy(&mk[(size_t)KREC * old_kpos[of]], &mk[(size_t)KREC * old_kpos[of]] + KREC,
@@ -867,7 +905,11 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
     std::vector<R> kbn((size_t)KBEL * K1, R(0)), lbn((size_t)LBEL * L1, R(0));
     std::copy(kb.begin(), kb.end(), kbn.begin());
     std::copy(lb.begin(), lb.end(), lbn.begin());
-    for (int i = 0; i < 6; ++i) kbn[(size_t)KBEL * K0 + i * (i + 1) / 2 + i] = s0 * kDn[6 * (size_t)K0 + i] * isig2;
+    {
+        R pd[6];
+        for (int i = 0; i < 6; ++i) pd[i] = s0 * kDn[6 * (size_t)K0 + i] * isig2;
+        kf_prior_record_host<R>(pd, &kbn[(size_t)KBEL * K0]);
+    }
     for (int j = L0; j < L1; ++j)
         for (int i = 0; i < 3; ++i) lbn[(size_t)LBEL * j + i * (i + 1) / 2 + i] = s0 * lDn[3 * (size_t)j + i] * isig2;
     R* mk_cur = (t & 1) ? s.mk2 : s.mk;
@@ -880,6 +922,10 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
     CK(cudaMemcpyAsync(s.hist, histn.data(), sizeof(float) * histn.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(mk_cur, mkn.data(), sizeof(R) * mkn.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(mk_other, mkpn.data(), sizeof(R) * mkpn.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.kj, kjn.data(), sizeof(R) * kjn.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.lin, linn.data(), sizeof(R) * linn.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(s.kjs, 0, sizeof(R) * KJ * (size_t)F1, st));
+    CK(cudaMemsetAsync(s.mlx, 0, sizeof(R) * 9 * (size_t)F1, st));
     CK(cudaMemcpyAsync(s.kf_bel, kbn.data(), sizeof(R) * kbn.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.lm_bel, lbn.data(), sizeof(R) * lbn.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(g->ctl, ctl.data(), sizeof(int32_t) * CTL_N, cudaMemcpyHostToDevice, st));
@@ -1203,7 +1249,7 @@ gbp_status gbp_get_means(const gbp_graph* cg, double* kf_mu, double* lm_mu) {
     gbp_status st = download_beliefs(g, kb, lb);
     if (st != GBP_OK) return st;
     for (int v = 0; v < g->n_kf; ++v)
-        for (int i = 0; i < 6; ++i) kf_mu[6 * v + i] = kb[(size_t)KBEL * v + 27 + i];
+        for (int i = 0; i < 6; ++i) kf_mu[6 * v + i] = kb[(size_t)KBEL * v + KB_MU + i];
     for (int v = 0; v < g->n_lm; ++v)
         for (int i = 0; i < 3; ++i) lm_mu[3 * v + i] = lb[(size_t)LBEL * v + 9 + i];
     return read_ctl(g);
@@ -1216,7 +1262,7 @@ gbp_status gbp_get_beliefs(const gbp_graph* cg, double* kf_Rt, double* lm_xyz, d
     gbp_status st = download_beliefs(g, kb, lb);
     if (st != GBP_OK) return st;
     for (int v = 0; v < g->n_kf; ++v) {
-        const double* mu = &kb[(size_t)KBEL * v + 27];
+        const double* mu = &kb[(size_t)KBEL * v + KB_MU];
         double E[9], R[9], c[3];
         so3_exp_host(mu + 3, E);
         const double* Rr = &g->kf_R[9 * (size_t)v];
@@ -1227,7 +1273,7 @@ gbp_status gbp_get_beliefs(const gbp_graph* cg, double* kf_Rt, double* lm_xyz, d
         double* o = kf_Rt + 12 * (size_t)v;
         for (int i = 0; i < 9; ++i) o[i] = R[i];
         for (int i = 0; i < 3; ++i) o[9 + i] = -(R[3 * i] * c[0] + R[3 * i + 1] * c[1] + R[3 * i + 2] * c[2]);
-        if (kf_cov && !packed_inverse(6, &kb[(size_t)KBEL * v], kf_cov + 36 * (size_t)v))
+        if (kf_cov && !packed_inverse(6, &kb[(size_t)KBEL * v + KB_LAM], kf_cov + 36 * (size_t)v))
             return fail(g, GBP_EDIVERGED, "keyframe belief not positive definite");
     }
     for (int v = 0; v < g->n_lm; ++v) {
@@ -1348,7 +1394,7 @@ gbp_status gbp_profile_iterations(gbp_graph* g, int32_t n_iters, double* ms_out)
     // (b) the factor kernel alone, replayed with its outputs in scratch
     const size_t rs = g->storage ? sizeof(double) : sizeof(float);
     void* scratch[3] = {nullptr, nullptr, nullptr};
-    const size_t sizes[3] = {rs * KREC * std::max(g->n_f, 1), rs * 9 * std::max(g->n_f, 1),
+    const size_t sizes[3] = {rs * KREC * std::max(g->n_f, 1), rs * NML * std::max(g->n_f, 1),
                              rs * LBEL * std::max(g->n_lm, 1)};
     cudaGraphExec_t ex = nullptr;
     float ms_fac = 0.f;

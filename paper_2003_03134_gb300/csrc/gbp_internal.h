@@ -1,20 +1,42 @@
 // gbp_internal.h -- device-side data layout shared by the kernels and the
 // host side of libgbp (not part of the public ABI).
 //
+// A reprojection factor's information is rank 2 (Sec. 4: Lambda_f = W J^T J,
+// eta_f = W J^T y), and so is each of its two messages: every message is
+// stored in the exact compact form Lambda = J_v^T M J_v, eta = J_v^T g with
+// M a symmetric 2 x 2 and g a 2-vector, J_v the factor's Jacobian block of
+// the receiving variable at the factor's current linearisation point.
+//
 // Layout in HBM (n_f factors sorted by landmark then keyframe):
-//   per factor, static:   z (2 Real), fk, fm (int32)
+//   per factor, static:   z (2 Real), fk, fm, kpos (int32)
 //   per factor, dynamic:  x0  -- linearisation point [dc dw | dl], 9 Real, SoA (9 x n_f)
 //                         tlin -- iteration of the last (re)linearisation, int32
-//                         mk  -- message to the keyframe, AoS record of KREC Real:
-//                                Lambda packed lower 6x6 (21), eta (6), pad;
-//                                stored in keyframe CSR order (slot kpos[f]) so
-//                                that a keyframe's messages are contiguous; two
-//                                buffers, alternating by iteration parity
-//                         ml  -- message to the landmark, SoA (9 x n_f):
-//                                Lambda packed lower 3x3 (6), eta (3)
+//                         lin -- that linearisation: y = J x0 + r (2), Huber-
+//                                weighted W (Sec. 6), |r|^2; SoA (NLIN x n_f)
+//                         ml  -- message to the landmark, compact, SoA (NML x n_f):
+//                                M00 M01 M11 g0 g1
+//                         mlx -- the same expanded (Lambda 6, eta 3), SoA 9 x n_f,
+//                                written only for factors of landmarks split
+//                                across tiles (read by the belief phase)
+//   per factor, in keyframe CSR order (slot kpos[f], so that a keyframe's
+//   records are contiguous):
+//                         mk  -- message to the keyframe, compact record of KREC
+//                                Real: M00 M01 M11 g0 g1, t_lin of the
+//                                linearisation it was formed at (int bits),
+//                                pad; two buffers, alternating by iteration
+//                                parity
+//                         kj  -- the keyframe Jacobian block (2 x 6) of the
+//                                factor's current linearisation, which both
+//                                of its messages are expressed in
+//                         kjs -- staging: the new block of factors
+//                                (re)linearised in this iteration (the
+//                                belief phase moves it into kj)
 //   per keyframe:         Rref (9 double), cref (3 double), prior diagonal D (6),
 //                         anchor diagonal (6), belief record KBEL Real:
-//                                Lambda (21), eta (6), mu (6), pad
+//                                Cholesky factor of Lambda (packed lower, 1/L_ii
+//                                on the diagonal) 21, mu 6, tr Lambda 1 -- the
+//                                part the factor phase reads -- then
+//                                Lambda 21, eta 6, pad
 //   per landmark:         lref (3 double), prior diagonal (3), belief record
 //                         LBEL Real: Lambda (6), eta (3), mu (3)
 //   per factor, learned damping: hist -- relative message changes of the
@@ -32,8 +54,19 @@ struct gbp_mlp;
 
 namespace gbp {
 
-constexpr int KREC = 28;   // keyframe message record (Real elements)
-constexpr int KBEL = 36;   // keyframe belief record
+constexpr int KREC = 8;    // compact keyframe message record (Real elements)
+constexpr int KREC_TL = 5; // its slot holding t_lin of the record's linearisation (int bits)
+constexpr int KJ = 12;     // keyframe Jacobian block record: row 0 (6), row 1 (6)
+constexpr int NML = 5;     // compact landmark message (SoA rows)
+constexpr int NLIN = 4;    // per-factor linearisation record (SoA rows): y0, y1, W, |r|^2
+// keyframe belief record
+constexpr int KB_L = 0;    // Cholesky factor of Lambda, packed lower, 1/L_ii on the diagonal (21)
+constexpr int KB_MU = 21;  // mean (6)
+constexpr int KB_TR = 27;  // trace of Lambda
+constexpr int KB_A = 28;   // the factor phase reads [0, KB_A)
+constexpr int KB_LAM = 28; // Lambda, packed lower (21)
+constexpr int KB_ETA = 49; // eta (6)
+constexpr int KBEL = 56;
 constexpr int LBEL = 12;   // landmark belief record
 
 // Solver parameters as the kernels see them, in the kernel's own precision
@@ -49,6 +82,8 @@ struct KParams {
     R relin_beta;
     R anchor_scale;
     R pivot_ratio;
+    R cav_ratio;              // FP32 path: a keyframe cavity keeping less than this share of its belief's
+                              // precision volume (det(I - M G)) is formed again in FP64
     const R* prior_s;         // device table: prior scale at iteration t is prior_s[min(t, prior_T)]
     int32_t prior_T;
     int32_t relin_interval;
@@ -97,11 +132,15 @@ struct DevGraph {
     // dynamic
     R* x0;                    // 9 x n_f
     int32_t* tlin;            // n_f
-    R* mk;                    // n_f x KREC, messages of even iterations
+    R* mk;                    // n_f x KREC, messages of even iterations (slot order)
     R* mk2;                   // n_f x KREC, messages of odd iterations
     R* mk_redirect;           // if set, receives the keyframe-message writes (kernel timing)
-    R* ml;                    // 9 x n_f      (read by the factor kernel)
+    R* kj;                    // n_f x KJ, Jacobian blocks of the current keyframe messages (slot order)
+    R* lin;                   // NLIN x n_f: y0, y1, W, |r|^2 of each factor's current linearisation
+    R* kjs;                   // n_f x KJ, staging for factors (re)linearised in this iteration
+    R* ml;                    // NML x n_f    (read by the factor kernel)
     R* ml_out;                // where the factor kernel writes m^{t+1} (normally == ml)
+    R* mlx;                   // 9 x n_f expanded landmark messages of split landmarks' factors
     R* kf_bel;                // n_kf x KBEL  (read as b^t)
     R* lm_bel;                // n_lm x LBEL  (read as b^t)
     R* kf_bel_out;            // where b^{t+1} is written (normally == kf_bel)

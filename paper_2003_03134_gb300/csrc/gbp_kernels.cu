@@ -5,15 +5,18 @@
 // mode).
 //
 // Iteration t (Sec. 5, synchronous schedule):
-//   factor kernel  -- one thread per factor: decide relinearisation (Sec. 5,
-//                     Sec. 8), rebuild J and the residual at the factor's
-//                     linearisation point, Huber weight (Sec. 6), both
-//                     factor-to-variable messages (eqs. messageeta,
-//                     messagelambda), damping of eta (Sec. 5, Sec. 8).
-//   belief kernel  -- one block per keyframe (fixed-order tree reduction
-//                     over its CSR list), one thread per landmark (its
-//                     contiguous factor range): prior(t+1) + sum of messages
-//                     (eqs. beliefeta, belieflambda), Cholesky mean.
+//   factor kernel  -- a warp per tile of whole landmarks, a lane per factor:
+//                     both incoming messages, the relinearisation test
+//                     (Sec. 5, Sec. 8), the Jacobian and residual at the
+//                     factor's linearisation point, the Huber weight
+//                     (Sec. 6), both factor-to-variable messages (eqs.
+//                     messageeta, messagelambda), damping of eta (Sec. 5,
+//                     Sec. 8); the beliefs of the landmarks inside the tile.
+//   belief kernel  -- a block (small graphs) or a warp per keyframe: a
+//                     fixed-order reduction of its messages, expanded from
+//                     their compact form: prior(t+1) + sum of messages
+//                     (eqs. beliefeta, belieflambda), its Cholesky factor
+//                     and mean.
 // No atomics touch floating-point sums: every reduction has a fixed order,
 // so results are bitwise reproducible.
 //
@@ -22,11 +25,15 @@
 // (incoming precision P_b = Lambda_belief_b - Lambda_msg_b and vector
 // q_b = eta_belief_b - eta_msg_b) out of the product of the factor and the
 // incoming message gives, by the matrix inversion lemma, exactly
-//   Lambda_{f->a} = J_a^T (W N) J_a,   eta_{f->a} = J_a^T W N (y - s)
+//   Lambda_{f->a} = J_a^T M J_a,  eta_{f->a} = J_a^T g,  M = W N,  g = M (y - s)
 // with Q = J_b P_b^-1 J_b^T (2x2), s = J_b P_b^-1 q_b, N = (I + W Q)^-1.
 // This equals the printed Schur complement A_aa - A_ab (A_bb + P_b)^-1 A_ba
-// but never subtracts two large matrices, and Q = V^T V with
-// V = L_b^-1 J_b^T (Cholesky P_b = L_b L_b^T) is PSD by construction.
+// and never forms a 9x9 matrix.  Messages are stored as (M, g): 5 numbers
+// per side.  Damping eta (Sec. 5) damps g, since a factor's J changes only
+// when it relinearises, and messages are never damped then (Sec. 8).  The
+// keyframe's incoming precision B - J^T M J is never formed: with B's
+// Cholesky factor L (computed once per keyframe by the belief kernel) every
+// quantity reduces to 2x2 ones (KfSide), so no factor factorises a 6x6.
 #include "gbp_internal.h"
 #include "gbp_mlp.cuh"
 
@@ -298,129 +305,13 @@ __device__ __forceinline__ void linearise(const KParams<R>& P, const double* __r
 }
 
 // ------------------------------------------------------------------------
-// one factor-to-variable message.  Incoming precision Pb (packed nb x nb,
-// destroyed), incoming vector qb (nb), Jacobian rows of the marginalised
-// block Jb (2 x nb) and of the target block Ja (2 x na).  Output Lambda
-// (packed na x na) and eta (na).  Returns false when the Cholesky of Pb
-// failed; *ratio receives its pivot ratio.
-
-template <typename C, int na, int nb>
-__device__ __forceinline__ bool message(C* Pb, const C* qb, const C Jb[2][nb], const C Ja[2][na], const C y[2],
-                                        C W, C* lam, C* eta, C& ratio) {
-    C inv_d[nb];
-    bool ok = chol_packed<C, nb>(Pb, inv_d, ratio);
-    C V0[nb], V1[nb], u[nb];
-#pragma unroll
-    for (int i = 0; i < nb; ++i) { V0[i] = Jb[0][i]; V1[i] = Jb[1][i]; u[i] = qb[i]; }
-    fwd_solve<C, nb>(Pb, inv_d, V0);
-    fwd_solve<C, nb>(Pb, inv_d, V1);
-    fwd_solve<C, nb>(Pb, inv_d, u);
-    C Q00 = C(0), Q01 = C(0), Q11 = C(0), s0 = C(0), s1 = C(0);
-#pragma unroll
-    for (int i = 0; i < nb; ++i) {
-        Q00 += V0[i] * V0[i];
-        Q01 += V0[i] * V1[i];
-        Q11 += V1[i] * V1[i];
-        s0 += V0[i] * u[i];
-        s1 += V1[i] * u[i];
-    }
-    // N = (I + W Q)^-1
-    C a00 = C(1) + W * Q00, a01 = W * Q01, a11 = C(1) + W * Q11;
-    C idet = rcp(a00 * a11 - a01 * a01);
-    C N00 = a11 * idet, N01 = -a01 * idet, N11 = a00 * idet;
-    C M00 = W * N00, M01 = W * N01, M11 = W * N11;
-    C e0 = y[0] - s0, e1 = y[1] - s1;
-    C g0 = M00 * e0 + M01 * e1, g1 = M01 * e0 + M11 * e1;
-    C ua[na], va[na];
-#pragma unroll
-    for (int i = 0; i < na; ++i) {
-        ua[i] = M00 * Ja[0][i] + M01 * Ja[1][i];
-        va[i] = M01 * Ja[0][i] + M11 * Ja[1][i];
-        eta[i] = Ja[0][i] * g0 + Ja[1][i] * g1;
-    }
-#pragma unroll
-    for (int i = 0; i < na; ++i)
-#pragma unroll
-        for (int j = 0; j <= i; ++j) lam[pk(i, j)] = ua[i] * Ja[0][j] + va[i] * Ja[1][j];
-    return ok;
-}
-
-// The keyframe's incoming message for the FP64 fallback, summed from its
-// parts: the keyframe's prior at iteration t (as the belief b^t added it)
-// plus every OTHER factor's current message to it -- b^t - m^t without the
-// rounding of the FP32 belief, whose sum over ~100 messages can leave the
-// difference indefinite when this factor's message dominates a direction.
-// A keyframe's messages m^t sit contiguously in its CSR slots [i0, i1) of
-// the buffer this iteration only reads.
-template <typename R>
-struct KfCavity {
-    const R* msgs;          // m^t in keyframe CSR order
-    const int32_t* kf_off;  // CSR offsets
-    const R* D;             // the keyframe's prior diagonal (6) and anchor diagonal (6), sigma = 1
-    const R* A;
-    int k, self;
-    R s, anchor_scale, inv_sigma2;   // prior scale s(t), anchor factor, 1 / sigma^2
-};
-
-// FP64 redo of one message of factor f from FP32 state (the fallback for an
-// ill-conditioned FP32 factorisation).  It re-reads its inputs -- the
-// factor's linearisation point and the incoming message's parts, none of
-// which the calling thread has overwritten yet -- and writes the undamped
-// message to out (element i at out[i * out_stride]), so that the FP32 path
-// keeps all of its operands in registers.  Message to the keyframe: the
-// landmark's incoming message is b^t - m^t from bel_other and msg_other.
-// Message to the landmark: the keyframe's b^t - m^t first; if that is not
-// positive definite, summed exactly from its parts (KfCavity, a loop over
-// the keyframe's messages) and tried again.  All reads go through L2: in
-// the persistent kernel other SMs write these between iterations.
-template <typename R, bool to_landmark>
-__device__ __noinline__ bool message_fp64(const R* x0s, int n_f, int f, const double* __restrict__ Rref,
-                                          const double* __restrict__ cref, const double* __restrict__ lref,
-                                          const R* zf, const R* bel_other, const R* msg_other, int stride_other,
-                                          KfCavity<R> kc, R* out, int out_stride,
-                                          double fx, double fy, double cx, double cy, double inv_sigma2,
-                                          double inv_sigma, double huber_n, double z_min) {
-    KParams<double> P{};
-    P.fx = fx; P.fy = fy; P.cx = cx; P.cy = cy;
-    P.inv_sigma2 = inv_sigma2; P.inv_sigma = inv_sigma; P.huber_n = huber_n; P.z_min = z_min;
-    double x0[9];
-    for (int i = 0; i < 9; ++i) x0[i] = double(__ldcg(x0s + (size_t)i * n_f + f));
-    Lin<double> L;
-    linearise<double>(P, Rref, cref, lref, x0, double(__ldcg(zf)), double(__ldcg(zf + 1)), L);
-    constexpr int na = to_landmark ? 3 : 6, nb = to_landmark ? 6 : 3;
-    constexpr int pa = na * (na + 1) / 2, pb = nb * (nb + 1) / 2;
-    double Pb[pb], q[nb], lam[pa], eta[na], ratio;
-    // incoming = belief of the marginalised variable / previous message to it
-    for (int i = 0; i < pb; ++i)
-        Pb[i] = double(__ldcg(bel_other + i)) - double(__ldcg(msg_other + (size_t)i * stride_other));
-    for (int i = 0; i < nb; ++i)
-        q[i] = double(__ldcg(bel_other + pb + i)) - double(__ldcg(msg_other + (size_t)(pb + i) * stride_other));
-    bool ok;
-    if constexpr (to_landmark) {
-        ok = message<double, 3, 6>(Pb, q, L.Jk, L.Jl, L.y, L.W, lam, eta, ratio);
-        if (!ok) {
-            for (int i = 0; i < pb; ++i) Pb[i] = 0.0;
-            for (int i = 0; i < nb; ++i) {
-                // as b^t added it, in the kernel's precision
-                Pb[pk(i, i)] = double((kc.s * kc.D[i] + kc.anchor_scale * kc.A[i]) * kc.inv_sigma2);
-                q[i] = 0.0;   // the prior mean is the chart origin
-            }
-            const int i0 = kc.kf_off[kc.k], i1 = kc.kf_off[kc.k + 1];
-            for (int j = i0; j < i1; ++j) {
-                if (j == kc.self) continue;
-                const R* r = kc.msgs + (size_t)j * KREC;
-                for (int i = 0; i < pb; ++i) Pb[i] += double(__ldcg(r + i));
-                for (int i = 0; i < nb; ++i) q[i] += double(__ldcg(r + pb + i));
-            }
-            ok = message<double, 3, 6>(Pb, q, L.Jk, L.Jl, L.y, L.W, lam, eta, ratio);
-        }
-    } else {
-        ok = message<double, 6, 3>(Pb, q, L.Jl, L.Jk, L.y, L.W, lam, eta, ratio);
-    }
-    for (int i = 0; i < pa; ++i) out[(size_t)i * out_stride] = R(lam[i]);
-    for (int i = 0; i < na; ++i) out[(size_t)(pa + i) * out_stride] = R(eta[i]);
-    return ok;
-}
+// messages in compact form.  A factor's information is W J^T J with J the
+// 2 x 9 Jacobian, so each factor-to-variable message is J_a^T M J_a (M a
+// symmetric 2 x 2) with eta J_a^T g.  Marginalising block b with incoming
+// precision P_b and vector q_b (Sec. 5) gives, by the matrix inversion lemma,
+//   Q = J_b P_b^-1 J_b^T,  s = J_b P_b^-1 q_b,  N = (I + W Q)^-1,
+//   M = W N,  g = M (y - s).
+// This equals the printed Schur complement A_aa - A_ab (A_bb + P_b)^-1 A_ba.
 
 template <typename R> struct Vec4;
 template <> struct Vec4<float> { typedef float4 T; };
@@ -449,6 +340,414 @@ __device__ __forceinline__ void store_rec(R* dst, const R* src) {
         d[i] = v;
     }
 }
+
+// L2-coherent loads (bypass L1) for data that other SMs write during the
+// same launch (the persistent kernel runs many iterations in one launch).
+template <typename R, int N>
+__device__ __forceinline__ void load_rec_cg(const R* src, R* dst) {
+    if constexpr (sizeof(R) == 4) {
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i) {
+            float4 v = __ldcg(s4 + i);
+            dst[4 * i + 0] = v.x; dst[4 * i + 1] = v.y; dst[4 * i + 2] = v.z; dst[4 * i + 3] = v.w;
+        }
+    } else {
+        const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            double2 v = __ldcg(s2 + i);
+            dst[2 * i + 0] = v.x; dst[2 * i + 1] = v.y;
+        }
+    }
+}
+
+// An iteration index kept in a Real slot of a record, by its bits.
+template <typename R>
+__device__ __forceinline__ R int_bits(int v) {
+    if constexpr (sizeof(R) == 4) return __int_as_float(v);
+    else return __longlong_as_double((long long)v);
+}
+template <typename R>
+__device__ __forceinline__ int bits_int(R v) {
+    if constexpr (sizeof(R) == 4) return __float_as_int(v);
+    else return (int)__double_as_longlong(v);
+}
+
+// Lambda = J^T M J (packed n x n) and eta = J^T g of a compact message.
+template <typename R, int n>
+__device__ __forceinline__ void expand_msg(const R J[2][n], R M00, R M01, R M11, R g0, R g1, R* lam, R* eta) {
+    R ua[n], va[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        ua[i] = M00 * J[0][i] + M01 * J[1][i];
+        va[i] = M01 * J[0][i] + M11 * J[1][i];
+        eta[i] = J[0][i] * g0 + J[1][i] * g1;
+    }
+#pragma unroll
+    for (int i = 0; i < n; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) lam[pk(i, j)] = ua[i] * J[0][j] + va[i] * J[1][j];
+}
+
+// tr(J^T M J) and J^T g of a compact message (learned-damping features).
+template <typename R, int n>
+__device__ __forceinline__ R msg_trace(const R J[2][n], R M00, R M01, R M11) {
+    R a = R(0), b = R(0), c = R(0);
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        a += J[0][i] * J[0][i];
+        b += J[0][i] * J[1][i];
+        c += J[1][i] * J[1][i];
+    }
+    return M00 * a + R(2) * M01 * b + M11 * c;
+}
+template <typename R, int n>
+__device__ __forceinline__ void msg_eta(const R J[2][n], R g0, R g1, R* eta) {
+#pragma unroll
+    for (int i = 0; i < n; ++i) eta[i] = J[0][i] * g0 + J[1][i] * g1;
+}
+
+// A factor's lin record (SoA rows y0, y1, W, |r|^2): its linearisation
+// between relinearisations, with the keyframe Jacobian block in kj.
+template <typename R>
+__device__ __forceinline__ void store_lin(const DevGraph<R>& g, int f, const Lin<R>& L) {
+    const size_t n_f = g.n_f;
+    g.lin[f] = L.y[0];
+    g.lin[n_f + f] = L.y[1];
+    g.lin[2 * n_f + f] = L.W;
+    g.lin[3 * n_f + f] = L.r2;
+}
+
+// A keyframe Jacobian block record (row 0, then row 1).
+template <typename R>
+__device__ __forceinline__ void store_jac(R* dst, const R J[2][6]) {
+    R jr[KJ];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { jr[i] = J[0][i]; jr[6 + i] = J[1][i]; }
+    store_rec<R, KJ>(dst, jr);
+}
+
+// M = W (I + W Q)^-1 and g = M (y - s); out = {M00, M01, M11, g0, g1}.
+template <typename C>
+__device__ __forceinline__ void compact_from_Qs(C Q00, C Q01, C Q11, C s0, C s1, const C y[2], C W, C* out) {
+    const C a00 = C(1) + W * Q00, a01 = W * Q01, a11 = C(1) + W * Q11;
+    const C idet = rcp(a00 * a11 - a01 * a01);
+    const C N00 = a11 * idet, N01 = -a01 * idet, N11 = a00 * idet;
+    const C M00 = W * N00, M01 = W * N01, M11 = W * N11;
+    const C e0 = y[0] - s0, e1 = y[1] - s1;
+    out[0] = M00;
+    out[1] = M01;
+    out[2] = M11;
+    out[3] = M00 * e0 + M01 * e1;
+    out[4] = M01 * e0 + M11 * e1;
+}
+
+// Compact message from an explicit incoming precision: Lb, inv_d its
+// Cholesky factor (chol_packed), qb the incoming vector, Jb the Jacobian
+// block of the marginalised variable.
+template <typename C, int nb>
+__device__ __forceinline__ void message_chol(const C* Lb, const C* inv_d, const C* qb, const C Jb[2][nb],
+                                             const C y[2], C W, C* out) {
+    C V0[nb], V1[nb], u[nb];
+#pragma unroll
+    for (int i = 0; i < nb; ++i) { V0[i] = Jb[0][i]; V1[i] = Jb[1][i]; u[i] = qb[i]; }
+    fwd_solve<C, nb>(Lb, inv_d, V0);
+    fwd_solve<C, nb>(Lb, inv_d, V1);
+    fwd_solve<C, nb>(Lb, inv_d, u);
+    C Q00 = C(0), Q01 = C(0), Q11 = C(0), s0 = C(0), s1 = C(0);
+#pragma unroll
+    for (int i = 0; i < nb; ++i) {
+        Q00 += V0[i] * V0[i];
+        Q01 += V0[i] * V1[i];
+        Q11 += V1[i] * V1[i];
+        s0 += V0[i] * u[i];
+        s1 += V1[i] * u[i];
+    }
+    compact_from_Qs<C>(Q00, Q01, Q11, s0, s1, y, W, out);
+}
+
+// v <- L^-1 v with a keyframe belief's stored factor (packed lower, 1/L_ii
+// on the diagonal), kept in registers.
+template <typename R>
+__device__ __forceinline__ void fwd_solve_stored(const R* Ls, R* v) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        R s = v[i];
+#pragma unroll
+        for (int p = 0; p < i; ++p) s -= Ls[pk(i, p)] * v[p];
+        v[i] = s * Ls[pk(i, i)];
+    }
+}
+
+// The keyframe side of a factor in the basis of its stored messages
+// (Jacobian block Jo): with the keyframe belief B = L L^T, its mean mu and
+// the factor's previous message to the keyframe Jo^T Mo Jo (eta Jo^T go),
+// the incoming precision is P = B - Jo^T Mo Jo.  With Vo = L^-1 Jo^T,
+// G = Vo^T Vo = Jo B^-1 Jo^T and a = Jo mu - G go:
+//   P^-1 = B^-1 + B^-1 Jo^T (I - Mo G)^-1 Mo Jo B^-1,
+// so every quantity of the message to the landmark reduces to 2 x 2 ones,
+// and P is positive definite iff both eigenvalues of I - Mo G are positive
+// (B being so); det(I - Mo G) is the share of B's precision volume left.
+template <typename R>
+struct KfSide {
+    R G00, G01, G11;       // G = Vo^T Vo
+    R a0, a1;              // Jo mu - G go
+    R K00, K01, K11;       // K = (I - Mo G)^-1 Mo (symmetric)
+    R det;                 // det(I - Mo G)
+    bool pd;               // P positive definite
+};
+
+template <typename R>
+__device__ __forceinline__ void kf_side(const R* Ls, const R* mu, const R Jo[2][6], const R* mo, KfSide<R>& s) {
+    R V0[6], V1[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { V0[i] = Jo[0][i]; V1[i] = Jo[1][i]; }
+    fwd_solve_stored<R>(Ls, V0);
+    fwd_solve_stored<R>(Ls, V1);
+    R G00 = R(0), G01 = R(0), G11 = R(0), jm0 = R(0), jm1 = R(0);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        G00 += V0[i] * V0[i];
+        G01 += V0[i] * V1[i];
+        G11 += V1[i] * V1[i];
+        jm0 += Jo[0][i] * mu[i];
+        jm1 += Jo[1][i] * mu[i];
+    }
+    s.G00 = G00; s.G01 = G01; s.G11 = G11;
+    const R M00 = mo[0], M01 = mo[1], M11 = mo[2];
+    s.a0 = jm0 - (G00 * mo[3] + G01 * mo[4]);
+    s.a1 = jm1 - (G01 * mo[3] + G11 * mo[4]);
+    // D = I - M G
+    const R D00 = R(1) - (M00 * G00 + M01 * G01), D01 = -(M00 * G01 + M01 * G11);
+    const R D10 = -(M01 * G00 + M11 * G01), D11 = R(1) - (M01 * G01 + M11 * G11);
+    const R det = D00 * D11 - D01 * D10;
+    s.det = det;
+    s.pd = det > R(0) && D00 + D11 > R(0);
+    // K = D^-1 M = adj(D) M / det
+    const R id = s.pd ? rcp(det) : R(0);
+    s.K00 = (D11 * M00 - D01 * M01) * id;
+    s.K01 = (D11 * M01 - D01 * M11) * id;
+    s.K11 = (-D10 * M01 + D00 * M11) * id;
+}
+
+// Compact message to the landmark from KfSide when the basis is unchanged:
+//   Q = G + G K G,  s = a + G K a.
+template <typename R>
+__device__ __forceinline__ void message_to_landmark(const KfSide<R>& s, const R y[2], R W, R* out) {
+    const R Y00 = s.G00 * s.K00 + s.G01 * s.K01, Y01 = s.G00 * s.K01 + s.G01 * s.K11;
+    const R Y10 = s.G01 * s.K00 + s.G11 * s.K01, Y11 = s.G01 * s.K01 + s.G11 * s.K11;
+    compact_from_Qs<R>(s.G00 + (Y00 * s.G00 + Y01 * s.G01), s.G01 + (Y00 * s.G01 + Y01 * s.G11),
+                       s.G11 + (Y10 * s.G01 + Y11 * s.G11), s.a0 + (Y00 * s.a0 + Y01 * s.a1),
+                       s.a1 + (Y10 * s.a0 + Y11 * s.a1), y, W, out);
+}
+
+// ------------------------------------------------------------------------
+// Rare paths, kept out of line so that their state does not weigh on the
+// register allocation of the common path: arguments and results by value.
+
+// What a linearisation needs besides the factor's x0 and pixel.
+template <typename R>
+struct LinArgs {
+    const double* Rref;
+    const double* cref;
+    const double* lref;
+    R zu, zv;
+    R fx, fy, cx, cy, inv_sigma2, inv_sigma, huber_n, z_min;
+};
+
+template <typename R>
+__device__ __forceinline__ LinArgs<R> lin_args(const KParams<R>& P, const double* Rref, const double* cref,
+                                               const double* lref, R zu, R zv) {
+    return LinArgs<R>{Rref, cref, lref, zu, zv, P.fx, P.fy, P.cx, P.cy, P.inv_sigma2, P.inv_sigma, P.huber_n,
+                      P.z_min};
+}
+
+template <typename C, typename R>
+__device__ __forceinline__ void lin_from_args(const LinArgs<R>& A, const C* x0, Lin<C>& L) {
+    KParams<C> P{};
+    P.fx = C(A.fx); P.fy = C(A.fy); P.cx = C(A.cx); P.cy = C(A.cy);
+    P.inv_sigma2 = C(A.inv_sigma2); P.inv_sigma = C(A.inv_sigma); P.huber_n = C(A.huber_n); P.z_min = C(A.z_min);
+    linearise<C>(P, A.Rref, A.cref, A.lref, x0, C(A.zu), C(A.zv), L);
+}
+
+template <typename R> struct Arr9 { R v[9]; };
+template <typename R> struct Arr12 { R v[12]; };
+template <typename R> struct Msg5 { R v[5]; };
+
+// A factor's linearisation at x0 (its first; out of line, since it happens
+// once per linearisation point while the stored one serves every other
+// iteration).
+template <typename R>
+__device__ __noinline__ Lin<R> linearise_at(Arr9<R> x0, LinArgs<R> A) {
+    Lin<R> L;
+    lin_from_args<R, R>(A, x0.v, L);
+    return L;
+}
+
+// A relinearisation in this iteration: the factor's linearisation at its
+// new point x0n, and its message to the landmark in that new basis from the
+// keyframe side computed in the old basis Jo (KfSide), by the two-basis form
+//   Q = Gnn + Gno K Gno^T,  s = an + Gno K a,  Gno = Vn^T Vo,  an = Jn mu - Gno go.
+template <typename R>
+struct Rebased {
+    Lin<R> L;
+    R cl[5];
+};
+
+template <typename R>
+__device__ __noinline__ Rebased<R> rebase(const R* kbp, Arr12<R> Jo, R go0, R go1, R a0, R a1, R K00, R K01, R K11,
+                                          bool form_lm, Arr9<R> x0n, LinArgs<R> A) {
+    Rebased<R> out;
+    lin_from_args<R, R>(A, x0n.v, out.L);
+    for (int i = 0; i < 5; ++i) out.cl[i] = R(0);
+    if (!form_lm) return out;
+    R Ls[KB_A];
+    load_rec_cg<R, KB_A>(kbp, Ls);
+    const R* mu = Ls + KB_MU;
+    R Vo[2][6], Vn[2][6];
+    for (int i = 0; i < 6; ++i) {
+        Vo[0][i] = Jo.v[i]; Vo[1][i] = Jo.v[6 + i];
+        Vn[0][i] = out.L.Jk[0][i]; Vn[1][i] = out.L.Jk[1][i];
+    }
+    fwd_solve_stored<R>(Ls, Vo[0]);
+    fwd_solve_stored<R>(Ls, Vo[1]);
+    fwd_solve_stored<R>(Ls, Vn[0]);
+    fwd_solve_stored<R>(Ls, Vn[1]);
+    R Gn00 = R(0), Gn01 = R(0), Gn11 = R(0), X00 = R(0), X01 = R(0), X10 = R(0), X11 = R(0), jm0 = R(0), jm1 = R(0);
+    for (int i = 0; i < 6; ++i) {
+        Gn00 += Vn[0][i] * Vn[0][i];
+        Gn01 += Vn[0][i] * Vn[1][i];
+        Gn11 += Vn[1][i] * Vn[1][i];
+        X00 += Vn[0][i] * Vo[0][i];
+        X01 += Vn[0][i] * Vo[1][i];
+        X10 += Vn[1][i] * Vo[0][i];
+        X11 += Vn[1][i] * Vo[1][i];
+        jm0 += out.L.Jk[0][i] * mu[i];
+        jm1 += out.L.Jk[1][i] * mu[i];
+    }
+    const R an0 = jm0 - (X00 * go0 + X01 * go1), an1 = jm1 - (X10 * go0 + X11 * go1);
+    const R Y00 = X00 * K00 + X01 * K01, Y01 = X00 * K01 + X01 * K11;
+    const R Y10 = X10 * K00 + X11 * K01, Y11 = X10 * K01 + X11 * K11;
+    compact_from_Qs<R>(Gn00 + (Y00 * X00 + Y01 * X01), Gn01 + (Y00 * X10 + Y01 * X11), Gn11 + (Y10 * X10 + Y11 * X11),
+                       an0 + (Y00 * a0 + Y01 * a1), an1 + (Y10 * a0 + Y11 * a1), out.L.y, out.L.W, out.cl);
+    return out;
+}
+
+// FP64 redo for an incoming precision the FP32 arithmetic cannot take: the
+// incoming precision formed in FP64 from FP32 state; *_ok decides whether it
+// is positive definite, *_message (same decision) forms the compact message
+// (M00, M01, M11, g0, g1) in FP64 from the factor's FP32 linearisation (its
+// Jacobian and residual are well conditioned; the incoming precision is
+// what FP32 cannot take).  The decision uses iteration-t state only, so it
+// is taken before the relinearisation test and the message formed after it.
+
+template <typename R>
+__device__ __forceinline__ void widen_lin(const Lin<R>& L, Lin<double>& D) {
+    for (int a = 0; a < 2; ++a) {
+        for (int j = 0; j < 6; ++j) D.Jk[a][j] = double(L.Jk[a][j]);
+        for (int j = 0; j < 3; ++j) D.Jl[a][j] = double(L.Jl[a][j]);
+        D.y[a] = double(L.y[a]);
+    }
+    D.W = double(L.W);
+    D.r2 = double(L.r2);
+}
+
+// Message to the keyframe: the landmark's incoming precision as the FP32
+// path formed it (P 6, q 3).
+template <typename R>
+__device__ __noinline__ bool lm_incoming_ok64(Arr9<R> pq) {
+    double A[6], inv_d[3], ratio;
+    for (int i = 0; i < 6; ++i) A[i] = double(pq.v[i]);
+    return chol_packed<double, 3>(A, inv_d, ratio);
+}
+
+template <typename R>
+__device__ __noinline__ Msg5<R> lm_message64(Arr9<R> pq, Lin<R> Lf) {
+    double P[6], inv_d[3], q[3], ratio;
+    for (int i = 0; i < 6; ++i) P[i] = double(pq.v[i]);
+    for (int i = 0; i < 3; ++i) q[i] = double(pq.v[6 + i]);
+    chol_packed<double, 3>(P, inv_d, ratio);
+    Lin<double> L;
+    widen_lin<R>(Lf, L);
+    double o[5];
+    message_chol<double, 3>(P, inv_d, q, L.Jl, L.y, L.W, o);
+    Msg5<R> out;
+    for (int i = 0; i < 5; ++i) out.v[i] = R(o[i]);
+    return out;
+}
+
+// Message to the landmark: the keyframe's incoming precision b^t - m^t in
+// FP64 from the belief record's Lambda, eta and the factor's previous
+// message (its compact record and Jacobian block, exactly what the belief
+// summed).  If that is not positive definite (the FP32 belief's rounding,
+// summed over ~100 messages, can leave the difference indefinite where this
+// message dominates a direction), the incoming message is summed again
+// exactly from its parts: the keyframe's prior at iteration t plus every
+// other factor's current message, a loop over the keyframe's contiguous
+// slots [i0, i1) of the buffers this iteration only reads.
+template <typename R>
+struct KfCavity {
+    const R* kb;            // the keyframe's belief record (b^t)
+    const R* recs;          // m^t records, keyframe slot order
+    const R* jac;           // their Jacobian blocks
+    const R* D;             // the keyframe's prior diagonal (6) and anchor diagonal (6), sigma = 1
+    const R* A;
+    int i0, i1, self;
+    R s, anchor_scale, inv_sigma2;   // prior scale s(t), anchor factor, 1 / sigma^2
+};
+
+template <typename R>
+__device__ __forceinline__ void expand_slot64(const KfCavity<R>& kc, int j, double* lam, double* eta) {
+    const R* rec = kc.recs + (size_t)j * KREC;
+    const R* jr = kc.jac + (size_t)j * KJ;
+    double J[2][6];
+    for (int i = 0; i < 6; ++i) { J[0][i] = double(__ldcg(jr + i)); J[1][i] = double(__ldcg(jr + 6 + i)); }
+    expand_msg<double, 6>(J, double(__ldcg(rec)), double(__ldcg(rec + 1)), double(__ldcg(rec + 2)),
+                          double(__ldcg(rec + 3)), double(__ldcg(rec + 4)), lam, eta);
+}
+
+template <typename R>
+__device__ __forceinline__ bool kf_incoming64(const KfCavity<R>& kc, double* A, double* q, double* inv_d) {
+    double lam[21], eta[6], ratio;
+    expand_slot64<R>(kc, kc.self, lam, eta);
+    for (int i = 0; i < 21; ++i) A[i] = double(__ldcg(kc.kb + KB_LAM + i)) - lam[i];
+    for (int i = 0; i < 6; ++i) q[i] = double(__ldcg(kc.kb + KB_ETA + i)) - eta[i];
+    if (chol_packed<double, 6>(A, inv_d, ratio)) return true;
+    for (int i = 0; i < 21; ++i) A[i] = 0.0;
+    for (int i = 0; i < 6; ++i) {
+        // as b^t added it, in the kernel's precision
+        A[pk(i, i)] = double((kc.s * kc.D[i] + kc.anchor_scale * kc.A[i]) * kc.inv_sigma2);
+        q[i] = 0.0;   // the prior mean is the chart origin
+    }
+    for (int j = kc.i0; j < kc.i1; ++j) {
+        if (j == kc.self) continue;
+        expand_slot64<R>(kc, j, lam, eta);
+        for (int i = 0; i < 21; ++i) A[i] += lam[i];
+        for (int i = 0; i < 6; ++i) q[i] += eta[i];
+    }
+    return chol_packed<double, 6>(A, inv_d, ratio);
+}
+
+template <typename R>
+__device__ __noinline__ bool kf_incoming_ok64(KfCavity<R> kc) {
+    double A[21], q[6], inv_d[6];
+    return kf_incoming64<R>(kc, A, q, inv_d);
+}
+
+template <typename R>
+__device__ __noinline__ Msg5<R> kf_message64(KfCavity<R> kc, Lin<R> Lf) {
+    double A[21], q[6], inv_d[6];
+    kf_incoming64<R>(kc, A, q, inv_d);
+    Lin<double> L;
+    widen_lin<R>(Lf, L);
+    double o[5];
+    message_chol<double, 6>(A, inv_d, q, L.Jk, L.y, L.W, o);
+    Msg5<R> out;
+    for (int i = 0; i < 5; ++i) out.v[i] = R(o[i]);
+    return out;
+}
+
 
 __device__ __forceinline__ void raise_error(int32_t* ctl, int where) {
     if (atomicCAS(&ctl[CTL_ERR], 0, 1) == 0) ctl[CTL_ERR_WHERE] = where;
@@ -546,6 +845,46 @@ __device__ __forceinline__ float finish_landmark(const DevGraph<R>& g, const KPa
     return dmu;
 }
 
+// A keyframe belief record from Lambda and eta: the Cholesky factor (1/L_ii
+// on its diagonal), the mean, tr Lambda, Lambda and eta.  Returns false if
+// Lambda is not positive definite; *ratio receives the pivot ratio.
+template <typename R>
+__device__ __forceinline__ bool kf_record(const R* lam, const R* eta, R* out, R& ratio) {
+    R Lw[21], inv[6], mu[6];
+#pragma unroll
+    for (int j = 0; j < 21; ++j) Lw[j] = lam[j];
+    const bool ok = chol_packed<R, 6>(Lw, inv, ratio);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) mu[i] = eta[i];
+    fwd_solve<R, 6>(Lw, inv, mu);
+    bwd_solve<R, 6>(Lw, inv, mu);
+#pragma unroll
+    for (int j = 0; j < 21; ++j) out[KB_L + j] = Lw[j];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        out[KB_L + pk(i, i)] = inv[i];
+        out[KB_MU + i] = mu[i];
+        out[KB_ETA + i] = eta[i];
+    }
+    out[KB_TR] = lam[0] + lam[2] + lam[5] + lam[9] + lam[14] + lam[20];
+#pragma unroll
+    for (int j = 0; j < 21; ++j) out[KB_LAM + j] = lam[j];
+    out[KBEL - 1] = R(0);
+    return ok;
+}
+
+// FP64 redo of a keyframe record's factor and mean (rounded back to R).
+template <typename R>
+__device__ __noinline__ bool kf_record_fp64(R* out) {
+    double lam[21], eta[6], o[KBEL], ratio;
+    for (int j = 0; j < 21; ++j) lam[j] = double(out[KB_LAM + j]);
+    for (int i = 0; i < 6; ++i) eta[i] = double(out[KB_ETA + i]);
+    const bool ok = kf_record<double>(lam, eta, o, ratio);
+    for (int j = 0; j < 21; ++j) out[KB_L + j] = R(o[KB_L + j]);
+    for (int i = 0; i < 6; ++i) out[KB_MU + i] = R(o[KB_MU + i]);
+    return ok;
+}
+
 // Keyframe belief b^{t+1} = s(t+1) D + anchor + sum of messages and its
 // mean from the (already reduced) sums; writes the record to out and
 // returns |dmu|_inf against mu_old.
@@ -553,60 +892,47 @@ __device__ __forceinline__ float finish_landmark(const DevGraph<R>& g, const KPa
 template <typename R>
 __device__ __forceinline__ float finish_keyframe(const DevGraph<R>& g, const KParams<R>& P, int k, const R* prior,
                                                  const R* sum, const R* mu_old, R* out_bel) {
-    R lam[21], eta[6], mu[6], work[21], ratio;
+    R lam[21], eta[6], ratio;
 #pragma unroll
     for (int j = 0; j < 21; ++j) lam[j] = sum[j];
 #pragma unroll
     for (int j = 0; j < 6; ++j) eta[j] = sum[21 + j];
 #pragma unroll
     for (int i = 0; i < 6; ++i) lam[pk(i, i)] += prior[i];
-#pragma unroll
-    for (int j = 0; j < 21; ++j) work[j] = lam[j];
-    bool ok = solve_mean<R, 6>(work, eta, mu, ratio);
     R out[KBEL];
-#pragma unroll
-    for (int j = 0; j < 21; ++j) out[j] = lam[j];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) { out[21 + j] = eta[j]; out[27 + j] = mu[j]; }
-    out[33] = out[34] = out[35] = R(0);
-    R* rec = out_bel + (size_t)k * KBEL;
-    store_rec<R, KBEL>(rec, out);
+    bool ok = kf_record<R>(lam, eta, out, ratio);
     if (sizeof(R) == 4 && P.fallback && (!ok || ratio < P.pivot_ratio)) {
-        ok = solve_mean_fp64<R, 6>(rec);
-#pragma unroll
-        for (int i = 0; i < 6; ++i) mu[i] = rec[27 + i];
+        ok = kf_record_fp64<R>(out);
         atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
     }
+    store_rec<R, KBEL>(out_bel + (size_t)k * KBEL, out);
     float dmu = 0.0f;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        if (!isfinite(mu[i])) ok = false;
-        dmu = fmaxf(dmu, float(fabs(mu[i] - mu_old[i])));
+        if (!isfinite(out[KB_MU + i])) ok = false;
+        dmu = fmaxf(dmu, float(fabs(out[KB_MU + i] - mu_old[i])));
     }
     if (!ok) raise_error(g.ctl, k);
     return dmu;
 }
 
-// L2-coherent loads (bypass L1) for data that other SMs write during the
-// same launch (the persistent kernel runs many iterations in one launch).
-template <typename R, int N>
-__device__ __forceinline__ void load_rec_cg(const R* src, R* dst) {
-    if constexpr (sizeof(R) == 4) {
-        const float4* s4 = reinterpret_cast<const float4*>(src);
+// The record of a belief that is the prior alone (diagonal p), mean 0.
+template <typename R>
+__device__ __forceinline__ void kf_prior_record(const R* p, R* out) {
 #pragma unroll
-        for (int i = 0; i < N / 4; ++i) {
-            float4 v = __ldcg(s4 + i);
-            dst[4 * i + 0] = v.x; dst[4 * i + 1] = v.y; dst[4 * i + 2] = v.z; dst[4 * i + 3] = v.w;
-        }
-    } else {
-        const double2* s2 = reinterpret_cast<const double2*>(src);
+    for (int j = 0; j < KBEL; ++j) out[j] = R(0);
+    R tr = R(0);
 #pragma unroll
-        for (int i = 0; i < N / 2; ++i) {
-            double2 v = __ldcg(s2 + i);
-            dst[2 * i + 0] = v.x; dst[2 * i + 1] = v.y;
-        }
+    for (int i = 0; i < 6; ++i) {
+        R d, id;
+        sqrt_pair<R>(p[i], d, id);
+        out[KB_L + pk(i, i)] = id;
+        out[KB_LAM + pk(i, i)] = p[i];
+        tr += p[i];
     }
+    out[KB_TR] = tr;
 }
+
 
 // Keyframe messages are double-buffered by iteration parity: iteration t
 // reads m^t from buffer t & 1 and writes m^{t+1} to the other buffer
@@ -814,11 +1140,20 @@ __device__ __forceinline__ void mlp_load_wait() {
 
 // ------------------------------------------------------------------------
 // Phase A: one warp, one tile of whole landmarks (at most 32 factors,
-// consecutive in landmark order), one lane per factor -- relinearisation
-// test, Jacobian, Huber weight, both messages, damping (Sec. 4-6, 8); then
-// the landmark messages of the tile are summed per landmark by a segmented
-// warp scan (fixed lane order) and each landmark's last lane forms its
-// belief b^{t+1} and mean (a landmark wholly inside a tile is read by no
+// consecutive in landmark order), one lane per factor.  For each factor:
+//   1. its linearisation at x0 (the basis its stored messages are in);
+//   2. both incoming precisions (Sec. 5): the landmark's as prior(t) plus
+//      the other factors' previous messages (segmented warp scans, no
+//      cancellation), the keyframe's through the belief's stored Cholesky
+//      factor (KfSide); an FP64 redo where FP32 cannot take them;
+//   3. the relinearisation test (Sec. 5, Sec. 8), skipped by a factor one of
+//      whose messages must be kept (its incoming precision is not positive
+//      definite), then the linearisation at the new point;
+//   4. both new messages in compact form, the Huber weight (Sec. 6) inside W;
+//   5. damping of g, i.e. of eta (Sec. 5), after the undamped hold (Sec. 8);
+// then the landmark messages of the tile are summed per landmark by a
+// segmented warp scan (fixed lane order) and each landmark's last lane forms
+// its belief b^{t+1} and mean (a landmark wholly inside a tile is read by no
 // other warp).  Returns this lane's max |dmu|.
 // MODE selects the damping schedule (DampMode); the learned schedule
 // evaluates the network for the warp's 32 factors at once on the tensor
@@ -831,58 +1166,141 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
     const int ts = g.tile_start[tile], te = g.tile_start[tile + 1];
     const int f = ts + lane;
     const bool active = f < te;
-
-    R sum[9];           // this lane's new landmark message (Lambda 6, eta 3)
-    R mu_m_old[3] = {R(0), R(0), R(0)};
-    int m = -1, lo = 0, hi = 0;
-    // learned / record schedules: undamped new and previous eta of both
-    // messages, and the features
     constexpr bool FEAT = MODE != DAMP_FIXED;
-    R ek_new[6], ek_old[6], em_new[3], em_old[3], ek_prev[6];
-    float feat[N_FEAT];
-#pragma unroll
-    for (int i = 0; i < N_FEAT; ++i) feat[i] = 0.0f;
-    size_t ks_f = 0;
-    int tl_f = 0;
-    // feature inputs that do not depend on this iteration's messages, loaded
-    // first so that their latency overlaps the message arithmetic
-    float h[HIST];
-    int deg_k = 0, birth_m = 0;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) sum[i] = R(0);
 
-    // previous landmark messages m^t of the tile's lanes
-    R ml[9];
+    int m = -1, lo = 0, hi = 0, k = 0, slot = 0, tl = 0;
+    R cml[NML];          // this factor's previous message to the landmark (compact)
+#pragma unroll
+    for (int i = 0; i < NML; ++i) cml[i] = R(0);
     if (active) {
         m = g.fm[f];
+        k = g.fk[f];
+        slot = g.kpos[f];
         lo = g.lm_off[m];
         hi = g.lm_off[m + 1];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) ml[i] = g.ml[(size_t)i * n_f + f];
-        if constexpr (FEAT) {
-#pragma unroll
-            for (int j = 0; j < HIST; ++j) h[j] = g.hist[(size_t)j * n_f + f];
-            const int k = g.fk[f];
-            deg_k = g.kf_off[k + 1] - g.kf_off[k];
-            birth_m = g.lm_birth[m];
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) ml[i] = R(0);
+        for (int i = 0; i < NML; ++i) cml[i] = g.ml[(size_t)i * n_f + f];
+        tl = g.tlin[f];
     }
-    // For a landmark wholly inside the tile the incoming message (belief
-    // divided by this factor's previous message) is formed as prior(t) plus
-    // the sum of the OTHER factors' previous messages -- exclusive prefix
-    // and suffix sums over the landmark's lanes -- which equals b^t - m^t
-    // without the cancellation of subtracting one message from the belief.
     const bool whole = active && lo >= ts && hi <= te;
     const int seg0 = whole ? lo - ts : lane;
     const int seg1 = whole ? hi - ts - 1 : lane;
-    R cav[9];
+    // the linearisation point is needed for a factor's first linearisation
+    // and for the relinearisation test once the interval allows one
+    const bool fresh = active && tl == t;
+    const bool due = active && !P.linear && t - tl >= P.relin_interval;
+    R x0[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) x0[i] = (fresh || due) ? g.x0[(size_t)i * n_f + f] : R(0);
+
+    // 1. the factor's linearisation (Sec. 4), the basis of its stored
+    // messages: computed at its first iteration, else as stored when it was
+    // taken -- the keyframe block J_k from the slot's kj record (the landmark
+    // block is -J_k[:, 0:3]), y, W and |r|^2 from the factor's lin record
+    Lin<R> L;
+    if (fresh) {
+        Arr9<R> xv;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) xv.v[i] = x0[i];
+        L = linearise_at<R>(xv, lin_args<R>(P, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3,
+                                            g.lm_ref + (size_t)m * 3, g.z[2 * (size_t)f], g.z[2 * (size_t)f + 1]));
+        store_lin<R>(g, f, L);
+        store_jac<R>(g.kjs + (size_t)slot * KJ, L.Jk);
+    } else if (active) {
+        R jr[KJ];
+        load_rec<R, KJ>(g.kj + (size_t)slot * KJ, jr);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            L.Jk[0][j] = jr[j];
+            L.Jk[1][j] = jr[6 + j];
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            L.Jl[0][j] = -jr[j];
+            L.Jl[1][j] = -jr[6 + j];
+        }
+        L.y[0] = g.lin[f];
+        L.y[1] = g.lin[(size_t)n_f + f];
+        L.W = g.lin[2 * (size_t)n_f + f];
+        L.r2 = g.lin[3 * (size_t)n_f + f];
+    } else {
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+#pragma unroll
+            for (int j = 0; j < 6; ++j) L.Jk[a][j] = R(0);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) L.Jl[a][j] = R(0);
+            L.y[a] = R(0);
+        }
+        L.W = R(0);
+        L.r2 = R(0);
+    }
+
+    // 2a. keyframe incoming precision b^t - m^t through the belief's factor
+    const R* kbp = g.kf_bel + (size_t)k * KBEL;
+    R kmu[6];            // the keyframe's mean mu^t
+    R mo[KREC];          // the previous message to the keyframe (compact record)
+    KfSide<R> ks;
+    R tr_b = R(0);
+    {
+        R kb[KB_A];
+        if (active) {
+            load_rec_cg<R, KB_A>(kbp, kb);
+            load_rec<R, KREC>(mk_read(g, t) + (size_t)slot * KREC, mo);
+        } else {
+#pragma unroll
+            for (int i = 0; i < KB_A; ++i) kb[i] = R(0);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) kb[pk(i, i)] = R(1);
+#pragma unroll
+            for (int i = 0; i < KREC; ++i) mo[i] = R(0);
+        }
+        kf_side<R>(kb, kb + KB_MU, L.Jk, mo, ks);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) kmu[i] = kb[KB_MU + i];
+        tr_b = kb[KB_TR];
+    }
+    bool ok_k = ks.pd;
+
+    // learned / record schedules: quantities of the previous messages, in
+    // their basis, before a relinearisation replaces it
+    R ek_old[6], ek_prev[6], em_old[3];
+    R tr_pk = R(0), tr_pm = R(0);
+    float h[HIST];
+    int deg_k = 0, birth_m = 0;
+    if constexpr (FEAT) {
+        msg_eta<R, 6>(L.Jk, mo[3], mo[4], ek_old);
+        // m^{t-1} to the keyframe: still in the buffer this iteration writes
+        R pr[KREC];
+        if (active) load_rec<R, KREC>(mk_write(g, t) + (size_t)slot * KREC, pr);
+        else
+#pragma unroll
+            for (int i = 0; i < KREC; ++i) pr[i] = R(0);
+        msg_eta<R, 6>(L.Jk, pr[3], pr[4], ek_prev);
+        tr_pk = tr_b - msg_trace<R, 6>(L.Jk, mo[0], mo[1], mo[2]);
+#pragma unroll
+        for (int j = 0; j < HIST; ++j) h[j] = active ? g.hist[(size_t)j * n_f + f] : 0.0f;
+        if (active) {
+            deg_k = g.kf_off[k + 1] - g.kf_off[k];
+            birth_m = g.lm_birth[m];
+        }
+    }
+
+    // 2b. landmark incoming precision.  For a landmark wholly inside the
+    // tile: prior(t) plus the exclusive prefix and suffix sums of the other
+    // factors' previous messages, which equals b^t - m^t without the
+    // cancellation of subtracting one message from the belief.
+    R mlo[9];            // this factor's previous landmark message, expanded
+    expand_msg<R, 3>(L.Jl, cml[0], cml[1], cml[2], cml[3], cml[4], mlo, mlo + 6);
+    if constexpr (FEAT) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) em_old[i] = mlo[6 + i];
+    }
+    R Pm[6], qm[3];
     {
         R fw[9], bw[9];
 #pragma unroll
-        for (int j = 0; j < 9; ++j) { fw[j] = ml[j]; bw[j] = ml[j]; }
+        for (int j = 0; j < 9; ++j) { fw[j] = mlo[j]; bw[j] = mlo[j]; }
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
 #pragma unroll
@@ -897,254 +1315,229 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
         for (int j = 0; j < 9; ++j) {
             R pre = __shfl_up_sync(0xffffffffu, fw[j], 1);
             R suf = __shfl_down_sync(0xffffffffu, bw[j], 1);
-            cav[j] = (lane - 1 >= seg0 ? pre : R(0)) + (lane + 1 <= seg1 ? suf : R(0));
+            const R cv = (lane - 1 >= seg0 ? pre : R(0)) + (lane + 1 <= seg1 ? suf : R(0));
+            if (j < 6) Pm[j] = cv;
+            else qm[j - 6] = cv;
         }
     }
-
+    R lb_mu[3] = {R(0), R(0), R(0)};   // the landmark's mean mu^t
     if (active) {
-        const int k = g.fk[f];
-        const size_t ks = (size_t)g.kpos[f] * KREC;   // this factor's keyframe-message slot
-        const R* kbp = g.kf_bel + (size_t)k * KBEL;
-        // static geometry first: its loads need not wait for the
-        // relinearisation decision below (which may store to x0)
-        R Rr[9], dlc[3];
-        load_refs<R>(g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3, g.lm_ref + (size_t)m * 3, Rr, dlc);
-        const R zu = g.z[2 * (size_t)f], zv = g.z[2 * (size_t)f + 1];
-        R lb[LBEL];
-        load_rec_cg<R, LBEL>(g.lm_bel + (size_t)m * LBEL, lb);
-        mu_m_old[0] = lb[9];
-        mu_m_old[1] = lb[10];
-        mu_m_old[2] = lb[11];
-        R x0[9];
+        const R* lbp = g.lm_bel + (size_t)m * LBEL;
+        lb_mu[0] = __ldcg(lbp + 9);
+        lb_mu[1] = __ldcg(lbp + 10);
+        lb_mu[2] = __ldcg(lbp + 11);
+        if (whole) {
+            const R sp = lm_prior_scale(g, P, m, t) * P.inv_sigma2;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) x0[i] = g.x0[(size_t)i * n_f + f];
-        int tl = g.tlin[f];
-
-        // Sec. 5 / Sec. 8: relinearise when the adjacent means moved more
-        // than beta from the linearisation point, at most every
-        // relin_interval iterations.
-        if (!P.linear && t - tl >= P.relin_interval) {
-            R mu[9];
+            for (int i = 0; i < 3; ++i) Pm[pk(i, i)] += sp * g.lm_D[m * 3 + i];
+        } else {
+            // a landmark split across tiles: its belief divided by this message
+            R lb[9];
 #pragma unroll
-            for (int i = 0; i < 6; ++i) mu[i] = __ldcg(kbp + 27 + i);
-            mu[6] = lb[9];
-            mu[7] = lb[10];
-            mu[8] = lb[11];
-            R d2 = R(0);
+            for (int i = 0; i < 9; ++i) lb[i] = __ldcg(lbp + i);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) d2 += (mu[i] - x0[i]) * (mu[i] - x0[i]);
-            if (d2 > P.relin_beta * P.relin_beta) {
+            for (int i = 0; i < 6; ++i) Pm[i] = lb[i] - mlo[i];
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    x0[i] = mu[i];
-                    g.x0[(size_t)i * n_f + f] = mu[i];
-                }
-                tl = t;
-                g.tlin[f] = t;
-                atomicAdd(&g.ctl[CTL_RELINS], 1);
-            }
+            for (int i = 0; i < 3; ++i) qm[i] = lb[6 + i] - mlo[6 + i];
         }
-
-        Lin<R> L;
-        linearise_ref<R>(P, Rr, dlc, x0, zu, zv, L);
-        const bool damp = MODE != DAMP_LEARNED && t - tl >= P.damp_hold;   // learned: after the network
-        const R d = P.damping;
-        ks_f = ks;
-        tl_f = tl;
-        if constexpr (FEAT) {
-            // m^{t-1} to the keyframe: still in the buffer this iteration writes
-            const R* pw = mk_write(g, t) + ks;
+    } else {
 #pragma unroll
-            for (int i = 0; i < 6; ++i) ek_prev[i] = pw[21 + i];
+        for (int i = 0; i < 6; ++i) Pm[i] = R(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { Pm[pk(i, i)] = R(1); qm[i] = R(0); }   // idle lanes: any positive definite matrix
+    }
+    if constexpr (FEAT) tr_pm = Pm[0] + Pm[2] + Pm[5];
+    R Lm[6], im[3], rm;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) Lm[i] = Pm[i];
+    bool ok_m = chol_packed<R, 3>(Lm, im, rm);
+
+    // FP64 where FP32 cannot take an incoming precision (decided here, from
+    // iteration-t state only; the messages are formed after the
+    // relinearisation test)
+    bool m64 = false, k64 = false;
+    if (sizeof(R) == 4 && P.fallback && active) {
+        if (!ok_m) {
+            Arr9<R> pq;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) pq.v[i] = Pm[i];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) pq.v[6 + i] = qm[i];
+            ok_m = lm_incoming_ok64<R>(pq);
+            m64 = ok_m;
+            // kept for the FP64 message in this factor's (per-iteration)
+            // expanded-message slot, which is rewritten below
+            if (m64)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) g.mlx[(size_t)i * n_f + f] = pq.v[i];
+            atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
         }
-        float tr_pk = 0.0f, tr_pm = 0.0f, tr_lk = 0.0f;
+        if (!(ks.det >= P.cav_ratio)) {
+            ok_k = kf_incoming_ok64<R>(KfCavity<R>{kbp, mk_read(g, t), g.kj, g.kf_D + (size_t)k * 6,
+                                                   g.kf_A + (size_t)k * 6, g.kf_off[k], g.kf_off[k + 1], slot,
+                                                   kf_prior_scale(g, P, k, t), P.anchor_scale, P.inv_sigma2});
+            k64 = ok_k;
+            atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
+        }
+    }
+    if (active && !ok_m) atomicAdd(&g.ctl[CTL_HELD], 1);
+    if (active && !ok_k) atomicAdd(&g.ctl[CTL_HELD], 1);
 
-        // ---- message to the keyframe: marginalise the landmark ----
-        // incoming = landmark belief / this factor's previous message to it
-        {
-            R Pm[6], qm[3];
-            if (whole) {
-                const R sp = lm_prior_scale(g, P, m, t) * P.inv_sigma2;
+    // 3. Sec. 5 / Sec. 8: relinearise when the adjacent means moved more than
+    // beta from the linearisation point, at most every relin_interval
+    // iterations -- unless a message of this factor is kept this iteration
+    R cl[NML];            // the new message to the landmark: M00 M01 M11 g0 g1
 #pragma unroll
-                for (int i = 0; i < 6; ++i) Pm[i] = cav[i];
+    for (int i = 0; i < NML; ++i) cl[i] = cml[i];   // kept unless formed below
+    bool rebased = false;
+    if (due && ok_m && ok_k) {
+        R d2 = R(0);
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    Pm[pk(i, i)] += sp * g.lm_D[m * 3 + i];
-                    qm[i] = cav[6 + i];
-                }
-            } else {
+        for (int i = 0; i < 6; ++i) d2 += (kmu[i] - x0[i]) * (kmu[i] - x0[i]);
 #pragma unroll
-                for (int i = 0; i < 6; ++i) Pm[i] = lb[i] - ml[i];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) qm[i] = lb[6 + i] - ml[6 + i];
-            }
-            if constexpr (FEAT) tr_pm = float(Pm[0] + Pm[2] + Pm[5]);
-            R lam_k[21], eta_k[6], ratio_m;
-            bool ok_m = message<R, 6, 3>(Pm, qm, L.Jl, L.Jk, L.y, L.W, lam_k, eta_k, ratio_m);
-            if (sizeof(R) == 4 && P.fallback && !ok_m) {
-                R* o = mk_write(g, t) + ks;
-                ok_m = message_fp64<R, false>(g.x0, n_f, f, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3,
-                                              g.lm_ref + (size_t)m * 3, g.z + 2 * (size_t)f,
-                                              g.lm_bel + (size_t)m * LBEL, g.ml + f, n_f, KfCavity<R>{}, o, 1,
-                                              double(P.fx), double(P.fy), double(P.cx), double(P.cy),
-                                              double(P.inv_sigma2), double(P.inv_sigma), double(P.huber_n),
-                                              double(P.z_min));
-#pragma unroll
-                for (int i = 0; i < 21; ++i) lam_k[i] = o[i];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) eta_k[i] = o[21 + i];
-                atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
-            }
-            // an incoming precision that is not positive definite even in
-            // FP64 (rounding of stored FP32 messages in a direction the prior
-            // barely constrains) leaves the message at its previous value
-            if (!ok_m) atomicAdd(&g.ctl[CTL_HELD], 1);
-            // incoming for the landmark side: keyframe belief / this
-            // factor's previous message to the keyframe (read before the new
-            // message overwrites it)
-            R Pk[21], qk[6];
-            {
-                R kb[28], mk[KREC];
-                load_rec_cg<R, 28>(kbp, kb);
-                load_rec<R, KREC>(mk_read(g, t) + ks, mk);
-#pragma unroll
-                for (int i = 0; i < 21; ++i) Pk[i] = kb[i] - mk[i];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) qk[i] = kb[21 + i] - mk[21 + i];
-                if (!ok_m) {   // held
-#pragma unroll
-                    for (int i = 0; i < 21; ++i) lam_k[i] = mk[i];
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) eta_k[i] = mk[21 + i];
-                }
-                if constexpr (FEAT) {
-                    tr_pk = float(Pk[0] + Pk[2] + Pk[5] + Pk[9] + Pk[14] + Pk[20]);
-                    tr_lk = float(lam_k[0] + lam_k[2] + lam_k[5] + lam_k[9] + lam_k[14] + lam_k[20]);
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) {
-                        ek_new[i] = eta_k[i];
-                        ek_old[i] = mk[21 + i];
-                    }
-                }
-                // damping of eta (Sec. 5); undamped in the iteration of a
-                // (re)linearisation and for the next damp_hold - 1
-                // iterations (Sec. 8)
-                if (damp) {
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) eta_k[i] = (R(1) - d) * eta_k[i] + d * mk[21 + i];
-                }
-            }
-            // the keyframe-side fallback (rare) re-reads the previous
-            // landmark-side message, which is still intact here
-            R out[KREC];
-#pragma unroll
-            for (int i = 0; i < 21; ++i) out[i] = lam_k[i];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) out[21 + i] = eta_k[i];
-            out[27] = R(0);
-            store_rec<R, KREC>(mk_write(g, t) + ks, out);
-
-            // ---- message to the landmark: marginalise the keyframe (6x6) ----
-            R lam_m[6], eta_m[3], ratio_k;
-            bool ok_k = message<R, 3, 6>(Pk, qk, L.Jk, L.Jl, L.y, L.W, lam_m, eta_m, ratio_k);
-            if (sizeof(R) == 4 && P.fallback && (!ok_k || ratio_k < P.pivot_ratio)) {
-                R* o = g.ml_out + f;
-                const KfCavity<R> kc{mk_read(g, t), g.kf_off, g.kf_D + (size_t)k * 6, g.kf_A + (size_t)k * 6, k,
-                                     int(ks / KREC), kf_prior_scale(g, P, k, t), P.anchor_scale, P.inv_sigma2};
-                ok_k = message_fp64<R, true>(g.x0, n_f, f, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3,
-                                             g.lm_ref + (size_t)m * 3, g.z + 2 * (size_t)f,
-                                             g.kf_bel + (size_t)k * KBEL, mk_read(g, t) + ks, 1, kc, o, n_f,
-                                             double(P.fx), double(P.fy), double(P.cx), double(P.cy),
-                                             double(P.inv_sigma2), double(P.inv_sigma), double(P.huber_n),
-                                             double(P.z_min));
-#pragma unroll
-                for (int i = 0; i < 6; ++i) lam_m[i] = o[(size_t)i * n_f];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) eta_m[i] = o[(size_t)(6 + i) * n_f];
-                atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
-            }
-            if (!ok_k) {   // held, as above
-                atomicAdd(&g.ctl[CTL_HELD], 1);
-#pragma unroll
-                for (int i = 0; i < 6; ++i) lam_m[i] = ml[i];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) eta_m[i] = ml[6 + i];
-            }
-            if constexpr (FEAT) {
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    em_new[i] = eta_m[i];
-                    em_old[i] = ml[6 + i];
-                }
-                const float tr_lm = float(lam_m[0] + lam_m[2] + lam_m[5]);
-                const float M = float(sqrt(L.r2) * P.inv_sigma);
-                const float ck = rel_change<R, 6>(ek_new, ek_old);
-                const float cm = rel_change<R, 3>(em_new, em_old);
-                const R em_prev[3] = {R(h[4]), R(h[5]), R(h[6])};
-                feat[0] = log1pf(M) * (1.0f / 3.0f);
-                feat[1] = float(L.W / P.inv_sigma2);
-                feat[2] = tr_lk / (tr_lk + tr_pk + 1e-30f);
-                feat[3] = tr_lm / (tr_lm + tr_pm + 1e-30f);
-                feat[4] = ck;
-                feat[5] = h[0];
-                feat[6] = h[1];
-                feat[7] = step_cosine<R, 6>(ek_new, ek_old, ek_prev);
-                feat[8] = cm;
-                feat[9] = h[2];
-                feat[10] = h[3];
-                feat[11] = step_cosine<R, 3>(em_new, em_old, em_prev);
-                feat[12] = log1pf(float(deg_k)) * 0.2f;
-                feat[13] = log1pf(float(hi - lo)) * (1.0f / 3.0f);
-                feat[14] = float(min(t - tl, 50)) * 0.02f;
-                feat[15] = float(min(t - birth_m, 50)) * 0.02f;
-                const float hn[HIST] = {ck, h[0], cm, h[2], float(em_old[0]), float(em_old[1]), float(em_old[2]), 0.0f};
-#pragma unroll
-                for (int j = 0; j < HIST; ++j) g.hist[(size_t)j * n_f + f] = hn[j];
-                if constexpr (MODE == DAMP_RECORD) {
-                    R ik[6], im[3];
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) ik[i] = g.eta_inf[(size_t)i * n_f + f];
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) im[i] = g.eta_inf[(size_t)(6 + i) * n_f + f];
-                    bool vk, vm;
-                    const float dk = damping_vertex<R, 6>(ek_new, ek_old, ik, vk);
-                    const float dm = damping_vertex<R, 3>(em_new, em_old, im, vm);
-                    float target = (vk || vm) ? fminf(fmaxf((dk * float(vk) + dm * float(vm)) /
-                                                            float(int(vk) + int(vm)), 0.0f), MLP_DMAX)
-                                              : -1.0f;
-                    // samples the learned schedule never damps: the hold after
-                    // a (re)linearisation, a factor behind the camera
-                    if (t - tl < P.damp_hold || !(L.W > R(0))) target = -1.0f;
-                    float4* xo = reinterpret_cast<float4*>(g.rec_X + (size_t)f * N_FEAT);
-#pragma unroll
-                    for (int j = 0; j < N_FEAT / 4; ++j)
-                        xo[j] = make_float4(feat[4 * j], feat[4 * j + 1], feat[4 * j + 2], feat[4 * j + 3]);
-                    g.rec_T[f] = target;
-                }
-            }
-            if (damp) {
-#pragma unroll
-                for (int i = 0; i < 3; ++i) eta_m[i] = (R(1) - d) * eta_m[i] + d * ml[6 + i];
-            }
+        for (int i = 0; i < 3; ++i) d2 += (lb_mu[i] - x0[6 + i]) * (lb_mu[i] - x0[6 + i]);
+        if (d2 > P.relin_beta * P.relin_beta) {
+            Arr9<R> xn;
+            Arr12<R> Jo;
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
-                g.ml_out[(size_t)i * n_f + f] = lam_m[i];
-                sum[i] = lam_m[i];
+                xn.v[i] = kmu[i];
+                Jo.v[i] = L.Jk[0][i];
+                Jo.v[6 + i] = L.Jk[1][i];
             }
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                g.ml_out[(size_t)(6 + i) * n_f + f] = eta_m[i];
-                sum[6 + i] = eta_m[i];
+            for (int i = 0; i < 3; ++i) xn.v[6 + i] = lb_mu[i];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                x0[i] = xn.v[i];
+                g.x0[(size_t)i * n_f + f] = xn.v[i];
+            }
+            tl = t;
+            g.tlin[f] = t;
+            atomicAdd(&g.ctl[CTL_RELINS], 1);
+            rebased = true;
+            const Rebased<R> rb = rebase<R>(kbp, Jo, mo[3], mo[4], ks.a0, ks.a1, ks.K00, ks.K01, ks.K11, !k64, xn,
+                                            lin_args<R>(P, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3,
+                                                        g.lm_ref + (size_t)m * 3, g.z[2 * (size_t)f],
+                                                        g.z[2 * (size_t)f + 1]));
+            L = rb.L;
+            store_lin<R>(g, f, L);
+            store_jac<R>(g.kjs + (size_t)slot * KJ, L.Jk);
+            if (!k64)
+#pragma unroll
+                for (int i = 0; i < NML; ++i) cl[i] = rb.cl[i];
+        }
+    }
+
+    // 4. the new messages (compact), in the basis of L
+    R ck[NML];           // to the keyframe
+    if (!ok_m) {
+#pragma unroll
+        for (int i = 0; i < NML; ++i) ck[i] = mo[i];
+    } else if (m64) {
+        Arr9<R> pq;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) pq.v[i] = g.mlx[(size_t)i * n_f + f];
+        const Msg5<R> o = lm_message64<R>(pq, L);
+#pragma unroll
+        for (int i = 0; i < NML; ++i) ck[i] = o.v[i];
+    } else {
+        message_chol<R, 3>(Lm, im, qm, L.Jl, L.y, L.W, ck);
+    }
+    if (ok_k) {
+        if (k64) {
+            const Msg5<R> o = kf_message64<R>(
+                KfCavity<R>{kbp, mk_read(g, t), g.kj, g.kf_D + (size_t)k * 6, g.kf_A + (size_t)k * 6, g.kf_off[k],
+                            g.kf_off[k + 1], slot, kf_prior_scale(g, P, k, t), P.anchor_scale, P.inv_sigma2},
+                L);
+#pragma unroll
+            for (int i = 0; i < NML; ++i) cl[i] = o.v[i];
+        } else if (!rebased) {
+            message_to_landmark<R>(ks, L.y, L.W, cl);
+        }
+    }
+
+    // features of the learned schedule and targets of the record schedule
+    float feat[N_FEAT];
+#pragma unroll
+    for (int i = 0; i < N_FEAT; ++i) feat[i] = 0.0f;
+    R ek_new[6], em_new[3];
+    if constexpr (FEAT) {
+        msg_eta<R, 6>(L.Jk, ck[3], ck[4], ek_new);
+        msg_eta<R, 3>(L.Jl, cl[3], cl[4], em_new);
+        if (active) {
+            const float tr_lk = float(msg_trace<R, 6>(L.Jk, ck[0], ck[1], ck[2]));
+            const float tr_lm = float(msg_trace<R, 3>(L.Jl, cl[0], cl[1], cl[2]));
+            const float M = float(sqrt(L.r2) * P.inv_sigma);
+            const float cfk = rel_change<R, 6>(ek_new, ek_old);
+            const float cfm = rel_change<R, 3>(em_new, em_old);
+            const R em_prev[3] = {R(h[4]), R(h[5]), R(h[6])};
+            feat[0] = log1pf(M) * (1.0f / 3.0f);
+            feat[1] = float(L.W / P.inv_sigma2);
+            feat[2] = tr_lk / (tr_lk + float(tr_pk) + 1e-30f);
+            feat[3] = tr_lm / (tr_lm + float(tr_pm) + 1e-30f);
+            feat[4] = cfk;
+            feat[5] = h[0];
+            feat[6] = h[1];
+            // the three keyframe messages share one basis only from t_lin + 2 on
+            feat[7] = t - tl >= 2 ? step_cosine<R, 6>(ek_new, ek_old, ek_prev) : 0.0f;
+            feat[8] = cfm;
+            feat[9] = h[2];
+            feat[10] = h[3];
+            feat[11] = step_cosine<R, 3>(em_new, em_old, em_prev);
+            feat[12] = log1pf(float(deg_k)) * 0.2f;
+            feat[13] = log1pf(float(hi - lo)) * (1.0f / 3.0f);
+            feat[14] = float(min(t - tl, 50)) * 0.02f;
+            feat[15] = float(min(t - birth_m, 50)) * 0.02f;
+            const float hn[HIST] = {cfk, h[0], cfm, h[2], float(em_old[0]), float(em_old[1]), float(em_old[2]), 0.0f};
+#pragma unroll
+            for (int j = 0; j < HIST; ++j) g.hist[(size_t)j * n_f + f] = hn[j];
+            if constexpr (MODE == DAMP_RECORD) {
+                R ik[6], imm[3];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) ik[i] = g.eta_inf[(size_t)i * n_f + f];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) imm[i] = g.eta_inf[(size_t)(6 + i) * n_f + f];
+                bool vk, vm;
+                const float dk = damping_vertex<R, 6>(ek_new, ek_old, ik, vk);
+                const float dm = damping_vertex<R, 3>(em_new, em_old, imm, vm);
+                float target = (vk || vm) ? fminf(fmaxf((dk * float(vk) + dm * float(vm)) /
+                                                        float(int(vk) + int(vm)), 0.0f), MLP_DMAX)
+                                          : -1.0f;
+                // samples the learned schedule never damps: the hold after
+                // a (re)linearisation, a factor behind the camera
+                if (t - tl < P.damp_hold || !(L.W > R(0))) target = -1.0f;
+                float4* xo = reinterpret_cast<float4*>(g.rec_X + (size_t)f * N_FEAT);
+#pragma unroll
+                for (int j = 0; j < N_FEAT / 4; ++j)
+                    xo[j] = make_float4(feat[4 * j], feat[4 * j + 1], feat[4 * j + 2], feat[4 * j + 3]);
+                g.rec_T[f] = target;
             }
         }
     }
 
+    // 5. damping of eta (Sec. 5), i.e. of g: the message sent in the
+    // iteration of a (re)linearisation and the next damp_hold - 1 are
+    // undamped (Sec. 8); the learned schedule damps after the network
+    if constexpr (MODE != DAMP_LEARNED) {
+        if (active && t - tl >= P.damp_hold) {
+            const R d = P.damping;
+            if (ok_m) {
+                ck[3] = (R(1) - d) * ck[3] + d * mo[3];
+                ck[4] = (R(1) - d) * ck[4] + d * mo[4];
+            }
+            if (ok_k) {
+                cl[3] = (R(1) - d) * cl[3] + d * cml[3];
+                cl[4] = (R(1) - d) * cl[4] + d * cml[4];
+            }
+        }
+    }
     if constexpr (MODE == DAMP_LEARNED) {
         // the network for the warp's 32 factors (inactive lanes: zero rows),
-        // then eta damped by each factor's own d wherever the fixed schedule
+        // then g damped by each factor's own d wherever the fixed schedule
         // would damp (after the undamped hold of Sec. 8)
         const int w = threadIdx.x >> 5;
-        const bool damp_f = active && t - tl_f >= P.damp_hold;
+        const bool damp_f = active && t - tl >= P.damp_hold;
         if (weights_pending) mlp_load_wait();   // uniform per block: every warp of the block passes here once
         if (__any_sync(0xffffffffu, damp_f)) {   // uniform per warp: skipped while every lane is in its hold
             __nv_bfloat16* xt = reinterpret_cast<__nv_bfloat16*>(S.x[w]);
@@ -1158,17 +1551,38 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
             if (!(dl >= 0.0f && dl <= MLP_DMAX)) dl = float(P.damping);
             if (damp_f) {
                 const R dd = R(dl);
-                R* o = mk_write(g, t) + ks_f;
-#pragma unroll
-                for (int i = 0; i < 6; ++i) o[21 + i] = (R(1) - dd) * ek_new[i] + dd * ek_old[i];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const R e = (R(1) - dd) * em_new[i] + dd * em_old[i];
-                    g.ml_out[(size_t)(6 + i) * n_f + f] = e;
-                    sum[6 + i] = e;
+                if (ok_m) {
+                    ck[3] = (R(1) - dd) * ck[3] + dd * mo[3];
+                    ck[4] = (R(1) - dd) * ck[4] + dd * mo[4];
+                }
+                if (ok_k) {
+                    cl[3] = (R(1) - dd) * cl[3] + dd * cml[3];
+                    cl[4] = (R(1) - dd) * cl[4] + dd * cml[4];
                 }
             }
         }
+    }
+
+    // stores: the keyframe record (with the t_lin of its basis), the new
+    // basis for the belief phase when it changed, the landmark message
+    R sum[9];
+    if (active) {
+        R rec[KREC];
+#pragma unroll
+        for (int i = 0; i < NML; ++i) rec[i] = ck[i];
+        rec[KREC_TL] = int_bits<R>(tl);
+        rec[6] = R(0);
+        rec[7] = R(0);
+        store_rec<R, KREC>(mk_write(g, t) + (size_t)slot * KREC, rec);
+#pragma unroll
+        for (int i = 0; i < NML; ++i) g.ml_out[(size_t)i * n_f + f] = cl[i];
+        expand_msg<R, 3>(L.Jl, cl[0], cl[1], cl[2], cl[3], cl[4], sum, sum + 6);
+        if (!whole)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g.mlx[(size_t)i * n_f + f] = sum[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) sum[i] = R(0);
     }
 
     // landmarks wholly inside the tile: segmented inclusive scan over the
@@ -1182,10 +1596,13 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
         }
     }
     float dmu = 0.0f;
-    if (whole && lane == hi - ts - 1)
-        dmu = finish_landmark<R>(g, P, m, lm_prior_scale(g, P, m, t + 1), sum, mu_m_old, g.lm_bel_out);
+    if (whole && lane == hi - ts - 1) {
+        dmu = finish_landmark<R>(g, P, m, lm_prior_scale(g, P, m, t + 1), sum, lb_mu, g.lm_bel_out);
+    }
     return dmu;
 }
+
+
 
 // ------------------------------------------------------------------------
 // Phase B: one group of threads per work item -- one warp, or the whole
@@ -1263,19 +1680,30 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
                 prior[i] = (sp * g.kf_D[k * 6 + i] + P.anchor_scale * g.kf_A[k * 6 + i]) * P.inv_sigma2;
-                mu_old[i] = __ldcg(old + 27 + i);
+                mu_old[i] = __ldcg(old + KB_MU + i);
             }
         }
         R hi[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) hi[j] = R(0);
         const int b0 = g.kf_off[k], b1 = g.kf_off[k + 1];
-#pragma unroll 4
+#pragma unroll 2
         for (int i = b0 + tg; i < b1; i += gsize) {
-            R rec[KREC];
+            // the compact message m^{t+1} and the Jacobian block it is in: the
+            // staged new block when its factor (re)linearised in iteration t
+            // (which then becomes the slot's block)
+            R rec[KREC], jr[KJ];
             load_rec_cg<R, KREC>(msgs + (size_t)i * KREC, rec);
+            const bool fresh = bits_int<R>(rec[KREC_TL]) == t;
+            load_rec_cg<R, KJ>((fresh ? g.kjs : g.kj) + (size_t)i * KJ, jr);
+            if (fresh) store_rec<R, KJ>(g.kj + (size_t)i * KJ, jr);
+            const R J[2][6] = {{jr[0], jr[1], jr[2], jr[3], jr[4], jr[5]}, {jr[6], jr[7], jr[8], jr[9], jr[10], jr[11]}};
+            R lam[21], eta[6];
+            expand_msg<R, 6>(J, rec[0], rec[1], rec[2], rec[3], rec[4], lam, eta);
 #pragma unroll
-            for (int j = 0; j < 27; ++j) hi[j] += rec[j];
+            for (int j = 0; j < 21; ++j) hi[j] += lam[j];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) hi[21 + j] += eta[j];
         }
         R acc[27];
         group_total<R, 32, 27, W>(hi, acc);
@@ -1288,7 +1716,7 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
         const int b0 = g.lm_off[m], b1 = g.lm_off[m + 1];
         for (int f = b0 + tg; f < b1; f += gsize) {
 #pragma unroll
-            for (int j = 0; j < 9; ++j) hi[j] += __ldcg(g.ml_out + (size_t)j * g.n_f + f);
+            for (int j = 0; j < 9; ++j) hi[j] += __ldcg(g.mlx + (size_t)j * g.n_f + f);
         }
         R acc[9];
         group_total<R, 16, 9, W>(hi, acc);
@@ -1304,13 +1732,12 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
             const int v = g.orphan[i];
             const R isig2 = P.inv_sigma2;
             if (v < g.n_kf) {
-                R out[KBEL];
-#pragma unroll
-                for (int j = 0; j < KBEL; ++j) out[j] = R(0);
+                R p[6], out[KBEL];
 #pragma unroll
                 for (int q = 0; q < 6; ++q)
-                    out[pk(q, q)] = (kf_prior_scale(g, P, v, t + 1) * g.kf_D[v * 6 + q] +
-                                     P.anchor_scale * g.kf_A[v * 6 + q]) * isig2;
+                    p[q] = (kf_prior_scale(g, P, v, t + 1) * g.kf_D[v * 6 + q] + P.anchor_scale * g.kf_A[v * 6 + q]) *
+                           isig2;
+                kf_prior_record<R>(p, out);
                 store_rec<R, KBEL>(g.kf_bel_out + (size_t)v * KBEL, out);
             } else {
                 const int mm = v - g.n_kf;
@@ -1500,12 +1927,10 @@ __global__ void init_beliefs_kernel(DevGraph<R> g, KParams<R> P) {
     const R isig2 = P.inv_sigma2;
     if (v < g.n_kf) {
         const R s = kf_prior_scale(g, P, v, g.kf_birth[v]);
-        R out[KBEL];
+        R p[6], out[KBEL];
 #pragma unroll
-        for (int j = 0; j < KBEL; ++j) out[j] = R(0);
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-            out[pk(i, i)] = (s * g.kf_D[v * 6 + i] + P.anchor_scale * g.kf_A[v * 6 + i]) * isig2;
+        for (int i = 0; i < 6; ++i) p[i] = (s * g.kf_D[v * 6 + i] + P.anchor_scale * g.kf_A[v * 6 + i]) * isig2;
+        kf_prior_record<R>(p, out);
         store_rec<R, KBEL>(g.kf_bel + (size_t)v * KBEL, out);
     } else if (v < g.n_kf + g.n_lm) {
         const int m = v - g.n_kf;
@@ -1602,7 +2027,8 @@ __global__ void __launch_bounds__(METRIC_BLOCK) metrics_kernel(DevGraph<R> g, KP
         const int k = g.fk[f], m = g.fm[f];
         const R* kb = g.kf_bel + (size_t)k * KBEL;
         const R* lb = g.lm_bel + (size_t)m * LBEL;
-        R x[9] = {kb[27], kb[28], kb[29], kb[30], kb[31], kb[32], lb[9], lb[10], lb[11]};
+        R x[9] = {kb[KB_MU], kb[KB_MU + 1], kb[KB_MU + 2], kb[KB_MU + 3], kb[KB_MU + 4], kb[KB_MU + 5],
+                   lb[9], lb[10], lb[11]};
         KParams<R> Q = P;
         Q.huber_n = R(0);
         Lin<R> L;
@@ -1637,7 +2063,8 @@ __global__ void __launch_bounds__(METRIC_BLOCK) metrics_ref_kernel(DevGraph<R> g
         const int k = g.fk[f], m = g.fm[f];
         const R* kb = g.kf_bel + (size_t)k * KBEL;
         const R* lb = g.lm_bel + (size_t)m * LBEL;
-        R x[9] = {kb[27], kb[28], kb[29], kb[30], kb[31], kb[32], lb[9], lb[10], lb[11]};
+        R x[9] = {kb[KB_MU], kb[KB_MU + 1], kb[KB_MU + 2], kb[KB_MU + 3], kb[KB_MU + 4], kb[KB_MU + 5],
+                   lb[9], lb[10], lb[11]};
         KParams<R> Q = P;
         Q.huber_n = R(0);
         Lin<R> L;
@@ -1678,7 +2105,8 @@ __global__ void __launch_bounds__(METRIC_BLOCK) problem_metrics_kernel(DevGraph<
         const int k = g.fk[f], m = g.fm[f];
         const R* kb = g.kf_bel + (size_t)k * KBEL;
         const R* lb = g.lm_bel + (size_t)m * LBEL;
-        R x[9] = {kb[27], kb[28], kb[29], kb[30], kb[31], kb[32], lb[9], lb[10], lb[11]};
+        R x[9] = {kb[KB_MU], kb[KB_MU + 1], kb[KB_MU + 2], kb[KB_MU + 3], kb[KB_MU + 4], kb[KB_MU + 5],
+                   lb[9], lb[10], lb[11]};
         KParams<R> Q = P;
         Q.huber_n = R(0);
         Lin<R> L;
@@ -1794,16 +2222,25 @@ cudaError_t launch_persistent(const DevGraph<R>& g, const KParams<R>& p, int n_i
 
 // The current messages' eta in factor order (keyframe side 6, landmark side
 // 3; SoA 9 x n_f): the reference of the record schedule's damping targets.
+// Both messages of a factor are in the basis of its current Jacobian, whose
+// keyframe block the slot's kj record holds (the landmark block is minus its
+// first three columns).
 template <typename R>
 __global__ void capture_messages_kernel(DevGraph<R> g, const R* __restrict__ mk_cur, R* __restrict__ eta_inf) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= g.n_f) return;
     const size_t n_f = g.n_f;
     const R* rec = mk_cur + (size_t)g.kpos[f] * KREC;
+    const R* jr = g.kj + (size_t)g.kpos[f] * KJ;
+    const R J[2][6] = {{jr[0], jr[1], jr[2], jr[3], jr[4], jr[5]}, {jr[6], jr[7], jr[8], jr[9], jr[10], jr[11]}};
+    const R Jl[2][3] = {{-jr[0], -jr[1], -jr[2]}, {-jr[6], -jr[7], -jr[8]}};
+    R ek[6], el[3];
+    msg_eta<R, 6>(J, rec[3], rec[4], ek);
+    msg_eta<R, 3>(Jl, g.ml[3 * n_f + f], g.ml[4 * n_f + f], el);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) eta_inf[i * n_f + f] = rec[21 + i];
+    for (int i = 0; i < 6; ++i) eta_inf[i * n_f + f] = ek[i];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) eta_inf[(6 + i) * n_f + f] = g.ml[(6 + i) * n_f + f];
+    for (int i = 0; i < 3; ++i) eta_inf[(6 + i) * n_f + f] = el[i];
 }
 
 template <typename R>
