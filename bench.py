@@ -303,6 +303,7 @@ def measure_at_scale(gbp, stream, rank=0, world=1, n_problems=256, iters=20, lau
         mode, ms1, ms2 = launch_mode, None, None
     else:
         mode, ms1, ms2 = g.autotune(8)
+    tuning = g.tuning()
     import torch
     torch.cuda.nvtx.range_push("bench_scale")
     iter_ms, fac_ms = g.profile(iters)
@@ -319,7 +320,7 @@ def measure_at_scale(gbp, stream, rank=0, world=1, n_problems=256, iters=20, lau
                         f"graph ({n_kf} keyframes, {n_lm} points, {n_f} factors)",
             "value": job_f / (job_ms * 1e-3), "unit": UNIT, "ms_per_iteration": job_ms,
             "ranks": world, "partition": "size-balanced (largest first to the least-loaded rank)",
-            "autotune_ms_per_iteration": {"persistent": ms1, "per_phase": ms2},
+            "autotune_ms_per_iteration": {"persistent": ms1, "per_phase": ms2}, "tuning": tuning,
             "roofline": roofline(sz, iter_ms, fac_ms, mode, "hbm"), "fp64_fallbacks": st["fp64_fallbacks"]}
 
 
@@ -376,6 +377,7 @@ def run_gpu(args, rank, world, local):
     value = updates / (total_ms / 1e3)
     st_timed = g.stats()
     launches = int(st_timed["kernel_launches"] - launches0)   # counted by the library
+    tuning = g.tuning()
 
     # roofline of one iteration: live CUDA-event timing (profile replays
     # iterations in the mode gbp_iterate used, and the factor kernel alone)
@@ -472,7 +474,7 @@ def run_gpu(args, rank, world, local):
             "roofline": roof, "at_scale": at_scale, "cpu_baseline": cpu,
             "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s},
-            "gpu_launches": launches,
+            "gpu_launches": launches, "tuning": tuning,
             "clocks": clk.summary(),
         }
     g.close()

@@ -81,6 +81,16 @@ typedef struct {
                                    All modes give bitwise identical results.                        */
     int32_t damping_mode;       /* 0: the fixed d above (Sec. 5, Sec. 8); 1: per-factor d predicted by
                                    the damping network given to gbp_set_damping_model (see below)   */
+    int32_t factor_shape;       /* FP32 fixed schedule, per-phase launches: launch shape of the factor
+                                   kernel, -1 = the autotuner's choice (default; before tuning: 1 for
+                                   large graphs, else 0); 0: 128 threads per block, no register
+                                   budget; 1: 128 threads, >= 3 blocks per SM; 2: 128 threads, >= 4
+                                   blocks per SM; 3: 64 threads, no budget.  Every shape gives
+                                   bitwise identical results.                                       */
+    int32_t persistent_shape;   /* FP32 fixed schedule, persistent launches: -1 = autotuned (default;
+                                   before tuning 1); 0, 1, 2: >= 1, 3, 4 blocks per SM (2 only on
+                                   large graphs, which take a warp per belief item; small graphs run
+                                   2 as 1).  Bitwise identical results in every shape.               */
 } gbp_params;
 
 typedef struct {
@@ -228,13 +238,40 @@ gbp_status gbp_get_relin_iters(const gbp_graph* g, int32_t* tlin);
  * reset to iteration 0 afterwards (as gbp_reset()).  Synchronises. */
 gbp_status gbp_profile_iterations(gbp_graph* g, int32_t n_iters, double* ms_out);
 
-/* Autotuner: run n_trial iterations from the current state in each launch
- * mode, timing them with CUDA events, restore the state, and remember the
- * faster mode for launch_mode = 0.  *chosen (nullable) receives 1 or 2;
- * ms_out (nullable, 2 doubles) the mean time per iteration of modes 1 and 2
- * (a mode that cannot launch, e.g. a persistent grid that does not fit,
- * reports -1).  Synchronises the stream. */
+/* Autotuner: run n_trial iterations from the current state in every
+ * candidate launch configuration, timing each with CUDA events after one
+ * untimed run, restoring the state after each, and remember the fastest for
+ * launch_mode = 0 and shapes = -1.  The candidates change no summation
+ * order, so every one gives bitwise identical results: the launch mode
+ * (persistent or per phase) and, for the FP32 fixed schedule, the factor
+ * kernel's threads per block and register budget and the persistent
+ * kernel's register budget.  The warp tile (up to 32 factors, whole
+ * landmarks) is not tuned: it decides which landmarks are summed across
+ * tiles, and so the arithmetic.  *chosen (nullable) receives the chosen
+ * mode; ms_out (nullable, 2 doubles) the best mean time per iteration of
+ * modes 1 and 2 (-1: no candidate of that mode could launch, e.g. a
+ * persistent grid that does not fit).  gbp_get_tuning reports every
+ * candidate.  Synchronises the stream. */
 gbp_status gbp_autotune(gbp_graph* g, int32_t n_trial, int32_t* chosen, double* ms_out);
+
+#define GBP_MAX_TUNING_CANDIDATES 8
+typedef struct {
+    int32_t launch_mode;            /* chosen: 1 persistent, 2 per phase (0: not tuned yet)        */
+    int32_t factor_shape;           /* chosen factor-kernel shape (see gbp_params)                 */
+    int32_t persistent_shape;       /* chosen persistent-kernel shape                              */
+    int32_t factor_threads;         /* threads per block of the chosen factor-kernel shape         */
+    int32_t factor_min_blocks;      /* its blocks-per-SM register budget (1 = none)                */
+    int32_t persistent_min_blocks;  /* the persistent kernel's (1 = none)                          */
+    int32_t tile_factors;           /* factors per warp tile (fixed, see gbp_autotune)             */
+    int32_t n_candidates;           /* candidates timed by the last gbp_autotune                   */
+    int32_t cand_mode[GBP_MAX_TUNING_CANDIDATES];
+    int32_t cand_shape[GBP_MAX_TUNING_CANDIDATES];
+    double  cand_ms[GBP_MAX_TUNING_CANDIDATES];   /* mean ms per iteration, -1: could not launch  */
+} gbp_tuning;
+
+/* The launch configuration in use and the candidates of the last
+ * gbp_autotune (n_candidates = 0 before the first). */
+gbp_status gbp_get_tuning(const gbp_graph* g, gbp_tuning* out);
 
 void gbp_destroy_graph(gbp_graph* g);
 

@@ -144,6 +144,8 @@ struct gbp_graph {
     cudaGraphExec_t exec = nullptr;
     bool built = false;
     int tuned_mode = 0;                         // autotuner's choice (1 or 2), 0 = not tuned
+    int tuned_fshape = -1, tuned_pshape = -1;   // its launch shapes, -1 = not tuned
+    gbp_tuning tuning{};                        // candidates of the last gbp_autotune
     int last_mode = 0;                          // launch mode of the last gbp_iterate()
     int64_t launches = 0;                       // kernels launched (graph replays count their kernels)
     bool pdl = true;                            // programmatic dependent launch between the per-phase kernels
@@ -203,6 +205,29 @@ KParams<R> make_kparams(gbp_graph* g) {
     k.mlp_frag = g->mlp_frag;
     k.mlp_bias = g->mlp_bias;
     return k;
+}
+
+// Launch shapes in use: the parameter if set, else the autotuner's choice,
+// else by size (large graphs -- a warp per belief item -- take >= 3 blocks
+// per SM, which measured fastest there).
+bool tunable(const gbp_graph* g) { return g->storage == 0 && g->prm.damping_mode == 0; }
+int factor_shape(const gbp_graph* g) {
+    if (!tunable(g)) return 0;
+    if (g->prm.factor_shape >= 0) return g->prm.factor_shape;
+    if (g->tuned_fshape >= 0) return g->tuned_fshape;
+    return g->sf.g.b_warps == 1 ? 1 : 0;
+}
+// Persistent shapes of the graph's belief mapping: all three with the warp
+// mapping; with the block mapping (small graphs) shape 2 is not offered --
+// under that register budget the block reduction compiled to different
+// rounding (measured), so it runs as shape 1.
+int n_persistent_shapes(const gbp_graph* g) { return g->sf.g.b_warps == 1 ? N_PERSISTENT_SHAPES : 2; }
+int persistent_shape(const gbp_graph* g) {
+    if (!tunable(g)) return 0;
+    int s = 1;
+    if (g->prm.persistent_shape >= 0) s = g->prm.persistent_shape;
+    else if (g->tuned_pshape >= 0) s = g->tuned_pshape;
+    return std::min(s, n_persistent_shapes(g) - 1);
 }
 
 void destroy_exec(gbp_graph* g) {
@@ -490,7 +515,7 @@ cudaError_t enqueue_iterations(gbp_graph* g, int n, cudaStream_t st) {
     const DevGraph<R>& d = state<R>(g).g;
     KParams<R> kp = make_kparams<R>(g);
     for (int i = 0; i < n; ++i) {
-        cudaError_t e = launch_factor<R>(d, kp, st, g->prm.damping_mode, g->pdl);
+        cudaError_t e = launch_factor<R>(d, kp, st, g->prm.damping_mode, g->pdl, factor_shape(g));
         if (e != cudaSuccess) return e;
         e = launch_belief<R>(d, kp, st, g->pdl);
         if (e != cudaSuccess) return e;
@@ -572,6 +597,11 @@ gbp_status check_params(const gbp_params* p, std::string& why) {
     if (p->precision_mode < 0 || p->precision_mode > 2) { why = "precision_mode must be 0, 1 or 2"; return GBP_EINVAL; }
     if (p->launch_mode < 0 || p->launch_mode > 2) { why = "launch_mode must be 0, 1 or 2"; return GBP_EINVAL; }
     if (p->damping_mode < 0 || p->damping_mode > 1) { why = "damping_mode must be 0 or 1"; return GBP_EINVAL; }
+    if (p->factor_shape < -1 || p->factor_shape >= N_FACTOR_SHAPES) { why = "factor_shape must be -1 .. 3"; return GBP_EINVAL; }
+    if (p->persistent_shape < -1 || p->persistent_shape >= N_PERSISTENT_SHAPES) {
+        why = "persistent_shape must be -1 .. 2";
+        return GBP_EINVAL;
+    }
     if (!(p->conv_tol >= 0.0f)) { why = "conv_tol must be >= 0"; return GBP_EINVAL; }
     return GBP_OK;
 }
@@ -712,11 +742,14 @@ gbp_status iterate_phases(gbp_graph* g, int n, float conv_tol, int* done_out) {
 // cadence as above) runs on the device.
 gbp_status iterate_persistent(gbp_graph* g, int n, float conv_tol, int* done_out) {
     const int dm = g->prm.damping_mode;
-    const int grid = g->storage ? persistent_grid<double>(g->sd.g, dm) : persistent_grid<float>(g->sf.g, dm);
+    const int ps = persistent_shape(g);
+    const int grid = g->storage ? persistent_grid<double>(g->sd.g, dm, ps) : persistent_grid<float>(g->sf.g, dm, ps);
     if (grid <= 0) return fail(g, GBP_ECUDA, "persistent launch: occupancy query failed");
     cudaError_t e = g->storage
-        ? launch_persistent<double>(g->sd.g, make_kparams<double>(g), n, conv_tol, g->prm.check_every, grid, g->stream, dm)
-        : launch_persistent<float>(g->sf.g, make_kparams<float>(g), n, conv_tol, g->prm.check_every, grid, g->stream, dm);
+        ? launch_persistent<double>(g->sd.g, make_kparams<double>(g), n, conv_tol, g->prm.check_every, grid, g->stream,
+                                    dm, ps)
+        : launch_persistent<float>(g->sf.g, make_kparams<float>(g), n, conv_tol, g->prm.check_every, grid, g->stream,
+                                   dm, ps);
     if (e != cudaSuccess) return cuda_fail(g, e, "cooperative launch");
     g->launches += 1;
     if (conv_tol > 0.0f) {
@@ -976,6 +1009,8 @@ void gbp_default_params(gbp_params* p) {
     p->linear = 0;
     p->launch_mode = 0;
     p->damping_mode = 0;
+    p->factor_shape = -1;
+    p->persistent_shape = -1;
 }
 
 const char* gbp_status_string(gbp_status s) {
@@ -1186,7 +1221,10 @@ gbp_status gbp_set_params(gbp_graph* g, const gbp_params* p) {
     std::string why;
     if (check_params(p, why) != GBP_OK) return fail(g, GBP_EINVAL, why);
     bool sigma_changed = p->sigma_px != g->prm.sigma_px;
-    if (p->precision_mode != g->prm.precision_mode || p->damping_mode != g->prm.damping_mode) g->tuned_mode = 0;
+    if (p->precision_mode != g->prm.precision_mode || p->damping_mode != g->prm.damping_mode) {
+        g->tuned_mode = 0;
+        g->tuned_fshape = g->tuned_pshape = -1;
+    }
     g->prm = *p;
     destroy_exec(g);
     (void)sigma_changed;   // priors are stored at sigma = 1 and scaled in the kernels
@@ -1415,8 +1453,9 @@ gbp_status gbp_profile_iterations(gbp_graph* g, int32_t n_iters, double* ms_out)
         if (e == cudaSuccess) {
             cudaError_t le = cudaSuccess;
             for (int i = 0; i < n_iters && le == cudaSuccess; ++i)
-                le = g->storage ? launch_factor<double>(pd, kd_, g->capture, g->prm.damping_mode)
-                                : launch_factor<float>(pf, kf_, g->capture, g->prm.damping_mode);
+                le = g->storage ? launch_factor<double>(pd, kd_, g->capture, g->prm.damping_mode, false, 0)
+                                : launch_factor<float>(pf, kf_, g->capture, g->prm.damping_mode, false,
+                                                       factor_shape(g));
             e = cudaStreamEndCapture(g->capture, &graph);
             if (le != cudaSuccess) e = le;
         }
@@ -1451,6 +1490,11 @@ gbp_status gbp_autotune(gbp_graph* g, int32_t n_trial, int32_t* chosen, double* 
     if (st != GBP_OK) return st;
     if (g->prm.damping_mode == 1 && !g->has_model)
         return fail(g, GBP_ESTATE, "damping_mode 1 needs a network (gbp_set_damping_model)");
+    // candidates: (mode, shape); only the FP32 fixed schedule has several shapes
+    std::vector<std::pair<int, int>> cand;
+    const int np = tunable(g) ? n_persistent_shapes(g) : 1, nf = tunable(g) ? N_FACTOR_SHAPES : 1;
+    for (int s = 0; s < np; ++s) cand.push_back({1, s});
+    for (int s = 0; s < nf; ++s) cand.push_back({2, s});
     auto bufs = g->storage ? state_buffers<double>(g) : state_buffers<float>(g);
     std::vector<void*> snap(bufs.size(), nullptr);
     cudaError_t e = cudaSuccess;
@@ -1460,8 +1504,14 @@ gbp_status gbp_autotune(gbp_graph* g, int32_t n_trial, int32_t* chosen, double* 
     }
     cudaEvent_t ev[2] = {nullptr, nullptr};
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
-    double ms[2] = {-1.0, -1.0};
-    for (int mode = 1; mode <= 2 && e == cudaSuccess; ++mode) {
+    const gbp_params saved = g->prm;
+    std::vector<double> ms(cand.size(), -1.0);
+    for (size_t c = 0; c < cand.size() && e == cudaSuccess; ++c) {
+        const int mode = cand[c].first;
+        g->prm.launch_mode = mode;
+        g->prm.factor_shape = mode == 2 ? cand[c].second : 0;
+        g->prm.persistent_shape = mode == 1 ? cand[c].second : 0;
+        destroy_exec(g);
         if (mode == 2) {
             st = ensure_exec(g);
             if (st != GBP_OK) break;
@@ -1478,17 +1528,19 @@ gbp_status gbp_autotune(gbp_graph* g, int32_t n_trial, int32_t* chosen, double* 
                 g->err.clear();
                 cudaGetLastError();
                 e = cudaSuccess;
-                ms[mode - 1] = -1.0;
+                ms[c] = -1.0;
             } else if (e == cudaSuccess && rep == 1) {
                 float t = 0.f;
                 e = cudaEventElapsedTime(&t, ev[0], ev[1]);
-                ms[mode - 1] = double(t) / n_trial;
+                ms[c] = double(t) / n_trial;
             }
             for (size_t i = 0; i < bufs.size() && e == cudaSuccess; ++i)
                 e = cudaMemcpyAsync(bufs[i].first, snap[i], bufs[i].second, cudaMemcpyDeviceToDevice, g->stream);
             if (ms_st != GBP_OK) break;
         }
     }
+    g->prm = saved;
+    destroy_exec(g);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     for (auto& x : ev)
         if (x) cudaEventDestroy(x);
@@ -1496,13 +1548,51 @@ gbp_status gbp_autotune(gbp_graph* g, int32_t n_trial, int32_t* chosen, double* 
         if (p) cudaFree(p);
     if (st != GBP_OK) return st;
     if (e != cudaSuccess) return cuda_fail(g, e, "autotune");
-    if (ms[0] < 0 && ms[1] < 0) return fail(g, GBP_ECUDA, "autotune: no launch mode ran");
-    g->tuned_mode = (ms[0] >= 0 && (ms[1] < 0 || ms[0] <= ms[1])) ? 1 : 2;
+    int best = -1;
+    double best_mode[2] = {-1.0, -1.0};
+    for (size_t c = 0; c < cand.size(); ++c) {
+        if (ms[c] < 0) continue;
+        if (best < 0 || ms[c] < ms[best]) best = (int)c;
+        double& bm = best_mode[cand[c].first - 1];
+        if (bm < 0 || ms[c] < bm) bm = ms[c];
+    }
+    if (best < 0) return fail(g, GBP_ECUDA, "autotune: no launch configuration ran");
+    g->tuned_mode = cand[best].first;
+    // each mode keeps its own best shape (launch_mode may force the other)
+    for (size_t c = 0; c < cand.size(); ++c) {
+        if (ms[c] < 0 || ms[c] != best_mode[cand[c].first - 1]) continue;
+        if (cand[c].first == 1 && g->tuned_pshape < 0) g->tuned_pshape = cand[c].second;
+        if (cand[c].first == 2 && g->tuned_fshape < 0) g->tuned_fshape = cand[c].second;
+    }
+    if (!tunable(g)) g->tuned_fshape = g->tuned_pshape = 0;
+    gbp_tuning& T = g->tuning;
+    T.n_candidates = (int32_t)std::min<size_t>(cand.size(), GBP_MAX_TUNING_CANDIDATES);
+    for (int c = 0; c < T.n_candidates; ++c) {
+        T.cand_mode[c] = cand[c].first;
+        T.cand_shape[c] = cand[c].second;
+        T.cand_ms[c] = ms[c];
+    }
     if (chosen) *chosen = g->tuned_mode;
     if (ms_out) {
-        ms_out[0] = ms[0];
-        ms_out[1] = ms[1];
+        ms_out[0] = best_mode[0];
+        ms_out[1] = best_mode[1];
     }
+    return GBP_OK;
+}
+
+gbp_status gbp_get_tuning(const gbp_graph* g, gbp_tuning* out) {
+    if (!g || !out) return GBP_EINVAL;
+    static const int f_threads[N_FACTOR_SHAPES] = {128, 128, 128, 64};
+    static const int f_minb[N_FACTOR_SHAPES] = {1, 3, 4, 1};
+    static const int p_minb[N_PERSISTENT_SHAPES] = {1, 3, 4};
+    *out = g->tuning;
+    out->launch_mode = g->prm.launch_mode ? g->prm.launch_mode : g->tuned_mode;
+    out->factor_shape = factor_shape(g);
+    out->persistent_shape = persistent_shape(g);
+    out->factor_threads = f_threads[out->factor_shape];
+    out->factor_min_blocks = f_minb[out->factor_shape];
+    out->persistent_min_blocks = p_minb[out->persistent_shape];
+    out->tile_factors = 32;
     return GBP_OK;
 }
 

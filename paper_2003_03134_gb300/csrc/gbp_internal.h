@@ -182,15 +182,20 @@ constexpr int METRIC_BLOCK = 256;
 // kernel launchers (gbp_kernels.cu)
 // pdl: programmatic dependent launch (the kernel may start while the
 // previous kernel in the stream finishes; it waits for that kernel's writes)
+// shape: the FP32 fixed schedule's factor-kernel launch shape (autotuned):
+// 0 128 threads, no register budget; 1 128 threads, >= 3 blocks per SM;
+// 2 128 threads, >= 4 blocks per SM; 3 64 threads, no budget
+constexpr int N_FACTOR_SHAPES = 4;
+constexpr int N_PERSISTENT_SHAPES = 3;   // >= 1, 3, 4 blocks per SM
 template <typename R> cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s,
-                                                int mode = DAMP_FIXED, bool pdl = false);
+                                                int mode = DAMP_FIXED, bool pdl = false, int shape = 0);
 template <typename R> cudaError_t launch_init(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s);
 template <typename R> cudaError_t launch_belief(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s,
                                                 bool pdl = false);
-template <typename R> int persistent_grid(const DevGraph<R>& g, int mode);   // co-resident blocks; 0 on error
+template <typename R> int persistent_grid(const DevGraph<R>& g, int mode, int shape);   // co-resident blocks; 0 on error
 template <typename R> cudaError_t launch_persistent(const DevGraph<R>& g, const KParams<R>& p, int n_iters,
                                                     float conv_tol, int check_every, int grid, cudaStream_t s,
-                                                    int mode);
+                                                    int mode, int shape);
 template <typename R> cudaError_t launch_capture_messages(const DevGraph<R>& g, int t, R* eta_inf, cudaStream_t s);
 template <typename R> cudaError_t launch_prior(const DevGraph<R>& g, const KParams<R>& p, R* tmp_k, R* tmp_l,
                                                R* kf_D, R* lm_D, cudaStream_t s);

@@ -1779,13 +1779,13 @@ __device__ __forceinline__ int phase_b_item_of(int W, int block) {
 __device__ __forceinline__ void pdl_allow_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-template <typename R, int MODE>
+template <typename R, int MODE, int NT>
 __device__ __forceinline__ void factor_body(const DevGraph<R>& g, const KParams<R>& P) {
     __shared__ __align__(16) MlpSmem<MODE> S;
     mlp_load_async<MODE>(P, S);   // network weights do not change between iterations
     pdl_wait_prev();
     const int lane = threadIdx.x & 31;
-    const int tile = blockIdx.x * (FACTOR_BLOCK / 32) + (threadIdx.x >> 5);
+    const int tile = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
     const int t = g.ctl[CTL_ITER];
     float dmu = 0.0f;
     if (tile < g.n_tiles) dmu = tile_work<R, MODE>(g, P, tile, t, lane, S, MODE == DAMP_LEARNED);   // uniform per warp
@@ -1798,17 +1798,13 @@ __device__ __forceinline__ void factor_body(const DevGraph<R>& g, const KParams<
     if (blockIdx.x == 0 && threadIdx.x == 0) g.ctl[CTL_ITER_B] = t;
 }
 
-template <typename R, int MODE>
-__global__ void __launch_bounds__(FACTOR_BLOCK) factor_kernel(DevGraph<R> g, KParams<R> P) {
-    factor_body<R, MODE>(g, P);
-}
-
-// The FP32 fixed schedule on large graphs (a warp per belief item): at
-// least 4 blocks per SM (<= 128 registers), trading spills for the
-// occupancy that hides HBM latency; small graphs keep factor_kernel.
-template <typename R, int MODE>
-__global__ void __launch_bounds__(FACTOR_BLOCK, 4) factor_kernel_lg(DevGraph<R> g, KParams<R> P) {
-    factor_body<R, MODE>(g, P);
+// NT threads per block, and at least MINB blocks per SM (the register budget
+// per thread; 1 = no constraint).  Each warp does one tile whatever the
+// shape, so every shape gives bitwise identical results; the FP32 fixed
+// schedule is instantiated in several shapes for the autotuner.
+template <typename R, int MODE, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) factor_kernel(DevGraph<R> g, KParams<R> P) {
+    factor_body<R, MODE, NT>(g, P);
 }
 
 // BW = g.b_warps (warps per belief item), one instantiation per mapping
@@ -1870,13 +1866,13 @@ __device__ __forceinline__ bool grid_barrier(int32_t* ctl, int nblocks, int* fla
     return *flag_sh;
 }
 
-// The FP32 fixed schedule is held to 3 blocks per SM (<= 168 registers), 4
-// (<= 128) with the warp belief mapping (large graphs).
 // BW = g.b_warps (warps per belief item): a separate instantiation per
 // mapping, so that the block mapping's barriers and shared-memory reduction
 // do not weigh on the register allocation of the warp mapping's kernel.
-template <typename R, int MODE, int BW>
-__global__ void __launch_bounds__(FACTOR_BLOCK, (MODE == DAMP_FIXED && sizeof(R) == 4) ? (BW == 1 ? 4 : 3) : 1)
+// MINB: at least this many blocks per SM (the register budget; 1 = none),
+// a launch shape the autotuner chooses for the FP32 fixed schedule.
+template <typename R, int MODE, int BW, int MINB>
+__global__ void __launch_bounds__(FACTOR_BLOCK, MINB)
     persistent_kernel(DevGraph<R> g, KParams<R> P, int n_iters, float conv_tol, int check_every) {
     __shared__ int flag_sh;
     __shared__ __align__(16) MlpSmem<MODE> S;
@@ -2155,10 +2151,10 @@ int metrics_blocks(int n_f) {
 
 // One launch, with programmatic stream serialisation when pdl is set.
 template <typename... KArgs, typename... Args>
-cudaError_t launch_ex(void (*kernel)(KArgs...), int blocks, cudaStream_t s, bool pdl, Args&&... args) {
+cudaError_t launch_ex(void (*kernel)(KArgs...), int blocks, int threads, cudaStream_t s, bool pdl, Args&&... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
-    cfg.blockDim = dim3(FACTOR_BLOCK);
+    cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -2169,41 +2165,63 @@ cudaError_t launch_ex(void (*kernel)(KArgs...), int blocks, cudaStream_t s, bool
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-template <typename R>
-cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s, int mode, bool pdl) {
-    constexpr int wpb = FACTOR_BLOCK / 32;
+template <typename R, int MODE, int NT, int MINB>
+cudaError_t launch_factor_shape(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s, bool pdl) {
+    constexpr int wpb = NT / 32;
     const int blocks = std::max(1, (g.n_tiles + wpb - 1) / wpb);   // >= 1: it also publishes the iteration index
-    if (mode == DAMP_LEARNED) return launch_ex(factor_kernel<R, DAMP_LEARNED>, blocks, s, pdl, g, p);
-    if (mode == DAMP_RECORD) return launch_ex(factor_kernel<R, DAMP_RECORD>, blocks, s, pdl, g, p);
-    if (sizeof(R) == 4 && g.b_warps == 1) return launch_ex(factor_kernel_lg<R, DAMP_FIXED>, blocks, s, pdl, g, p);
-    return launch_ex(factor_kernel<R, DAMP_FIXED>, blocks, s, pdl, g, p);
+    return launch_ex(factor_kernel<R, MODE, NT, MINB>, blocks, NT, s, pdl, g, p);
+}
+
+template <typename R>
+cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s, int mode, bool pdl, int shape) {
+    if (mode == DAMP_LEARNED) return launch_factor_shape<R, DAMP_LEARNED, 128, 1>(g, p, s, pdl);
+    if (mode == DAMP_RECORD) return launch_factor_shape<R, DAMP_RECORD, 128, 1>(g, p, s, pdl);
+    if constexpr (sizeof(R) == 4) {
+        switch (shape) {
+            case 1: return launch_factor_shape<R, DAMP_FIXED, 128, 3>(g, p, s, pdl);
+            case 2: return launch_factor_shape<R, DAMP_FIXED, 128, 4>(g, p, s, pdl);
+            case 3: return launch_factor_shape<R, DAMP_FIXED, 64, 1>(g, p, s, pdl);
+            default: break;
+        }
+    }
+    return launch_factor_shape<R, DAMP_FIXED, 128, 1>(g, p, s, pdl);
 }
 
 template <typename R>
 cudaError_t launch_belief(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s, bool pdl) {
     int blocks = phase_b_blocks(g);
     if (blocks < 1) blocks = 1;
-    if (g.b_warps == FACTOR_BLOCK / 32) return launch_ex(belief_kernel<R, FACTOR_BLOCK / 32>, blocks, s, pdl, g, p);
-    return launch_ex(belief_kernel<R, 1>, blocks, s, pdl, g, p);
+    if (g.b_warps == FACTOR_BLOCK / 32)
+        return launch_ex(belief_kernel<R, FACTOR_BLOCK / 32>, blocks, FACTOR_BLOCK, s, pdl, g, p);
+    return launch_ex(belief_kernel<R, 1>, blocks, FACTOR_BLOCK, s, pdl, g, p);
 }
 
-// the persistent kernel for this graph's belief mapping and damping schedule
+// the persistent kernel for this graph's belief mapping, damping schedule
+// and launch shape (at least 1, 3 or 4 blocks per SM for shape 0, 1, 2 of
+// the FP32 fixed schedule)
+template <typename R, int BW>
+const void* persistent_fn_bw(int mode, int shape) {
+    if (mode == DAMP_LEARNED) return reinterpret_cast<const void*>(persistent_kernel<R, DAMP_LEARNED, BW, 1>);
+    if constexpr (sizeof(R) == 4) {
+        if (shape == 1) return reinterpret_cast<const void*>(persistent_kernel<R, DAMP_FIXED, BW, 3>);
+        if (shape == 2) return reinterpret_cast<const void*>(persistent_kernel<R, DAMP_FIXED, BW, 4>);
+    }
+    return reinterpret_cast<const void*>(persistent_kernel<R, DAMP_FIXED, BW, 1>);
+}
+
 template <typename R>
-const void* persistent_fn(const DevGraph<R>& g, int mode) {
+const void* persistent_fn(const DevGraph<R>& g, int mode, int shape) {
     constexpr int WPB = FACTOR_BLOCK / 32;
-    if (g.b_warps == WPB)
-        return mode == DAMP_LEARNED ? reinterpret_cast<const void*>(persistent_kernel<R, DAMP_LEARNED, WPB>)
-                                    : reinterpret_cast<const void*>(persistent_kernel<R, DAMP_FIXED, WPB>);
-    return mode == DAMP_LEARNED ? reinterpret_cast<const void*>(persistent_kernel<R, DAMP_LEARNED, 1>)
-                                : reinterpret_cast<const void*>(persistent_kernel<R, DAMP_FIXED, 1>);
+    return g.b_warps == WPB ? persistent_fn_bw<R, WPB>(mode, shape) : persistent_fn_bw<R, 1>(mode, shape);
 }
 
 template <typename R>
-int persistent_grid(const DevGraph<R>& g, int mode) {
+int persistent_grid(const DevGraph<R>& g, int mode, int shape) {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_fn(g, mode), FACTOR_BLOCK, 0);
+    const cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_fn(g, mode, shape), FACTOR_BLOCK, 0);
     if (e != cudaSuccess || per_sm <= 0) return 0;
     constexpr int wpb = FACTOR_BLOCK / 32;
     const int cap = sms * per_sm;
@@ -2213,11 +2231,11 @@ int persistent_grid(const DevGraph<R>& g, int mode) {
 
 template <typename R>
 cudaError_t launch_persistent(const DevGraph<R>& g, const KParams<R>& p, int n_iters, float conv_tol,
-                              int check_every, int grid, cudaStream_t s, int mode) {
+                              int check_every, int grid, cudaStream_t s, int mode, int shape) {
     DevGraph<R> gg = g;
     KParams<R> pp = p;
     void* args[] = {&gg, &pp, &n_iters, &conv_tol, &check_every};
-    return cudaLaunchCooperativeKernel(persistent_fn(g, mode), dim3(grid), dim3(FACTOR_BLOCK), args, 0, s);
+    return cudaLaunchCooperativeKernel(persistent_fn(g, mode, shape), dim3(grid), dim3(FACTOR_BLOCK), args, 0, s);
 }
 
 // The current messages' eta in factor order (keyframe side 6, landmark side
@@ -2285,13 +2303,13 @@ cudaError_t launch_problem_metrics(const DevGraph<R>& g, const KParams<R>& p, co
 }
 
 #define GBP_INSTANTIATE(R)                                                                                 \
-    template cudaError_t launch_factor<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t, int, bool); \
+    template cudaError_t launch_factor<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t, int, bool, int); \
     template cudaError_t launch_capture_messages<R>(const DevGraph<R>&, int, R*, cudaStream_t);            \
     template cudaError_t launch_init<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t);              \
     template cudaError_t launch_belief<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t, bool);      \
     template cudaError_t launch_problem_metrics<R>(const DevGraph<R>&, const KParams<R>&, const int32_t*, int, double*, cudaStream_t); \
-    template int persistent_grid<R>(const DevGraph<R>&, int);                                              \
-    template cudaError_t launch_persistent<R>(const DevGraph<R>&, const KParams<R>&, int, float, int, int, cudaStream_t, int); \
+    template int persistent_grid<R>(const DevGraph<R>&, int, int);                                         \
+    template cudaError_t launch_persistent<R>(const DevGraph<R>&, const KParams<R>&, int, float, int, int, cudaStream_t, int, int); \
     template cudaError_t launch_prior<R>(const DevGraph<R>&, const KParams<R>&, R*, R*, R*, R*, cudaStream_t); \
     template cudaError_t launch_metrics<R>(const DevGraph<R>&, const KParams<R>&, double*, int, double*, cudaStream_t);
 

@@ -41,10 +41,29 @@ class gbp_params(C.Structure):
                 ("anchor_scale", C.c_float), ("z_min", C.c_float), ("relin_beta", C.c_float),
                 ("relin_interval", C.c_int32), ("undamped_iters", C.c_int32),
                 ("fp64_pivot_ratio", C.c_float), ("precision_mode", C.c_int32), ("linear", C.c_int32),
-                ("launch_mode", C.c_int32), ("damping_mode", C.c_int32)]
+                ("launch_mode", C.c_int32), ("damping_mode", C.c_int32), ("factor_shape", C.c_int32),
+                ("persistent_shape", C.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+GBP_MAX_TUNING_CANDIDATES = 8
+
+
+class gbp_tuning(C.Structure):
+    _fields_ = [("launch_mode", C.c_int32), ("factor_shape", C.c_int32), ("persistent_shape", C.c_int32),
+                ("factor_threads", C.c_int32), ("factor_min_blocks", C.c_int32),
+                ("persistent_min_blocks", C.c_int32), ("tile_factors", C.c_int32), ("n_candidates", C.c_int32),
+                ("cand_mode", C.c_int32 * GBP_MAX_TUNING_CANDIDATES),
+                ("cand_shape", C.c_int32 * GBP_MAX_TUNING_CANDIDATES),
+                ("cand_ms", C.c_double * GBP_MAX_TUNING_CANDIDATES)]
+
+    def as_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_[:8]}
+        d["candidates"] = [{"launch_mode": self.cand_mode[i], "shape": self.cand_shape[i], "ms": self.cand_ms[i]}
+                           for i in range(self.n_candidates)]
+        return d
 
 
 class gbp_problem_desc(C.Structure):
@@ -75,7 +94,8 @@ EXPORTS = ["gbp_default_params", "gbp_create_graph", "gbp_set_params", "gbp_get_
            "gbp_last_error", "gbp_reprojection_error_noalloc", "gbp_autotune", "gbp_create_batch",
            "gbp_get_batch_info", "gbp_get_problem_are", "gbp_mlp_create", "gbp_mlp_set_params",
            "gbp_mlp_get_params", "gbp_mlp_forward", "gbp_mlp_gradient", "gbp_mlp_train_step", "gbp_mlp_destroy",
-           "gbp_set_damping_model", "gbp_capture_messages", "gbp_get_factor_order", "gbp_record_iterations"]
+           "gbp_set_damping_model", "gbp_capture_messages", "gbp_get_factor_order", "gbp_record_iterations",
+           "gbp_get_relin_iters", "gbp_get_tuning"]
 GBP_MLP_NFEAT = 16
 GBP_MLP_NPARAM = 5313
 GBP_NOALLOC_MAX_OBS = 1 << 20
@@ -108,6 +128,7 @@ def lib() -> C.CDLL:
     L.gbp_get_relin_iters.argtypes = [vp, _I]
     L.gbp_profile_iterations.argtypes = [vp, C.c_int32, _D]
     L.gbp_autotune.argtypes = [vp, C.c_int32, _I, _D]
+    L.gbp_get_tuning.argtypes = [vp, C.POINTER(gbp_tuning)]
     L.gbp_create_batch.argtypes = [C.POINTER(gbp_intrinsics), C.c_int32, C.POINTER(gbp_problem_desc), vp,
                                    C.POINTER(vp)]
     L.gbp_get_batch_info.argtypes = [vp, _I, _I, _I, _I]
@@ -311,6 +332,12 @@ def gbp_autotune(g: int, n_trial: int = 8):
     return chosen.value, float(ms[0]), float(ms[1])
 
 
+def gbp_get_tuning(g: int) -> dict:
+    t = gbp_tuning()
+    _check(lib().gbp_get_tuning(g, C.byref(t)), g)
+    return t.as_dict()
+
+
 def gbp_profile_iterations(g: int, n_iters: int):
     """(mean device ms per iteration in the current launch mode, mean ms of one factor-kernel launch)."""
     out = np.zeros(2)
@@ -477,6 +504,9 @@ class Graph:
 
     def autotune(self, n_trial: int = 8):
         return gbp_autotune(self.h, n_trial)
+
+    def tuning(self) -> dict:
+        return gbp_get_tuning(self.h)
 
     def set_reference(self, kf_Rt, lm_xyz):
         gbp_set_reference(self.h, kf_Rt, lm_xyz)

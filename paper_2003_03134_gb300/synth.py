@@ -105,20 +105,32 @@ def _visible(pc, fx, fy, cx, cy, w, h, min_depth):
 def _weighted_subsets(rng, weights: np.ndarray, counts: np.ndarray):
     """For each row, draw ``counts[row]`` distinct columns without replacement
     with probability proportional to ``weights`` (zero weight = never), by
-    the Gumbel-top-k construction of successive weighted sampling."""
+    the Gumbel-top-k construction of successive weighted sampling: the
+    columns of the ``counts[row]`` largest log-weight + Gumbel keys, in
+    column order."""
     with np.errstate(divide="ignore"):
         logw = np.where(weights > 0, np.log(np.maximum(weights, 1e-300)), -np.inf)
     g = rng.gumbel(size=weights.shape)
     keys = logw + g
-    order = np.argsort(-keys, axis=1, kind="stable")
-    rows, cols = [], []
-    for i, c in enumerate(counts):
-        sel = np.sort(order[i, :c])
-        rows.append(np.full(c, i, dtype=np.int64))
-        cols.append(sel)
-    if not rows:
+    n_rows, n_cols = keys.shape
+    counts = np.asarray(counts, dtype=np.int64)
+    if n_rows == 0 or counts.sum() == 0:
         return np.zeros(0, np.int64), np.zeros(0, np.int64)
-    return np.concatenate(rows), np.concatenate(cols)
+    cmax = int(counts.max())
+    # the cmax largest keys of every row (keys are continuous: no ties), then
+    # their order, then the first counts[row] of them
+    if cmax < n_cols:
+        top = np.argpartition(-keys, cmax - 1, axis=1)[:, :cmax]
+    else:
+        top = np.tile(np.arange(n_cols), (n_rows, 1))
+    tk = np.take_along_axis(keys, top, axis=1)
+    top = np.take_along_axis(top, np.argsort(-tk, axis=1, kind="stable"), axis=1)
+    take = np.arange(top.shape[1])[None, :] < counts[:, None]
+    sel = np.where(take, top, n_cols)          # columns not taken sort last
+    sel = np.sort(sel, axis=1)
+    rows = np.repeat(np.arange(n_rows, dtype=np.int64), counts)
+    cols = sel[np.arange(sel.shape[1])[None, :] < counts[:, None]].astype(np.int64)
+    return rows, cols
 
 
 def _perturb_init(rng, kf_true, lm_true, rot_sigma, pos_sigma, lm_sigma, anchors):

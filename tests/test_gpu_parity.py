@@ -341,6 +341,42 @@ def test_launch_modes_are_bitwise_identical_on_a_large_graph():
         np.testing.assert_array_equal(x, y)
 
 
+@pytest.mark.parametrize("large", [False, True])
+def test_every_autotuner_candidate_gives_bitwise_identical_results(large):
+    """The autotuner chooses among launch configurations that change no
+    summation order (launch mode, threads per block, register budget): a
+    batch solved in every one of them gives the same bits, each problem
+    equal to its own single-problem run, and the tuner reports what it
+    chose.  Small graphs take the block belief mapping, large ones the warp
+    mapping."""
+    probs = (synth.make_batch(6, kf_range=(150, 200), lm_range=(500, 800)) if large else _batch_problems())
+    ref = None
+    for mode, key, n_shapes in ((2, "factor_shape", 4), (1, "persistent_shape", 3)):
+        for s in range(n_shapes):
+            g = gbp.Graph(probs, huber_nsigma=2.0, launch_mode=mode, **{key: s})
+            g.iterate(30)
+            got = g.means()
+            tun = g.tuning()
+            assert tun["launch_mode"] == mode and tun[key] == (s if large or mode == 2 else min(s, 1))
+            g.close()
+            if ref is None:
+                ref = got
+            else:
+                for x, y in zip(ref, got):
+                    np.testing.assert_array_equal(x, y)
+    g = gbp.Graph(probs, huber_nsigma=2.0)
+    chosen, ms1, ms2 = g.autotune(4)
+    tun = g.tuning()
+    assert tun["n_candidates"] == (7 if large else 6) and tun["tile_factors"] == 32
+    assert chosen == tun["launch_mode"] and chosen in (1, 2)
+    best = min(c["ms"] for c in tun["candidates"] if c["ms"] > 0)
+    assert min(x for x in (ms1, ms2) if x > 0) == pytest.approx(best)
+    g.iterate(30)
+    for x, y in zip(ref, g.means()):
+        np.testing.assert_array_equal(x, y)
+    g.close()
+
+
 def test_convergence_stops_at_the_same_iteration_in_both_modes():
     p = synth.make_circle(2)
     done = []
