@@ -262,6 +262,82 @@ def per_belief_error(kf, lm, okf, olm):
             "keyframes_max": float(ek.max()) if ek.size else 0.0}
 
 
+def _oracle_rate(args):
+    """Factor-updates/s of the oracle on problem p over n iterations from the
+    initial estimate (run in a spawned process: the OpenMP build gets its own
+    runtime and the cores the parent set in OMP_NUM_THREADS)."""
+    p, n, omp = args
+    import oracle
+    oracle.build()
+    o = oracle.Oracle(p, omp=omp, **oracle_params())
+    t0 = time.perf_counter()
+    o.iterate(n)
+    return p.n_obs * n / (time.perf_counter() - t0)
+
+
+def oracle_rate_spawned(p, n, omp, cores):
+    import multiprocessing as mp
+    old = os.environ.get("OMP_NUM_THREADS")
+    os.environ["OMP_NUM_THREADS"] = str(cores)
+    try:
+        with mp.get_context("spawn").Pool(1) as pool:
+            return pool.map(_oracle_rate, [(p, n, omp)])[0]
+    finally:
+        if old is None:
+            os.environ.pop("OMP_NUM_THREADS", None)
+        else:
+            os.environ["OMP_NUM_THREADS"] = old
+
+
+def _make_loop_problem(seed):
+    from paper_2003_03134_gb300 import synth
+    return synth.make_loop(seed=seed)
+
+
+# Loop workload target: 50% of the HBM roofline at the paper-form bytes.
+C4_TARGET_FRAC = 0.5
+
+
+def measure_loop(gbp, stream, p, iters=20):
+    """The large single problem (2000 keyframes on two laps of a 30 m loop,
+    200k points, ~2M factors), FP32 with FP64 fallback: per-iteration time,
+    roofline and fallback count; the oracle's rate on its 10% subgraph
+    (keyframes 0-199 and the points they see twice) single-threaded and with
+    OpenMP on every host core."""
+    from paper_2003_03134_gb300 import synth
+    import torch
+    g = gbp.Graph(p, stream=stream.cuda_stream, huber_nsigma=HUBER)
+    n_kf, n_lm, n_f = gbp.gbp_get_sizes(g.h)
+    mode, ms1, ms2 = g.autotune(8)
+    g.iterate(30)
+    st = g.stats()
+    torch.cuda.nvtx.range_push("bench_loop")
+    iter_ms, fac_ms = g.profile(iters)
+    torch.cuda.nvtx.range_pop()
+    tuning = g.tuning()
+    g.close()
+
+    class _Size:
+        pass
+    sz = _Size()
+    sz.n_obs, sz.n_kf, sz.n_lm = n_f, n_kf, n_lm
+    roof = roofline(sz, iter_ms, fac_ms, mode, "hbm")
+    bytes_iter = roof["bytes_per_iteration"]
+    peak = roof["peak"]
+    sub = synth.subgraph(p, 200)
+    cores = cpu_cores()
+    return {"workload": f"loop{n_kf}x{n_lm}: {n_kf} keyframes on two laps of a 30 m loop, {n_lm} points, {n_f} "
+                        "factors, 2% outliers, Huber 2 sigma, d=0.4, FP32 with FP64 fallback",
+            "value": n_f / (iter_ms * 1e-3), "unit": UNIT, "us_per_iteration": iter_ms * 1e3,
+            "target_us_per_iteration": bytes_iter / (C4_TARGET_FRAC * peak * 1e9) * 1e6,
+            "roofline": roof, "fp64_fallbacks_first_30_iterations": st["fp64_fallbacks"],
+            "held_messages": st["held_messages"], "tuning": tuning,
+            "oracle_subgraph": {"factors": sub.n_obs, "keyframes": sub.n_kf, "points": sub.n_lm,
+                                "single_thread": oracle_rate_spawned(sub, 3, False, 1),
+                                "openmp": oracle_rate_spawned(sub, 5, True, cores), "openmp_cores": cores,
+                                "unit": UNIT}}
+
+
 def _batch_counts(seed):
     rng = np.random.Generator(np.random.PCG64(seed))
     return int(rng.integers(10, 201)), int(rng.integers(100, 5001))
@@ -329,6 +405,13 @@ def run_gpu(args, rank, world, local):
     from paper_2003_03134_gb300 import build, gbp, synth
 
     build.build()
+    loop_pool = loop_job = None
+    if rank == 0 and not args.no_loop:
+        # the ~2M-factor loop problem takes ~1.5 min to generate: in a spawned
+        # process while the GPU measures the rest
+        import multiprocessing as mp
+        loop_pool = mp.get_context("spawn").Pool(1)
+        loop_job = loop_pool.apply_async(_make_loop_problem, (0,))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -394,6 +477,13 @@ def run_gpu(args, rank, world, local):
         cpu = {"value": p.n_obs * o_iters / o_dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"one oracle solve of the rank-0 problem, {o_iters} iterations (cap {args.oracle_iters})",
                "ms_to_1px": (1e3 * o_dt / o_iters * o_1px) if o_1px else None}
+        import oracle
+        cpu_omp = None
+        if oracle.omp_available():
+            cores = cpu_cores()
+            cpu_omp = {"value": oracle_rate_spawned(p, 200, True, cores), "unit": UNIT, "cores": cores,
+                       "kind": "oracle, OpenMP build (same arithmetic, same results)",
+                       "sample": "200 oracle iterations of the rank-0 problem from the initial estimate"}
         # iterations and device time to ARE vs oracle < 1 px
         g.set_reference(kf_ref, lm_ref)
         g.reset()
@@ -446,6 +536,11 @@ def run_gpu(args, rank, world, local):
                         **{k: {"iters": v["iters"], "ms": v["ms"], "final_are": v["final"]["are"]}
                            for k, v in cmp.items()}}
 
+        loop = None
+        if loop_job is not None:
+            loop = measure_loop(gbp, stream, loop_job.get())
+            loop_pool.close()
+
         # end to end through the C ABI with host buffers: create (H2D), solve, read beliefs (D2H)
         e2e_t, e2e_updates = [], 0.0
         h2d = p.n_kf * 96 + p.n_lm * 24 + p.n_obs * (4 + 4 + 16) + 4 * len(p.anchor_kf)
@@ -471,7 +566,8 @@ def run_gpu(args, rank, world, local):
                        "iters_per_step": float(np.mean(iters))},
             "ms_to_1px_vs_oracle": ms_1px, "iters_to_1px_vs_oracle": t_1px, "learned_damping": learned_line,
             "fp32_error_vs_oracle": fp32_err,
-            "roofline": roof, "at_scale": at_scale, "cpu_baseline": cpu,
+            "roofline": roof, "at_scale": at_scale, "loop": loop, "cpu_baseline": cpu,
+            "cpu_baseline_openmp": cpu_omp,
             "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s},
             "gpu_launches": launches, "tuning": tuning,
@@ -512,6 +608,7 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=20, help="oracle iterations per reference step")
     ap.add_argument("--oracle-iters", type=int, default=1000, help="cap of the oracle solve (CPU baseline)")
     ap.add_argument("--no-scale", action="store_true", help="skip the batched at-scale measurement")
+    ap.add_argument("--no-loop", action="store_true", help="skip the large single-problem (loop) measurement")
     ap.add_argument("--scale-problems", type=int, default=256, help="problems in the batched measurement")
     ap.add_argument("--scale-only", action="store_true",
                     help="only the batched measurement (profiling runs); prints its own JSON line")

@@ -5,7 +5,10 @@ leg may import this package.  It shares no code with the CUDA library; the
 two only see the same seeded inputs from ``paper_2003_03134_gb300.synth``.
 
 ``build()`` compiles ``gbp_oracle.c`` with gcc into ``liboracle_gbp.so`` next
-to it; ``Oracle`` wraps one graph through ctypes.
+to it, and the same source with OpenMP into ``liboracle_gbp_omp.so`` (factors
+of an iteration, and variables of a belief update, run in parallel with the
+same arithmetic in the same order, so its results are bit for bit those of
+the single-threaded build); ``Oracle`` wraps one graph through ctypes.
 """
 from __future__ import annotations
 
@@ -18,18 +21,34 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gbp_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle_gbp.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_gbp_omp.so")
 _lib = None
+_lib_omp = None
+
+
+def _compile(out, extra, force):
+    if force or not os.path.exists(out) or os.path.getmtime(out) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "gbp_oracle.h"))):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-Wall", "-Wextra", *extra,
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle (plain C99, -O2, no fast-math) if out of date."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "gbp_oracle.h"))):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-Wall", "-Wextra",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+    """Compile the oracle (plain C99, -O2, no fast-math) if out of date, and
+    its OpenMP build (skipped if the compiler has no OpenMP)."""
+    _compile(_LIB, ["-Wno-unknown-pragmas"], force)
+    try:
+        _compile(_LIB_OMP, ["-fopenmp"], force)
+    except (subprocess.CalledProcessError, OSError):
+        pass
     return _LIB
+
+
+def omp_available() -> bool:
+    build()
+    return os.path.exists(_LIB_OMP)
 
 
 class _Cam(C.Structure):
@@ -47,11 +66,24 @@ _D = C.POINTER(C.c_double)
 _I = C.POINTER(C.c_int)
 
 
-def lib():
-    global _lib
+def lib(omp: bool = False):
+    """The oracle's ctypes handle; omp=True: its OpenMP build (threads from
+    OMP_NUM_THREADS, default all cores)."""
+    global _lib, _lib_omp
+    if omp:
+        if _lib_omp is None:
+            if not omp_available():
+                raise RuntimeError("the oracle's OpenMP build is not available")
+            _lib_omp = _declare(C.CDLL(_LIB_OMP))
+        return _lib_omp
     if _lib is None:
         build()
-        L = C.CDLL(_LIB)
+        _lib = _declare(C.CDLL(_LIB))
+    return _lib
+
+
+def _declare(L):
+    if True:
         L.orc_create.restype = C.c_void_p
         L.orc_create.argtypes = [C.POINTER(_Cam), C.POINTER(_Params), C.c_int, _D, C.c_int, _D,
                                  C.c_int, _I, _I, _D, C.c_int, _I]
@@ -94,8 +126,7 @@ def lib():
         L.orc_get_relin_iters.argtypes = [C.c_void_p, _I]
         L.orc_get_relin_iters.restype = None
         L.orc_set_messages.argtypes = [C.c_void_p, _D, _D, _D, _D]
-        _lib = L
-    return _lib
+    return L
 
 
 def _dp(a):
@@ -200,8 +231,10 @@ def net_forward(params, x) -> float:
 class Oracle:
     """One GBP graph in the FP64 oracle."""
 
-    def __init__(self, problem, anchors=None, **params):
+    def __init__(self, problem, anchors=None, omp=False, **params):
+        """omp=True runs the OpenMP build (same results, all cores)."""
         self.p = problem
+        self._L = lib(omp)
         self._cam = make_cam(problem.fx, problem.fy, problem.cx, problem.cy)
         self._prm = make_params(**params)
         self.params = dict(DEFAULTS, **{k: v for k, v in params.items() if k in DEFAULTS})
@@ -212,7 +245,7 @@ class Oracle:
         self._uv = _f64(problem.obs_uv)
         anc = problem.anchor_kf if anchors is None else anchors
         self._anc = np.ascontiguousarray(anc, dtype=np.int32)
-        h = lib().orc_create(C.byref(self._cam), C.byref(self._prm), problem.n_kf, _dp(self._kf),
+        h = self._L.orc_create(C.byref(self._cam), C.byref(self._prm), problem.n_kf, _dp(self._kf),
                              problem.n_lm, _dp(self._lm), problem.n_obs, _ip(self._ok), _ip(self._ol),
                              _dp(self._uv), int(self._anc.size), _ip(self._anc))
         if not h:
@@ -221,13 +254,13 @@ class Oracle:
 
     def __del__(self):
         h = getattr(self, "_h", None)
-        if h is not None and _lib is not None:
-            _lib.orc_destroy(h)
+        if h is not None and getattr(self, "_L", None) is not None:
+            self._L.orc_destroy(h)
             self._h = None
 
     def iterate(self, n: int) -> float:
         d = C.c_double(0.0)
-        if lib().orc_iterate(self._h, int(n), C.byref(d)) != 0:
+        if self._L.orc_iterate(self._h, int(n), C.byref(d)) != 0:
             raise FloatingPointError("a belief stopped being positive definite")
         return d.value
 
@@ -243,83 +276,83 @@ class Oracle:
 
     @property
     def t(self) -> int:
-        return lib().orc_iterations_done(self._h)
+        return self._L.orc_iterations_done(self._h)
 
     def means(self):
         nk, nl, _ = self.sizes()
         kf, lm = np.zeros((nk, 6)), np.zeros((nl, 3))
-        lib().orc_get_means(self._h, _dp(kf), _dp(lm))
+        self._L.orc_get_means(self._h, _dp(kf), _dp(lm))
         return kf, lm
 
     def world(self):
         nk, nl, _ = self.sizes()
         kf, lm = np.zeros((nk, 12)), np.zeros((nl, 3))
-        lib().orc_get_world(self._h, _dp(kf), _dp(lm))
+        self._L.orc_get_world(self._h, _dp(kf), _dp(lm))
         return kf, lm
 
     def beliefs(self):
         nk, nl, _ = self.sizes()
         kl, ke = np.zeros((nk, 6, 6)), np.zeros((nk, 6))
         ll, le = np.zeros((nl, 3, 3)), np.zeros((nl, 3))
-        lib().orc_get_beliefs(self._h, _dp(kl), _dp(ke), _dp(ll), _dp(le))
+        self._L.orc_get_beliefs(self._h, _dp(kl), _dp(ke), _dp(ll), _dp(le))
         return kl, ke, ll, le
 
     def prior_diag(self):
         nk, nl, _ = self.sizes()
         kd, ld = np.zeros((nk, 6)), np.zeros((nl, 3))
-        lib().orc_get_prior_diag(self._h, _dp(kd), _dp(ld))
+        self._L.orc_get_prior_diag(self._h, _dp(kd), _dp(ld))
         return kd, ld
 
     def messages(self):
         n = self.sizes()[2]
         a, b, c, d = np.zeros((n, 6, 6)), np.zeros((n, 6)), np.zeros((n, 3, 3)), np.zeros((n, 3))
-        lib().orc_get_messages(self._h, _dp(a), _dp(b), _dp(c), _dp(d))
+        self._L.orc_get_messages(self._h, _dp(a), _dp(b), _dp(c), _dp(d))
         return a, b, c, d
 
     def are(self, mask=None):
         cnt = C.c_int(0)
         if mask is None:
-            v = lib().orc_are(self._h, None, C.byref(cnt))
+            v = self._L.orc_are(self._h, None, C.byref(cnt))
         else:
             m = np.ascontiguousarray(mask, dtype=np.uint8)
-            v = lib().orc_are(self._h, m.ctypes.data_as(C.POINTER(C.c_ubyte)), C.byref(cnt))
+            v = self._L.orc_are(self._h, m.ctypes.data_as(C.POINTER(C.c_ubyte)), C.byref(cnt))
         return v, cnt.value
 
     def are_vs(self, ref_kf_Rt, ref_lm):
         cnt = C.c_int(0)
         a, b = _f64(ref_kf_Rt), _f64(ref_lm)
-        v = lib().orc_are_vs(self._h, _dp(a), _dp(b), C.byref(cnt))
+        v = self._L.orc_are_vs(self._h, _dp(a), _dp(b), C.byref(cnt))
         return v, cnt.value
 
     def huber_count(self) -> int:
-        return lib().orc_huber_count(self._h)
+        return self._L.orc_huber_count(self._h)
 
     def add_keyframe(self, obs_lm, obs_uv, kf_Rt_init=None, n_new_lm=0, new_lm_xyz=None) -> int:
         ol = np.ascontiguousarray(obs_lm, dtype=np.int32)
         uv = _f64(obs_uv)
         kf = None if kf_Rt_init is None else _f64(kf_Rt_init)
         nl = None if new_lm_xyz is None else _f64(new_lm_xyz)
-        r = lib().orc_add_keyframe(self._h, None if kf is None else _dp(kf), int(n_new_lm),
+        r = self._L.orc_add_keyframe(self._h, None if kf is None else _dp(kf), int(n_new_lm),
                                    None if nl is None else _dp(nl), ol.size, _ip(ol), _dp(uv))
         if r < 0:
             raise ValueError("oracle rejected the keyframe")
         a, b, c = C.c_int(), C.c_int(), C.c_int()
-        lib().orc_sizes(self._h, C.byref(a), C.byref(b), C.byref(c))
+        self._L.orc_sizes(self._h, C.byref(a), C.byref(b), C.byref(c))
         self.n_kf, self.n_lm, self.n_obs = a.value, b.value, c.value
         return r
 
     def sizes(self):
         a, b, c = C.c_int(), C.c_int(), C.c_int()
-        lib().orc_sizes(self._h, C.byref(a), C.byref(b), C.byref(c))
+        self._L.orc_sizes(self._h, C.byref(a), C.byref(b), C.byref(c))
         return a.value, b.value, c.value
 
     def relinearisations(self) -> int:
-        return lib().orc_relinearisations(self._h)
+        return self._L.orc_relinearisations(self._h)
 
     def relin_iters(self) -> np.ndarray:
         """Iteration of each factor's last (re)linearisation, observation order."""
         t = np.zeros(self.sizes()[2], dtype=np.int32)
-        lib().orc_get_relin_iters(self._h, _ip(t))
+        self._L.orc_get_relin_iters(self._h, _ip(t))
         return t
 
     def set_messages(self, mk_lam, mk_eta, ml_lam, ml_eta):
@@ -328,20 +361,20 @@ class Oracle:
         n = self.sizes()[2]
         a, b = _f64(mk_lam).reshape(n, 36), _f64(mk_eta).reshape(n, 6)
         c, d = _f64(ml_lam).reshape(n, 9), _f64(ml_eta).reshape(n, 3)
-        if lib().orc_set_messages(self._h, _dp(a), _dp(b), _dp(c), _dp(d)) != 0:
+        if self._L.orc_set_messages(self._h, _dp(a), _dp(b), _dp(c), _dp(d)) != 0:
             raise FloatingPointError("a belief is not positive definite")
 
     def held_messages(self) -> int:
-        return lib().orc_held_messages(self._h)
+        return self._L.orc_held_messages(self._h)
 
     # learned damping
     def set_damping_net(self, params):
         """Learned schedule with these network parameters; None: fixed schedule."""
         if params is None:
-            lib().orc_set_damping_net(self._h, None)
+            self._L.orc_set_damping_net(self._h, None)
             return
         self._net = _f64(params)
-        if self._net.size != N_NET_PARAMS or lib().orc_set_damping_net(self._h, _dp(self._net)) != 0:
+        if self._net.size != N_NET_PARAMS or self._L.orc_set_damping_net(self._h, _dp(self._net)) != 0:
             raise ValueError("bad network parameters")
 
     def set_reference_messages(self, mk_eta, ml_eta):
@@ -349,7 +382,7 @@ class Oracle:
         keyframes and (n_obs, 3) to the landmarks."""
         self._ref = np.ascontiguousarray(np.concatenate([_f64(mk_eta).reshape(-1, 6), _f64(ml_eta).reshape(-1, 3)],
                                                         axis=1))
-        lib().orc_set_reference_messages(self._h, _dp(self._ref))
+        self._L.orc_set_reference_messages(self._h, _dp(self._ref))
 
     def capture_messages(self):
         """The current messages become the reference."""
@@ -361,7 +394,7 @@ class Oracle:
         and damping targets (n, n_obs) in observation order."""
         nf = self.sizes()[2]
         X, T = np.zeros((n, nf, N_FEAT)), np.zeros((n, nf))
-        rc = lib().orc_iterate_record(self._h, int(n), _dp(X), _dp(T))
+        rc = self._L.orc_iterate_record(self._h, int(n), _dp(X), _dp(T))
         if rc == -2:
             raise RuntimeError("no reference messages set")
         if rc != 0:

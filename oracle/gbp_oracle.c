@@ -300,16 +300,48 @@ struct orc_graph {
     double *pk_eta;                      /* per factor: eta of the message to the keyframe at t-1        */
     double *net;                         /* damping network parameters (ORC_NET_NPARAM) or NULL         */
     double *eta_ref;                     /* per factor: reference eta (keyframe 6, landmark 3) or NULL   */
+    /* the factors of every variable in increasing factor order (rebuilt
+     * when the graph grows): each belief sums its messages in that order */
+    int *kf_off, *kf_fac, *lm_off, *lm_fac;
+    int csr_nf, csr_nk, csr_nl;
 };
 
 static void* zalloc(size_t n) { return calloc(n ? n : 1, 1); }
 
 enum { ORC_HIST = 8 };
 
+static void build_csr(orc_graph* g)
+{
+    if (g->kf_off && g->csr_nf == g->n_f && g->csr_nk == g->n_kf && g->csr_nl == g->n_lm) return;
+    free(g->kf_off); free(g->kf_fac); free(g->lm_off); free(g->lm_fac);
+    g->kf_off = zalloc(sizeof(int) * (size_t)(g->n_kf + 1));
+    g->lm_off = zalloc(sizeof(int) * (size_t)(g->n_lm + 1));
+    g->kf_fac = zalloc(sizeof(int) * (size_t)g->n_f);
+    g->lm_fac = zalloc(sizeof(int) * (size_t)g->n_f);
+    for (int f = 0; f < g->n_f; ++f) { g->kf_off[g->fk[f] + 1]++; g->lm_off[g->fm[f] + 1]++; }
+    for (int v = 0; v < g->n_kf; ++v) g->kf_off[v + 1] += g->kf_off[v];
+    for (int v = 0; v < g->n_lm; ++v) g->lm_off[v + 1] += g->lm_off[v];
+    int* fill = zalloc(sizeof(int) * (size_t)(g->n_kf > g->n_lm ? g->n_kf + 1 : g->n_lm + 1));
+    for (int v = 0; v < g->n_kf; ++v) fill[v] = g->kf_off[v];
+    for (int f = 0; f < g->n_f; ++f) g->kf_fac[fill[g->fk[f]]++] = f;
+    for (int v = 0; v < g->n_lm; ++v) fill[v] = g->lm_off[v];
+    for (int f = 0; f < g->n_f; ++f) g->lm_fac[fill[g->fm[f]]++] = f;
+    free(fill);
+    g->csr_nf = g->n_f;
+    g->csr_nk = g->n_kf;
+    g->csr_nl = g->n_lm;
+}
+
 /* Belief b^t of every variable: prior(t) + sum of the current messages
- * (Sec. 5, belief equations); then its mean by a Cholesky solve. */
+ * (Sec. 5, belief equations), the messages added in increasing factor
+ * order; then its mean by a Cholesky solve.  Variables are independent (an
+ * OpenMP build runs them in parallel with the same arithmetic). */
 static int update_beliefs(orc_graph* g, double* max_dmu)
 {
+    build_csr(g);
+    double dmu = 0.0;
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(max : dmu) reduction(| : bad)
     for (int v = 0; v < g->n_kf; ++v) {
         double s = orc_prior_scale(&g->prm, g->t - g->kf_birth[v]);
         double* L = g->kf_lam + 36 * v;
@@ -320,41 +352,43 @@ static int update_beliefs(orc_graph* g, double* max_dmu)
             L[i * 6 + i] = s * g->Dk[6 * v + i];
             if (g->anchored[v]) L[i * 6 + i] += g->prm.anchor_scale * g->Dk[6 * v + i];
         }
-    }
-    for (int v = 0; v < g->n_lm; ++v) {
-        double s = orc_prior_scale(&g->prm, g->t - g->lm_birth[v]);
-        double* L = g->lm_lam + 9 * v;
-        memset(L, 0, sizeof(double) * 9);
-        memset(g->lm_eta + 3 * v, 0, sizeof(double) * 3);
-        for (int i = 0; i < 3; ++i) L[i * 3 + i] = s * g->Dl[3 * v + i];
-    }
-    for (int f = 0; f < g->n_f; ++f) {
-        int k = g->fk[f], m = g->fm[f];
-        for (int i = 0; i < 36; ++i) g->kf_lam[36 * k + i] += g->mk_lam[36 * f + i];
-        for (int i = 0; i < 6; ++i) g->kf_eta[6 * k + i] += g->mk_eta[6 * f + i];
-        for (int i = 0; i < 9; ++i) g->lm_lam[9 * m + i] += g->ml_lam[9 * f + i];
-        for (int i = 0; i < 3; ++i) g->lm_eta[3 * m + i] += g->ml_eta[3 * f + i];
-    }
-    double dmu = 0.0;
-    double Lf[36], mu[6];
-    for (int v = 0; v < g->n_kf; ++v) {
-        if (cholesky(6, g->kf_lam + 36 * v, Lf) != 0) return -1;
-        cholesky_solve(6, Lf, g->kf_eta + 6 * v, mu);
+        for (int j = g->kf_off[v]; j < g->kf_off[v + 1]; ++j) {
+            int f = g->kf_fac[j];
+            for (int i = 0; i < 36; ++i) L[i] += g->mk_lam[36 * f + i];
+            for (int i = 0; i < 6; ++i) e[i] += g->mk_eta[6 * f + i];
+        }
+        double Lf[36], mu[6];
+        if (cholesky(6, L, Lf) != 0) { bad = 1; continue; }
+        cholesky_solve(6, Lf, e, mu);
         for (int i = 0; i < 6; ++i) {
             double d = fabs(mu[i] - g->kf_mu[6 * v + i]);
             if (d > dmu) dmu = d;
             g->kf_mu[6 * v + i] = mu[i];
         }
     }
+#pragma omp parallel for schedule(static) reduction(max : dmu) reduction(| : bad)
     for (int v = 0; v < g->n_lm; ++v) {
-        if (cholesky(3, g->lm_lam + 9 * v, Lf) != 0) return -1;
-        cholesky_solve(3, Lf, g->lm_eta + 3 * v, mu);
+        double s = orc_prior_scale(&g->prm, g->t - g->lm_birth[v]);
+        double* L = g->lm_lam + 9 * v;
+        double* e = g->lm_eta + 3 * v;
+        memset(L, 0, sizeof(double) * 9);
+        memset(e, 0, sizeof(double) * 3);
+        for (int i = 0; i < 3; ++i) L[i * 3 + i] = s * g->Dl[3 * v + i];
+        for (int j = g->lm_off[v]; j < g->lm_off[v + 1]; ++j) {
+            int f = g->lm_fac[j];
+            for (int i = 0; i < 9; ++i) L[i] += g->ml_lam[9 * f + i];
+            for (int i = 0; i < 3; ++i) e[i] += g->ml_eta[3 * f + i];
+        }
+        double Lf[9], mu[3];
+        if (cholesky(3, L, Lf) != 0) { bad = 1; continue; }
+        cholesky_solve(3, Lf, e, mu);
         for (int i = 0; i < 3; ++i) {
             double d = fabs(mu[i] - g->lm_mu[3 * v + i]);
             if (d > dmu) dmu = d;
             g->lm_mu[3 * v + i] = mu[i];
         }
     }
+    if (bad) return -1;
     if (max_dmu) *max_dmu = dmu;
     return 0;
 }
@@ -493,7 +527,7 @@ void orc_destroy(orc_graph* g)
                      g->kf_lam, g->kf_eta, g->lm_lam, g->lm_eta, g->kf_mu, g->lm_mu,
                      g->mk_lam, g->mk_eta, g->ml_lam, g->ml_eta, g->nk_lam, g->nk_eta, g->nl_lam, g->nl_eta,
                      g->linA, g->linc, g->x0, g->tlin, g->lin_r2, g->lin_k, g->hist, g->pk_eta, g->net,
-                     g->eta_ref };
+                     g->eta_ref, g->kf_off, g->kf_fac, g->lm_off, g->lm_fac };
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(g);
 }
@@ -640,7 +674,6 @@ void orc_set_reference_messages(orc_graph* g, const double* eta_ref)
  * hold of Sec. 8; the learned one with d_f in place of d. */
 static int iterate_impl(orc_graph* g, int n, double* max_dmu, int mode, double* X, double* T)
 {
-    double J[18], r[2], k;
     int *deg_k = NULL, *deg_l = NULL;
     if (mode != 0) {
         deg_k = zalloc(sizeof(int) * (size_t)g->n_kf);
@@ -649,7 +682,12 @@ static int iterate_impl(orc_graph* g, int n, double* max_dmu, int mode, double* 
     }
     int status = 0;
     for (int it = 0; it < n && status == 0; ++it) {
+        long relin_add = 0, held_add = 0;
+        /* factors are independent within an iteration: they read b^t and m^t
+         * only (an OpenMP build runs them in parallel) */
+#pragma omp parallel for schedule(static) reduction(+ : relin_add, held_add)
         for (int f = 0; f < g->n_f; ++f) {
+            double J[18], r[2], k;
             int kk = g->fk[f], m = g->fm[f];
             double* x0 = g->x0 + 9 * f;
             /* the variable-to-factor messages: each variable's belief divided
@@ -683,7 +721,7 @@ static int iterate_impl(orc_graph* g, int n, double* max_dmu, int mode, double* 
                     for (int i = 0; i < 6; ++i) x0[i] = g->kf_mu[6 * kk + i];
                     for (int i = 0; i < 3; ++i) x0[6 + i] = g->lm_mu[3 * m + i];
                     g->tlin[f] = g->t;
-                    g->n_relin += 1;
+                    relin_add += 1;
                 }
             }
             const double* A = g->linA + 81 * f;
@@ -692,13 +730,13 @@ static int iterate_impl(orc_graph* g, int n, double* max_dmu, int mode, double* 
             if (!ok_l || orc_factor_message(A, c, 0, lam_inl, eta_inl, g->nk_lam + 36 * f, g->nk_eta + 6 * f) != 0) {
                 memcpy(g->nk_lam + 36 * f, g->mk_lam + 36 * f, sizeof(double) * 36);
                 memcpy(g->nk_eta + 6 * f, g->mk_eta + 6 * f, sizeof(double) * 6);
-                g->n_held += 1;
+                held_add += 1;
             }
             /* to the landmark, marginalising the keyframe */
             if (!ok_k || orc_factor_message(A, c, 1, lam_ink, eta_ink, g->nl_lam + 9 * f, g->nl_eta + 3 * f) != 0) {
                 memcpy(g->nl_lam + 9 * f, g->ml_lam + 9 * f, sizeof(double) * 9);
                 memcpy(g->nl_eta + 3 * f, g->ml_eta + 3 * f, sizeof(double) * 3);
-                g->n_held += 1;
+                held_add += 1;
             }
             /* damping of the eta update (Sec. 5): messages stay undamped for
              * undamped_iters iterations after a (re)linearisation (Sec. 8); the
@@ -733,6 +771,8 @@ static int iterate_impl(orc_graph* g, int n, double* max_dmu, int mode, double* 
                 for (int i = 0; i < 3; ++i) g->nl_eta[3 * f + i] = (1.0 - d) * g->nl_eta[3 * f + i] + d * g->ml_eta[3 * f + i];
             }
         }
+        g->n_relin += relin_add;
+        g->n_held += held_add;
         if (status != 0) break;
         /* synchronous schedule: every factor used m^t; now m^{t+1} replaces it */
         memcpy(g->pk_eta, g->mk_eta, sizeof(double) * 6 * (size_t)g->n_f);

@@ -562,6 +562,22 @@ def test_held_message_defers_its_factors_relinearisation():
     assert o.relinearisations() == p.n_obs - 1
 
 
+def test_openmp_build_gives_the_same_bits():
+    """The OpenMP build (factors of an iteration and variables of a belief
+    update in parallel, every sum in the same order) is the oracle itself:
+    bit for bit the single-threaded results, relinearisations included."""
+    if not oracle.omp_available():
+        pytest.skip("no OpenMP compiler")
+    p = synth.make_walk(1, n_kf=30, n_lm=400)
+    a = oracle.Oracle(p, huber_nsigma=2.0)
+    b = oracle.Oracle(p, huber_nsigma=2.0, omp=True)
+    a.iterate(45)
+    b.iterate(45)
+    for x, y in zip(a.means() + a.messages(), b.means() + b.messages()):
+        np.testing.assert_array_equal(x, y)
+    assert a.relinearisations() == b.relinearisations() > 0
+
+
 # ------------------------------------------------------- incremental (Sec. 9.2)
 
 def test_added_keyframe_and_points_start_where_the_paper_puts_them():
