@@ -405,13 +405,6 @@ def run_gpu(args, rank, world, local):
     from paper_2003_03134_gb300 import build, gbp, synth
 
     build.build()
-    loop_pool = loop_job = None
-    if rank == 0 and not args.no_loop:
-        # the ~2M-factor loop problem takes ~1.5 min to generate: in a spawned
-        # process while the GPU measures the rest
-        import multiprocessing as mp
-        loop_pool = mp.get_context("spawn").Pool(1)
-        loop_job = loop_pool.apply_async(_make_loop_problem, (0,))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -467,6 +460,14 @@ def run_gpu(args, rank, world, local):
     g.reset()
     iter_ms, fac_ms = g.profile(64)
     roof = roofline(p, iter_ms, fac_ms, st_timed["launch_mode"])
+    loop_pool = loop_job = None
+    if rank == 0 and not args.no_loop:
+        # the ~2M-factor loop problem takes ~1.5 min to generate: in a spawned
+        # process (after the timed region, whose host-side checks it would
+        # slow) while the GPU measures the rest
+        import multiprocessing as mp
+        loop_pool = mp.get_context("spawn").Pool(1)
+        loop_job = loop_pool.apply_async(_make_loop_problem, (0,))
     at_scale = None if args.no_scale else measure_at_scale(gbp, stream, rank, world, args.scale_problems,
                                                              device=dev)
 

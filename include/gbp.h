@@ -224,6 +224,14 @@ gbp_status gbp_get_stats(const gbp_graph* g, gbp_stats* out);
 
 gbp_status gbp_get_sizes(const gbp_graph* g, int32_t* n_kf, int32_t* n_lm, int32_t* n_obs);
 
+/* Reprojection error of every observation at the current means (Sec. 9.1):
+ * err[i] = |z_i - pi(R l + t)| in pixels, caller's observation order (host,
+ * n_obs doubles), or -1 where the point lies closer than z_min to its
+ * camera.  With huber_nsigma N, an observation with err > N sigma_px is in
+ * the linear (outlier) regime of the Huber loss (Sec. 6).  Synchronises the
+ * stream. */
+gbp_status gbp_get_residuals(const gbp_graph* g, double* err);
+
 /* Iteration at which each observation's factor was last (re)linearised
  * (t_lin of the lazy schedule of Sec. 5 / Sec. 8; 0 = still at its first
  * linearisation), n_obs int32 in the caller's observation order (host).

@@ -1396,6 +1396,23 @@ gbp_status gbp_get_relin_iters(const gbp_graph* cg, int32_t* tlin) {
     return read_ctl(g);
 }
 
+gbp_status gbp_get_residuals(const gbp_graph* cg, double* err) {
+    gbp_graph* g = const_cast<gbp_graph*>(cg);
+    if (!g || (g->n_f && !err)) return GBP_EINVAL;
+    if (g->n_f == 0) return GBP_OK;
+    double* d = nullptr;
+    CK(cudaMalloc(reinterpret_cast<void**>(&d), sizeof(double) * g->n_f));
+    cudaError_t e = g->storage ? launch_residuals<double>(g->sd.g, make_kparams<double>(g), d, g->stream)
+                               : launch_residuals<float>(g->sf.g, make_kparams<float>(g), d, g->stream);
+    std::vector<double> h(g->n_f);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(g, e, "residuals");
+    for (int f = 0; f < g->n_f; ++f) err[g->obs_index[f]] = h[f];
+    return read_ctl(g);
+}
+
 gbp_status gbp_get_sizes(const gbp_graph* g, int32_t* n_kf, int32_t* n_lm, int32_t* n_obs) {
     if (!g) return GBP_EINVAL;
     if (n_kf) *n_kf = g->n_kf;

@@ -204,6 +204,8 @@ template <typename R> cudaError_t launch_metrics(const DevGraph<R>& g, const KPa
 template <typename R> cudaError_t launch_problem_metrics(const DevGraph<R>& g, const KParams<R>& p,
                                                          const int32_t* prob_f0, int n_problems, double* out,
                                                          cudaStream_t s);
+template <typename R> cudaError_t launch_residuals(const DevGraph<R>& g, const KParams<R>& p, double* out,
+                                                   cudaStream_t s);
 int metrics_blocks(int n_f);
 
 // damping network (gbp_mlp.cu): device-to-device copy of a network's packed

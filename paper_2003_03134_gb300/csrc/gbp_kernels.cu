@@ -2126,6 +2126,25 @@ __global__ void __launch_bounds__(METRIC_BLOCK) problem_metrics_kernel(DevGraph<
         for (int j = 0; j < 3; ++j) out[3 * (size_t)p + j] = red[j][0];
 }
 
+// Per-factor reprojection error |z - h(mu)| at the current means (Sec. 9.1),
+// -1 for a point closer than z_min to its camera.
+template <typename R>
+__global__ void __launch_bounds__(METRIC_BLOCK) residual_kernel(DevGraph<R> g, KParams<R> P, double* out) {
+    const int f = blockIdx.x * METRIC_BLOCK + threadIdx.x;
+    if (f >= g.n_f) return;
+    const int k = g.fk[f], m = g.fm[f];
+    const R* kb = g.kf_bel + (size_t)k * KBEL;
+    const R* lb = g.lm_bel + (size_t)m * LBEL;
+    R x[9] = {kb[KB_MU], kb[KB_MU + 1], kb[KB_MU + 2], kb[KB_MU + 3], kb[KB_MU + 4], kb[KB_MU + 5],
+              lb[9], lb[10], lb[11]};
+    KParams<R> Q = P;
+    Q.huber_n = R(0);
+    Lin<R> L;
+    linearise<R>(Q, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3, g.lm_ref + (size_t)m * 3, x,
+                 g.z[2 * (size_t)f], g.z[2 * (size_t)f + 1], L);
+    out[f] = L.W > R(0) ? sqrt(double(L.r2)) : -1.0;
+}
+
 __global__ void metrics_finish_kernel(const double* partials, int nb, int with_ref, double* out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double s[6] = {0, 0, 0, 0, 0, 0};
@@ -2302,6 +2321,12 @@ cudaError_t launch_problem_metrics(const DevGraph<R>& g, const KParams<R>& p, co
     return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t launch_residuals(const DevGraph<R>& g, const KParams<R>& p, double* out, cudaStream_t s) {
+    if (g.n_f > 0) residual_kernel<R><<<(g.n_f + METRIC_BLOCK - 1) / METRIC_BLOCK, METRIC_BLOCK, 0, s>>>(g, p, out);
+    return cudaGetLastError();
+}
+
 #define GBP_INSTANTIATE(R)                                                                                 \
     template cudaError_t launch_factor<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t, int, bool, int); \
     template cudaError_t launch_capture_messages<R>(const DevGraph<R>&, int, R*, cudaStream_t);            \
@@ -2311,7 +2336,8 @@ cudaError_t launch_problem_metrics(const DevGraph<R>& g, const KParams<R>& p, co
     template int persistent_grid<R>(const DevGraph<R>&, int, int);                                         \
     template cudaError_t launch_persistent<R>(const DevGraph<R>&, const KParams<R>&, int, float, int, int, cudaStream_t, int, int); \
     template cudaError_t launch_prior<R>(const DevGraph<R>&, const KParams<R>&, R*, R*, R*, R*, cudaStream_t); \
-    template cudaError_t launch_metrics<R>(const DevGraph<R>&, const KParams<R>&, double*, int, double*, cudaStream_t);
+    template cudaError_t launch_metrics<R>(const DevGraph<R>&, const KParams<R>&, double*, int, double*, cudaStream_t); \
+    template cudaError_t launch_residuals<R>(const DevGraph<R>&, const KParams<R>&, double*, cudaStream_t);
 
 GBP_INSTANTIATE(float)
 GBP_INSTANTIATE(double)

@@ -95,7 +95,7 @@ EXPORTS = ["gbp_default_params", "gbp_create_graph", "gbp_set_params", "gbp_get_
            "gbp_get_batch_info", "gbp_get_problem_are", "gbp_mlp_create", "gbp_mlp_set_params",
            "gbp_mlp_get_params", "gbp_mlp_forward", "gbp_mlp_gradient", "gbp_mlp_train_step", "gbp_mlp_destroy",
            "gbp_set_damping_model", "gbp_capture_messages", "gbp_get_factor_order", "gbp_record_iterations",
-           "gbp_get_relin_iters", "gbp_get_tuning"]
+           "gbp_get_relin_iters", "gbp_get_tuning", "gbp_get_residuals"]
 GBP_MLP_NFEAT = 16
 GBP_MLP_NPARAM = 5313
 GBP_NOALLOC_MAX_OBS = 1 << 20
@@ -126,6 +126,7 @@ def lib() -> C.CDLL:
     L.gbp_get_stats.argtypes = [vp, C.POINTER(gbp_stats)]
     L.gbp_get_sizes.argtypes = [vp, _I, _I, _I]
     L.gbp_get_relin_iters.argtypes = [vp, _I]
+    L.gbp_get_residuals.argtypes = [vp, _D]
     L.gbp_profile_iterations.argtypes = [vp, C.c_int32, _D]
     L.gbp_autotune.argtypes = [vp, C.c_int32, _I, _D]
     L.gbp_get_tuning.argtypes = [vp, C.POINTER(gbp_tuning)]
@@ -318,6 +319,14 @@ def gbp_get_relin_iters(g: int) -> np.ndarray:
     return t
 
 
+def gbp_get_residuals(g: int) -> np.ndarray:
+    """Reprojection error of every observation at the current means
+    (observation order), -1 where the point is closer than z_min."""
+    e = np.zeros(gbp_get_sizes(g)[2])
+    _check(lib().gbp_get_residuals(g, _dp(e)), g)
+    return e
+
+
 def gbp_get_stats(g: int) -> gbp_stats:
     s = gbp_stats()
     _check(lib().gbp_get_stats(g, C.byref(s)), g)
@@ -501,6 +510,9 @@ class Graph:
 
     def relin_iters(self) -> np.ndarray:
         return gbp_get_relin_iters(self.h)
+
+    def residuals(self) -> np.ndarray:
+        return gbp_get_residuals(self.h)
 
     def autotune(self, n_trial: int = 8):
         return gbp_autotune(self.h, n_trial)

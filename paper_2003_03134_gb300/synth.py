@@ -237,14 +237,17 @@ def _smooth_track(rng, n_kf, step=0.08, turn_sigma_deg=1.0, max_turn_deg=8.0):
 def make_walk(seed: int = 0, n_kf: int = 125, n_lm: int = 1919, obs_range=(4, 15),
               outlier_frac: float = 0.02, noise_px: float = 1.0, rot_sigma: float = 0.05,
               pos_sigma: float = 0.1, lm_sigma: float = 0.1, anchors=(0,),
-              name: str | None = None, smooth: bool = False) -> Problem:
+              name: str | None = None, smooth: bool = False, bad_assoc_frac: float = 0.0) -> Problem:
     """Keyframes on a smooth random walk (height 1.5 m, AR(1) velocity,
     heading along the velocity, horizontal optical axis) inside a
     10 x 10 x 3 m volume of points; each point seen by 4-15 keyframes drawn
     with visibility weight exp(-depth / 3 m); 2% outlier pixels.  With
     ``smooth`` the keyframes follow a video-like track instead (8 cm steps,
     a few degrees of turn per keyframe; see _smooth_track), as a SLAM front
-    end would select them."""
+    end would select them.  ``bad_assoc_frac`` of the (inlier) observations
+    become wrong data associations: the pixel of another point seen by the
+    same keyframe (labelled as outliers; drawn after everything else, so 0
+    leaves the problem unchanged)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     fx, fy, cx, cy, w, h = CAMERA
     kf = []
@@ -299,9 +302,33 @@ def make_walk(seed: int = 0, n_kf: int = 125, n_lm: int = 1919, obs_range=(4, 15
     n_out = int(outlier.sum())
     uv[outlier] = np.stack([rng.uniform(0, w, n_out), rng.uniform(0, h, n_out)], axis=1)
     kf_init, lm_init = _perturb_init(rng, kf_true, lm_true, rot_sigma, pos_sigma, lm_sigma, set(anchors))
+    if bad_assoc_frac > 0.0:
+        uv, outlier = _bad_associations(rng, obs_kf, uv, outlier, bad_assoc_frac)
     params = dict(damping=0.4, huber_nsigma=2.0, sigma_px=1.0, iterations=1000, conv_tol=1e-6)
     return _finish(name or f"walk{n_kf}x{n_lm}", seed, CAMERA, kf_true, kf_init, lm_true, lm_init,
                    obs_kf, obs_lm, uv, outlier, anchors, params)
+
+
+def _bad_associations(rng, obs_kf, uv, outlier, frac):
+    """Wrong correspondences: a ``frac`` share of the inlier observations take
+    the pixel of another observation of the same keyframe."""
+    uv = uv.copy()
+    outlier = outlier.copy()
+    pick = (rng.uniform(size=obs_kf.size) < frac) & ~outlier
+    by_kf = {}
+    for i, k in enumerate(obs_kf):
+        by_kf.setdefault(int(k), []).append(i)
+    src = uv.copy()
+    for i in np.flatnonzero(pick):
+        same = by_kf[int(obs_kf[i])]
+        if len(same) < 2:
+            continue
+        j = i
+        while j == i:
+            j = same[int(rng.integers(len(same)))]
+        uv[i] = src[j]
+        outlier[i] = True
+    return uv, outlier
 
 
 def make_loop(seed: int = 0, n_kf: int = 2000, n_lm: int = 200_000, loops: int = 2,
