@@ -262,6 +262,41 @@ def per_belief_error(kf, lm, okf, olm):
             "keyframes_max": float(ek.max()) if ek.size else 0.0}
 
 
+def _projections(p, kf_Rt, lm_xyz):
+    R = kf_Rt[p.obs_kf, :9].reshape(-1, 3, 3)
+    pc = np.einsum("nij,nj->ni", R, lm_xyz[p.obs_lm]) + kf_Rt[p.obs_kf, 9:]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        uv = np.stack([p.fx * pc[:, 0] / pc[:, 2] + p.cx, p.fy * pc[:, 1] / pc[:, 2] + p.cy], axis=1)
+    return uv, pc[:, 2] >= 0.05
+
+
+def lm_baseline(p, kf_ref, lm_ref, max_iters=50):
+    """The project's CPU Levenberg-Marquardt bundle adjuster (dense Schur
+    complement, single thread) on the same problem and objective: seconds per
+    iteration, iterations and seconds until its ARE against the oracle's
+    converged GBP solution falls below 1 px, and to convergence."""
+    from paper_2003_03134_gb300.lm import LM
+    ref_uv, ref_ok = _projections(p, kf_ref, lm_ref)
+    lm = LM(p, huber_nsigma=HUBER)
+    t_total, t_1px, it_1px, are_ref = 0.0, None, None, None
+    while lm.iterations < max_iters and not lm.converged:
+        t0 = time.perf_counter()
+        lm.step(1)
+        t_total += time.perf_counter() - t0
+        uv, ok = _projections(p, *lm.world())
+        ok &= ref_ok
+        are_ref = float(np.linalg.norm(uv[ok] - ref_uv[ok], axis=1).mean())
+        if t_1px is None and are_ref < 1.0:
+            t_1px, it_1px = t_total, lm.iterations
+    res = {"kind": "Levenberg-Marquardt, dense Schur complement, single-threaded C (same objective, Huber 2 sigma)",
+           "iterations": lm.iterations, "converged": lm.converged, "seconds": t_total,
+           "ms_per_iteration": 1e3 * t_total / max(lm.iterations, 1), "iters_to_1px_vs_oracle": it_1px,
+           "ms_to_1px_vs_oracle": 1e3 * t_1px if t_1px is not None else None, "final_are_vs_oracle": are_ref,
+           "cores": 1}
+    lm.close()
+    return res
+
+
 def _oracle_rate(args):
     """Factor-updates/s of the oracle on problem p over n iterations from the
     initial estimate (run in a spawned process: the OpenMP build gets its own
@@ -478,6 +513,7 @@ def run_gpu(args, rank, world, local):
         cpu = {"value": p.n_obs * o_iters / o_dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"one oracle solve of the rank-0 problem, {o_iters} iterations (cap {args.oracle_iters})",
                "ms_to_1px": (1e3 * o_dt / o_iters * o_1px) if o_1px else None}
+        lm_line = lm_baseline(p, kf_ref, lm_ref)
         import oracle
         cpu_omp = None
         if oracle.omp_available():
@@ -568,7 +604,7 @@ def run_gpu(args, rank, world, local):
             "ms_to_1px_vs_oracle": ms_1px, "iters_to_1px_vs_oracle": t_1px, "learned_damping": learned_line,
             "fp32_error_vs_oracle": fp32_err,
             "roofline": roof, "at_scale": at_scale, "loop": loop, "cpu_baseline": cpu,
-            "cpu_baseline_openmp": cpu_omp,
+            "cpu_baseline_openmp": cpu_omp, "lm_baseline": lm_line,
             "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s},
             "gpu_launches": launches, "tuning": tuning,

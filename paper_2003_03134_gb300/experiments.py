@@ -15,6 +15,9 @@ run through the batched GPU path.
 * ``huber_ablation`` (Sec. 9.4): the converged ARE of the correct
   measurements with and without the Huber loss for growing shares of wrong
   associations.
+* ``lm_convergence_basin``: the basin trials solved by the project's CPU
+  Levenberg-Marquardt baseline (``paper_2003_03134_gb300.lm``), the
+  comparison the paper makes against Ceres.
 
 The paper runs these on TUM sequences; these synthetic problems stand in for
 them (30-keyframe and 20-keyframe video-like tracks, ``synth.make_walk`` with
@@ -75,6 +78,32 @@ def convergence_basin(noise_levels=(0.02, 0.07, 0.15, 0.3, 0.5, 0.8), trials=100
         ok = first >= 0
         out.append({"pos_sigma_m": sigma, "trials": trials, "success": float(ok.mean()),
                     "median_iters": float(np.median(first[ok])) if ok.any() else None})
+    return out
+
+
+def _lm_trial(args):
+    """One trial with the CPU Levenberg-Marquardt baseline: iterations until
+    ARE < 1.5 px (or -1 if it converged above it / ran out of iterations)."""
+    seed, sigma, max_iters, huber_nsigma = args
+    from .lm import LM, reprojection_error
+    p = basin_problem(seed, sigma)
+    lm = LM(p, huber_nsigma=huber_nsigma)
+    while lm.iterations < max_iters and not lm.converged:
+        lm.step(1)
+        if reprojection_error(p, *lm.world()) < SUCCESS_PX:
+            return lm.iterations
+    return -1
+
+
+def lm_convergence_basin(noise_levels=(0.02, 0.07, 0.15, 0.3, 0.5, 0.8), trials=100, max_iters=100, huber_nsigma=2.0):
+    """The same trials solved by the CPU Levenberg-Marquardt baseline (the
+    paper's comparison in Sec. 9.3 is Ceres, an LM solver)."""
+    out = []
+    for sigma in noise_levels:
+        its = np.array(_problems(_lm_trial, [(s, sigma, max_iters, huber_nsigma) for s in range(trials)]))
+        ok = its >= 0
+        out.append({"pos_sigma_m": sigma, "trials": trials, "success": float(ok.mean()),
+                    "median_iters": float(np.median(its[ok])) if ok.any() else None})
     return out
 
 
@@ -146,6 +175,7 @@ def main():
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream().cuda_stream
     res = {"convergence_basin": convergence_basin(stream=stream),
+           "convergence_basin_lm": lm_convergence_basin(),
            "outlier_classification": outlier_classification(stream=stream),
            "huber_ablation": huber_ablation(stream=stream)}
     print(json.dumps(res), flush=True)
