@@ -281,6 +281,45 @@ typedef struct {
  * gbp_autotune (n_candidates = 0 before the first). */
 gbp_status gbp_get_tuning(const gbp_graph* g, gbp_tuning* out);
 
+/* ------------------------------------------------------------------------
+ * One graph split across ranks (GPUs).  The paper runs one graph on one
+ * IPU and points to multi-chip scaling as the way forward (Sec. 10); here
+ * each rank holds the whole graph's layout but forms the messages of the
+ * factors of its landmarks and the beliefs of its keyframes and landmarks,
+ * and per iteration exchanges, host-staged, the boundary records:
+ *   1. gbp_split_phase(g, 0)  -- the factor phase of iteration t (Sec. 5) on
+ *      this rank's factors;
+ *   2. message records (kind 0) of this rank's factors whose keyframe
+ *      another rank owns go to that owner (gbp_get_split_records there,
+ *      gbp_put_split_records on the owner);
+ *   3. gbp_split_phase(g, 1)  -- the belief phase for this rank's keyframes
+ *      and landmarks (closes iteration t);
+ *   4. keyframe records (kind 1) of this rank's keyframes that other ranks'
+ *      factors observe go to those ranks.
+ * Every keyframe then sums exactly the messages the whole graph would, in
+ * the same order, so the split run gives the whole graph's bits (FP32 path,
+ * fixed damping schedule).  Landmarks must be numbered so that each rank's
+ * are contiguous.  ------------------------------------------------------- */
+#define GBP_SPLIT_MSG_FLOATS 20   /* kind 0: a factor's compact message to its keyframe (8) and Jacobian block (12) */
+#define GBP_SPLIT_KF_FLOATS 56    /* kind 1: a keyframe's belief record                                          */
+
+/* Keyframes [kf_begin, kf_end) and landmarks [lm_begin, lm_end) are this
+ * graph's part (lm_end < 0: the whole graph again).  Rebuilds the layout (its
+ * tiles break at the landmark range) and resets to iteration 0; gbp_iterate
+ * then refuses (GBP_ESTATE) until the partition is removed.  GBP_ESTATE for
+ * a batch or the FP64 mode; GBP_EINVAL for ranges out of bounds. */
+gbp_status gbp_set_partition(gbp_graph* g, int32_t kf_begin, int32_t kf_end, int32_t lm_begin, int32_t lm_end);
+/* phase 0: the factor phase of the current iteration on this part's
+ * factors; phase 1: the belief phase of this part's variables, which closes
+ * the iteration.  Asynchronous on the graph's stream. */
+gbp_status gbp_split_phase(gbp_graph* g, int32_t phase);
+/* Read (get) or write (put) n records, host float arrays of n x
+ * GBP_SPLIT_MSG_FLOATS (kind 0, index = caller observation indices; valid
+ * between phase 0 and phase 1) or n x GBP_SPLIT_KF_FLOATS (kind 1, index =
+ * keyframes; after phase 1).  Synchronise the stream. */
+gbp_status gbp_get_split_records(const gbp_graph* g, int32_t kind, int32_t n, const int32_t* index, float* out);
+gbp_status gbp_put_split_records(gbp_graph* g, int32_t kind, int32_t n, const int32_t* index, const float* in);
+
 void gbp_destroy_graph(gbp_graph* g);
 
 /* Largest n_obs that gbp_reprojection_error_noalloc() accepts. */

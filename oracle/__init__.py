@@ -126,6 +126,16 @@ def _declare(L):
         L.orc_get_relin_iters.argtypes = [C.c_void_p, _I]
         L.orc_get_relin_iters.restype = None
         L.orc_set_messages.argtypes = [C.c_void_p, _D, _D, _D, _D]
+        _U = C.POINTER(C.c_ubyte)
+        L.orc_set_part.argtypes = [C.c_void_p, _U, _U]
+        L.orc_factor_phase.argtypes = [C.c_void_p]
+        L.orc_belief_phase.argtypes = [C.c_void_p, _D]
+        for name in ("orc_get_new_kf_messages", "orc_put_new_kf_messages"):
+            getattr(L, name).argtypes = [C.c_void_p, C.c_int, _I, _D, _D]
+            getattr(L, name).restype = None
+        for name in ("orc_get_kf_beliefs", "orc_put_kf_beliefs"):
+            getattr(L, name).argtypes = [C.c_void_p, C.c_int, _I, _D]
+            getattr(L, name).restype = None
     return L
 
 
@@ -363,6 +373,46 @@ class Oracle:
         c, d = _f64(ml_lam).reshape(n, 9), _f64(ml_eta).reshape(n, 3)
         if self._L.orc_set_messages(self._h, _dp(a), _dp(b), _dp(c), _dp(d)) != 0:
             raise FloatingPointError("a belief is not positive definite")
+
+    # one graph solved in parts (multi-rank split)
+    def set_part(self, fac_mask, var_mask):
+        """Compute only these factors' messages and these variables' beliefs
+        (keyframes then landmarks); None = all."""
+        U = C.POINTER(C.c_ubyte)
+        self._fm = None if fac_mask is None else np.ascontiguousarray(fac_mask, dtype=np.uint8)
+        self._vm = None if var_mask is None else np.ascontiguousarray(var_mask, dtype=np.uint8)
+        self._L.orc_set_part(self._h, None if self._fm is None else self._fm.ctypes.data_as(U),
+                             None if self._vm is None else self._vm.ctypes.data_as(U))
+
+    def factor_phase(self):
+        if self._L.orc_factor_phase(self._h) != 0:
+            raise RuntimeError("the factor phase runs the fixed schedule only")
+
+    def belief_phase(self) -> float:
+        d = C.c_double(0.0)
+        if self._L.orc_belief_phase(self._h, C.byref(d)) != 0:
+            raise FloatingPointError("a belief stopped being positive definite")
+        return d.value
+
+    def new_kf_messages(self, factors):
+        f = np.ascontiguousarray(factors, dtype=np.int32)
+        lam, eta = np.zeros((f.size, 36)), np.zeros((f.size, 6))
+        self._L.orc_get_new_kf_messages(self._h, f.size, _ip(f), _dp(lam), _dp(eta))
+        return lam, eta
+
+    def put_new_kf_messages(self, factors, lam, eta):
+        f = np.ascontiguousarray(factors, dtype=np.int32)
+        self._L.orc_put_new_kf_messages(self._h, f.size, _ip(f), _dp(_f64(lam)), _dp(_f64(eta)))
+
+    def kf_beliefs(self, kfs):
+        k = np.ascontiguousarray(kfs, dtype=np.int32)
+        rec = np.zeros((k.size, 48))
+        self._L.orc_get_kf_beliefs(self._h, k.size, _ip(k), _dp(rec))
+        return rec
+
+    def put_kf_beliefs(self, kfs, rec):
+        k = np.ascontiguousarray(kfs, dtype=np.int32)
+        self._L.orc_put_kf_beliefs(self._h, k.size, _ip(k), _dp(_f64(rec)))
 
     def held_messages(self) -> int:
         return self._L.orc_held_messages(self._h)

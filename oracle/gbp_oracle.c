@@ -304,9 +304,19 @@ struct orc_graph {
      * when the graph grows): each belief sums its messages in that order */
     int *kf_off, *kf_fac, *lm_off, *lm_fac;
     int csr_nf, csr_nk, csr_nl;
+    /* a part of the graph (orc_set_part): the factors whose messages and the
+     * variables whose beliefs this graph computes (NULL = all) */
+    unsigned char *fac_mask, *var_mask;
 };
 
 static void* zalloc(size_t n) { return calloc(n ? n : 1, 1); }
+
+static unsigned char* dup_bytes(const unsigned char* src, size_t n)
+{
+    unsigned char* d = zalloc(n);
+    memcpy(d, src, n);
+    return d;
+}
 
 enum { ORC_HIST = 8 };
 
@@ -343,6 +353,7 @@ static int update_beliefs(orc_graph* g, double* max_dmu)
     int bad = 0;
 #pragma omp parallel for schedule(static) reduction(max : dmu) reduction(| : bad)
     for (int v = 0; v < g->n_kf; ++v) {
+        if (g->var_mask && !g->var_mask[v]) continue;
         double s = orc_prior_scale(&g->prm, g->t - g->kf_birth[v]);
         double* L = g->kf_lam + 36 * v;
         double* e = g->kf_eta + 6 * v;
@@ -368,6 +379,7 @@ static int update_beliefs(orc_graph* g, double* max_dmu)
     }
 #pragma omp parallel for schedule(static) reduction(max : dmu) reduction(| : bad)
     for (int v = 0; v < g->n_lm; ++v) {
+        if (g->var_mask && !g->var_mask[g->n_kf + v]) continue;
         double s = orc_prior_scale(&g->prm, g->t - g->lm_birth[v]);
         double* L = g->lm_lam + 9 * v;
         double* e = g->lm_eta + 3 * v;
@@ -527,7 +539,7 @@ void orc_destroy(orc_graph* g)
                      g->kf_lam, g->kf_eta, g->lm_lam, g->lm_eta, g->kf_mu, g->lm_mu,
                      g->mk_lam, g->mk_eta, g->ml_lam, g->ml_eta, g->nk_lam, g->nk_eta, g->nl_lam, g->nl_eta,
                      g->linA, g->linc, g->x0, g->tlin, g->lin_r2, g->lin_k, g->hist, g->pk_eta, g->net,
-                     g->eta_ref, g->kf_off, g->kf_fac, g->lm_off, g->lm_fac };
+                     g->eta_ref, g->kf_off, g->kf_fac, g->lm_off, g->lm_fac, g->fac_mask, g->var_mask };
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(g);
 }
@@ -672,6 +684,122 @@ void orc_set_reference_messages(orc_graph* g, const double* eta_ref)
  * toward eta_ref into T (n x n_f; -1 where the schedule does not damp or
  * neither message changed).  Both schedules damp only after the undamped
  * hold of Sec. 8; the learned one with d_f in place of d. */
+/* One synchronous iteration t in two phases (Sec. 5).  The factor phase
+ * forms m^{t+1} of every factor from b^t and m^t (relinearisation, both
+ * messages, damping); mode 0: the fixed schedule, 1: learned d_f, 2: fixed
+ * schedule recording features and targets into row block `it` of X / T.
+ * deg_k / deg_l: variable degrees (modes 1 and 2). */
+static void factor_phase(orc_graph* g, int mode, double* X, double* T, int it, const int* deg_k, const int* deg_l)
+{
+    long relin_add = 0, held_add = 0;
+    /* factors are independent within an iteration: they read b^t and m^t
+     * only (an OpenMP build runs them in parallel) */
+#pragma omp parallel for schedule(static) reduction(+ : relin_add, held_add)
+    for (int f = 0; f < g->n_f; ++f) {
+        if (g->fac_mask && !g->fac_mask[f]) continue;
+        double J[18], r[2], k;
+        int kk = g->fk[f], m = g->fm[f];
+        double* x0 = g->x0 + 9 * f;
+        /* the variable-to-factor messages: each variable's belief divided
+         * by this factor's previous message to it (Sec. 5); they do not
+         * depend on this iteration's linearisation */
+        double lam_inl[9], eta_inl[3], lam_ink[36], eta_ink[6], Ltmp[36];
+        for (int i = 0; i < 9; ++i) lam_inl[i] = g->lm_lam[9 * m + i] - g->ml_lam[9 * f + i];
+        for (int i = 0; i < 3; ++i) eta_inl[i] = g->lm_eta[3 * m + i] - g->ml_eta[3 * f + i];
+        for (int i = 0; i < 36; ++i) lam_ink[i] = g->kf_lam[36 * kk + i] - g->mk_lam[36 * f + i];
+        for (int i = 0; i < 6; ++i) eta_ink[i] = g->kf_eta[6 * kk + i] - g->mk_eta[6 * f + i];
+        /* a message whose incoming precision is not positive definite
+         * cannot be formed and keeps its previous value; a factor with
+         * such a message keeps its linearisation point for the iteration
+         * (a relinearisation that is due waits), so that a kept message
+         * and its factor's linearisation stay the same */
+        const int ok_l = cholesky(3, lam_inl, Ltmp) == 0;
+        const int ok_k = cholesky(6, lam_ink, Ltmp) == 0;
+        if (!g->prm.linear && ok_l && ok_k && g->t - g->tlin[f] >= g->prm.relin_interval) {
+            /* Sec. 5 / Sec. 8: relinearise when the adjacent beliefs moved
+             * more than beta from the factor's linearisation point, at
+             * most once every relin_interval iterations */
+            double dist2 = 0.0;
+            for (int i = 0; i < 6; ++i) dist2 += (g->kf_mu[6 * kk + i] - x0[i]) * (g->kf_mu[6 * kk + i] - x0[i]);
+            for (int i = 0; i < 3; ++i) dist2 += (g->lm_mu[3 * m + i] - x0[6 + i]) * (g->lm_mu[3 * m + i] - x0[6 + i]);
+            if (sqrt(dist2) > g->prm.relin_beta) {
+                int active = orc_linearise(&g->cam, &g->prm, g->Rref + 9 * kk, g->cref + 3 * kk, g->lref + 3 * m,
+                                           g->kf_mu + 6 * kk, g->lm_mu + 3 * m, g->z + 2 * f, J, r, &k,
+                                           g->linA + 81 * f, g->linc + 9 * f);
+                g->lin_r2[f] = active ? r[0] * r[0] + r[1] * r[1] : 0.0;
+                g->lin_k[f] = active ? k : 0.0;
+                for (int i = 0; i < 6; ++i) x0[i] = g->kf_mu[6 * kk + i];
+                for (int i = 0; i < 3; ++i) x0[6 + i] = g->lm_mu[3 * m + i];
+                g->tlin[f] = g->t;
+                relin_add += 1;
+            }
+        }
+        const double* A = g->linA + 81 * f;
+        const double* c = g->linc + 9 * f;
+        /* to the keyframe, marginalising the landmark */
+        if (!ok_l || orc_factor_message(A, c, 0, lam_inl, eta_inl, g->nk_lam + 36 * f, g->nk_eta + 6 * f) != 0) {
+            memcpy(g->nk_lam + 36 * f, g->mk_lam + 36 * f, sizeof(double) * 36);
+            memcpy(g->nk_eta + 6 * f, g->mk_eta + 6 * f, sizeof(double) * 6);
+            held_add += 1;
+        }
+        /* to the landmark, marginalising the keyframe */
+        if (!ok_k || orc_factor_message(A, c, 1, lam_ink, eta_ink, g->nl_lam + 9 * f, g->nl_eta + 3 * f) != 0) {
+            memcpy(g->nl_lam + 9 * f, g->ml_lam + 9 * f, sizeof(double) * 9);
+            memcpy(g->nl_eta + 3 * f, g->ml_eta + 3 * f, sizeof(double) * 3);
+            held_add += 1;
+        }
+        /* damping of the eta update (Sec. 5): messages stay undamped for
+         * undamped_iters iterations after a (re)linearisation (Sec. 8); the
+         * message sent in the iteration of a (re)linearisation -- including
+         * a factor's first message -- is never damped.  Then d, or the
+         * network's d_f in the learned schedule. */
+        const int hold = g->prm.undamped_iters > 1 ? g->prm.undamped_iters : 1;
+        double feat[ORC_NET_NFEAT];
+        if (mode != 0) factor_features(g, f, deg_k, deg_l, feat);
+        if (mode == 2) {
+            double* xo = X + ((size_t)it * g->n_f + f) * ORC_NET_NFEAT;
+            for (int j = 0; j < ORC_NET_NFEAT; ++j) xo[j] = feat[j];
+            /* the d in [0, 0.9] minimising the sum over the changed sides of
+             * |(1 - d) new + d old - ref|^2 / |old - new|^2: each term is a
+             * unit-curvature parabola around its vertex, so the minimiser
+             * is the clipped mean of the vertices */
+            int vk, vm;
+            double dk = damping_vertex(g->nk_eta + 6 * f, g->mk_eta + 6 * f, g->eta_ref + 9 * f, 6, &vk);
+            double dm = damping_vertex(g->nl_eta + 3 * f, g->ml_eta + 3 * f, g->eta_ref + 9 * f + 6, 3, &vm);
+            double target = -1.0;
+            if (vk || vm) {
+                target = (vk * dk + vm * dm) / (vk + vm);
+                target = target < 0.0 ? 0.0 : (target > 0.9 ? 0.9 : target);
+            }
+            if (g->t - g->tlin[f] < hold || !(g->lin_k[f] > 0.0)) target = -1.0;
+            T[(size_t)it * g->n_f + f] = target;
+        }
+        double d = -1.0;
+        if (g->t - g->tlin[f] >= hold) d = mode == 1 ? orc_net_forward(g->net, feat) : g->prm.damping;
+        if (d >= 0.0) {
+            for (int i = 0; i < 6; ++i) g->nk_eta[6 * f + i] = (1.0 - d) * g->nk_eta[6 * f + i] + d * g->mk_eta[6 * f + i];
+            for (int i = 0; i < 3; ++i) g->nl_eta[3 * f + i] = (1.0 - d) * g->nl_eta[3 * f + i] + d * g->ml_eta[3 * f + i];
+        }
+    }
+    g->n_relin += relin_add;
+    g->n_held += held_add;
+}
+
+/* The belief phase: m^{t+1} replaces m^t, t advances, and every belief
+ * b^{t+1} = prior(t+1) + sum of messages is formed with its mean. */
+static int belief_phase(orc_graph* g, double* max_dmu)
+{
+    /* synchronous schedule: every factor used m^t; now m^{t+1} replaces it */
+    memcpy(g->pk_eta, g->mk_eta, sizeof(double) * 6 * (size_t)g->n_f);
+    double* tmp;
+    tmp = g->mk_lam; g->mk_lam = g->nk_lam; g->nk_lam = tmp;
+    tmp = g->mk_eta; g->mk_eta = g->nk_eta; g->nk_eta = tmp;
+    tmp = g->ml_lam; g->ml_lam = g->nl_lam; g->nl_lam = tmp;
+    tmp = g->ml_eta; g->ml_eta = g->nl_eta; g->nl_eta = tmp;
+    g->t += 1;
+    return update_beliefs(g, max_dmu);
+}
+
 static int iterate_impl(orc_graph* g, int n, double* max_dmu, int mode, double* X, double* T)
 {
     int *deg_k = NULL, *deg_l = NULL;
@@ -682,111 +810,67 @@ static int iterate_impl(orc_graph* g, int n, double* max_dmu, int mode, double* 
     }
     int status = 0;
     for (int it = 0; it < n && status == 0; ++it) {
-        long relin_add = 0, held_add = 0;
-        /* factors are independent within an iteration: they read b^t and m^t
-         * only (an OpenMP build runs them in parallel) */
-#pragma omp parallel for schedule(static) reduction(+ : relin_add, held_add)
-        for (int f = 0; f < g->n_f; ++f) {
-            double J[18], r[2], k;
-            int kk = g->fk[f], m = g->fm[f];
-            double* x0 = g->x0 + 9 * f;
-            /* the variable-to-factor messages: each variable's belief divided
-             * by this factor's previous message to it (Sec. 5); they do not
-             * depend on this iteration's linearisation */
-            double lam_inl[9], eta_inl[3], lam_ink[36], eta_ink[6], Ltmp[36];
-            for (int i = 0; i < 9; ++i) lam_inl[i] = g->lm_lam[9 * m + i] - g->ml_lam[9 * f + i];
-            for (int i = 0; i < 3; ++i) eta_inl[i] = g->lm_eta[3 * m + i] - g->ml_eta[3 * f + i];
-            for (int i = 0; i < 36; ++i) lam_ink[i] = g->kf_lam[36 * kk + i] - g->mk_lam[36 * f + i];
-            for (int i = 0; i < 6; ++i) eta_ink[i] = g->kf_eta[6 * kk + i] - g->mk_eta[6 * f + i];
-            /* a message whose incoming precision is not positive definite
-             * cannot be formed and keeps its previous value; a factor with
-             * such a message keeps its linearisation point for the iteration
-             * (a relinearisation that is due waits), so that a kept message
-             * and its factor's linearisation stay the same */
-            const int ok_l = cholesky(3, lam_inl, Ltmp) == 0;
-            const int ok_k = cholesky(6, lam_ink, Ltmp) == 0;
-            if (!g->prm.linear && ok_l && ok_k && g->t - g->tlin[f] >= g->prm.relin_interval) {
-                /* Sec. 5 / Sec. 8: relinearise when the adjacent beliefs moved
-                 * more than beta from the factor's linearisation point, at
-                 * most once every relin_interval iterations */
-                double dist2 = 0.0;
-                for (int i = 0; i < 6; ++i) dist2 += (g->kf_mu[6 * kk + i] - x0[i]) * (g->kf_mu[6 * kk + i] - x0[i]);
-                for (int i = 0; i < 3; ++i) dist2 += (g->lm_mu[3 * m + i] - x0[6 + i]) * (g->lm_mu[3 * m + i] - x0[6 + i]);
-                if (sqrt(dist2) > g->prm.relin_beta) {
-                    int active = orc_linearise(&g->cam, &g->prm, g->Rref + 9 * kk, g->cref + 3 * kk, g->lref + 3 * m,
-                                               g->kf_mu + 6 * kk, g->lm_mu + 3 * m, g->z + 2 * f, J, r, &k,
-                                               g->linA + 81 * f, g->linc + 9 * f);
-                    g->lin_r2[f] = active ? r[0] * r[0] + r[1] * r[1] : 0.0;
-                    g->lin_k[f] = active ? k : 0.0;
-                    for (int i = 0; i < 6; ++i) x0[i] = g->kf_mu[6 * kk + i];
-                    for (int i = 0; i < 3; ++i) x0[6 + i] = g->lm_mu[3 * m + i];
-                    g->tlin[f] = g->t;
-                    relin_add += 1;
-                }
-            }
-            const double* A = g->linA + 81 * f;
-            const double* c = g->linc + 9 * f;
-            /* to the keyframe, marginalising the landmark */
-            if (!ok_l || orc_factor_message(A, c, 0, lam_inl, eta_inl, g->nk_lam + 36 * f, g->nk_eta + 6 * f) != 0) {
-                memcpy(g->nk_lam + 36 * f, g->mk_lam + 36 * f, sizeof(double) * 36);
-                memcpy(g->nk_eta + 6 * f, g->mk_eta + 6 * f, sizeof(double) * 6);
-                held_add += 1;
-            }
-            /* to the landmark, marginalising the keyframe */
-            if (!ok_k || orc_factor_message(A, c, 1, lam_ink, eta_ink, g->nl_lam + 9 * f, g->nl_eta + 3 * f) != 0) {
-                memcpy(g->nl_lam + 9 * f, g->ml_lam + 9 * f, sizeof(double) * 9);
-                memcpy(g->nl_eta + 3 * f, g->ml_eta + 3 * f, sizeof(double) * 3);
-                held_add += 1;
-            }
-            /* damping of the eta update (Sec. 5): messages stay undamped for
-             * undamped_iters iterations after a (re)linearisation (Sec. 8); the
-             * message sent in the iteration of a (re)linearisation -- including
-             * a factor's first message -- is never damped.  Then d, or the
-             * network's d_f in the learned schedule. */
-            const int hold = g->prm.undamped_iters > 1 ? g->prm.undamped_iters : 1;
-            double feat[ORC_NET_NFEAT];
-            if (mode != 0) factor_features(g, f, deg_k, deg_l, feat);
-            if (mode == 2) {
-                double* xo = X + ((size_t)it * g->n_f + f) * ORC_NET_NFEAT;
-                for (int j = 0; j < ORC_NET_NFEAT; ++j) xo[j] = feat[j];
-                /* the d in [0, 0.9] minimising the sum over the changed sides of
-                 * |(1 - d) new + d old - ref|^2 / |old - new|^2: each term is a
-                 * unit-curvature parabola around its vertex, so the minimiser
-                 * is the clipped mean of the vertices */
-                int vk, vm;
-                double dk = damping_vertex(g->nk_eta + 6 * f, g->mk_eta + 6 * f, g->eta_ref + 9 * f, 6, &vk);
-                double dm = damping_vertex(g->nl_eta + 3 * f, g->ml_eta + 3 * f, g->eta_ref + 9 * f + 6, 3, &vm);
-                double target = -1.0;
-                if (vk || vm) {
-                    target = (vk * dk + vm * dm) / (vk + vm);
-                    target = target < 0.0 ? 0.0 : (target > 0.9 ? 0.9 : target);
-                }
-                if (g->t - g->tlin[f] < hold || !(g->lin_k[f] > 0.0)) target = -1.0;
-                T[(size_t)it * g->n_f + f] = target;
-            }
-            double d = -1.0;
-            if (g->t - g->tlin[f] >= hold) d = mode == 1 ? orc_net_forward(g->net, feat) : g->prm.damping;
-            if (d >= 0.0) {
-                for (int i = 0; i < 6; ++i) g->nk_eta[6 * f + i] = (1.0 - d) * g->nk_eta[6 * f + i] + d * g->mk_eta[6 * f + i];
-                for (int i = 0; i < 3; ++i) g->nl_eta[3 * f + i] = (1.0 - d) * g->nl_eta[3 * f + i] + d * g->ml_eta[3 * f + i];
-            }
-        }
-        g->n_relin += relin_add;
-        g->n_held += held_add;
-        if (status != 0) break;
-        /* synchronous schedule: every factor used m^t; now m^{t+1} replaces it */
-        memcpy(g->pk_eta, g->mk_eta, sizeof(double) * 6 * (size_t)g->n_f);
-        double* tmp;
-        tmp = g->mk_lam; g->mk_lam = g->nk_lam; g->nk_lam = tmp;
-        tmp = g->mk_eta; g->mk_eta = g->nk_eta; g->nk_eta = tmp;
-        tmp = g->ml_lam; g->ml_lam = g->nl_lam; g->nl_lam = tmp;
-        tmp = g->ml_eta; g->ml_eta = g->nl_eta; g->nl_eta = tmp;
-        g->t += 1;
-        if (update_beliefs(g, max_dmu) != 0) status = -1;
+        factor_phase(g, mode, X, T, it, deg_k, deg_l);
+        if (belief_phase(g, max_dmu) != 0) status = -1;
     }
     free(deg_k);
     free(deg_l);
     return status;
+}
+
+int orc_factor_phase(orc_graph* g)
+{
+    if (g->net) return -1;
+    factor_phase(g, 0, NULL, NULL, 0, NULL, NULL);
+    return 0;
+}
+
+int orc_belief_phase(orc_graph* g, double* max_dmu) { return belief_phase(g, max_dmu); }
+
+int orc_set_part(orc_graph* g, const unsigned char* fac_mask, const unsigned char* var_mask)
+{
+    free(g->fac_mask);
+    free(g->var_mask);
+    g->fac_mask = g->var_mask = NULL;
+    if (fac_mask) g->fac_mask = dup_bytes(fac_mask, (size_t)g->n_f);
+    if (var_mask) g->var_mask = dup_bytes(var_mask, (size_t)(g->n_kf + g->n_lm));
+    return 0;
+}
+
+void orc_get_new_kf_messages(const orc_graph* g, int n, const int* f, double* lam, double* eta)
+{
+    for (int i = 0; i < n; ++i) {
+        memcpy(lam + 36 * (size_t)i, g->nk_lam + 36 * (size_t)f[i], sizeof(double) * 36);
+        memcpy(eta + 6 * (size_t)i, g->nk_eta + 6 * (size_t)f[i], sizeof(double) * 6);
+    }
+}
+
+void orc_put_new_kf_messages(orc_graph* g, int n, const int* f, const double* lam, const double* eta)
+{
+    for (int i = 0; i < n; ++i) {
+        memcpy(g->nk_lam + 36 * (size_t)f[i], lam + 36 * (size_t)i, sizeof(double) * 36);
+        memcpy(g->nk_eta + 6 * (size_t)f[i], eta + 6 * (size_t)i, sizeof(double) * 6);
+    }
+}
+
+void orc_get_kf_beliefs(const orc_graph* g, int n, const int* k, double* rec)
+{
+    for (int i = 0; i < n; ++i) {
+        double* o = rec + 48 * (size_t)i;
+        memcpy(o, g->kf_lam + 36 * (size_t)k[i], sizeof(double) * 36);
+        memcpy(o + 36, g->kf_eta + 6 * (size_t)k[i], sizeof(double) * 6);
+        memcpy(o + 42, g->kf_mu + 6 * (size_t)k[i], sizeof(double) * 6);
+    }
+}
+
+void orc_put_kf_beliefs(orc_graph* g, int n, const int* k, const double* rec)
+{
+    for (int i = 0; i < n; ++i) {
+        const double* o = rec + 48 * (size_t)i;
+        memcpy(g->kf_lam + 36 * (size_t)k[i], o, sizeof(double) * 36);
+        memcpy(g->kf_eta + 6 * (size_t)k[i], o + 36, sizeof(double) * 6);
+        memcpy(g->kf_mu + 6 * (size_t)k[i], o + 42, sizeof(double) * 6);
+    }
 }
 
 int orc_iterate(orc_graph* g, int n, double* max_dmu)

@@ -118,6 +118,22 @@ long orc_relinearisations(const orc_graph* g);
  * not positive definite, so the Schur complement of Sec. 5 does not exist. */
 long orc_held_messages(const orc_graph* g);
 
+/* ---- one graph solved in parts (the multi-rank split of the iteration) ----
+ * orc_set_part restricts which factors form messages (fac_mask, n_f bytes)
+ * and which variables form beliefs (var_mask: keyframes then landmarks);
+ * NULL = all.  orc_iterate is orc_factor_phase then orc_belief_phase.
+ * Between the two, the new messages to keyframes (m^{t+1}, full 6x6 and 6)
+ * of chosen factors can be read and written; after the belief phase, chosen
+ * keyframe beliefs (Lambda 36, eta 6, mean 6 per keyframe) likewise.  Fixed
+ * damping schedule only (orc_factor_phase returns -1 with a network set). */
+int orc_set_part(orc_graph* g, const unsigned char* fac_mask, const unsigned char* var_mask);
+int orc_factor_phase(orc_graph* g);
+int orc_belief_phase(orc_graph* g, double* max_dmu);
+void orc_get_new_kf_messages(const orc_graph* g, int n, const int* f, double* lam, double* eta);
+void orc_put_new_kf_messages(orc_graph* g, int n, const int* f, const double* lam, const double* eta);
+void orc_get_kf_beliefs(const orc_graph* g, int n, const int* k, double* rec /* n x 48 */);
+void orc_put_kf_beliefs(orc_graph* g, int n, const int* k, const double* rec);
+
 /* ---- learned damping (no counterpart in the paper: a per-factor d in place
  * of the fixed d of Sec. 5 / Sec. 8) ----
  * Network: 16 features -> 64 -> 64 -> 1, ReLU hidden layers, output

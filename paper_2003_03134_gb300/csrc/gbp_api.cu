@@ -20,6 +20,9 @@
 
 using namespace gbp;
 
+static_assert(GBP_SPLIT_MSG_FLOATS == KREC + KJ, "split message record");
+static_assert(GBP_SPLIT_KF_FLOATS == KBEL, "split keyframe record");
+
 namespace {
 
 constexpr int GRAPH_CHUNK = 8;   // iterations per captured CUDA graph
@@ -145,6 +148,10 @@ struct gbp_graph {
     bool built = false;
     int tuned_mode = 0;                         // autotuner's choice (1 or 2), 0 = not tuned
     int tuned_fshape = -1, tuned_pshape = -1;   // its launch shapes, -1 = not tuned
+    // one graph split across ranks (gbp_set_partition): the keyframes and
+    // landmarks whose beliefs this graph forms; lm1 < 0 = not split
+    int part_kf0 = 0, part_kf1 = -1, part_lm0 = 0, part_lm1 = -1;
+    std::vector<int32_t> f_of_obs;              // internal factor of each caller observation
     gbp_tuning tuning{};                        // candidates of the last gbp_autotune
     int last_mode = 0;                          // launch mode of the last gbp_iterate()
     int64_t launches = 0;                       // kernels launched (graph replays count their kernels)
@@ -291,16 +298,24 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
     for (int v = 0; v < nk; ++v)
         if (kf_off[v + 1] == kf_off[v]) orphan.push_back(v);
     {
+        // a tile never spans two problems of a batch, nor the landmark range
+        // of a partition
+        std::vector<int32_t> breaks(g->prob_lm0.begin() + 1, g->prob_lm0.end() - 1);
+        if (g->part_lm1 >= 0) {
+            breaks.push_back(g->part_lm0);
+            breaks.push_back(g->part_lm1);
+        }
+        std::sort(breaks.begin(), breaks.end());
         int cur = 0;
-        size_t next_prob = 1;   // a tile never spans two problems of a batch
+        size_t next_brk = 0;
         for (int m = 0; m < nl; ++m) {
             const int lo = lm_off[m], hi = lm_off[m + 1], d = hi - lo;
-            while (next_prob + 1 < g->prob_lm0.size() && g->prob_lm0[next_prob] <= m) {
-                if (g->prob_lm0[next_prob] == m && cur > 0) {
+            while (next_brk < breaks.size() && breaks[next_brk] <= m) {
+                if (breaks[next_brk] == m && cur > 0) {
                     tiles.push_back(lo);
                     cur = 0;
                 }
-                ++next_prob;
+                ++next_brk;
             }
             if (d == 0) {
                 orphan.push_back(nk + m);
@@ -407,15 +422,42 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
     d.n_tiles = n_tiles;
     d.n_big = (int32_t)big.size();
     d.n_orphan = (int32_t)orphan.size();
+    d.tile_off = 0;
+    d.kf_item_off = 0;
+    d.kf_item_n = nk;
+    d.big_item_off = 0;
+    d.big_item_n = d.n_big;
+    if (g->part_lm1 >= 0) {
+        // this rank's tiles: those of its landmarks (contiguous, tiles break
+        // at the range's ends); its split landmarks likewise
+        int t0 = 0, t1 = 0;
+        for (int t = 0; t < n_tiles; ++t) {
+            const int lm = g->fm[tiles[t]];
+            if (lm < g->part_lm0) t0 = t + 1;
+            if (lm < g->part_lm1) t1 = t + 1;
+        }
+        int b0 = 0, b1 = 0;
+        for (size_t i = 0; i < big.size(); ++i) {
+            if (big[i] < g->part_lm0) b0 = (int)i + 1;
+            if (big[i] < g->part_lm1) b1 = (int)i + 1;
+        }
+        d.tile_off = t0;
+        d.n_tiles = t1 - t0;
+        d.kf_item_off = g->part_kf0;
+        d.kf_item_n = g->part_kf1 - g->part_kf0;
+        d.big_item_off = b0;
+        d.big_item_n = b1 - b0;
+    }
     {
         // a block per belief item while a warp per item would leave SMs
         // idle (at most one block of FACTOR_BLOCK / 32 items per SM), else
         // a warp per item, so that the single-thread solves of many
-        // keyframes run side by side
+        // keyframes run side by side (decided on the whole graph, so that
+        // every part of a split graph sums as the whole graph would)
         int dev = 0, sms = 0;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        d.b_warps = (nk + d.n_big) <= sms * (FACTOR_BLOCK / 32) ? FACTOR_BLOCK / 32 : 1;
+        d.b_warps = (nk + (int)big.size()) <= sms * (FACTOR_BLOCK / 32) ? FACTOR_BLOCK / 32 : 1;
     }
     d.kf_D = s.kf_D;
     d.kf_A = s.kf_A;
@@ -630,6 +672,8 @@ void order_factors(gbp_graph* g, const std::vector<int32_t>& ok, const std::vect
         g->z[2 * i + 1] = uv[2 * s + 1];
         g->obs_index[i] = idx[s];
     }
+    g->f_of_obs.assign(n, 0);
+    for (int i = 0; i < n; ++i) g->f_of_obs[g->obs_index[i]] = i;
 }
 
 template <typename R>
@@ -1262,6 +1306,7 @@ gbp_status gbp_iterate(gbp_graph* g, int32_t n_iters, int32_t* iters_done) {
     gbp_status st = ensure_built(g);
     if (st != GBP_OK) return st;
     int n = n_iters > 0 ? n_iters : g->prm.iterations;
+    if (g->part_lm1 >= 0) return fail(g, GBP_ESTATE, "a partitioned graph iterates with gbp_split_phase");
     if (g->n_f == 0 && g->n_kf == 0 && g->n_lm == 0) return GBP_OK;
     if (g->prm.damping_mode == 1 && !g->has_model)
         return fail(g, GBP_ESTATE, "damping_mode 1 needs a network (gbp_set_damping_model)");
@@ -1638,6 +1683,83 @@ gbp_status gbp_add_keyframe(gbp_graph* g, const double* kf_Rt_init, int32_t n_ne
                     : add_keyframe_impl<float>(g, kf_Rt_init, n_new_lm, new_lm_xyz, n_obs, obs_lm, obs_uv);
     if (st == GBP_OK && new_kf_index) *new_kf_index = g->n_kf - 1;
     return st;
+}
+
+gbp_status gbp_set_partition(gbp_graph* g, int32_t kf_begin, int32_t kf_end, int32_t lm_begin, int32_t lm_end) {
+    if (!g) return GBP_EINVAL;
+    if (g->prob_kf0.size() != 2) return fail(g, GBP_ESTATE, "partitions apply to a single-problem graph");
+    if (g->prm.precision_mode == 2) return fail(g, GBP_ESTATE, "partitions run the FP32 path");
+    if (lm_end < 0) {   // back to the whole graph
+        g->part_lm1 = -1;
+    } else {
+        if (kf_begin < 0 || kf_begin > kf_end || kf_end > g->n_kf || lm_begin < 0 || lm_begin > lm_end ||
+            lm_end > g->n_lm)
+            return fail(g, GBP_EINVAL, "partition range out of bounds");
+        g->part_kf0 = kf_begin;
+        g->part_kf1 = kf_end;
+        g->part_lm0 = lm_begin;
+        g->part_lm1 = lm_end;
+    }
+    destroy_exec(g);
+    g->built = false;   // the tiles break at the landmark range: rebuilt, and reset to iteration 0
+    return ensure_built(g);
+}
+
+gbp_status gbp_split_phase(gbp_graph* g, int32_t phase) {
+    if (!g || phase < 0 || phase > 1) return GBP_EINVAL;
+    if (g->part_lm1 < 0) return fail(g, GBP_ESTATE, "gbp_split_phase needs gbp_set_partition");
+    if (g->prm.damping_mode != 0) return fail(g, GBP_ESTATE, "a partitioned graph runs the fixed damping schedule");
+    gbp_status st = ensure_built(g);
+    if (st != GBP_OK) return st;
+    (void)cudaGetLastError();
+    const DevGraph<float>& d = g->sf.g;
+    const KParams<float> kp = make_kparams<float>(g);
+    CK(phase == 0 ? launch_factor<float>(d, kp, g->stream, DAMP_FIXED, false, factor_shape(g))
+                  : launch_belief<float>(d, kp, g->stream, false));
+    g->launches += 1;
+    g->last_mode = 2;
+    return GBP_OK;
+}
+
+namespace {
+gbp_status split_records(gbp_graph* g, int32_t kind, int32_t n, const int32_t* index, float* io, bool put) {
+    if (!g || (kind != 0 && kind != 1) || n < 0 || (n && (!index || !io))) return GBP_EINVAL;
+    if (g->storage != 0) return fail(g, GBP_ESTATE, "split records are FP32");
+    if (n == 0) return GBP_OK;
+    std::vector<int32_t> idx(n);
+    for (int i = 0; i < n; ++i) {
+        const int32_t v = index[i];
+        if (kind == 0) {
+            if (v < 0 || v >= g->n_f) return fail(g, GBP_EINVAL, "observation index out of range");
+            idx[i] = g->f_of_obs[v];
+        } else {
+            if (v < 0 || v >= g->n_kf) return fail(g, GBP_EINVAL, "keyframe index out of range");
+            idx[i] = v;
+        }
+    }
+    const size_t width = kind == 0 ? (size_t)GBP_SPLIT_MSG_FLOATS : (size_t)GBP_SPLIT_KF_FLOATS;
+    int32_t* d_idx = nullptr;
+    float* d_io = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&d_idx), sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&d_io), sizeof(float) * width * n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_idx, idx.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess && put) e = cudaMemcpyAsync(d_io, io, sizeof(float) * width * n, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = launch_split_records<float>(g->sf.g, kind, put ? 1 : 0, n, d_idx, d_io, g->stream);
+    if (e == cudaSuccess && !put) e = cudaMemcpyAsync(io, d_io, sizeof(float) * width * n, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (d_idx) cudaFree(d_idx);
+    if (d_io) cudaFree(d_io);
+    if (e != cudaSuccess) return cuda_fail(g, e, "split records");
+    return GBP_OK;
+}
+}  // namespace
+
+gbp_status gbp_get_split_records(const gbp_graph* g, int32_t kind, int32_t n, const int32_t* index, float* out) {
+    return split_records(const_cast<gbp_graph*>(g), kind, n, index, out, false);
+}
+
+gbp_status gbp_put_split_records(gbp_graph* g, int32_t kind, int32_t n, const int32_t* index, const float* in) {
+    return split_records(g, kind, n, index, const_cast<float*>(in), true);
 }
 
 void gbp_destroy_graph(gbp_graph* g) {

@@ -122,6 +122,11 @@ struct DevGraph {
     const int32_t* big_lm;    // landmarks split across tiles (more than 32 factors)
     const int32_t* orphan;    // variables without factors: keyframe v, or n_kf + landmark
     int32_t n_tiles, n_big, n_orphan;
+    // the part of the graph a launch covers (the whole graph unless it is
+    // split across ranks): tiles [tile_off, tile_off + n_tiles) -- n_tiles
+    // counts them -- and belief items: keyframes [kf_item_off, + kf_item_n),
+    // split landmarks big_lm[big_item_off, + big_item_n), every orphan
+    int32_t tile_off, kf_item_off, kf_item_n, big_item_off, big_item_n;
     int32_t b_warps;          // warps per belief-phase item: 4 (a block) for small graphs, else 1
     const int32_t* kf_birth;  // n_kf: iteration at which the keyframe was added (prior anneal start)
     const int32_t* lm_birth;  // n_lm
@@ -206,6 +211,8 @@ template <typename R> cudaError_t launch_problem_metrics(const DevGraph<R>& g, c
                                                          cudaStream_t s);
 template <typename R> cudaError_t launch_residuals(const DevGraph<R>& g, const KParams<R>& p, double* out,
                                                    cudaStream_t s);
+template <typename R> cudaError_t launch_split_records(const DevGraph<R>& g, int kind, int put, int n,
+                                                       const int32_t* idx, float* io, cudaStream_t s);
 int metrics_blocks(int n_f);
 
 // damping network (gbp_mlp.cu): device-to-device copy of a network's packed

@@ -408,6 +408,13 @@ __device__ __forceinline__ void msg_eta(const R J[2][n], R g0, R g1, R* eta) {
     for (int i = 0; i < n; ++i) eta[i] = J[0][i] * g0 + J[1][i] * g1;
 }
 
+// Whether keyframe k's belief is formed in this graph (always, unless the
+// graph is one rank's part of a split graph).
+template <typename R>
+__device__ __forceinline__ bool kf_in_part(const DevGraph<R>& g, int k) {
+    return k >= g.kf_item_off && k < g.kf_item_off + g.kf_item_n;
+}
+
 // A factor's lin record (SoA rows y0, y1, W, |r|^2): its linearisation
 // between relinearisations, with the keyframe Jacobian block in kj.
 template <typename R>
@@ -714,6 +721,7 @@ __device__ __forceinline__ bool kf_incoming64(const KfCavity<R>& kc, double* A, 
     for (int i = 0; i < 21; ++i) A[i] = double(__ldcg(kc.kb + KB_LAM + i)) - lam[i];
     for (int i = 0; i < 6; ++i) q[i] = double(__ldcg(kc.kb + KB_ETA + i)) - eta[i];
     if (chol_packed<double, 6>(A, inv_d, ratio)) return true;
+    if (kc.i0 < 0) return false;   // the keyframe's other messages are not all on this rank
     for (int i = 0; i < 21; ++i) A[i] = 0.0;
     for (int i = 0; i < 6; ++i) {
         // as b^t added it, in the kernel's precision
@@ -1206,6 +1214,9 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
                                             g.lm_ref + (size_t)m * 3, g.z[2 * (size_t)f], g.z[2 * (size_t)f + 1]));
         store_lin<R>(g, f, L);
         store_jac<R>(g.kjs + (size_t)slot * KJ, L.Jk);
+        // a keyframe of another rank's part: no belief phase here moves the
+        // staged block, so the factor keeps its own copy up to date
+        if (!kf_in_part(g, k)) store_jac<R>(g.kj + (size_t)slot * KJ, L.Jk);
     } else if (active) {
         R jr[KJ];
         load_rec<R, KJ>(g.kj + (size_t)slot * KJ, jr);
@@ -1374,7 +1385,7 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
         }
         if (!(ks.det >= P.cav_ratio)) {
             ok_k = kf_incoming_ok64<R>(KfCavity<R>{kbp, mk_read(g, t), g.kj, g.kf_D + (size_t)k * 6,
-                                                   g.kf_A + (size_t)k * 6, g.kf_off[k], g.kf_off[k + 1], slot,
+                                                   g.kf_A + (size_t)k * 6, kf_in_part(g, k) ? g.kf_off[k] : -1, g.kf_off[k + 1], slot,
                                                    kf_prior_scale(g, P, k, t), P.anchor_scale, P.inv_sigma2});
             k64 = ok_k;
             atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
@@ -1423,6 +1434,7 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
             L = rb.L;
             store_lin<R>(g, f, L);
             store_jac<R>(g.kjs + (size_t)slot * KJ, L.Jk);
+            if (!kf_in_part(g, k)) store_jac<R>(g.kj + (size_t)slot * KJ, L.Jk);
             if (!k64)
 #pragma unroll
                 for (int i = 0; i < NML; ++i) cl[i] = rb.cl[i];
@@ -1447,8 +1459,9 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
     if (ok_k) {
         if (k64) {
             const Msg5<R> o = kf_message64<R>(
-                KfCavity<R>{kbp, mk_read(g, t), g.kj, g.kf_D + (size_t)k * 6, g.kf_A + (size_t)k * 6, g.kf_off[k],
-                            g.kf_off[k + 1], slot, kf_prior_scale(g, P, k, t), P.anchor_scale, P.inv_sigma2},
+                KfCavity<R>{kbp, mk_read(g, t), g.kj, g.kf_D + (size_t)k * 6, g.kf_A + (size_t)k * 6,
+                            kf_in_part(g, k) ? g.kf_off[k] : -1, g.kf_off[k + 1], slot, kf_prior_scale(g, P, k, t),
+                            P.anchor_scale, P.inv_sigma2},
                 L);
 #pragma unroll
             for (int i = 0; i < NML; ++i) cl[i] = o.v[i];
@@ -1669,8 +1682,8 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
     const int gsize = 32 * W;
     const int tg = threadIdx.x & (gsize - 1);   // thread within the group
     float dmu = 0.0f;
-    if (item < g.n_kf) {
-        const int k = item;
+    if (item < g.kf_item_n) {
+        const int k = g.kf_item_off + item;
         const R* msgs = mk_write(g, t);
         // the first thread's own inputs first, so their loads overlap the reduction
         R prior[6], mu_old[6];
@@ -1708,8 +1721,8 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
         R acc[27];
         group_total<R, 32, 27, W>(hi, acc);
         if (tg == 0) dmu = finish_keyframe<R>(g, P, k, prior, acc, mu_old, g.kf_bel_out);
-    } else if (item < g.n_kf + g.n_big) {
-        const int m = g.big_lm[item - g.n_kf];
+    } else if (item < g.kf_item_n + g.big_item_n) {
+        const int m = g.big_lm[g.big_item_off + item - g.kf_item_n];
         R hi[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) hi[j] = R(0);
@@ -1727,7 +1740,7 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
         }
     } else {
         // variables without factors: prior-only beliefs, mean 0
-        const int i = (item - g.n_kf - g.n_big) * gsize + tg;
+        const int i = (item - g.kf_item_n - g.big_item_n) * gsize + tg;
         if (i < g.n_orphan) {
             const int v = g.orphan[i];
             const R isig2 = P.inv_sigma2;
@@ -1756,7 +1769,7 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
 // phase-B work items, and the blocks that hold them at one item per group
 template <typename R>
 __host__ __device__ inline int phase_b_items(const DevGraph<R>& g) {
-    return g.n_kf + g.n_big + (g.n_orphan + 32 * g.b_warps - 1) / (32 * g.b_warps);
+    return g.kf_item_n + g.big_item_n + (g.n_orphan + 32 * g.b_warps - 1) / (32 * g.b_warps);
 }
 template <typename R>
 __host__ __device__ inline int phase_b_blocks(const DevGraph<R>& g) {
@@ -1788,7 +1801,7 @@ __device__ __forceinline__ void factor_body(const DevGraph<R>& g, const KParams<
     const int tile = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
     const int t = g.ctl[CTL_ITER];
     float dmu = 0.0f;
-    if (tile < g.n_tiles) dmu = tile_work<R, MODE>(g, P, tile, t, lane, S, MODE == DAMP_LEARNED);   // uniform per warp
+    if (tile < g.n_tiles) dmu = tile_work<R, MODE>(g, P, g.tile_off + tile, t, lane, S, MODE == DAMP_LEARNED);   // uniform per warp
     else if constexpr (MODE == DAMP_LEARNED) mlp_load_wait();   // the block's barrier, for warps without a tile
     pdl_allow_next();
     dmu = warp_max(dmu);
@@ -1891,7 +1904,7 @@ __global__ void __launch_bounds__(FACTOR_BLOCK, MINB)
         // phase A: factors and landmarks wholly inside a tile
         float dmu = 0.0f;
         for (int tile = gwarp; tile < g.n_tiles; tile += nwarps)
-            dmu = fmaxf(dmu, tile_work<R, MODE>(g, P, tile, t, lane, S));
+            dmu = fmaxf(dmu, tile_work<R, MODE>(g, P, g.tile_off + tile, t, lane, S));
         dmu = warp_max(dmu);
         if (lane == 0 && dmu > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), dmu);
         if (!grid_barrier(g.ctl, nb, &flag_sh)) break;
@@ -2327,6 +2340,51 @@ cudaError_t launch_residuals(const DevGraph<R>& g, const KParams<R>& p, double* 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------
+// One graph split across ranks: the records a rank exchanges between the
+// phases of an iteration.  Message records (kind 0), per factor: its
+// compact message to the keyframe of iteration t+1 (KREC) and its staged
+// Jacobian block (KJ) -- what the keyframe's owner needs to sum it.
+// Keyframe records (kind 1): the belief record (KBEL).
+
+constexpr int SPLIT_MSG = KREC + KJ;
+
+template <typename R>
+__global__ void split_records_kernel(DevGraph<R> g, int kind, int put, int n, const int32_t* __restrict__ idx,
+                                     float* io) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (kind == 0) {
+        const int t = g.ctl[CTL_ITER];
+        const size_t slot = (size_t)g.kpos[idx[i]];
+        R* rec = mk_write(g, t) + slot * KREC;
+        R* jr = g.kjs + slot * KJ;
+        float* o = io + (size_t)i * SPLIT_MSG;
+        for (int j = 0; j < KREC; ++j) {
+            if (put) rec[j] = R(o[j]);
+            else o[j] = float(rec[j]);
+        }
+        for (int j = 0; j < KJ; ++j) {
+            if (put) jr[j] = R(o[KREC + j]);
+            else o[KREC + j] = float(jr[j]);
+        }
+    } else {
+        R* rec = g.kf_bel + (size_t)idx[i] * KBEL;
+        float* o = io + (size_t)i * KBEL;
+        for (int j = 0; j < KBEL; ++j) {
+            if (put) rec[j] = R(o[j]);
+            else o[j] = float(rec[j]);
+        }
+    }
+}
+
+template <typename R>
+cudaError_t launch_split_records(const DevGraph<R>& g, int kind, int put, int n, const int32_t* idx, float* io,
+                                 cudaStream_t s) {
+    if (n > 0) split_records_kernel<R><<<(n + 127) / 128, 128, 0, s>>>(g, kind, put, n, idx, io);
+    return cudaGetLastError();
+}
+
 #define GBP_INSTANTIATE(R)                                                                                 \
     template cudaError_t launch_factor<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t, int, bool, int); \
     template cudaError_t launch_capture_messages<R>(const DevGraph<R>&, int, R*, cudaStream_t);            \
@@ -2337,7 +2395,8 @@ cudaError_t launch_residuals(const DevGraph<R>& g, const KParams<R>& p, double* 
     template cudaError_t launch_persistent<R>(const DevGraph<R>&, const KParams<R>&, int, float, int, int, cudaStream_t, int, int); \
     template cudaError_t launch_prior<R>(const DevGraph<R>&, const KParams<R>&, R*, R*, R*, R*, cudaStream_t); \
     template cudaError_t launch_metrics<R>(const DevGraph<R>&, const KParams<R>&, double*, int, double*, cudaStream_t); \
-    template cudaError_t launch_residuals<R>(const DevGraph<R>&, const KParams<R>&, double*, cudaStream_t);
+    template cudaError_t launch_residuals<R>(const DevGraph<R>&, const KParams<R>&, double*, cudaStream_t); \
+    template cudaError_t launch_split_records<R>(const DevGraph<R>&, int, int, int, const int32_t*, float*, cudaStream_t);
 
 GBP_INSTANTIATE(float)
 GBP_INSTANTIATE(double)

@@ -95,7 +95,10 @@ EXPORTS = ["gbp_default_params", "gbp_create_graph", "gbp_set_params", "gbp_get_
            "gbp_get_batch_info", "gbp_get_problem_are", "gbp_mlp_create", "gbp_mlp_set_params",
            "gbp_mlp_get_params", "gbp_mlp_forward", "gbp_mlp_gradient", "gbp_mlp_train_step", "gbp_mlp_destroy",
            "gbp_set_damping_model", "gbp_capture_messages", "gbp_get_factor_order", "gbp_record_iterations",
-           "gbp_get_relin_iters", "gbp_get_tuning", "gbp_get_residuals"]
+           "gbp_get_relin_iters", "gbp_get_tuning", "gbp_get_residuals", "gbp_set_partition", "gbp_split_phase",
+           "gbp_get_split_records", "gbp_put_split_records"]
+GBP_SPLIT_MSG_FLOATS = 20
+GBP_SPLIT_KF_FLOATS = 56
 GBP_MLP_NFEAT = 16
 GBP_MLP_NPARAM = 5313
 GBP_NOALLOC_MAX_OBS = 1 << 20
@@ -127,6 +130,10 @@ def lib() -> C.CDLL:
     L.gbp_get_sizes.argtypes = [vp, _I, _I, _I]
     L.gbp_get_relin_iters.argtypes = [vp, _I]
     L.gbp_get_residuals.argtypes = [vp, _D]
+    L.gbp_set_partition.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+    L.gbp_split_phase.argtypes = [vp, C.c_int32]
+    L.gbp_get_split_records.argtypes = [vp, C.c_int32, C.c_int32, _I, C.POINTER(C.c_float)]
+    L.gbp_put_split_records.argtypes = [vp, C.c_int32, C.c_int32, _I, C.POINTER(C.c_float)]
     L.gbp_profile_iterations.argtypes = [vp, C.c_int32, _D]
     L.gbp_autotune.argtypes = [vp, C.c_int32, _I, _D]
     L.gbp_get_tuning.argtypes = [vp, C.POINTER(gbp_tuning)]
@@ -325,6 +332,33 @@ def gbp_get_residuals(g: int) -> np.ndarray:
     e = np.zeros(gbp_get_sizes(g)[2])
     _check(lib().gbp_get_residuals(g, _dp(e)), g)
     return e
+
+
+def gbp_set_partition(g: int, kf_range, lm_range) -> None:
+    """This graph's part of a graph split across ranks (None: the whole graph)."""
+    if lm_range is None:
+        _check(lib().gbp_set_partition(g, 0, 0, 0, -1), g)
+    else:
+        _check(lib().gbp_set_partition(g, int(kf_range[0]), int(kf_range[1]), int(lm_range[0]), int(lm_range[1])), g)
+
+
+def gbp_split_phase(g: int, phase: int) -> None:
+    _check(lib().gbp_split_phase(g, int(phase)), g)
+
+
+def gbp_get_split_records(g: int, kind: int, index) -> np.ndarray:
+    idx = _i32(index)
+    width = GBP_SPLIT_MSG_FLOATS if kind == 0 else GBP_SPLIT_KF_FLOATS
+    out = np.zeros((idx.size, width), dtype=np.float32)
+    _check(lib().gbp_get_split_records(g, int(kind), idx.size, _ip(idx), out.ctypes.data_as(C.POINTER(C.c_float))), g)
+    return out
+
+
+def gbp_put_split_records(g: int, kind: int, index, recs) -> None:
+    idx = _i32(index)
+    width = GBP_SPLIT_MSG_FLOATS if kind == 0 else GBP_SPLIT_KF_FLOATS
+    r = np.ascontiguousarray(recs, dtype=np.float32).reshape(idx.size, width)
+    _check(lib().gbp_put_split_records(g, int(kind), idx.size, _ip(idx), r.ctypes.data_as(C.POINTER(C.c_float))), g)
 
 
 def gbp_get_stats(g: int) -> gbp_stats:
