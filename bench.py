@@ -288,7 +288,7 @@ def lm_baseline(p, kf_ref, lm_ref, max_iters=50):
         are_ref = float(np.linalg.norm(uv[ok] - ref_uv[ok], axis=1).mean())
         if t_1px is None and are_ref < 1.0:
             t_1px, it_1px = t_total, lm.iterations
-    res = {"kind": "Levenberg-Marquardt, dense Schur complement, single-threaded C (same objective, Huber 2 sigma)",
+    res = {"kind": "Levenberg-Marquardt, dense Schur complement, single-threaded C (the energy of the same factors, Huber 2 sigma)",
            "iterations": lm.iterations, "converged": lm.converged, "seconds": t_total,
            "ms_per_iteration": 1e3 * t_total / max(lm.iterations, 1), "iters_to_1px_vs_oracle": it_1px,
            "ms_to_1px_vs_oracle": 1e3 * t_1px if t_1px is not None else None, "final_are_vs_oracle": are_ref,

@@ -2,7 +2,7 @@
 CPU: the comparison baseline of the paper's timing experiments (Sec. 9.1),
 written for this project (``lm_ba.c``; plain single-threaded C).
 
-It minimises the objective GBP's iteration settles on -- reprojection errors
+It minimises the energy of GBP's factors -- reprojection errors
 under the Huber loss (Sec. 6), the weak priors of Sec. 4 at their final
 strength (Sec. 8) and the anchor of the first keyframe -- in the same chart
 (every variable perturbs its initial value).  ``LM(problem).solve()`` runs to

@@ -4,7 +4,8 @@
  * paper compares GBP against an LM solver with dense Schur elimination and
  * Cholesky, Sec. 9.1).
  *
- * Objective (the one GBP's iteration settles on, Sec. 4 / Sec. 6 / Sec. 8):
+ * Objective (the energy of GBP's factors, Sec. 4 / Sec. 6 / Sec. 8; with the quadratic
+ * loss its minimiser is GBP's fixed point):
  *   E(x) = sum_f rho(|r_f| / sigma) + 1/2 sum_v x_v^T P_v x_v
  *   r_f  = z_f - pi(R_k (l_m - c_k)),  R_k = Exp(w_k) Rref_k,  c_k = cref_k + dc_k,
  *          l_m = lref_m + dl_m      (the chart of every variable: its initial value)

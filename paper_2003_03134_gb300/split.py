@@ -4,11 +4,14 @@ The paper runs a graph on one IPU and names multi-chip scaling as the way to
 larger problems (Sec. 10).  Here a large graph (the 2000-keyframe loop) is
 cut into parts, one per rank:
 
-* ``partition``: keyframes in contiguous segments of the trajectory, one per
-  rank; each landmark goes to the rank that owns the majority of the
+* ``partition``: keyframes in groups of about equal factor counts, one per
+  rank -- by default spatial groups (recursive bisection of the initial
+  camera centres along the widest axis), so that a place the camera
+  revisits (a loop closure) stays on one rank; or contiguous segments of the
+  sequence.  Each landmark goes to the rank that owns the majority of the
   keyframes observing it (ties to the lowest rank), and with it all of its
-  factors.  Landmarks are renumbered so that each rank's are contiguous (a
-  relabelling of the same problem).
+  factors.  Keyframes and landmarks are renumbered so that each rank's are
+  contiguous (a relabelling of the same problem).
 * ``SplitRank``: one rank's side of an iteration, over an *engine* that runs
   the rank's part -- its factors' messages (factor phase), its variables'
   beliefs (belief phase) -- and reads and writes boundary records:
@@ -59,16 +62,61 @@ def kf_owner(n_kf: int, world: int) -> np.ndarray:
     return (np.arange(n_kf, dtype=np.int64) * world) // max(n_kf, 1)
 
 
-def partition(problem, world: int):
-    """(renumbered problem, landmark permutation old -> new, [Part per rank])."""
-    own_k = kf_owner(problem.n_kf, world)
+def camera_centres(kf_Rt: np.ndarray) -> np.ndarray:
+    """c = -R^T t of each (R | t) world-to-camera pose."""
+    R = kf_Rt[:, :9].reshape(-1, 3, 3)
+    return -np.einsum("kji,kj->ki", R, kf_Rt[:, 9:])
+
+
+def spatial_groups(centres: np.ndarray, weight: np.ndarray, world: int) -> list:
+    """Recursive coordinate bisection: split the keyframes at the weighted
+    median of the widest axis of their bounding box, the weight shared out in
+    proportion to the ranks on each side, until there is one group per rank.
+    Each group lists its keyframes in increasing order."""
+    def rec(ids, w):
+        if w == 1 or ids.size <= 1:
+            return [ids] + [ids[:0]] * (w - 1)
+        c = centres[ids]
+        ax = int(np.argmax(c.max(axis=0) - c.min(axis=0)))
+        o = ids[np.argsort(c[:, ax], kind="stable")]
+        w1 = w // 2
+        cw = np.cumsum(weight[o])
+        cut = int(np.searchsorted(cw, cw[-1] * w1 / w)) + 1
+        cut = min(max(cut, 1), o.size - 1)
+        return rec(np.sort(o[:cut]), w1) + rec(np.sort(o[cut:]), w - w1)
+    return rec(np.arange(centres.shape[0]), world)
+
+
+def partition(problem, world: int, kf_split: str = "spatial"):
+    """(renumbered problem, landmark permutation old -> new, [Part per rank]).
+    ``kf_split``: "spatial" (``spatial_groups`` weighted by observation
+    counts) or "sequence" (``kf_owner``).  With "sequence" the keyframes keep
+    their numbers."""
+    if kf_split == "spatial" and world > 1:
+        counts = np.bincount(problem.obs_kf, minlength=problem.n_kf).astype(np.float64)
+        groups = spatial_groups(camera_centres(problem.kf_Rt_init), counts, world)
+        order_k = np.concatenate(groups)                      # new keyframe i = old order_k[i]
+        sizes = np.array([g.size for g in groups])
+        own_k = np.repeat(np.arange(world), sizes)
+    elif kf_split in ("spatial", "sequence"):
+        order_k = np.arange(problem.n_kf)
+        own_k = kf_owner(problem.n_kf, world)
+    else:
+        raise ValueError(f"unknown kf_split {kf_split!r}")
+    new_k_of_old = np.empty(problem.n_kf, dtype=np.int64)
+    new_k_of_old[order_k] = np.arange(problem.n_kf)
+    obs_kf = new_k_of_old[problem.obs_kf]
     votes = np.zeros((problem.n_lm, world), dtype=np.int64)
-    np.add.at(votes, (problem.obs_lm, own_k[problem.obs_kf]), 1)
+    np.add.at(votes, (problem.obs_lm, own_k[obs_kf]), 1)
     own_l = np.argmax(votes, axis=1)                       # majority, ties to the lowest rank
     order = np.argsort(own_l, kind="stable")               # new landmark i = old order[i]
     new_of_old = np.empty(problem.n_lm, dtype=np.int64)
     new_of_old[order] = np.arange(problem.n_lm)
     q = copy.copy(problem)
+    q.kf_Rt_true = problem.kf_Rt_true[order_k]
+    q.kf_Rt_init = problem.kf_Rt_init[order_k]
+    q.obs_kf = obs_kf.astype(np.int32)
+    q.anchor_kf = np.sort(new_k_of_old[problem.anchor_kf]).astype(np.int32)
     q.lm_true = problem.lm_true[order]
     q.lm_init = problem.lm_init[order]
     q.obs_lm = new_of_old[problem.obs_lm].astype(np.int32)
@@ -94,6 +142,16 @@ def partition(problem, world: int):
                 p.send_kfs[s] = np.unique(q.obs_kf[inc])
         parts.append(p)
     return q, new_of_old, parts
+
+
+def boundary_stats(parts) -> dict:
+    """Records each iteration exchanges: messages to keyframes of another
+    rank and keyframe beliefs sent back, in total and for the busiest rank."""
+    msgs = [sum(len(o) for o in p.send_msgs.values()) for p in parts]
+    kfs = [sum(len(o) for o in p.send_kfs.values()) for p in parts]
+    return {"messages": int(sum(msgs)), "keyframe_beliefs": int(sum(kfs)),
+            "max_rank_messages": int(max(msgs)), "max_rank_keyframe_beliefs": int(max(kfs)),
+            "factors_per_rank": [int(len(p.factors)) for p in parts]}
 
 
 class SplitRank:

@@ -22,20 +22,27 @@ def _loop(n_kf=120, n_lm=3000, seed=0):
     return synth.make_loop(seed=seed, n_kf=n_kf, n_lm=n_lm, radius=8.0)
 
 
-@pytest.mark.parametrize("world", [1, 2, 4])
-def test_partition_invariants(world):
+@pytest.mark.parametrize("kf_split", ["spatial", "sequence"])
+@pytest.mark.parametrize("world", [1, 2, 3, 4])
+def test_partition_invariants(world, kf_split):
     p = _loop()
-    q, new_of_old, parts = split.partition(p, world)
-    # a relabelling of the same problem
+    q, new_of_old, parts = split.partition(p, world, kf_split=kf_split)
+    # a relabelling of the same problem: every observation keeps its pose, point and pixel
     np.testing.assert_array_equal(q.lm_init[new_of_old], p.lm_init)
     np.testing.assert_array_equal(q.obs_lm, new_of_old[p.obs_lm])
+    np.testing.assert_array_equal(q.kf_Rt_init[q.obs_kf], p.kf_Rt_init[p.obs_kf])
+    np.testing.assert_array_equal(q.kf_Rt_true[q.obs_kf], p.kf_Rt_true[p.obs_kf])
+    np.testing.assert_array_equal(q.obs_uv, p.obs_uv)
+    np.testing.assert_array_equal(np.sort(q.kf_Rt_init[q.anchor_kf], axis=0), np.sort(p.kf_Rt_init[p.anchor_kf], axis=0))
+    if kf_split == "sequence":
+        np.testing.assert_array_equal(q.obs_kf, p.obs_kf)
     # contiguous keyframe segments and landmark ranges covering everything once
     assert parts[0].kf_range[0] == 0 and parts[-1].kf_range[1] == p.n_kf
     assert parts[0].lm_range[0] == 0 and parts[-1].lm_range[1] == p.n_lm
     for a, b in zip(parts, parts[1:]):
         assert a.kf_range[1] == b.kf_range[0] and a.lm_range[1] == b.lm_range[0]
     np.testing.assert_array_equal(np.sort(np.concatenate([r.factors for r in parts])), np.arange(p.n_obs))
-    owner_k = split.kf_owner(p.n_kf, world)
+    owner_k = np.repeat(np.arange(world), [r.kf_range[1] - r.kf_range[0] for r in parts])
     for r in parts:
         # a rank's factors are those of its landmarks, whose majority of observers it owns
         assert np.all((q.obs_lm[r.factors] >= r.lm_range[0]) & (q.obs_lm[r.factors] < r.lm_range[1]))
@@ -49,6 +56,30 @@ def test_partition_invariants(world):
             np.testing.assert_array_equal(parts[s].send_kfs[r.rank], r.recv_kfs[s])
     if world > 1:
         assert sum(len(o) for r in parts for o in r.send_msgs.values()) > 0
+        # no rank idle, none with more than twice its share of factors
+        n = np.array([len(r.factors) for r in parts])
+        assert n.min() > 0 and n.max() <= 2 * p.n_obs / world
+
+
+def test_spatial_split_keeps_loop_closures_on_one_rank():
+    """On two laps of a loop, contiguous segments of the sequence put the
+    two visits of every place on different ranks; spatial groups do not."""
+    p = _loop()
+    seq = split.boundary_stats(split.partition(p, 4, kf_split="sequence")[2])
+    spa = split.boundary_stats(split.partition(p, 4, kf_split="spatial")[2])
+    assert spa["messages"] < 0.5 * seq["messages"]
+
+
+def test_spatial_groups_balance_weight():
+    rng = np.random.default_rng(0)
+    c = rng.normal(size=(500, 3)) * [10, 3, 1]
+    w = rng.integers(1, 20, size=500).astype(float)
+    for world in (2, 3, 5, 8):
+        groups = split.spatial_groups(c, w, world)
+        assert len(groups) == world
+        np.testing.assert_array_equal(np.sort(np.concatenate(groups)), np.arange(500))
+        share = np.array([w[g].sum() for g in groups]) / w.sum()
+        assert np.all(np.abs(share - 1 / world) < 0.05)
 
 
 class OracleEngine:
