@@ -397,7 +397,8 @@ def batch_problems(seeds):
         return [_make_batch_problem(s) for s in seeds]
 
 
-def measure_at_scale(gbp, stream, rank=0, world=1, n_problems=256, iters=20, launch_mode=0, device=None):
+def measure_at_scale(gbp, stream, rank=0, world=1, n_problems=256, iters=20, launch_mode=0, device=None,
+                     factor_shape=-1):
     """Throughput and HBM roofline on the batched workload: n_problems
     independent problems of uneven size, shared out over the ranks by size
     (their point counts, which set the factor counts) and solved as one
@@ -410,7 +411,7 @@ def measure_at_scale(gbp, stream, rank=0, world=1, n_problems=256, iters=20, lau
     g = gbp.Graph(probs if len(probs) > 1 else probs[0], stream=stream.cuda_stream, huber_nsigma=HUBER)
     n_kf, n_lm, n_f = gbp.gbp_get_sizes(g.h)
     if launch_mode:
-        g.set_params(launch_mode=launch_mode)
+        g.set_params(launch_mode=launch_mode, factor_shape=factor_shape)
         mode, ms1, ms2 = launch_mode, None, None
     else:
         mode, ms1, ms2 = g.autotune(8)
@@ -449,7 +450,7 @@ def run_gpu(args, rank, world, local):
     p = synth.make_walk(seed=rank)
     # launch_mode 0: the library's autotuner picks (measured on first use)
     params = dict(huber_nsigma=HUBER, conv_tol=CONV_TOL, check_every=CHECK_EVERY, iterations=MAX_ITERS,
-                  launch_mode=args.launch_mode)
+                  launch_mode=args.launch_mode, factor_shape=args.factor_shape)
     g = gbp.Graph(p, stream=stream.cuda_stream, **params)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
@@ -629,7 +630,7 @@ def run_scale_only(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     r = measure_at_scale(gbp, torch.cuda.current_stream(dev), rank, world, args.scale_problems,
-                         launch_mode=args.launch_mode, device=dev)
+                         launch_mode=args.launch_mode, device=dev, factor_shape=args.factor_shape)
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
@@ -652,6 +653,9 @@ def main():
     ap.add_argument("--launch-mode", type=int, default=0, choices=(0, 1, 2),
                     help="0 autotune (default), 1 persistent, 2 per phase; a profiler's serialisation changes "
                          "what the autotuner measures, so a capture pins the mode the live run chose")
+    ap.add_argument("--factor-shape", type=int, default=-1,
+                    help="with --launch-mode 2: the factor kernel's launch shape (-1 the library's choice); "
+                         "for profiling one shape")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.scale_only:

@@ -44,6 +44,8 @@ struct DevState {
     double* kf_R = nullptr;
     double* kf_c = nullptr;
     double* lm_ref = nullptr;
+    R* kf_Rr = nullptr;
+    R* f_dlc = nullptr;
     int32_t* kf_off = nullptr;
     int32_t* kf_list = nullptr;
     int32_t* kpos = nullptr;
@@ -73,7 +75,7 @@ struct DevState {
     R* eta_inf = nullptr;      // record schedule: 9 x n_f reference messages (gbp_capture_messages)
 
     void release() {
-        void* ptrs[] = {z, fk, fm, kf_R, kf_c, lm_ref, kf_off, kf_list, kpos, lm_off, tile_start, big_lm, orphan, kf_birth, lm_birth, kf_D, kf_A, lm_D,
+        void* ptrs[] = {z, fk, fm, kf_R, kf_c, lm_ref, kf_Rr, f_dlc, kf_off, kf_list, kpos, lm_off, tile_start, big_lm, orphan, kf_birth, lm_birth, kf_D, kf_A, lm_D,
                         uv_ref, x0, tlin, mk, mk2, kj, kjs, lin, ml, mlx, kf_bel, lm_bel, prior_s, hist, eta_inf};
         for (void* p : ptrs)
             if (p) cudaFree(p);
@@ -342,6 +344,13 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
     const int n_tiles = (int)tiles.size() - 1;
     std::vector<R> zr(2 * (size_t)nf), anc(6 * (size_t)nk, R(0));
     for (size_t i = 0; i < zr.size(); ++i) zr[i] = R(g->z[i]);
+    // the linearisation's references in R: the rotation rounded, and each
+    // factor's point-minus-centre difference taken in double, then rounded
+    std::vector<R> rr(9 * (size_t)nk), dlc(3 * (size_t)nf);
+    for (size_t i = 0; i < rr.size(); ++i) rr[i] = R(g->kf_R[i]);
+    for (int f = 0; f < nf; ++f)
+        for (int j = 0; j < 3; ++j)
+            dlc[(size_t)j * nf + f] = R(g->lm_ref[3 * (size_t)g->fm[f] + j] - g->kf_c[3 * (size_t)g->fk[f] + j]);
     for (int v = 0; v < nk; ++v)
         if (g->anchored[v])
             for (int i = 0; i < 6; ++i) anc[6 * v + i] = R(1);   // scaled by D after the prior pass
@@ -352,6 +361,8 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
     CK(dev_alloc(&s.kf_R, 9 * (size_t)nk));
     CK(dev_alloc(&s.kf_c, 3 * (size_t)nk));
     CK(dev_alloc(&s.lm_ref, 3 * (size_t)nl));
+    CK(dev_alloc(&s.kf_Rr, 9 * (size_t)nk));
+    CK(dev_alloc(&s.f_dlc, 3 * (size_t)nf));
     CK(dev_alloc(&s.kf_off, nk + 1));
     CK(dev_alloc(&s.kf_list, nf));
     CK(dev_alloc(&s.kpos, nf));
@@ -383,6 +394,8 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
     CK(cudaMemcpyAsync(s.kf_R, g->kf_R.data(), sizeof(double) * 9 * nk, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.kf_c, g->kf_c.data(), sizeof(double) * 3 * nk, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.lm_ref, g->lm_ref.data(), sizeof(double) * 3 * nl, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.kf_Rr, rr.data(), sizeof(R) * rr.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.f_dlc, dlc.data(), sizeof(R) * dlc.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.kf_off, kf_off.data(), sizeof(int32_t) * (nk + 1), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.kf_list, kf_list.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.kpos, kpos.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice, st));
@@ -410,6 +423,8 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
     d.kf_R = s.kf_R;
     d.kf_c = s.kf_c;
     d.lm_ref = s.lm_ref;
+    d.kf_Rr = s.kf_Rr;
+    d.f_dlc = s.f_dlc;
     d.kf_off = s.kf_off;
     d.kf_list = s.kf_list;
     d.kpos = s.kpos;

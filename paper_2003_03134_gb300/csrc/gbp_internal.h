@@ -114,6 +114,9 @@ struct DevGraph {
     const double* kf_R;       // n_kf x 9
     const double* kf_c;       // n_kf x 3
     const double* lm_ref;     // n_lm x 3
+    const R* kf_Rr;           // n_kf x 9: kf_R rounded to R (the linearisation's reference rotation)
+    const R* f_dlc;           // 3 x n_f: lm_ref[m] - kf_c[k] of each factor, subtracted in double and
+                              // rounded to R (the large world coordinates cancel there)
     const int32_t* kf_off;    // n_kf + 1
     const int32_t* kf_list;   // n_f
     const int32_t* kpos;      // n_f: slot of factor f's keyframe message = its position in kf_list

@@ -553,29 +553,35 @@ __device__ __forceinline__ void message_to_landmark(const KfSide<R>& s, const R 
 // Rare paths, kept out of line so that their state does not weigh on the
 // register allocation of the common path: arguments and results by value.
 
-// What a linearisation needs besides the factor's x0 and pixel.
+// What a linearisation needs besides the factor's x0: the keyframe's
+// reference rotation and the factor's point-minus-centre difference, both
+// rounded to R on the host, the pixel and the camera and noise parameters.
 template <typename R>
 struct LinArgs {
-    const double* Rref;
-    const double* cref;
-    const double* lref;
+    const R* Rr;
+    R dlc0, dlc1, dlc2;
     R zu, zv;
     R fx, fy, cx, cy, inv_sigma2, inv_sigma, huber_n, z_min;
 };
 
 template <typename R>
-__device__ __forceinline__ LinArgs<R> lin_args(const KParams<R>& P, const double* Rref, const double* cref,
-                                               const double* lref, R zu, R zv) {
-    return LinArgs<R>{Rref, cref, lref, zu, zv, P.fx, P.fy, P.cx, P.cy, P.inv_sigma2, P.inv_sigma, P.huber_n,
-                      P.z_min};
+__device__ __forceinline__ LinArgs<R> lin_args(const KParams<R>& P, const DevGraph<R>& g, int k, int f) {
+    const size_t n_f = (size_t)g.n_f;
+    return LinArgs<R>{g.kf_Rr + (size_t)k * 9, g.f_dlc[f], g.f_dlc[n_f + f], g.f_dlc[2 * n_f + f],
+                      g.z[2 * (size_t)f], g.z[2 * (size_t)f + 1], P.fx, P.fy, P.cx, P.cy, P.inv_sigma2, P.inv_sigma,
+                      P.huber_n, P.z_min};
 }
 
-template <typename C, typename R>
-__device__ __forceinline__ void lin_from_args(const LinArgs<R>& A, const C* x0, Lin<C>& L) {
-    KParams<C> P{};
-    P.fx = C(A.fx); P.fy = C(A.fy); P.cx = C(A.cx); P.cy = C(A.cy);
-    P.inv_sigma2 = C(A.inv_sigma2); P.inv_sigma = C(A.inv_sigma); P.huber_n = C(A.huber_n); P.z_min = C(A.z_min);
-    linearise<C>(P, A.Rref, A.cref, A.lref, x0, C(A.zu), C(A.zv), L);
+template <typename R>
+__device__ __forceinline__ void lin_from_args(const LinArgs<R>& A, const R* x0, Lin<R>& L) {
+    KParams<R> P{};
+    P.fx = A.fx; P.fy = A.fy; P.cx = A.cx; P.cy = A.cy;
+    P.inv_sigma2 = A.inv_sigma2; P.inv_sigma = A.inv_sigma; P.huber_n = A.huber_n; P.z_min = A.z_min;
+    R Rr[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Rr[i] = A.Rr[i];
+    const R dlc[3] = {A.dlc0, A.dlc1, A.dlc2};
+    linearise_ref<R>(P, Rr, dlc, x0, A.zu, A.zv, L);
 }
 
 template <typename R> struct Arr9 { R v[9]; };
@@ -588,7 +594,7 @@ template <typename R> struct Msg5 { R v[5]; };
 template <typename R>
 __device__ __noinline__ Lin<R> linearise_at(Arr9<R> x0, LinArgs<R> A) {
     Lin<R> L;
-    lin_from_args<R, R>(A, x0.v, L);
+    lin_from_args<R>(A, x0.v, L);
     return L;
 }
 
@@ -606,7 +612,7 @@ template <typename R>
 __device__ __noinline__ Rebased<R> rebase(const R* kbp, Arr12<R> Jo, R go0, R go1, R a0, R a1, R K00, R K01, R K11,
                                           bool form_lm, Arr9<R> x0n, LinArgs<R> A) {
     Rebased<R> out;
-    lin_from_args<R, R>(A, x0n.v, out.L);
+    lin_from_args<R>(A, x0n.v, out.L);
     for (int i = 0; i < 5; ++i) out.cl[i] = R(0);
     if (!form_lm) return out;
     R Ls[KB_A];
@@ -909,16 +915,23 @@ __device__ __forceinline__ float finish_keyframe(const DevGraph<R>& g, const KPa
     for (int i = 0; i < 6; ++i) lam[pk(i, i)] += prior[i];
     R out[KBEL];
     bool ok = kf_record<R>(lam, eta, out, ratio);
+    R* rec = out_bel + (size_t)k * KBEL;
+    store_rec<R, KBEL>(rec, out);
+    R mu[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) mu[i] = out[KB_MU + i];
     if (sizeof(R) == 4 && P.fallback && (!ok || ratio < P.pivot_ratio)) {
-        ok = kf_record_fp64<R>(out);
+        // the stored record's Lambda and eta, factorised again in FP64
+        ok = kf_record_fp64<R>(rec);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) mu[i] = rec[KB_MU + i];
         atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
     }
-    store_rec<R, KBEL>(out_bel + (size_t)k * KBEL, out);
     float dmu = 0.0f;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        if (!isfinite(out[KB_MU + i])) ok = false;
-        dmu = fmaxf(dmu, float(fabs(out[KB_MU + i] - mu_old[i])));
+        if (!isfinite(mu[i])) ok = false;
+        dmu = fmaxf(dmu, float(fabs(mu[i] - mu_old[i])));
     }
     if (!ok) raise_error(g.ctl, k);
     return dmu;
@@ -1176,30 +1189,71 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
     const bool active = f < te;
     constexpr bool FEAT = MODE != DAMP_FIXED;
 
-    int m = -1, lo = 0, hi = 0, k = 0, slot = 0, tl = 0;
+    // Every load of the common path is issued in two waves before anything
+    // is stored: the factor's own entries (wave 1), then what they index
+    // (wave 2).  A store in between (the first linearisation writes the
+    // lin record and the keyframe block) would keep later loads behind it.
+    int m = -1, lo = 0, hi = 0, k = 0, slot = 0, tl = 0, lbirth = 0;
     R cml[NML];          // this factor's previous message to the landmark (compact)
+    R lin4[NLIN];        // y0, y1, W, |r|^2 of its stored linearisation
 #pragma unroll
     for (int i = 0; i < NML; ++i) cml[i] = R(0);
+#pragma unroll
+    for (int i = 0; i < NLIN; ++i) lin4[i] = R(0);
     if (active) {
         m = g.fm[f];
         k = g.fk[f];
         slot = g.kpos[f];
-        lo = g.lm_off[m];
-        hi = g.lm_off[m + 1];
+        tl = g.tlin[f];
 #pragma unroll
         for (int i = 0; i < NML; ++i) cml[i] = g.ml[(size_t)i * n_f + f];
-        tl = g.tlin[f];
+#pragma unroll
+        for (int i = 0; i < NLIN; ++i) lin4[i] = g.lin[(size_t)i * n_f + f];
     }
-    const bool whole = active && lo >= ts && hi <= te;
-    const int seg0 = whole ? lo - ts : lane;
-    const int seg1 = whole ? hi - ts - 1 : lane;
     // the linearisation point is needed for a factor's first linearisation
     // and for the relinearisation test once the interval allows one
     const bool fresh = active && tl == t;
     const bool due = active && !P.linear && t - tl >= P.relin_interval;
+    const R* kbp = g.kf_bel + (size_t)k * KBEL;
     R x0[9];
+    R jr[KJ];            // the stored keyframe block of the factor's messages
+    R kb[KB_A];          // the keyframe belief's Cholesky factor, mean and trace
+    R mo[KREC];          // the previous message to the keyframe (compact record)
+    R lb_mu[3];          // the landmark's mean mu^t
+    R lD[3];             // the landmark's prior diagonal
+    if (active) {
+        lo = g.lm_off[m];
+        hi = g.lm_off[m + 1];
+        lbirth = g.lm_birth[m];
+        load_rec<R, KJ>(g.kj + (size_t)slot * KJ, jr);
+        load_rec_cg<R, KB_A>(kbp, kb);
+        load_rec<R, KREC>(mk_read(g, t) + (size_t)slot * KREC, mo);
+        const R* lbp = g.lm_bel + (size_t)m * LBEL;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            lb_mu[i] = __ldcg(lbp + 9 + i);
+            lD[i] = g.lm_D[m * 3 + i];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < KJ; ++i) jr[i] = R(0);
+#pragma unroll
+        for (int i = 0; i < KB_A; ++i) kb[i] = R(0);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) kb[pk(i, i)] = R(1);
+#pragma unroll
+        for (int i = 0; i < KREC; ++i) mo[i] = R(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { lb_mu[i] = R(0); lD[i] = R(0); }
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) x0[i] = (fresh || due) ? g.x0[(size_t)i * n_f + f] : R(0);
+    const bool whole = active && lo >= ts && hi <= te;
+    const int seg0 = whole ? lo - ts : lane;
+    const int seg1 = whole ? hi - ts - 1 : lane;
+    // the scans below need steps d < the longest landmark segment of the
+    // tile; the steps they skip would add nothing
+    const int seg_max = __reduce_max_sync(0xffffffffu, unsigned(seg1 - seg0 + 1));
 
     // 1. the factor's linearisation (Sec. 4), the basis of its stored
     // messages: computed at its first iteration, else as stored when it was
@@ -1210,16 +1264,13 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
         Arr9<R> xv;
 #pragma unroll
         for (int i = 0; i < 9; ++i) xv.v[i] = x0[i];
-        L = linearise_at<R>(xv, lin_args<R>(P, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3,
-                                            g.lm_ref + (size_t)m * 3, g.z[2 * (size_t)f], g.z[2 * (size_t)f + 1]));
+        L = linearise_at<R>(xv, lin_args<R>(P, g, k, f));
         store_lin<R>(g, f, L);
         store_jac<R>(g.kjs + (size_t)slot * KJ, L.Jk);
         // a keyframe of another rank's part: no belief phase here moves the
         // staged block, so the factor keeps its own copy up to date
         if (!kf_in_part(g, k)) store_jac<R>(g.kj + (size_t)slot * KJ, L.Jk);
-    } else if (active) {
-        R jr[KJ];
-        load_rec<R, KJ>(g.kj + (size_t)slot * KJ, jr);
+    } else {
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
             L.Jk[0][j] = jr[j];
@@ -1230,47 +1281,19 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
             L.Jl[0][j] = -jr[j];
             L.Jl[1][j] = -jr[6 + j];
         }
-        L.y[0] = g.lin[f];
-        L.y[1] = g.lin[(size_t)n_f + f];
-        L.W = g.lin[2 * (size_t)n_f + f];
-        L.r2 = g.lin[3 * (size_t)n_f + f];
-    } else {
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-#pragma unroll
-            for (int j = 0; j < 6; ++j) L.Jk[a][j] = R(0);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) L.Jl[a][j] = R(0);
-            L.y[a] = R(0);
-        }
-        L.W = R(0);
-        L.r2 = R(0);
+        L.y[0] = lin4[0];
+        L.y[1] = lin4[1];
+        L.W = lin4[2];
+        L.r2 = lin4[3];
     }
 
     // 2a. keyframe incoming precision b^t - m^t through the belief's factor
-    const R* kbp = g.kf_bel + (size_t)k * KBEL;
     R kmu[6];            // the keyframe's mean mu^t
-    R mo[KREC];          // the previous message to the keyframe (compact record)
     KfSide<R> ks;
-    R tr_b = R(0);
-    {
-        R kb[KB_A];
-        if (active) {
-            load_rec_cg<R, KB_A>(kbp, kb);
-            load_rec<R, KREC>(mk_read(g, t) + (size_t)slot * KREC, mo);
-        } else {
+    kf_side<R>(kb, kb + KB_MU, L.Jk, mo, ks);
 #pragma unroll
-            for (int i = 0; i < KB_A; ++i) kb[i] = R(0);
-#pragma unroll
-            for (int i = 0; i < 6; ++i) kb[pk(i, i)] = R(1);
-#pragma unroll
-            for (int i = 0; i < KREC; ++i) mo[i] = R(0);
-        }
-        kf_side<R>(kb, kb + KB_MU, L.Jk, mo, ks);
-#pragma unroll
-        for (int i = 0; i < 6; ++i) kmu[i] = kb[KB_MU + i];
-        tr_b = kb[KB_TR];
-    }
+    for (int i = 0; i < 6; ++i) kmu[i] = kb[KB_MU + i];
+    const R tr_b = kb[KB_TR];
     bool ok_k = ks.pd;
 
     // learned / record schedules: quantities of the previous messages, in
@@ -1312,8 +1335,7 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
         R fw[9], bw[9];
 #pragma unroll
         for (int j = 0; j < 9; ++j) { fw[j] = mlo[j]; bw[j] = mlo[j]; }
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
+        for (int d = 1; d < seg_max; d <<= 1) {
 #pragma unroll
             for (int j = 0; j < 9; ++j) {
                 R o = __shfl_up_sync(0xffffffffu, fw[j], d);
@@ -1331,16 +1353,12 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
             else qm[j - 6] = cv;
         }
     }
-    R lb_mu[3] = {R(0), R(0), R(0)};   // the landmark's mean mu^t
     if (active) {
         const R* lbp = g.lm_bel + (size_t)m * LBEL;
-        lb_mu[0] = __ldcg(lbp + 9);
-        lb_mu[1] = __ldcg(lbp + 10);
-        lb_mu[2] = __ldcg(lbp + 11);
         if (whole) {
-            const R sp = lm_prior_scale(g, P, m, t) * P.inv_sigma2;
+            const R sp = prior_scale(P, t - lbirth) * P.inv_sigma2;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) Pm[pk(i, i)] += sp * g.lm_D[m * 3 + i];
+            for (int i = 0; i < 3; ++i) Pm[pk(i, i)] += sp * lD[i];
         } else {
             // a landmark split across tiles: its belief divided by this message
             R lb[9];
@@ -1428,9 +1446,7 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
             atomicAdd(&g.ctl[CTL_RELINS], 1);
             rebased = true;
             const Rebased<R> rb = rebase<R>(kbp, Jo, mo[3], mo[4], ks.a0, ks.a1, ks.K00, ks.K01, ks.K11, !k64, xn,
-                                            lin_args<R>(P, g.kf_R + (size_t)k * 9, g.kf_c + (size_t)k * 3,
-                                                        g.lm_ref + (size_t)m * 3, g.z[2 * (size_t)f],
-                                                        g.z[2 * (size_t)f + 1]));
+                                            lin_args<R>(P, g, k, f));
             L = rb.L;
             store_lin<R>(g, f, L);
             store_jac<R>(g.kjs + (size_t)slot * KJ, L.Jk);
@@ -1600,8 +1616,7 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
 
     // landmarks wholly inside the tile: segmented inclusive scan over the
     // lanes holding the same landmark (landmark ranges are contiguous)
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
+    for (int d = 1; d < seg_max; d <<= 1) {
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
             R o = __shfl_up_sync(0xffffffffu, sum[j], d);
@@ -1610,7 +1625,7 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
     }
     float dmu = 0.0f;
     if (whole && lane == hi - ts - 1) {
-        dmu = finish_landmark<R>(g, P, m, lm_prior_scale(g, P, m, t + 1), sum, lb_mu, g.lm_bel_out);
+        dmu = finish_landmark<R>(g, P, m, prior_scale(P, t + 1 - lbirth), sum, lb_mu, g.lm_bel_out);
     }
     return dmu;
 }
@@ -1704,12 +1719,15 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
         for (int i = b0 + tg; i < b1; i += gsize) {
             // the compact message m^{t+1} and the Jacobian block it is in: the
             // staged new block when its factor (re)linearised in iteration t
-            // (which then becomes the slot's block)
+            // (which then becomes the slot's block).  Both records are
+            // loaded at once; the staged block only where it is needed.
             R rec[KREC], jr[KJ];
             load_rec_cg<R, KREC>(msgs + (size_t)i * KREC, rec);
-            const bool fresh = bits_int<R>(rec[KREC_TL]) == t;
-            load_rec_cg<R, KJ>((fresh ? g.kjs : g.kj) + (size_t)i * KJ, jr);
-            if (fresh) store_rec<R, KJ>(g.kj + (size_t)i * KJ, jr);
+            load_rec_cg<R, KJ>(g.kj + (size_t)i * KJ, jr);
+            if (bits_int<R>(rec[KREC_TL]) == t) {
+                load_rec_cg<R, KJ>(g.kjs + (size_t)i * KJ, jr);
+                store_rec<R, KJ>(g.kj + (size_t)i * KJ, jr);
+            }
             const R J[2][6] = {{jr[0], jr[1], jr[2], jr[3], jr[4], jr[5]}, {jr[6], jr[7], jr[8], jr[9], jr[10], jr[11]}};
             R lam[21], eta[6];
             expand_msg<R, 6>(J, rec[0], rec[1], rec[2], rec[3], rec[4], lam, eta);
