@@ -85,12 +85,12 @@ typedef struct {
                                    kernel, -1 = the autotuner's choice (default; before tuning: 1 for
                                    large graphs, else 0); 0: 128 threads per block, no register
                                    budget; 1: 128 threads, >= 3 blocks per SM; 2: 128 threads, >= 4
-                                   blocks per SM; 3: 64 threads, no budget.  Every shape gives
-                                   bitwise identical results.                                       */
-    int32_t persistent_shape;   /* FP32 fixed schedule, persistent launches: -1 = autotuned (default;
-                                   before tuning 1); 0, 1, 2: >= 1, 3, 4 blocks per SM (2 only on
-                                   large graphs, which take a warp per belief item; small graphs run
-                                   2 as 1).  Bitwise identical results in every shape.               */
+                                   blocks per SM; 3: 64 threads, no budget; 4 and 5: 128 threads, >= 4
+                                   or >= 3 blocks per SM, the rare tiles that need the FP64 redo left
+                                   to a second kernel (so the first holds no registers for it).
+                                   Every shape gives bitwise identical results.                     */
+    int32_t persistent_shape;   /* persistent launches: -1 (default) or 0, the one shape (no
+                                   register budget); kept for the autotuner's report.               */
 } gbp_params;
 
 typedef struct {
@@ -262,7 +262,7 @@ gbp_status gbp_profile_iterations(gbp_graph* g, int32_t n_iters, double* ms_out)
  * candidate.  Synchronises the stream. */
 gbp_status gbp_autotune(gbp_graph* g, int32_t n_trial, int32_t* chosen, double* ms_out);
 
-#define GBP_MAX_TUNING_CANDIDATES 8
+#define GBP_MAX_TUNING_CANDIDATES 12
 typedef struct {
     int32_t launch_mode;            /* chosen: 1 persistent, 2 per phase (0: not tuned yet)        */
     int32_t factor_shape;           /* chosen factor-kernel shape (see gbp_params)                 */

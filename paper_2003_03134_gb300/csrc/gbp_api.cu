@@ -52,6 +52,7 @@ struct DevState {
     int32_t* lm_off = nullptr;
     int32_t* tile_start = nullptr;
     int32_t* big_lm = nullptr;
+    int32_t* deferred = nullptr;
     int32_t* orphan = nullptr;
     int32_t* kf_birth = nullptr;
     int32_t* lm_birth = nullptr;
@@ -75,7 +76,7 @@ struct DevState {
     R* eta_inf = nullptr;      // record schedule: 9 x n_f reference messages (gbp_capture_messages)
 
     void release() {
-        void* ptrs[] = {z, fk, fm, kf_R, kf_c, lm_ref, kf_Rr, f_dlc, kf_off, kf_list, kpos, lm_off, tile_start, big_lm, orphan, kf_birth, lm_birth, kf_D, kf_A, lm_D,
+        void* ptrs[] = {z, fk, fm, kf_R, kf_c, lm_ref, kf_Rr, f_dlc, kf_off, kf_list, kpos, lm_off, tile_start, big_lm, deferred, orphan, kf_birth, lm_birth, kf_D, kf_A, lm_D,
                         uv_ref, x0, tlin, mk, mk2, kj, kjs, lin, ml, mlx, kf_bel, lm_bel, prior_s, hist, eta_inf};
         for (void* p : ptrs)
             if (p) cudaFree(p);
@@ -217,27 +218,21 @@ KParams<R> make_kparams(gbp_graph* g) {
 }
 
 // Launch shapes in use: the parameter if set, else the autotuner's choice,
-// else by size (large graphs -- a warp per belief item -- take >= 3 blocks
-// per SM, which measured fastest there).
+// else by size (large graphs -- a warp per belief item -- take the deferring
+// kernel at >= 4 blocks per SM, which measured fastest there).
 bool tunable(const gbp_graph* g) { return g->storage == 0 && g->prm.damping_mode == 0; }
 int factor_shape(const gbp_graph* g) {
     if (!tunable(g)) return 0;
     if (g->prm.factor_shape >= 0) return g->prm.factor_shape;
     if (g->tuned_fshape >= 0) return g->tuned_fshape;
-    return g->sf.g.b_warps == 1 ? 1 : 0;
+    return g->sf.g.b_warps == 1 ? 4 : 0;
 }
-// Persistent shapes of the graph's belief mapping: all three with the warp
-// mapping; with the block mapping (small graphs) shape 2 is not offered --
-// under that register budget the block reduction compiled to different
-// rounding (measured), so it runs as shape 1.
-int n_persistent_shapes(const gbp_graph* g) { return g->sf.g.b_warps == 1 ? N_PERSISTENT_SHAPES : 2; }
-int persistent_shape(const gbp_graph* g) {
-    if (!tunable(g)) return 0;
-    int s = 1;
-    if (g->prm.persistent_shape >= 0) s = g->prm.persistent_shape;
-    else if (g->tuned_pshape >= 0) s = g->tuned_pshape;
-    return std::min(s, n_persistent_shapes(g) - 1);
-}
+// The persistent kernel runs in one shape, with no register budget: under
+// a budget (>= 3 or >= 4 blocks per SM) it compiled to different rounding
+// from the per-phase kernels (measured), and it is the slower launch mode
+// at every size measured, so budgets are not offered.
+int n_persistent_shapes(const gbp_graph*) { return N_PERSISTENT_SHAPES; }
+int persistent_shape(const gbp_graph*) { return 0; }
 
 void destroy_exec(gbp_graph* g) {
     if (g->exec) {
@@ -369,6 +364,7 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
     CK(dev_alloc(&s.lm_off, nl + 1));
     CK(dev_alloc(&s.tile_start, tiles.size()));
     CK(dev_alloc(&s.big_lm, big.size()));
+    CK(dev_alloc(&s.deferred, (size_t)n_tiles));
     CK(dev_alloc(&s.orphan, orphan.size()));
     CK(dev_alloc(&s.kf_birth, nk));
     CK(dev_alloc(&s.lm_birth, nl));
@@ -431,6 +427,7 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
     d.lm_off = s.lm_off;
     d.tile_start = s.tile_start;
     d.big_lm = s.big_lm;
+    d.deferred = s.deferred;
     d.orphan = s.orphan;
     d.kf_birth = s.kf_birth;
     d.lm_birth = s.lm_birth;
@@ -654,9 +651,9 @@ gbp_status check_params(const gbp_params* p, std::string& why) {
     if (p->precision_mode < 0 || p->precision_mode > 2) { why = "precision_mode must be 0, 1 or 2"; return GBP_EINVAL; }
     if (p->launch_mode < 0 || p->launch_mode > 2) { why = "launch_mode must be 0, 1 or 2"; return GBP_EINVAL; }
     if (p->damping_mode < 0 || p->damping_mode > 1) { why = "damping_mode must be 0 or 1"; return GBP_EINVAL; }
-    if (p->factor_shape < -1 || p->factor_shape >= N_FACTOR_SHAPES) { why = "factor_shape must be -1 .. 3"; return GBP_EINVAL; }
+    if (p->factor_shape < -1 || p->factor_shape >= N_FACTOR_SHAPES) { why = "factor_shape must be -1 .. 5"; return GBP_EINVAL; }
     if (p->persistent_shape < -1 || p->persistent_shape >= N_PERSISTENT_SHAPES) {
-        why = "persistent_shape must be -1 .. 2";
+        why = "persistent_shape must be -1 or 0";
         return GBP_EINVAL;
     }
     if (!(p->conv_tol >= 0.0f)) { why = "conv_tol must be >= 0"; return GBP_EINVAL; }
@@ -1659,9 +1656,9 @@ gbp_status gbp_autotune(gbp_graph* g, int32_t n_trial, int32_t* chosen, double* 
 
 gbp_status gbp_get_tuning(const gbp_graph* g, gbp_tuning* out) {
     if (!g || !out) return GBP_EINVAL;
-    static const int f_threads[N_FACTOR_SHAPES] = {128, 128, 128, 64};
-    static const int f_minb[N_FACTOR_SHAPES] = {1, 3, 4, 1};
-    static const int p_minb[N_PERSISTENT_SHAPES] = {1, 3, 4};
+    static const int f_threads[N_FACTOR_SHAPES] = {128, 128, 128, 64, 128, 128};
+    static const int f_minb[N_FACTOR_SHAPES] = {1, 3, 4, 1, 4, 3};
+    static const int p_minb[N_PERSISTENT_SHAPES] = {1};
     *out = g->tuning;
     out->launch_mode = g->prm.launch_mode ? g->prm.launch_mode : g->tuned_mode;
     out->factor_shape = factor_shape(g);

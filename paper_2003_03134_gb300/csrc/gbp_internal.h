@@ -123,6 +123,7 @@ struct DevGraph {
     const int32_t* lm_off;    // n_lm + 1
     const int32_t* tile_start;// n_tiles + 1: warp tiles of whole landmarks (<= 32 factors each)
     const int32_t* big_lm;    // landmarks split across tiles (more than 32 factors)
+    int32_t* deferred;        // n_tiles: tiles left to factor_deferred_kernel in this iteration
     const int32_t* orphan;    // variables without factors: keyframe v, or n_kf + landmark
     int32_t n_tiles, n_big, n_orphan;
     // the part of the graph a launch covers (the whole graph unless it is
@@ -178,7 +179,10 @@ enum Ctl : int {
     CTL_ITERS_RUN = 11,    // iterations run by the last persistent launch
     CTL_HELD = 12,         // messages left at their previous value (incoming precision not positive definite)
     CTL_ITER_B = 13,       // per-phase launches: the iteration the belief kernel closes (set by the factor kernel)
-    CTL_N = 16
+    CTL_DEFER_N0 = 14,     // tiles listed for factor_deferred_kernel in even iterations
+    CTL_DEFER_N1 = 15,     // in odd iterations
+    CTL_DEFER_DONE = 16,   // blocks of factor_deferred_kernel done (its last block clears the list)
+    CTL_N = 20
 };
 
 // metrics reduction output (double slots)
@@ -192,9 +196,11 @@ constexpr int METRIC_BLOCK = 256;
 // previous kernel in the stream finishes; it waits for that kernel's writes)
 // shape: the FP32 fixed schedule's factor-kernel launch shape (autotuned):
 // 0 128 threads, no register budget; 1 128 threads, >= 3 blocks per SM;
-// 2 128 threads, >= 4 blocks per SM; 3 64 threads, no budget
-constexpr int N_FACTOR_SHAPES = 4;
-constexpr int N_PERSISTENT_SHAPES = 3;   // >= 1, 3, 4 blocks per SM
+// 2 128 threads, >= 4 blocks per SM; 3 64 threads, no budget; 4 and 5: 128
+// threads, >= 4 or >= 3 blocks per SM, with tiles that need the FP64 redo
+// deferred to factor_deferred_kernel (launched right after)
+constexpr int N_FACTOR_SHAPES = 6;
+constexpr int N_PERSISTENT_SHAPES = 1;   // no register budget
 template <typename R> cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s,
                                                 int mode = DAMP_FIXED, bool pdl = false, int shape = 0);
 template <typename R> cudaError_t launch_init(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s);

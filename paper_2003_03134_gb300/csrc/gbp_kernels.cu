@@ -375,19 +375,33 @@ __device__ __forceinline__ int bits_int(R v) {
 }
 
 // Lambda = J^T M J (packed n x n) and eta = J^T g of a compact message.
+// Explicitly rounded multiply and fused multiply-add: the compiler may not
+// contract or split these, so an expansion rounds the same way in every
+// kernel it is inlined into, whatever the register budget.
+template <typename R>
+__device__ __forceinline__ R mul_rn(R a, R b) {
+    if constexpr (sizeof(R) == 4) return __fmul_rn(a, b);
+    else return __dmul_rn(a, b);
+}
+template <typename R>
+__device__ __forceinline__ R fma_rn(R a, R b, R c) {
+    if constexpr (sizeof(R) == 4) return __fmaf_rn(a, b, c);
+    else return __fma_rn(a, b, c);
+}
+
 template <typename R, int n>
 __device__ __forceinline__ void expand_msg(const R J[2][n], R M00, R M01, R M11, R g0, R g1, R* lam, R* eta) {
     R ua[n], va[n];
 #pragma unroll
     for (int i = 0; i < n; ++i) {
-        ua[i] = M00 * J[0][i] + M01 * J[1][i];
-        va[i] = M01 * J[0][i] + M11 * J[1][i];
-        eta[i] = J[0][i] * g0 + J[1][i] * g1;
+        ua[i] = fma_rn(M00, J[0][i], mul_rn(M01, J[1][i]));
+        va[i] = fma_rn(M01, J[0][i], mul_rn(M11, J[1][i]));
+        eta[i] = fma_rn(J[0][i], g0, mul_rn(J[1][i], g1));
     }
 #pragma unroll
     for (int i = 0; i < n; ++i)
 #pragma unroll
-        for (int j = 0; j <= i; ++j) lam[pk(i, j)] = ua[i] * J[0][j] + va[i] * J[1][j];
+        for (int j = 0; j <= i; ++j) lam[pk(i, j)] = fma_rn(ua[i], J[0][j], mul_rn(va[i], J[1][j]));
 }
 
 // tr(J^T M J) and J^T g of a compact message (learned-damping features).
@@ -1159,6 +1173,158 @@ __device__ __forceinline__ void mlp_load_wait() {
     __syncthreads();
 }
 
+// One factor's messages once both incoming precisions are known (Lm, im:
+// the landmark side's FP32 Cholesky factor; ks: the keyframe side): the
+// FP64 redo where FP32 cannot take an incoming precision (FP64 = true),
+// the kept messages, the relinearisation test and the linearisation at the
+// new point, and both new messages in compact form (ck to the keyframe, cl
+// to the landmark), in the basis of L.
+template <typename R, bool FP64>
+__device__ __forceinline__ void form_messages(const DevGraph<R>& g, const KParams<R>& P, int f, int k, int slot, int t,
+                                              int& tl, bool due, bool active, const R* kbp, Lin<R>& L,
+                                              const KfSide<R>& ks, const R* mo, const R* cml, const R* kmu,
+                                              const R* lb_mu, const R* x0, const R* Pm, const R* qm, const R* Lm,
+                                              const R* im, bool& ok_m, bool& ok_k, R* ck, R* cl) {
+    const int n_f = g.n_f;
+    // FP64 where FP32 cannot take an incoming precision (decided here, from
+    // iteration-t state only; the messages are formed after the
+    // relinearisation test)
+    bool m64 = false, k64 = false;
+    if (FP64 && sizeof(R) == 4 && P.fallback && active) {
+        if (!ok_m) {
+            Arr9<R> pq;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) pq.v[i] = Pm[i];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) pq.v[6 + i] = qm[i];
+            ok_m = lm_incoming_ok64<R>(pq);
+            m64 = ok_m;
+            // kept for the FP64 message in this factor's (per-iteration)
+            // expanded-message slot, which is rewritten below
+            if (m64)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) g.mlx[(size_t)i * n_f + f] = pq.v[i];
+            atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
+        }
+        if (!(ks.det >= P.cav_ratio)) {
+            ok_k = kf_incoming_ok64<R>(KfCavity<R>{kbp, mk_read(g, t), g.kj, g.kf_D + (size_t)k * 6,
+                                                   g.kf_A + (size_t)k * 6, kf_in_part(g, k) ? g.kf_off[k] : -1, g.kf_off[k + 1], slot,
+                                                   kf_prior_scale(g, P, k, t), P.anchor_scale, P.inv_sigma2});
+            k64 = ok_k;
+            atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
+        }
+    }
+    if (active && !ok_m) atomicAdd(&g.ctl[CTL_HELD], 1);
+    if (active && !ok_k) atomicAdd(&g.ctl[CTL_HELD], 1);
+
+    // 3. Sec. 5 / Sec. 8: relinearise when the adjacent means moved more than
+    // beta from the linearisation point, at most every relin_interval
+    // iterations -- unless a message of this factor is kept this iteration
+#pragma unroll
+    for (int i = 0; i < NML; ++i) cl[i] = cml[i];   // kept unless formed below
+    bool rebased = false;
+    if (due && ok_m && ok_k) {
+        R d2 = R(0);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) d2 += (kmu[i] - x0[i]) * (kmu[i] - x0[i]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) d2 += (lb_mu[i] - x0[6 + i]) * (lb_mu[i] - x0[6 + i]);
+        if (d2 > P.relin_beta * P.relin_beta) {
+            Arr9<R> xn;
+            Arr12<R> Jo;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                xn.v[i] = kmu[i];
+                Jo.v[i] = L.Jk[0][i];
+                Jo.v[6 + i] = L.Jk[1][i];
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) xn.v[6 + i] = lb_mu[i];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g.x0[(size_t)i * n_f + f] = xn.v[i];
+            tl = t;
+            g.tlin[f] = t;
+            atomicAdd(&g.ctl[CTL_RELINS], 1);
+            rebased = true;
+            const Rebased<R> rb = rebase<R>(kbp, Jo, mo[3], mo[4], ks.a0, ks.a1, ks.K00, ks.K01, ks.K11, !k64, xn,
+                                            lin_args<R>(P, g, k, f));
+            L = rb.L;
+            store_lin<R>(g, f, L);
+            store_jac<R>(g.kjs + (size_t)slot * KJ, L.Jk);
+            if (!kf_in_part(g, k)) store_jac<R>(g.kj + (size_t)slot * KJ, L.Jk);
+            if (!k64)
+#pragma unroll
+                for (int i = 0; i < NML; ++i) cl[i] = rb.cl[i];
+        }
+    }
+
+    // 4. the new messages (compact), in the basis of L
+    if (!ok_m) {
+#pragma unroll
+        for (int i = 0; i < NML; ++i) ck[i] = mo[i];
+    } else if (m64) {
+        Arr9<R> pq;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) pq.v[i] = g.mlx[(size_t)i * n_f + f];
+        const Msg5<R> o = lm_message64<R>(pq, L);
+#pragma unroll
+        for (int i = 0; i < NML; ++i) ck[i] = o.v[i];
+    } else {
+        message_chol<R, 3>(Lm, im, qm, L.Jl, L.y, L.W, ck);
+    }
+    if (ok_k) {
+        if (k64) {
+            const Msg5<R> o = kf_message64<R>(
+                KfCavity<R>{kbp, mk_read(g, t), g.kj, g.kf_D + (size_t)k * 6, g.kf_A + (size_t)k * 6,
+                            kf_in_part(g, k) ? g.kf_off[k] : -1, g.kf_off[k + 1], slot, kf_prior_scale(g, P, k, t),
+                            P.anchor_scale, P.inv_sigma2},
+                L);
+#pragma unroll
+            for (int i = 0; i < NML; ++i) cl[i] = o.v[i];
+        } else if (!rebased) {
+            message_to_landmark<R>(ks, L.y, L.W, cl);
+        }
+    }
+
+}
+
+// Damping of eta (Sec. 5), i.e. of g, in the fixed schedule -- the message
+// sent in the iteration of a (re)linearisation and the next damp_hold - 1
+// are undamped (Sec. 8) -- then the stores: the keyframe record (with the
+// t_lin of its basis), the landmark message, and for a landmark split
+// across tiles the expanded one.  sum receives the expanded landmark
+// message for the tile's landmark sums.
+template <typename R>
+__device__ __forceinline__ void damp_store_fixed(const DevGraph<R>& g, const KParams<R>& P, int f, int slot, int t,
+                                                 int tl, bool whole, bool ok_m, bool ok_k, R* ck, R* cl, const R* mo,
+                                                 const R* cml, const Lin<R>& L, R* sum) {
+    const int n_f = g.n_f;
+    if (t - tl >= P.damp_hold) {
+        const R d = P.damping;
+        if (ok_m) {
+            ck[3] = (R(1) - d) * ck[3] + d * mo[3];
+            ck[4] = (R(1) - d) * ck[4] + d * mo[4];
+        }
+        if (ok_k) {
+            cl[3] = (R(1) - d) * cl[3] + d * cml[3];
+            cl[4] = (R(1) - d) * cl[4] + d * cml[4];
+        }
+    }
+    R rec[KREC];
+#pragma unroll
+    for (int i = 0; i < NML; ++i) rec[i] = ck[i];
+    rec[KREC_TL] = int_bits<R>(tl);
+    rec[6] = R(0);
+    rec[7] = R(0);
+    store_rec<R, KREC>(mk_write(g, t) + (size_t)slot * KREC, rec);
+#pragma unroll
+    for (int i = 0; i < NML; ++i) g.ml_out[(size_t)i * n_f + f] = cl[i];
+    expand_msg<R, 3>(L.Jl, cl[0], cl[1], cl[2], cl[3], cl[4], sum, sum + 6);
+    if (!whole)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g.mlx[(size_t)i * n_f + f] = sum[i];
+}
+
 // ------------------------------------------------------------------------
 // Phase A: one warp, one tile of whole landmarks (at most 32 factors,
 // consecutive in landmark order), one lane per factor.  For each factor:
@@ -1180,7 +1346,11 @@ __device__ __forceinline__ void mlp_load_wait() {
 // evaluates the network for the warp's 32 factors at once on the tensor
 // cores, between forming the messages and damping them.
 
-template <typename R, int MODE>
+// DEFER (fixed FP32 schedule): a tile with a factor whose incoming
+// precision FP32 cannot take is not worked here -- it stores nothing and is
+// listed for factor_deferred_kernel, which works it with the FP64 redo --
+// so that this kernel carries no state for the FP64 path.
+template <typename R, int MODE, bool DEFER = false>
 __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R>& P, int tile, int t, int lane,
                                            MlpSmem<MODE>& S, bool weights_pending = false) {
     const int n_f = g.n_f;
@@ -1225,7 +1395,9 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
         lo = g.lm_off[m];
         hi = g.lm_off[m + 1];
         lbirth = g.lm_birth[m];
-        load_rec<R, KJ>(g.kj + (size_t)slot * KJ, jr);
+        // the keyframe block is moved into kj by the belief phase, on another
+        // SM within one persistent launch: read through L2, as the beliefs
+        load_rec_cg<R, KJ>(g.kj + (size_t)slot * KJ, jr);
         load_rec_cg<R, KB_A>(kbp, kb);
         load_rec<R, KREC>(mk_read(g, t) + (size_t)slot * KREC, mo);
         const R* lbp = g.lm_bel + (size_t)m * LBEL;
@@ -1381,237 +1553,159 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
     for (int i = 0; i < 6; ++i) Lm[i] = Pm[i];
     bool ok_m = chol_packed<R, 3>(Lm, im, rm);
 
-    // FP64 where FP32 cannot take an incoming precision (decided here, from
-    // iteration-t state only; the messages are formed after the
-    // relinearisation test)
-    bool m64 = false, k64 = false;
-    if (sizeof(R) == 4 && P.fallback && active) {
-        if (!ok_m) {
-            Arr9<R> pq;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) pq.v[i] = Pm[i];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) pq.v[6 + i] = qm[i];
-            ok_m = lm_incoming_ok64<R>(pq);
-            m64 = ok_m;
-            // kept for the FP64 message in this factor's (per-iteration)
-            // expanded-message slot, which is rewritten below
-            if (m64)
-#pragma unroll
-                for (int i = 0; i < 9; ++i) g.mlx[(size_t)i * n_f + f] = pq.v[i];
-            atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
-        }
-        if (!(ks.det >= P.cav_ratio)) {
-            ok_k = kf_incoming_ok64<R>(KfCavity<R>{kbp, mk_read(g, t), g.kj, g.kf_D + (size_t)k * 6,
-                                                   g.kf_A + (size_t)k * 6, kf_in_part(g, k) ? g.kf_off[k] : -1, g.kf_off[k + 1], slot,
-                                                   kf_prior_scale(g, P, k, t), P.anchor_scale, P.inv_sigma2});
-            k64 = ok_k;
-            atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
-        }
-    }
-    if (active && !ok_m) atomicAdd(&g.ctl[CTL_HELD], 1);
-    if (active && !ok_k) atomicAdd(&g.ctl[CTL_HELD], 1);
-
-    // 3. Sec. 5 / Sec. 8: relinearise when the adjacent means moved more than
-    // beta from the linearisation point, at most every relin_interval
-    // iterations -- unless a message of this factor is kept this iteration
-    R cl[NML];            // the new message to the landmark: M00 M01 M11 g0 g1
-#pragma unroll
-    for (int i = 0; i < NML; ++i) cl[i] = cml[i];   // kept unless formed below
-    bool rebased = false;
-    if (due && ok_m && ok_k) {
-        R d2 = R(0);
-#pragma unroll
-        for (int i = 0; i < 6; ++i) d2 += (kmu[i] - x0[i]) * (kmu[i] - x0[i]);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) d2 += (lb_mu[i] - x0[6 + i]) * (lb_mu[i] - x0[6 + i]);
-        if (d2 > P.relin_beta * P.relin_beta) {
-            Arr9<R> xn;
-            Arr12<R> Jo;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                xn.v[i] = kmu[i];
-                Jo.v[i] = L.Jk[0][i];
-                Jo.v[6 + i] = L.Jk[1][i];
+    // 3, 4 and 5
+    R ck[NML], cl[NML];  // the new messages: to the keyframe, to the landmark
+    R sum[9];            // the new landmark message, expanded
+    if constexpr (DEFER) {
+        static_assert(MODE == DAMP_FIXED && sizeof(R) == 4, "deferral: fixed FP32 schedule");
+        // a tile with a factor that needs the FP64 redo is left to
+        // factor_deferred_kernel: nothing of it is stored here (a first
+        // linearisation above stores what the deferred run stores again)
+        const bool needs64 = P.fallback && active && (!ok_m || !(ks.det >= P.cav_ratio));
+        if (__any_sync(0xffffffffu, needs64)) {
+            if (lane == 0) {
+                const int i = atomicAdd(&g.ctl[CTL_DEFER_N0 + (t & 1)], 1);
+                if (i < g.n_tiles) g.deferred[i] = tile;
             }
-#pragma unroll
-            for (int i = 0; i < 3; ++i) xn.v[6 + i] = lb_mu[i];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                x0[i] = xn.v[i];
-                g.x0[(size_t)i * n_f + f] = xn.v[i];
-            }
-            tl = t;
-            g.tlin[f] = t;
-            atomicAdd(&g.ctl[CTL_RELINS], 1);
-            rebased = true;
-            const Rebased<R> rb = rebase<R>(kbp, Jo, mo[3], mo[4], ks.a0, ks.a1, ks.K00, ks.K01, ks.K11, !k64, xn,
-                                            lin_args<R>(P, g, k, f));
-            L = rb.L;
-            store_lin<R>(g, f, L);
-            store_jac<R>(g.kjs + (size_t)slot * KJ, L.Jk);
-            if (!kf_in_part(g, k)) store_jac<R>(g.kj + (size_t)slot * KJ, L.Jk);
-            if (!k64)
-#pragma unroll
-                for (int i = 0; i < NML; ++i) cl[i] = rb.cl[i];
+            return 0.0f;
         }
-    }
-
-    // 4. the new messages (compact), in the basis of L
-    R ck[NML];           // to the keyframe
-    if (!ok_m) {
-#pragma unroll
-        for (int i = 0; i < NML; ++i) ck[i] = mo[i];
-    } else if (m64) {
-        Arr9<R> pq;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) pq.v[i] = g.mlx[(size_t)i * n_f + f];
-        const Msg5<R> o = lm_message64<R>(pq, L);
-#pragma unroll
-        for (int i = 0; i < NML; ++i) ck[i] = o.v[i];
-    } else {
-        message_chol<R, 3>(Lm, im, qm, L.Jl, L.y, L.W, ck);
-    }
-    if (ok_k) {
-        if (k64) {
-            const Msg5<R> o = kf_message64<R>(
-                KfCavity<R>{kbp, mk_read(g, t), g.kj, g.kf_D + (size_t)k * 6, g.kf_A + (size_t)k * 6,
-                            kf_in_part(g, k) ? g.kf_off[k] : -1, g.kf_off[k + 1], slot, kf_prior_scale(g, P, k, t),
-                            P.anchor_scale, P.inv_sigma2},
-                L);
-#pragma unroll
-            for (int i = 0; i < NML; ++i) cl[i] = o.v[i];
-        } else if (!rebased) {
-            message_to_landmark<R>(ks, L.y, L.W, cl);
-        }
-    }
-
-    // features of the learned schedule and targets of the record schedule
-    float feat[N_FEAT];
-#pragma unroll
-    for (int i = 0; i < N_FEAT; ++i) feat[i] = 0.0f;
-    R ek_new[6], em_new[3];
-    if constexpr (FEAT) {
-        msg_eta<R, 6>(L.Jk, ck[3], ck[4], ek_new);
-        msg_eta<R, 3>(L.Jl, cl[3], cl[4], em_new);
         if (active) {
-            const float tr_lk = float(msg_trace<R, 6>(L.Jk, ck[0], ck[1], ck[2]));
-            const float tr_lm = float(msg_trace<R, 3>(L.Jl, cl[0], cl[1], cl[2]));
-            const float M = float(sqrt(L.r2) * P.inv_sigma);
-            const float cfk = rel_change<R, 6>(ek_new, ek_old);
-            const float cfm = rel_change<R, 3>(em_new, em_old);
-            const R em_prev[3] = {R(h[4]), R(h[5]), R(h[6])};
-            feat[0] = log1pf(M) * (1.0f / 3.0f);
-            feat[1] = float(L.W / P.inv_sigma2);
-            feat[2] = tr_lk / (tr_lk + float(tr_pk) + 1e-30f);
-            feat[3] = tr_lm / (tr_lm + float(tr_pm) + 1e-30f);
-            feat[4] = cfk;
-            feat[5] = h[0];
-            feat[6] = h[1];
-            // the three keyframe messages share one basis only from t_lin + 2 on
-            feat[7] = t - tl >= 2 ? step_cosine<R, 6>(ek_new, ek_old, ek_prev) : 0.0f;
-            feat[8] = cfm;
-            feat[9] = h[2];
-            feat[10] = h[3];
-            feat[11] = step_cosine<R, 3>(em_new, em_old, em_prev);
-            feat[12] = log1pf(float(deg_k)) * 0.2f;
-            feat[13] = log1pf(float(hi - lo)) * (1.0f / 3.0f);
-            feat[14] = float(min(t - tl, 50)) * 0.02f;
-            feat[15] = float(min(t - birth_m, 50)) * 0.02f;
-            const float hn[HIST] = {cfk, h[0], cfm, h[2], float(em_old[0]), float(em_old[1]), float(em_old[2]), 0.0f};
+            form_messages<R, false>(g, P, f, k, slot, t, tl, due, active, kbp, L, ks, mo, cml, kmu, lb_mu, x0, Pm, qm,
+                                    Lm, im, ok_m, ok_k, ck, cl);
+            damp_store_fixed<R>(g, P, f, slot, t, tl, whole, ok_m, ok_k, ck, cl, mo, cml, L, sum);
+        } else {
 #pragma unroll
-            for (int j = 0; j < HIST; ++j) g.hist[(size_t)j * n_f + f] = hn[j];
-            if constexpr (MODE == DAMP_RECORD) {
-                R ik[6], imm[3];
+            for (int i = 0; i < 9; ++i) sum[i] = R(0);
+        }
+    } else {
+        form_messages<R, true>(g, P, f, k, slot, t, tl, due, active, kbp, L, ks, mo, cml, kmu, lb_mu, x0, Pm, qm, Lm,
+                               im, ok_m, ok_k, ck, cl);
+        // features of the learned schedule and targets of the record schedule
+        float feat[N_FEAT];
 #pragma unroll
-                for (int i = 0; i < 6; ++i) ik[i] = g.eta_inf[(size_t)i * n_f + f];
+        for (int i = 0; i < N_FEAT; ++i) feat[i] = 0.0f;
+        R ek_new[6], em_new[3];
+        if constexpr (FEAT) {
+            msg_eta<R, 6>(L.Jk, ck[3], ck[4], ek_new);
+            msg_eta<R, 3>(L.Jl, cl[3], cl[4], em_new);
+            if (active) {
+                const float tr_lk = float(msg_trace<R, 6>(L.Jk, ck[0], ck[1], ck[2]));
+                const float tr_lm = float(msg_trace<R, 3>(L.Jl, cl[0], cl[1], cl[2]));
+                const float M = float(sqrt(L.r2) * P.inv_sigma);
+                const float cfk = rel_change<R, 6>(ek_new, ek_old);
+                const float cfm = rel_change<R, 3>(em_new, em_old);
+                const R em_prev[3] = {R(h[4]), R(h[5]), R(h[6])};
+                feat[0] = log1pf(M) * (1.0f / 3.0f);
+                feat[1] = float(L.W / P.inv_sigma2);
+                feat[2] = tr_lk / (tr_lk + float(tr_pk) + 1e-30f);
+                feat[3] = tr_lm / (tr_lm + float(tr_pm) + 1e-30f);
+                feat[4] = cfk;
+                feat[5] = h[0];
+                feat[6] = h[1];
+                // the three keyframe messages share one basis only from t_lin + 2 on
+                feat[7] = t - tl >= 2 ? step_cosine<R, 6>(ek_new, ek_old, ek_prev) : 0.0f;
+                feat[8] = cfm;
+                feat[9] = h[2];
+                feat[10] = h[3];
+                feat[11] = step_cosine<R, 3>(em_new, em_old, em_prev);
+                feat[12] = log1pf(float(deg_k)) * 0.2f;
+                feat[13] = log1pf(float(hi - lo)) * (1.0f / 3.0f);
+                feat[14] = float(min(t - tl, 50)) * 0.02f;
+                feat[15] = float(min(t - birth_m, 50)) * 0.02f;
+                const float hn[HIST] = {cfk, h[0], cfm, h[2], float(em_old[0]), float(em_old[1]), float(em_old[2]), 0.0f};
 #pragma unroll
-                for (int i = 0; i < 3; ++i) imm[i] = g.eta_inf[(size_t)(6 + i) * n_f + f];
-                bool vk, vm;
-                const float dk = damping_vertex<R, 6>(ek_new, ek_old, ik, vk);
-                const float dm = damping_vertex<R, 3>(em_new, em_old, imm, vm);
-                float target = (vk || vm) ? fminf(fmaxf((dk * float(vk) + dm * float(vm)) /
-                                                        float(int(vk) + int(vm)), 0.0f), MLP_DMAX)
-                                          : -1.0f;
-                // samples the learned schedule never damps: the hold after
-                // a (re)linearisation, a factor behind the camera
-                if (t - tl < P.damp_hold || !(L.W > R(0))) target = -1.0f;
-                float4* xo = reinterpret_cast<float4*>(g.rec_X + (size_t)f * N_FEAT);
+                for (int j = 0; j < HIST; ++j) g.hist[(size_t)j * n_f + f] = hn[j];
+                if constexpr (MODE == DAMP_RECORD) {
+                    R ik[6], imm[3];
 #pragma unroll
-                for (int j = 0; j < N_FEAT / 4; ++j)
-                    xo[j] = make_float4(feat[4 * j], feat[4 * j + 1], feat[4 * j + 2], feat[4 * j + 3]);
-                g.rec_T[f] = target;
+                    for (int i = 0; i < 6; ++i) ik[i] = g.eta_inf[(size_t)i * n_f + f];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) imm[i] = g.eta_inf[(size_t)(6 + i) * n_f + f];
+                    bool vk, vm;
+                    const float dk = damping_vertex<R, 6>(ek_new, ek_old, ik, vk);
+                    const float dm = damping_vertex<R, 3>(em_new, em_old, imm, vm);
+                    float target = (vk || vm) ? fminf(fmaxf((dk * float(vk) + dm * float(vm)) /
+                                                            float(int(vk) + int(vm)), 0.0f), MLP_DMAX)
+                                              : -1.0f;
+                    // samples the learned schedule never damps: the hold after
+                    // a (re)linearisation, a factor behind the camera
+                    if (t - tl < P.damp_hold || !(L.W > R(0))) target = -1.0f;
+                    float4* xo = reinterpret_cast<float4*>(g.rec_X + (size_t)f * N_FEAT);
+#pragma unroll
+                    for (int j = 0; j < N_FEAT / 4; ++j)
+                        xo[j] = make_float4(feat[4 * j], feat[4 * j + 1], feat[4 * j + 2], feat[4 * j + 3]);
+                    g.rec_T[f] = target;
+                }
             }
         }
-    }
 
-    // 5. damping of eta (Sec. 5), i.e. of g: the message sent in the
-    // iteration of a (re)linearisation and the next damp_hold - 1 are
-    // undamped (Sec. 8); the learned schedule damps after the network
-    if constexpr (MODE != DAMP_LEARNED) {
-        if (active && t - tl >= P.damp_hold) {
-            const R d = P.damping;
-            if (ok_m) {
-                ck[3] = (R(1) - d) * ck[3] + d * mo[3];
-                ck[4] = (R(1) - d) * ck[4] + d * mo[4];
-            }
-            if (ok_k) {
-                cl[3] = (R(1) - d) * cl[3] + d * cml[3];
-                cl[4] = (R(1) - d) * cl[4] + d * cml[4];
-            }
-        }
-    }
-    if constexpr (MODE == DAMP_LEARNED) {
-        // the network for the warp's 32 factors (inactive lanes: zero rows),
-        // then g damped by each factor's own d wherever the fixed schedule
-        // would damp (after the undamped hold of Sec. 8)
-        const int w = threadIdx.x >> 5;
-        const bool damp_f = active && t - tl >= P.damp_hold;
-        if (weights_pending) mlp_load_wait();   // uniform per block: every warp of the block passes here once
-        if (__any_sync(0xffffffffu, damp_f)) {   // uniform per warp: skipped while every lane is in its hold
-            __nv_bfloat16* xt = reinterpret_cast<__nv_bfloat16*>(S.x[w]);
-#pragma unroll
-            for (int j = 0; j < N_FEAT; j += 2)
-                *reinterpret_cast<uint32_t*>(xt + lane * XS + j) = pack_bf16(feat[j], feat[j + 1]);
-            __syncwarp();
-            const float z3 = mlp_forward_regs(S.frag, S.bias, xt, lane);
-            __syncwarp();   // the tile is rewritten by the warp's next tile
-            float dl = mlp_output(z3);
-            if (!(dl >= 0.0f && dl <= MLP_DMAX)) dl = float(P.damping);
-            if (damp_f) {
-                const R dd = R(dl);
+        // 5. damping of eta (Sec. 5), i.e. of g: the message sent in the
+        // iteration of a (re)linearisation and the next damp_hold - 1 are
+        // undamped (Sec. 8); the learned schedule damps after the network
+        if constexpr (MODE != DAMP_LEARNED) {
+            if (active && t - tl >= P.damp_hold) {
+                const R d = P.damping;
                 if (ok_m) {
-                    ck[3] = (R(1) - dd) * ck[3] + dd * mo[3];
-                    ck[4] = (R(1) - dd) * ck[4] + dd * mo[4];
+                    ck[3] = (R(1) - d) * ck[3] + d * mo[3];
+                    ck[4] = (R(1) - d) * ck[4] + d * mo[4];
                 }
                 if (ok_k) {
-                    cl[3] = (R(1) - dd) * cl[3] + dd * cml[3];
-                    cl[4] = (R(1) - dd) * cl[4] + dd * cml[4];
+                    cl[3] = (R(1) - d) * cl[3] + d * cml[3];
+                    cl[4] = (R(1) - d) * cl[4] + d * cml[4];
                 }
             }
         }
-    }
+        if constexpr (MODE == DAMP_LEARNED) {
+            // the network for the warp's 32 factors (inactive lanes: zero rows),
+            // then g damped by each factor's own d wherever the fixed schedule
+            // would damp (after the undamped hold of Sec. 8)
+            const int w = threadIdx.x >> 5;
+            const bool damp_f = active && t - tl >= P.damp_hold;
+            if (weights_pending) mlp_load_wait();   // uniform per block: every warp of the block passes here once
+            if (__any_sync(0xffffffffu, damp_f)) {   // uniform per warp: skipped while every lane is in its hold
+                __nv_bfloat16* xt = reinterpret_cast<__nv_bfloat16*>(S.x[w]);
+#pragma unroll
+                for (int j = 0; j < N_FEAT; j += 2)
+                    *reinterpret_cast<uint32_t*>(xt + lane * XS + j) = pack_bf16(feat[j], feat[j + 1]);
+                __syncwarp();
+                const float z3 = mlp_forward_regs(S.frag, S.bias, xt, lane);
+                __syncwarp();   // the tile is rewritten by the warp's next tile
+                float dl = mlp_output(z3);
+                if (!(dl >= 0.0f && dl <= MLP_DMAX)) dl = float(P.damping);
+                if (damp_f) {
+                    const R dd = R(dl);
+                    if (ok_m) {
+                        ck[3] = (R(1) - dd) * ck[3] + dd * mo[3];
+                        ck[4] = (R(1) - dd) * ck[4] + dd * mo[4];
+                    }
+                    if (ok_k) {
+                        cl[3] = (R(1) - dd) * cl[3] + dd * cml[3];
+                        cl[4] = (R(1) - dd) * cl[4] + dd * cml[4];
+                    }
+                }
+            }
+        }
 
-    // stores: the keyframe record (with the t_lin of its basis), the new
-    // basis for the belief phase when it changed, the landmark message
-    R sum[9];
-    if (active) {
-        R rec[KREC];
+        // stores: the keyframe record (with the t_lin of its basis), the new
+        // basis for the belief phase when it changed, the landmark message
+        if (active) {
+            R rec[KREC];
 #pragma unroll
-        for (int i = 0; i < NML; ++i) rec[i] = ck[i];
-        rec[KREC_TL] = int_bits<R>(tl);
-        rec[6] = R(0);
-        rec[7] = R(0);
-        store_rec<R, KREC>(mk_write(g, t) + (size_t)slot * KREC, rec);
+            for (int i = 0; i < NML; ++i) rec[i] = ck[i];
+            rec[KREC_TL] = int_bits<R>(tl);
+            rec[6] = R(0);
+            rec[7] = R(0);
+            store_rec<R, KREC>(mk_write(g, t) + (size_t)slot * KREC, rec);
 #pragma unroll
-        for (int i = 0; i < NML; ++i) g.ml_out[(size_t)i * n_f + f] = cl[i];
-        expand_msg<R, 3>(L.Jl, cl[0], cl[1], cl[2], cl[3], cl[4], sum, sum + 6);
-        if (!whole)
+            for (int i = 0; i < NML; ++i) g.ml_out[(size_t)i * n_f + f] = cl[i];
+            expand_msg<R, 3>(L.Jl, cl[0], cl[1], cl[2], cl[3], cl[4], sum, sum + 6);
+            if (!whole)
 #pragma unroll
-            for (int i = 0; i < 9; ++i) g.mlx[(size_t)i * n_f + f] = sum[i];
-    } else {
+                for (int i = 0; i < 9; ++i) g.mlx[(size_t)i * n_f + f] = sum[i];
+        } else {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) sum[i] = R(0);
+            for (int i = 0; i < 9; ++i) sum[i] = R(0);
+        }
     }
 
     // landmarks wholly inside the tile: segmented inclusive scan over the
@@ -1715,26 +1809,40 @@ __device__ __forceinline__ float phase_b_item(const DevGraph<R>& g, const KParam
 #pragma unroll
         for (int j = 0; j < 32; ++j) hi[j] = R(0);
         const int b0 = g.kf_off[k], b1 = g.kf_off[k + 1];
-#pragma unroll 2
-        for (int i = b0 + tg; i < b1; i += gsize) {
+        // BU entries per thread at a time: their loads are all issued before
+        // any of them is summed (the summation order stays entry by entry)
+        constexpr int BU = 4;
+        for (int i0 = b0 + tg; i0 < b1; i0 += BU * gsize) {
             // the compact message m^{t+1} and the Jacobian block it is in: the
             // staged new block when its factor (re)linearised in iteration t
-            // (which then becomes the slot's block).  Both records are
-            // loaded at once; the staged block only where it is needed.
-            R rec[KREC], jr[KJ];
-            load_rec_cg<R, KREC>(msgs + (size_t)i * KREC, rec);
-            load_rec_cg<R, KJ>(g.kj + (size_t)i * KJ, jr);
-            if (bits_int<R>(rec[KREC_TL]) == t) {
-                load_rec_cg<R, KJ>(g.kjs + (size_t)i * KJ, jr);
-                store_rec<R, KJ>(g.kj + (size_t)i * KJ, jr);
+            // (which then becomes the slot's block)
+            R rec[BU][KREC], jr[BU][KJ];
+#pragma unroll
+            for (int u = 0; u < BU; ++u) {
+                const int i = i0 + u * gsize;
+                if (i < b1) {
+                    load_rec_cg<R, KREC>(msgs + (size_t)i * KREC, rec[u]);
+                    load_rec_cg<R, KJ>(g.kj + (size_t)i * KJ, jr[u]);
+                }
             }
-            const R J[2][6] = {{jr[0], jr[1], jr[2], jr[3], jr[4], jr[5]}, {jr[6], jr[7], jr[8], jr[9], jr[10], jr[11]}};
-            R lam[21], eta[6];
-            expand_msg<R, 6>(J, rec[0], rec[1], rec[2], rec[3], rec[4], lam, eta);
 #pragma unroll
-            for (int j = 0; j < 21; ++j) hi[j] += lam[j];
+            for (int u = 0; u < BU; ++u) {
+                const int i = i0 + u * gsize;
+                if (i < b1) {
+                    if (bits_int<R>(rec[u][KREC_TL]) == t) {
+                        load_rec_cg<R, KJ>(g.kjs + (size_t)i * KJ, jr[u]);
+                        store_rec<R, KJ>(g.kj + (size_t)i * KJ, jr[u]);
+                    }
+                    const R J[2][6] = {{jr[u][0], jr[u][1], jr[u][2], jr[u][3], jr[u][4], jr[u][5]},
+                                       {jr[u][6], jr[u][7], jr[u][8], jr[u][9], jr[u][10], jr[u][11]}};
+                    R lam[21], eta[6];
+                    expand_msg<R, 6>(J, rec[u][0], rec[u][1], rec[u][2], rec[u][3], rec[u][4], lam, eta);
 #pragma unroll
-            for (int j = 0; j < 6; ++j) hi[21 + j] += eta[j];
+                    for (int j = 0; j < 21; ++j) hi[j] += lam[j];
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) hi[21 + j] += eta[j];
+                }
+            }
         }
         R acc[27];
         group_total<R, 32, 27, W>(hi, acc);
@@ -1810,7 +1918,7 @@ __device__ __forceinline__ int phase_b_item_of(int W, int block) {
 __device__ __forceinline__ void pdl_allow_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-template <typename R, int MODE, int NT>
+template <typename R, int MODE, int NT, bool DEFER>
 __device__ __forceinline__ void factor_body(const DevGraph<R>& g, const KParams<R>& P) {
     __shared__ __align__(16) MlpSmem<MODE> S;
     mlp_load_async<MODE>(P, S);   // network weights do not change between iterations
@@ -1819,7 +1927,8 @@ __device__ __forceinline__ void factor_body(const DevGraph<R>& g, const KParams<
     const int tile = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
     const int t = g.ctl[CTL_ITER];
     float dmu = 0.0f;
-    if (tile < g.n_tiles) dmu = tile_work<R, MODE>(g, P, g.tile_off + tile, t, lane, S, MODE == DAMP_LEARNED);   // uniform per warp
+    if (tile < g.n_tiles)   // uniform per warp
+        dmu = tile_work<R, MODE, DEFER>(g, P, g.tile_off + tile, t, lane, S, MODE == DAMP_LEARNED);
     else if constexpr (MODE == DAMP_LEARNED) mlp_load_wait();   // the block's barrier, for warps without a tile
     pdl_allow_next();
     dmu = warp_max(dmu);
@@ -1833,9 +1942,40 @@ __device__ __forceinline__ void factor_body(const DevGraph<R>& g, const KParams<
 // per thread; 1 = no constraint).  Each warp does one tile whatever the
 // shape, so every shape gives bitwise identical results; the FP32 fixed
 // schedule is instantiated in several shapes for the autotuner.
-template <typename R, int MODE, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) factor_kernel(DevGraph<R> g, KParams<R> P) {
-    factor_body<R, MODE, NT>(g, P);
+template <typename R, int MODE, int NT, int MINB, bool DEFER = false>
+__global__ void __launch_bounds__(NT, MINB) factor_kernel(const __grid_constant__ DevGraph<R> g,
+                                                          const __grid_constant__ KParams<R> P) {
+    factor_body<R, MODE, NT, DEFER>(g, P);
+}
+
+// The tiles that factor_kernel<..., DEFER = true> left in this iteration
+// (a factor of theirs needs the FP64 redo), worked with it: warps walk the
+// list.  No store of theirs happened before, so they see the same state.
+// The last block to finish clears the list for the next use of its slot.
+template <typename R>
+__global__ void __launch_bounds__(FACTOR_BLOCK) factor_deferred_kernel(const __grid_constant__ DevGraph<R> g,
+                                                                       const __grid_constant__ KParams<R> P) {
+    constexpr int WPB = FACTOR_BLOCK / 32;
+    MlpSmem<DAMP_FIXED> S;
+    pdl_wait_prev();
+    const int lane = threadIdx.x & 31;
+    const int t = g.ctl[CTL_ITER];
+    const int slot = CTL_DEFER_N0 + (t & 1);
+    const int n = min(g.ctl[slot], g.n_tiles);
+    float dmu = 0.0f;
+    for (int i = blockIdx.x * WPB + (threadIdx.x >> 5); i < n; i += gridDim.x * WPB)
+        dmu = fmaxf(dmu, tile_work<R, DAMP_FIXED, false>(g, P, g.deferred[i], t, lane, S));
+    pdl_allow_next();
+    dmu = warp_max(dmu);
+    if (lane == 0 && dmu > 0.0f) dmu_atomic_max_slot(g.ctl, dmu_slot(t), dmu);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&g.ctl[CTL_DEFER_DONE], 1) == int(gridDim.x) - 1) {
+            g.ctl[slot] = 0;
+            g.ctl[CTL_DEFER_DONE] = 0;
+        }
+    }
 }
 
 // BW = g.b_warps (warps per belief item), one instantiation per mapping
@@ -1904,7 +2044,8 @@ __device__ __forceinline__ bool grid_barrier(int32_t* ctl, int nblocks, int* fla
 // a launch shape the autotuner chooses for the FP32 fixed schedule.
 template <typename R, int MODE, int BW, int MINB>
 __global__ void __launch_bounds__(FACTOR_BLOCK, MINB)
-    persistent_kernel(DevGraph<R> g, KParams<R> P, int n_iters, float conv_tol, int check_every) {
+    persistent_kernel(const __grid_constant__ DevGraph<R> g, const __grid_constant__ KParams<R> P, int n_iters,
+                      float conv_tol, int check_every) {
     __shared__ int flag_sh;
     __shared__ __align__(16) MlpSmem<MODE> S;
     mlp_load<MODE>(P, S);
@@ -2215,11 +2356,18 @@ cudaError_t launch_ex(void (*kernel)(KArgs...), int blocks, int threads, cudaStr
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-template <typename R, int MODE, int NT, int MINB>
+template <typename R, int MODE, int NT, int MINB, bool DEFER = false>
 cudaError_t launch_factor_shape(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s, bool pdl) {
     constexpr int wpb = NT / 32;
     const int blocks = std::max(1, (g.n_tiles + wpb - 1) / wpb);   // >= 1: it also publishes the iteration index
-    return launch_ex(factor_kernel<R, MODE, NT, MINB>, blocks, NT, s, pdl, g, p);
+    cudaError_t e = launch_ex(factor_kernel<R, MODE, NT, MINB, DEFER>, blocks, NT, s, pdl, g, p);
+    if constexpr (DEFER) {
+        // deferred tiles are rare: a few hundred warps walk the list
+        constexpr int wpd = FACTOR_BLOCK / 32;
+        const int nb = std::max(1, std::min((g.n_tiles + wpd - 1) / wpd, 608));
+        if (e == cudaSuccess) e = launch_ex(factor_deferred_kernel<R>, nb, FACTOR_BLOCK, s, pdl, g, p);
+    }
+    return e;
 }
 
 template <typename R>
@@ -2231,6 +2379,8 @@ cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_
             case 1: return launch_factor_shape<R, DAMP_FIXED, 128, 3>(g, p, s, pdl);
             case 2: return launch_factor_shape<R, DAMP_FIXED, 128, 4>(g, p, s, pdl);
             case 3: return launch_factor_shape<R, DAMP_FIXED, 64, 1>(g, p, s, pdl);
+            case 4: return launch_factor_shape<R, DAMP_FIXED, 128, 4, true>(g, p, s, pdl);
+            case 5: return launch_factor_shape<R, DAMP_FIXED, 128, 3, true>(g, p, s, pdl);
             default: break;
         }
     }
@@ -2246,16 +2396,11 @@ cudaError_t launch_belief(const DevGraph<R>& g, const KParams<R>& p, cudaStream_
     return launch_ex(belief_kernel<R, 1>, blocks, FACTOR_BLOCK, s, pdl, g, p);
 }
 
-// the persistent kernel for this graph's belief mapping, damping schedule
-// and launch shape (at least 1, 3 or 4 blocks per SM for shape 0, 1, 2 of
-// the FP32 fixed schedule)
+// the persistent kernel for this graph's belief mapping and damping
+// schedule (one launch shape)
 template <typename R, int BW>
-const void* persistent_fn_bw(int mode, int shape) {
+const void* persistent_fn_bw(int mode, int) {
     if (mode == DAMP_LEARNED) return reinterpret_cast<const void*>(persistent_kernel<R, DAMP_LEARNED, BW, 1>);
-    if constexpr (sizeof(R) == 4) {
-        if (shape == 1) return reinterpret_cast<const void*>(persistent_kernel<R, DAMP_FIXED, BW, 3>);
-        if (shape == 2) return reinterpret_cast<const void*>(persistent_kernel<R, DAMP_FIXED, BW, 4>);
-    }
     return reinterpret_cast<const void*>(persistent_kernel<R, DAMP_FIXED, BW, 1>);
 }
 

@@ -48,7 +48,7 @@ class gbp_params(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
-GBP_MAX_TUNING_CANDIDATES = 8
+GBP_MAX_TUNING_CANDIDATES = 12
 
 
 class gbp_tuning(C.Structure):
