@@ -333,7 +333,7 @@ def _make_loop_problem(seed):
 C4_TARGET_FRAC = 0.5
 
 
-def measure_loop(gbp, stream, p, iters=20):
+def measure_loop(gbp, stream, p, iters=20, launch_mode=0, factor_shape=-1, with_oracle=True):
     """The large single problem (2000 keyframes on two laps of a 30 m loop,
     200k points, ~2M factors), FP32 with FP64 fallback: per-iteration time,
     roofline and fallback count; the oracle's rate on its 10% subgraph
@@ -343,7 +343,11 @@ def measure_loop(gbp, stream, p, iters=20):
     import torch
     g = gbp.Graph(p, stream=stream.cuda_stream, huber_nsigma=HUBER)
     n_kf, n_lm, n_f = gbp.gbp_get_sizes(g.h)
-    mode, ms1, ms2 = g.autotune(8)
+    if launch_mode:
+        g.set_params(launch_mode=launch_mode, factor_shape=factor_shape)
+        mode = launch_mode
+    else:
+        mode, ms1, ms2 = g.autotune(8)
     g.iterate(30)
     st = g.stats()
     torch.cuda.nvtx.range_push("bench_loop")
@@ -359,18 +363,20 @@ def measure_loop(gbp, stream, p, iters=20):
     roof = roofline(sz, iter_ms, fac_ms, mode, "hbm")
     bytes_iter = roof["bytes_per_iteration"]
     peak = roof["peak"]
-    sub = synth.subgraph(p, 200)
-    cores = cpu_cores()
-    return {"workload": f"loop{n_kf}x{n_lm}: {n_kf} keyframes on two laps of a 30 m loop, {n_lm} points, {n_f} "
+    out = {"workload": f"loop{n_kf}x{n_lm}: {n_kf} keyframes on two laps of a 30 m loop, {n_lm} points, {n_f} "
                         "factors, 2% outliers, Huber 2 sigma, d=0.4, FP32 with FP64 fallback",
             "value": n_f / (iter_ms * 1e-3), "unit": UNIT, "us_per_iteration": iter_ms * 1e3,
             "target_us_per_iteration": bytes_iter / (C4_TARGET_FRAC * peak * 1e9) * 1e6,
             "roofline": roof, "fp64_fallbacks_first_30_iterations": st["fp64_fallbacks"],
-            "held_messages": st["held_messages"], "tuning": tuning,
-            "oracle_subgraph": {"factors": sub.n_obs, "keyframes": sub.n_kf, "points": sub.n_lm,
-                                "single_thread": oracle_rate_spawned(sub, 3, False, 1),
-                                "openmp": oracle_rate_spawned(sub, 5, True, cores), "openmp_cores": cores,
-                                "unit": UNIT}}
+            "held_messages": st["held_messages"], "tuning": tuning}
+    if with_oracle:
+        sub = synth.subgraph(p, 200)
+        cores = cpu_cores()
+        out["oracle_subgraph"] = {"factors": sub.n_obs, "keyframes": sub.n_kf, "points": sub.n_lm,
+                                  "single_thread": oracle_rate_spawned(sub, 3, False, 1),
+                                  "openmp": oracle_rate_spawned(sub, 5, True, cores), "openmp_cores": cores,
+                                  "unit": UNIT}
+    return out
 
 
 def _batch_counts(seed):
@@ -637,6 +643,18 @@ def run_scale_only(args, rank, world, local):
         print(json.dumps({"at_scale": r}), flush=True)
 
 
+def run_loop_only(args):
+    """The loop measurement alone, its GPU part (profiling runs)."""
+    import torch
+    from paper_2003_03134_gb300 import build, gbp
+    build.build()
+    torch.cuda.set_device(0)
+    p = _make_loop_problem(0)
+    r = measure_loop(gbp, torch.cuda.current_stream(), p, launch_mode=args.launch_mode,
+                     factor_shape=args.factor_shape, with_oracle=False)
+    print(json.dumps({"loop": r}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -648,6 +666,8 @@ def main():
     ap.add_argument("--no-scale", action="store_true", help="skip the batched at-scale measurement")
     ap.add_argument("--no-loop", action="store_true", help="skip the large single-problem (loop) measurement")
     ap.add_argument("--scale-problems", type=int, default=256, help="problems in the batched measurement")
+    ap.add_argument("--loop-only", action="store_true",
+                    help="only the loop measurement's GPU part (profiling runs); prints its own JSON line")
     ap.add_argument("--scale-only", action="store_true",
                     help="only the batched measurement (profiling runs); prints its own JSON line")
     ap.add_argument("--launch-mode", type=int, default=0, choices=(0, 1, 2),
@@ -660,6 +680,8 @@ def main():
     rank, world, local = dist_env()
     if args.scale_only:
         run_scale_only(args, rank, world, local)
+    elif args.loop_only:
+        run_loop_only(args)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -580,22 +580,33 @@ def test_openmp_build_gives_the_same_bits():
 
 # ------------------------------------------------------- incremental (Sec. 9.2)
 
-def test_added_keyframe_and_points_start_where_the_paper_puts_them():
-    p = synth.make_walk(2, n_kf=14, n_lm=150)
-    init, steps = synth.stream_plan(p, 8)
+def test_added_keyframe_and_points_start_where_the_rule_puts_them():
+    """Sec. 9.2 leaves the initial values of added variables to the front
+    end; the rule here: the new keyframe at the latest keyframe's current
+    estimate, each new point 1 m in front of it on the ray that first
+    observes it."""
+    p = synth.make_walk(2, n_kf=30, n_lm=500, smooth=True)
+    init, steps = synth.stream_plan(p, 10)
     o = oracle.Oracle(init)
     o.iterate(25)
-    kf_before, _ = o.world()
-    st = steps[0]
+    # steps before the first one that brings new points
+    n = 0
+    while steps[n].n_new_lm == 0:
+        o.add_keyframe(steps[n].obs_lm, steps[n].obs_uv, n_new_lm=0)
+        o.iterate(5)
+        n += 1
+    kf_before, lm_before = o.world()
+    n_lm0 = lm_before.shape[0]
+    st = steps[n]
     k = o.add_keyframe(st.obs_lm, st.obs_uv, n_new_lm=st.n_new_lm)
-    assert k == init.n_kf
+    assert k == kf_before.shape[0] and st.n_new_lm > 0
     kf, lm = o.world()
-    # new keyframe = the latest keyframe's current estimate
+    # new keyframe = the latest keyframe's current estimate; old variables untouched
     np.testing.assert_allclose(kf[k], kf_before[k - 1], atol=1e-12)
     np.testing.assert_allclose(kf[:k], kf_before, atol=0)
-    # a new point sits 1 m in front of the new keyframe on its observed ray
+    np.testing.assert_allclose(lm[:n_lm0], lm_before, atol=0)
     R, t = kf[k, :9].reshape(3, 3), kf[k, 9:]
-    for j in range(init.n_lm, init.n_lm + st.n_new_lm):
+    for j in range(n_lm0, n_lm0 + st.n_new_lm):
         i = int(np.nonzero(st.obs_lm == j)[0][0])
         pc = R @ lm[j] + t
         assert pc[2] == pytest.approx(1.0, abs=1e-12)
