@@ -202,13 +202,15 @@ def compare(torch, problem, net: gbp.DampingNet, thresholds=(1.0, 0.1, 0.01), ma
     return res
 
 
-def stream_compare(torch, net: gbp.DampingNet, init, steps, per_step: int = 20, stream=None, **solver):
+def stream_compare(torch, net: gbp.DampingNet, init, steps, per_step: int = 20, stream=None, new_lm_xyz=None,
+                   **solver):
     """The incremental stream of Sec. 9.2 (one keyframe added every
     ``per_step`` iterations) with fixed d = 0.4 and with the learned
     schedule: per step the ARE of the current graph after its iterations,
     and the device time of all iterations (CUDA events around each step's
     gbp_iterate; gbp_add_keyframe's host re-layout is the same for both and
-    not included)."""
+    not included).  new_lm_xyz: per step the initial positions of its new
+    points, or None for the library's rule (1 m along the first ray)."""
     prm = dict(SOLVER, **solver)
     out = {}
     cur = torch.cuda.current_stream()
@@ -220,7 +222,8 @@ def stream_compare(torch, net: gbp.DampingNet, init, steps, per_step: int = 20, 
         for i in range(len(steps) + 1):
             if i:
                 st = steps[i - 1]
-                g.add_keyframe(st.obs_lm, st.obs_uv, n_new_lm=st.n_new_lm)
+                xyz = None if new_lm_xyz is None or not st.n_new_lm else new_lm_xyz[i - 1]
+                g.add_keyframe(st.obs_lm, st.obs_uv, n_new_lm=st.n_new_lm, new_lm_xyz=xyz)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(cur)
             g.iterate(per_step)

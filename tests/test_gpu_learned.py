@@ -282,11 +282,12 @@ def test_stream_learned_against_fixed():
     points at 1 m along their first ray).  On the stream where both
     schedules keep tracking (seed 1: the error of the growing graph settles
     near the noise-and-outlier floor) the learned schedule keeps it at least
-    as low as fixed d = 0.4 on most steps.  (On streams where the graph
-    drifts away from the truth -- new points start 1 m along their first ray
-    and are triangulated from baselines of a few centimetres -- the two
-    schedules trade places from step to step, so no ordering is asserted
-    there.)"""
+    as low as fixed d = 0.4 on most steps.  On the other seeds the 1 m depth
+    of new points is far from their true depth (1-10 m) and is corrected only
+    slowly from baselines of 8 cm per keyframe, the misplaced points pull the
+    keyframes, and the graph drifts under either schedule, so no ordering is
+    asserted there (test_streams_track_with_new_points_near_their_depth shows
+    that the drift is the initialisation's)."""
     import torch
     init, steps = synth.make_stream(1)
     net = gbp.DampingNet(learned.trained_params())
@@ -298,4 +299,26 @@ def test_stream_learned_against_fixed():
     assert fx["final_are"] < 10.0
     assert lr["mean_are"] <= fx["mean_are"]
     assert (b <= a).mean() >= 0.75
+    net.close()
+
+
+@pytest.mark.parametrize("seed", [0, 2, 3])
+def test_streams_track_with_new_points_near_their_depth(seed):
+    """The streams that drift with the 1 m rule track under both schedules
+    when each new point starts within ~5 cm of its true position: the error
+    of the growing graph stays near the noise-and-outlier floor (~7 px) over
+    all 490 steps.  So their drift comes from the new points' initial depth,
+    not from the iteration."""
+    import torch
+    init, steps = synth.make_stream(seed)
+    rng = np.random.default_rng(seed)
+    xyz = [st.new_lm_true + rng.normal(0.0, 0.05, st.new_lm_true.shape) for st in steps]
+    net = gbp.DampingNet(learned.trained_params())
+    r = learned.stream_compare(torch, net, init, steps, per_step=20, new_lm_xyz=xyz)
+    fx, lr = r["fixed"], r["learned"]
+    print(seed, {k: (fx[k], lr[k]) for k in ("mean_are", "final_are", "device_ms")})
+    for s in (fx, lr):
+        a = np.array(s["are_per_step"])
+        assert np.isfinite(a).all()
+        assert s["final_are"] < 10.0 and a.max() < 20.0
     net.close()
