@@ -1325,35 +1325,6 @@ __device__ __forceinline__ void damp_store_fixed(const DevGraph<R>& g, const KPa
         for (int i = 0; i < 9; ++i) g.mlx[(size_t)i * n_f + f] = sum[i];
 }
 
-// What a tile needs that no iteration changes: its factor range and, per
-// lane, the factor's landmark, keyframe and keyframe slot, the landmark's
-// factor range, birth iteration and prior diagonal.  The per-phase kernel
-// loads it before it waits for the previous kernel.
-template <typename R>
-struct TileStatic {
-    int ts, te, m, k, slot, lo, hi, lbirth;
-    R lD[3];
-};
-
-template <typename R>
-__device__ __forceinline__ void load_tile_static(const DevGraph<R>& g, int tile, int lane, TileStatic<R>& s) {
-    s.ts = g.tile_start[tile];
-    s.te = g.tile_start[tile + 1];
-    const int f = s.ts + lane;
-    s.m = -1; s.k = 0; s.slot = 0; s.lo = 0; s.hi = 0; s.lbirth = 0;
-    s.lD[0] = s.lD[1] = s.lD[2] = R(0);
-    if (f < s.te) {
-        s.m = g.fm[f];
-        s.k = g.fk[f];
-        s.slot = g.kpos[f];
-        s.lo = g.lm_off[s.m];
-        s.hi = g.lm_off[s.m + 1];
-        s.lbirth = g.lm_birth[s.m];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) s.lD[i] = g.lm_D[s.m * 3 + i];
-    }
-}
-
 // ------------------------------------------------------------------------
 // Phase A: one warp, one tile of whole landmarks (at most 32 factors,
 // consecutive in landmark order), one lane per factor.  For each factor:
@@ -1379,13 +1350,11 @@ __device__ __forceinline__ void load_tile_static(const DevGraph<R>& g, int tile,
 // precision FP32 cannot take is not worked here -- it stores nothing and is
 // listed for factor_deferred_kernel, which works it with the FP64 redo --
 // so that this kernel carries no state for the FP64 path.
-// st (when given): the tile's static inputs, loaded by the caller.
 template <typename R, int MODE, bool DEFER = false>
 __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R>& P, int tile, int t, int lane,
-                                           MlpSmem<MODE>& S, bool weights_pending = false,
-                                           const TileStatic<R>* st = nullptr) {
+                                           MlpSmem<MODE>& S, bool weights_pending = false) {
     const int n_f = g.n_f;
-    const int ts = st ? st->ts : g.tile_start[tile], te = st ? st->te : g.tile_start[tile + 1];
+    const int ts = g.tile_start[tile], te = g.tile_start[tile + 1];
     const int f = ts + lane;
     const bool active = f < te;
     constexpr bool FEAT = MODE != DAMP_FIXED;
@@ -1402,15 +1371,9 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
 #pragma unroll
     for (int i = 0; i < NLIN; ++i) lin4[i] = R(0);
     if (active) {
-        if (st) {
-            m = st->m;
-            k = st->k;
-            slot = st->slot;
-        } else {
-            m = g.fm[f];
-            k = g.fk[f];
-            slot = g.kpos[f];
-        }
+        m = g.fm[f];
+        k = g.fk[f];
+        slot = g.kpos[f];
         tl = g.tlin[f];
 #pragma unroll
         for (int i = 0; i < NML; ++i) cml[i] = g.ml[(size_t)i * n_f + f];
@@ -1429,15 +1392,9 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
     R lb_mu[3];          // the landmark's mean mu^t
     R lD[3];             // the landmark's prior diagonal
     if (active) {
-        if (st) {
-            lo = st->lo;
-            hi = st->hi;
-            lbirth = st->lbirth;
-        } else {
-            lo = g.lm_off[m];
-            hi = g.lm_off[m + 1];
-            lbirth = g.lm_birth[m];
-        }
+        lo = g.lm_off[m];
+        hi = g.lm_off[m + 1];
+        lbirth = g.lm_birth[m];
         // the keyframe block is moved into kj by the belief phase, on another
         // SM within one persistent launch: read through L2, as the beliefs
         load_rec_cg<R, KJ>(g.kj + (size_t)slot * KJ, jr);
@@ -1447,7 +1404,7 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             lb_mu[i] = __ldcg(lbp + 9 + i);
-            lD[i] = st ? st->lD[i] : g.lm_D[m * 3 + i];
+            lD[i] = g.lm_D[m * 3 + i];
         }
     } else {
 #pragma unroll
@@ -1965,16 +1922,13 @@ template <typename R, int MODE, int NT, bool DEFER>
 __device__ __forceinline__ void factor_body(const DevGraph<R>& g, const KParams<R>& P) {
     __shared__ __align__(16) MlpSmem<MODE> S;
     mlp_load_async<MODE>(P, S);   // network weights do not change between iterations
+    pdl_wait_prev();
     const int lane = threadIdx.x & 31;
     const int tile = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
-    // what no iteration changes, before the wait for the previous kernel
-    TileStatic<R> ts;
-    if (tile < g.n_tiles) load_tile_static(g, g.tile_off + tile, lane, ts);
-    pdl_wait_prev();
     const int t = g.ctl[CTL_ITER];
     float dmu = 0.0f;
     if (tile < g.n_tiles)   // uniform per warp
-        dmu = tile_work<R, MODE, DEFER>(g, P, g.tile_off + tile, t, lane, S, MODE == DAMP_LEARNED, &ts);
+        dmu = tile_work<R, MODE, DEFER>(g, P, g.tile_off + tile, t, lane, S, MODE == DAMP_LEARNED);
     else if constexpr (MODE == DAMP_LEARNED) mlp_load_wait();   // the block's barrier, for warps without a tile
     pdl_allow_next();
     dmu = warp_max(dmu);
