@@ -270,6 +270,40 @@ def _projections(p, kf_Rt, lm_xyz):
     return uv, pc[:, 2] >= 0.05
 
 
+def measure_incremental(gbp, stream, seed=1, per_step=20):
+    """Incremental SLAM (Sec. 9.2): the 500-keyframe stream, one keyframe
+    added every per_step iterations.  Wall time of each gbp_add_keyframe
+    (host layout and device re-layout, synchronised), device time of the
+    iterations, the graph's ARE at the end."""
+    import torch
+    from paper_2003_03134_gb300 import synth
+    init, steps = synth.make_stream(seed)
+    g = gbp.Graph(init, stream=stream.cuda_stream, huber_nsigma=HUBER)
+    g.iterate(per_step)
+    t_add, it_ms = [], 0.0
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for st in steps:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.add_keyframe(st.obs_lm, st.obs_uv, n_new_lm=st.n_new_lm)
+        torch.cuda.synchronize()
+        t_add.append(time.perf_counter() - t0)
+        a.record(stream)
+        g.iterate(per_step)
+        b.record(stream)
+        b.synchronize()
+        it_ms += a.elapsed_time(b)
+    n_kf, n_lm, n_f = gbp.gbp_get_sizes(g.h)
+    are = g.stats()["are"]
+    g.close()
+    t = np.array(t_add) * 1e3
+    return {"workload": f"stream{seed}: {len(steps)} keyframes added to {init.n_kf}, {per_step} iterations each, "
+                        f"ending at {n_kf} keyframes, {n_lm} points, {n_f} factors",
+            "add_keyframe_ms_first50": float(t[:50].mean()), "add_keyframe_ms_last50": float(t[-50:].mean()),
+            "add_keyframe_total_s": float(t.sum() / 1e3), "iterations_device_s": it_ms / 1e3,
+            "final_are": are}
+
+
 def lm_baseline(p, kf_ref, lm_ref, max_iters=50):
     """The project's CPU Levenberg-Marquardt bundle adjuster (dense Schur
     complement, single thread) on the same problem and objective: seconds per
@@ -580,6 +614,8 @@ def run_gpu(args, rank, world, local):
                         **{k: {"iters": v["iters"], "ms": v["ms"], "final_are": v["final"]["are"]}
                            for k, v in cmp.items()}}
 
+        incremental = measure_incremental(gbp, stream)
+
         loop = None
         if loop_job is not None:
             loop = measure_loop(gbp, stream, loop_job.get())
@@ -610,7 +646,7 @@ def run_gpu(args, rank, world, local):
                        "iters_per_step": float(np.mean(iters))},
             "ms_to_1px_vs_oracle": ms_1px, "iters_to_1px_vs_oracle": t_1px, "learned_damping": learned_line,
             "fp32_error_vs_oracle": fp32_err,
-            "roofline": roof, "at_scale": at_scale, "loop": loop, "cpu_baseline": cpu,
+            "roofline": roof, "at_scale": at_scale, "loop": loop, "incremental": incremental, "cpu_baseline": cpu,
             "cpu_baseline_openmp": cpu_omp, "lm_baseline": lm_line,
             "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s},

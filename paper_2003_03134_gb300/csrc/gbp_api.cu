@@ -268,7 +268,9 @@ gbp_status upload_prior_table(gbp_graph* g) {
 // Upload the problem into freshly allocated device buffers of type R and
 // generate the priors; leaves the dynamic state uninitialised.
 template <typename R>
-gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
+// x0_init: linearisation points for the prior pass (host), or rs: gathered
+// on the device from a previous layout (a keyframe was added), else zero.
+gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr, const RelayoutSrc<R>* rs = nullptr) {
     DevState<R>& s = state<R>(g);
     s.release();
     const int nk = g->n_kf, nl = g->n_lm, nf = g->n_f;
@@ -406,7 +408,7 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
     // linearisation points (the references at creation) for the prior pass
     if (x0_init && nf)
         CK(cudaMemcpyAsync(s.x0, x0_init->data(), sizeof(R) * 9 * (size_t)nf, cudaMemcpyHostToDevice, st));
-    else if (nf)
+    else if (nf && !rs)
         CK(cudaMemsetAsync(s.x0, 0, sizeof(R) * 9 * (size_t)nf, st));
 
     DevGraph<R>& d = s.g;
@@ -495,6 +497,7 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr) {
     d.rec_X = nullptr;
     d.rec_T = nullptr;
     d.ctl = g->ctl;
+    if (rs && nf) CK(launch_relayout<R>(d, *rs, 0, st));
 
     // priors: per-factor diagonal information at the reference (temporary
     // buffers reuse the message storage, which is cleared afterwards)
@@ -843,37 +846,71 @@ std::vector<int32_t> keyframe_slots(const std::vector<int32_t>& fk, int n_kf) {
 // take their prior from their own factors at those factors' linearisation
 // points, annealed from this iteration on; new factors are linearised at the
 // current means with zero messages.
+// The grown factor set's order without a sort: the old factors are in
+// (landmark, keyframe, caller) order and every new factor has the new,
+// largest keyframe, so each landmark's factors are its old ones followed by
+// its new ones in observation order -- what a stable sort of the caller's
+// observations by (landmark, keyframe) gives.  src_f receives each factor's
+// previous internal index (-1 for a new one).
+void order_factors_append(gbp_graph* g, int L1, int K0, int n_obs, const int32_t* obs_lm, const double* obs_uv,
+                          std::vector<int32_t>& src_f) {
+    const int F0 = g->n_f, F1 = F0 + n_obs;
+    std::vector<int32_t> off(L1 + 1, 0), by_lm(n_obs);
+    for (int i = 0; i < n_obs; ++i) off[obs_lm[i] + 1]++;
+    for (int m = 0; m < L1; ++m) off[m + 1] += off[m];
+    {
+        std::vector<int32_t> fill(off.begin(), off.end() - 1);
+        for (int i = 0; i < n_obs; ++i) by_lm[fill[obs_lm[i]]++] = i;
+    }
+    std::vector<int32_t> fk(F1), fm(F1), oi(F1);
+    std::vector<double> z(2 * (size_t)F1);
+    src_f.assign(F1, -1);
+    int f = 0, o = 0;
+    for (int m = 0; m < L1; ++m) {
+        for (; o < F0 && g->fm[o] == m; ++o, ++f) {
+            fk[f] = g->fk[o];
+            fm[f] = m;
+            z[2 * (size_t)f] = g->z[2 * (size_t)o];
+            z[2 * (size_t)f + 1] = g->z[2 * (size_t)o + 1];
+            oi[f] = g->obs_index[o];
+            src_f[f] = o;
+        }
+        for (int q = off[m]; q < off[m + 1]; ++q, ++f) {
+            const int i = by_lm[q];
+            fk[f] = K0;
+            fm[f] = m;
+            z[2 * (size_t)f] = obs_uv[2 * i];
+            z[2 * (size_t)f + 1] = obs_uv[2 * i + 1];
+            oi[f] = F0 + i;
+        }
+    }
+    g->n_f = F1;
+    g->fk.swap(fk);
+    g->fm.swap(fm);
+    g->z.swap(z);
+    g->obs_index.swap(oi);
+    g->f_of_obs.assign(F1, 0);
+    for (int q = 0; q < F1; ++q) g->f_of_obs[g->obs_index[q]] = q;
+}
+
+// Incremental SLAM (Sec. 9.2): the grown graph's layout is built on the host
+// from the index arrays alone (no state leaves the device), and the state is
+// gathered on the device from the previous layout's buffers
+// (relayout_kernel); the host reads back only the control block, the latest
+// keyframe's mean and the new variables' prior diagonals.
 template <typename R>
 gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_lm, const double* new_lm_xyz,
                              int n_obs, const int32_t* obs_lm, const double* obs_uv) {
     cudaStream_t st = g->stream;
     const int K0 = g->n_kf, L0 = g->n_lm, F0 = g->n_f;
     const int K1 = K0 + 1, L1 = L0 + n_new_lm, F1 = F0 + n_obs;
-    std::vector<int32_t> ctl(CTL_N), tlin(F0);
-    std::vector<R> x0(9 * (size_t)F0), mk((size_t)KREC * F0), mkp((size_t)KREC * F0), kj((size_t)KJ * F0),
-        lin((size_t)NLIN * F0),
-        ml((size_t)NML * F0), kb((size_t)KBEL * K0),
-        lb((size_t)LBEL * L0), kD(6 * (size_t)K0), kA(6 * (size_t)K0), lD(3 * (size_t)L0);
-    std::vector<float> hist(HIST * (size_t)F0);
+    int32_t ctl[CTL_N];
+    R mu_last[6];
     {
         DevState<R>& s = state<R>(g);
-        CK(cudaMemcpyAsync(ctl.data(), g->ctl, sizeof(int32_t) * CTL_N, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        const R* mk_cur = (ctl[CTL_ITER] & 1) ? s.mk2 : s.mk;
-        const R* mk_prev = (ctl[CTL_ITER] & 1) ? s.mk : s.mk2;   // m^{t-1}, read by the learned schedule
-        CK(cudaMemcpyAsync(x0.data(), s.x0, sizeof(R) * x0.size(), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(tlin.data(), s.tlin, sizeof(int32_t) * tlin.size(), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(mk.data(), mk_cur, sizeof(R) * mk.size(), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(mkp.data(), mk_prev, sizeof(R) * mkp.size(), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(kj.data(), s.kj, sizeof(R) * kj.size(), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(lin.data(), s.lin, sizeof(R) * lin.size(), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(ml.data(), s.ml, sizeof(R) * ml.size(), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(hist.data(), s.hist, sizeof(float) * hist.size(), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(kb.data(), s.kf_bel, sizeof(R) * kb.size(), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(lb.data(), s.lm_bel, sizeof(R) * lb.size(), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(kD.data(), s.kf_D, sizeof(R) * kD.size(), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(kA.data(), s.kf_A, sizeof(R) * kA.size(), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(lD.data(), s.lm_D, sizeof(R) * lD.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ctl, g->ctl, sizeof(int32_t) * CTL_N, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(mu_last, s.kf_bel + (size_t)KBEL * (K0 - 1) + KB_MU, sizeof(R) * 6, cudaMemcpyDeviceToHost,
+                           st));
         CK(cudaStreamSynchronize(st));
     }
     const int t = ctl[CTL_ITER];
@@ -884,40 +921,17 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
     if (kf_Rt_init) {
         std::copy(kf_Rt_init, kf_Rt_init + 12, Rt);
     } else {
-        const R* mu = &kb[(size_t)KBEL * (K0 - 1) + KB_MU];
-        double w[3] = {double(mu[3]), double(mu[4]), double(mu[5])}, E[9];
+        double w[3] = {double(mu_last[3]), double(mu_last[4]), double(mu_last[5])}, E[9];
         so3_exp_host(w, E);
         const double* Rr = &g->kf_R[9 * (size_t)(K0 - 1)];
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) Rt[3 * i + j] = E[3 * i] * Rr[j] + E[3 * i + 1] * Rr[3 + j] + E[3 * i + 2] * Rr[6 + j];
         double c[3];
-        for (int i = 0; i < 3; ++i) c[i] = g->kf_c[3 * (K0 - 1) + i] + double(mu[i]);
+        for (int i = 0; i < 3; ++i) c[i] = g->kf_c[3 * (K0 - 1) + i] + double(mu_last[i]);
         for (int i = 0; i < 3; ++i) Rt[9 + i] = -(Rt[3 * i] * c[0] + Rt[3 * i + 1] * c[1] + Rt[3 * i + 2] * c[2]);
     }
     double cnew[3];
     for (int i = 0; i < 3; ++i) cnew[i] = -(Rt[i] * Rt[9] + Rt[3 + i] * Rt[10] + Rt[6 + i] * Rt[11]);
-
-    // state of the old factors by caller observation index
-    std::vector<int32_t> old_index = g->obs_index;
-    std::vector<int32_t> old_kpos = keyframe_slots(g->fk, K0);
-    std::vector<int32_t> ok(F1), ol(F1), idx(F1);
-    std::vector<double> uv(2 * (size_t)F1);
-    std::vector<int32_t> where(F1, -1);   // caller index -> old internal factor
-    for (int f = 0; f < F0; ++f) {
-        const int ci = old_index[f];
-        ok[ci] = g->fk[f];
-        ol[ci] = g->fm[f];
-        uv[2 * ci] = g->z[2 * f];
-        uv[2 * ci + 1] = g->z[2 * f + 1];
-        where[ci] = f;
-    }
-    for (int i = 0; i < n_obs; ++i) {
-        ok[F0 + i] = K0;
-        ol[F0 + i] = obs_lm[i];
-        uv[2 * (F0 + i)] = obs_uv[2 * i];
-        uv[2 * (F0 + i) + 1] = obs_uv[2 * i + 1];
-    }
-    std::iota(idx.begin(), idx.end(), 0);
 
     // new variables
     for (int i = 0; i < 9; ++i) g->kf_R.push_back(Rt[i]);
@@ -940,85 +954,75 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
     }
     g->n_kf = K1;
     g->n_lm = L1;
-    order_factors(g, ok, ol, uv, idx);
+    std::vector<int32_t> src_f;
+    order_factors_append(g, L1, K0, n_obs, obs_lm, obs_uv, src_f);
     g->prob_kf0 = {0, K1};
     g->prob_lm0 = {0, L1};
     g->prob_f0 = {0, F1};
     CK(cudaMemcpy(g->d_prob_f0, g->prob_f0.data(), sizeof(int32_t) * 2, cudaMemcpyHostToDevice));
     g->uv_ref.clear();   // the reference projections no longer cover every factor
 
-    // linearisation points in the new order: old factors keep theirs, new
-    // ones take the current means (a new variable's mean is 0 in its chart)
-    std::vector<R> x0n(9 * (size_t)F1), mln((size_t)NML * F1, R(0)), mkn((size_t)KREC * F1, R(0)),
-        mkpn((size_t)KREC * F1, R(0)), kjn((size_t)KJ * F1, R(0)), linn((size_t)NLIN * F1, R(0));
-    std::vector<float> histn(HIST * (size_t)F1, 0.0f);
-    std::vector<int32_t> tlinn(F1);
-    std::vector<int32_t> kpos = keyframe_slots(g->fk, K1);
-    for (int f = 0; f < F1; ++f) {
-        const int ci = g->obs_index[f];
-        const int of = ci < F0 ? where[ci] : -1;
-        if (of >= 0) {
-            for (int i = 0; i < 9; ++i) x0n[(size_t)i * F1 + f] = x0[(size_t)i * F0 + of];
-            for (int i = 0; i < NML; ++i) mln[(size_t)i * F1 + f] = ml[(size_t)i * F0 + of];
-            for (int i = 0; i < NLIN; ++i) linn[(size_t)i * F1 + f] = lin[(size_t)i * F0 + of];
-            std::copy(&kj[(size_t)KJ * old_kpos[of]], &kj[(size_t)KJ * old_kpos[of]] + KJ, &kjn[(size_t)KJ * kpos[f]]);
-            tlinn[f] = tlin[of];
-            for (int j = 0; j < HIST; ++j) histn[(size_t)j * F1 + f] = hist[(size_t)j * F0 + of];
-            std::copy(&mk[(size_t)KREC * old_kpos[of]], &mk[(size_t)KREC * old_kpos[of]] + KREC,
-                      &mkn[(size_t)KREC * kpos[f]]);
-            std::copy(&mkp[(size_t)KREC * old_kpos[of]], &mkp[(size_t)KREC * old_kpos[of]] + KREC,
-                      &mkpn[(size_t)KREC * kpos[f]]);
-        } else {
-            const int m = g->fm[f];
-            for (int i = 0; i < 6; ++i) x0n[(size_t)i * F1 + f] = R(0);
-            for (int i = 0; i < 3; ++i) x0n[(size_t)(6 + i) * F1 + f] = m < L0 ? lb[(size_t)LBEL * m + 9 + i] : R(0);
-            tlinn[f] = t;
+    // the previous layout stays alive until its state is gathered
+    DevState<R> old = state<R>(g);
+    state<R>(g) = DevState<R>();
+    int32_t* d_src = nullptr;
+    cudaError_t e = dev_alloc(&d_src, (size_t)F1);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_src, src_f.data(), sizeof(int32_t) * (size_t)F1, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        old.release();
+        if (d_src) cudaFree(d_src);
+        return cuda_fail(g, e, "add_keyframe");
+    }
+    const RelayoutSrc<R> rs{d_src, F0, L0, t, old.x0, old.tlin, old.ml, old.lin, old.hist, old.kpos, old.kj,
+                            (t & 1) ? old.mk2 : old.mk, (t & 1) ? old.mk : old.mk2, old.lm_bel};
+    destroy_exec(g);
+    gbp_status bst = build_device<R>(g, nullptr, &rs);
+    DevState<R>& s = state<R>(g);
+    if (bst == GBP_OK) {
+        // factor state in the new layout
+        e = launch_relayout<R>(s.g, rs, 1, st);
+        // priors and beliefs: old variables keep theirs (the prior pass just
+        // run covers the new ones), new ones start at their prior at s(0)
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.kf_D, old.kf_D, sizeof(R) * 6 * (size_t)K0, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.kf_A, old.kf_A, sizeof(R) * 6 * (size_t)K0, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.lm_D, old.lm_D, sizeof(R) * 3 * (size_t)L0, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s.kf_bel, old.kf_bel, sizeof(R) * KBEL * (size_t)K0, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s.lm_bel, old.lm_bel, sizeof(R) * LBEL * (size_t)L0, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s.kjs, 0, sizeof(R) * KJ * (size_t)F1, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s.mlx, 0, sizeof(R) * 9 * (size_t)F1, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s.kf_A + 6 * (size_t)K0, 0, sizeof(R) * 6, st);
+        std::vector<R> kD(6), lD(3 * (size_t)n_new_lm);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(kD.data(), s.kf_D + 6 * (size_t)K0, sizeof(R) * 6, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && n_new_lm)
+            e = cudaMemcpyAsync(lD.data(), s.lm_D + 3 * (size_t)L0, sizeof(R) * lD.size(), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) {
+            const R s0 = g->prm.prior_anneal_iters > 0 ? R(1) : R(g->prm.prior_final_scale);
+            const R isig2 = R(1.0 / (double(g->prm.sigma_px) * double(g->prm.sigma_px)));
+            std::vector<R> kbn(KBEL), lbn(LBEL * (size_t)n_new_lm, R(0));
+            R pd[6];
+            for (int i = 0; i < 6; ++i) pd[i] = s0 * kD[i] * isig2;
+            kf_prior_record_host<R>(pd, kbn.data());
+            for (int j = 0; j < n_new_lm; ++j)
+                for (int i = 0; i < 3; ++i) lbn[(size_t)LBEL * j + i * (i + 1) / 2 + i] = s0 * lD[3 * (size_t)j + i] * isig2;
+            e = cudaMemcpyAsync(s.kf_bel + (size_t)KBEL * K0, kbn.data(), sizeof(R) * KBEL, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess && n_new_lm)
+                e = cudaMemcpyAsync(s.lm_bel + (size_t)LBEL * L0, lbn.data(), sizeof(R) * lbn.size(),
+                                    cudaMemcpyHostToDevice, st);
+            // the control block as it was (the prior pass leaves it alone; kept
+            // explicit so that the iteration count and flags carry over)
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(g->ctl, ctl, sizeof(int32_t) * CTL_N, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         }
     }
-    destroy_exec(g);
-    gbp_status bst = build_device<R>(g, &x0n);
+    old.release();
+    cudaFree(d_src);
     if (bst != GBP_OK) return bst;
-
-    // priors: old variables keep theirs, new ones take the pass just run
-    DevState<R>& s = state<R>(g);
-    std::vector<R> kDn(6 * (size_t)K1), lDn(3 * (size_t)L1), kAn(6 * (size_t)K1, R(0));
-    CK(cudaMemcpyAsync(kDn.data(), s.kf_D, sizeof(R) * kDn.size(), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(lDn.data(), s.lm_D, sizeof(R) * lDn.size(), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    std::copy(kD.begin(), kD.end(), kDn.begin());
-    std::copy(lD.begin(), lD.end(), lDn.begin());
-    std::copy(kA.begin(), kA.end(), kAn.begin());
-    // beliefs: old carried over, new = their prior at scale s(0), mean 0
-    const R s0 = g->prm.prior_anneal_iters > 0 ? R(1) : R(g->prm.prior_final_scale);
-    const R isig2 = R(1.0 / (double(g->prm.sigma_px) * double(g->prm.sigma_px)));
-    std::vector<R> kbn((size_t)KBEL * K1, R(0)), lbn((size_t)LBEL * L1, R(0));
-    std::copy(kb.begin(), kb.end(), kbn.begin());
-    std::copy(lb.begin(), lb.end(), lbn.begin());
-    {
-        R pd[6];
-        for (int i = 0; i < 6; ++i) pd[i] = s0 * kDn[6 * (size_t)K0 + i] * isig2;
-        kf_prior_record_host<R>(pd, &kbn[(size_t)KBEL * K0]);
-    }
-    for (int j = L0; j < L1; ++j)
-        for (int i = 0; i < 3; ++i) lbn[(size_t)LBEL * j + i * (i + 1) / 2 + i] = s0 * lDn[3 * (size_t)j + i] * isig2;
-    R* mk_cur = (t & 1) ? s.mk2 : s.mk;
-    R* mk_other = (t & 1) ? s.mk : s.mk2;
-    CK(cudaMemcpyAsync(s.kf_D, kDn.data(), sizeof(R) * kDn.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(s.lm_D, lDn.data(), sizeof(R) * lDn.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(s.kf_A, kAn.data(), sizeof(R) * kAn.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(s.tlin, tlinn.data(), sizeof(int32_t) * tlinn.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(s.ml, mln.data(), sizeof(R) * mln.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(s.hist, histn.data(), sizeof(float) * histn.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(mk_cur, mkn.data(), sizeof(R) * mkn.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(mk_other, mkpn.data(), sizeof(R) * mkpn.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(s.kj, kjn.data(), sizeof(R) * kjn.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(s.lin, linn.data(), sizeof(R) * linn.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(s.kjs, 0, sizeof(R) * KJ * (size_t)F1, st));
-    CK(cudaMemsetAsync(s.mlx, 0, sizeof(R) * 9 * (size_t)F1, st));
-    CK(cudaMemcpyAsync(s.kf_bel, kbn.data(), sizeof(R) * kbn.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(s.lm_bel, lbn.data(), sizeof(R) * lbn.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(g->ctl, ctl.data(), sizeof(int32_t) * CTL_N, cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));
+    if (e != cudaSuccess) return cuda_fail(g, e, "add_keyframe");
     return GBP_OK;
 }
 

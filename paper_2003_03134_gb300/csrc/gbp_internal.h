@@ -203,6 +203,26 @@ constexpr int N_FACTOR_SHAPES = 6;
 constexpr int N_PERSISTENT_SHAPES = 1;   // no register budget
 template <typename R> cudaError_t launch_factor(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s,
                                                 int mode = DAMP_FIXED, bool pdl = false, int shape = 0);
+// The previous layout's per-factor state, for relayout_kernel (incremental
+// SLAM): src_f maps the new layout's factors to the previous internal
+// indices (-1: a factor of the new keyframe).
+template <typename R>
+struct RelayoutSrc {
+    const int32_t* src_f;
+    int32_t n_f, n_lm, t;
+    const R* x0;
+    const int32_t* tlin;
+    const R* ml;
+    const R* lin;
+    const float* hist;
+    const int32_t* kpos;
+    const R* kj;
+    const R* mk_cur;          // m^t, slot order
+    const R* mk_oth;          // m^{t-1}
+    const R* lm_bel;
+};
+template <typename R> cudaError_t launch_relayout(const DevGraph<R>& nw, const RelayoutSrc<R>& o, int phase,
+                                                  cudaStream_t s);
 template <typename R> cudaError_t launch_init(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s);
 template <typename R> cudaError_t launch_belief(const DevGraph<R>& g, const KParams<R>& p, cudaStream_t s,
                                                 bool pdl = false);

@@ -2548,6 +2548,69 @@ cudaError_t launch_split_records(const DevGraph<R>& g, int kind, int put, int n,
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------
+// Re-layout after a keyframe is added (incremental SLAM): the per-factor
+// state of the grown graph gathered on the device from the previous
+// layout's buffers.  src_f[f]: the previous internal index of the new
+// layout's factor f, or -1 for a factor of the new keyframe.
+//   phase 0: linearisation points -- kept, or for a new factor the current
+//            means (its keyframe's chart origin and its landmark's mean,
+//            or 0 for a new landmark);
+//   phase 1: t_lin, the stored linearisation, the landmark message, the
+//            learned schedule's history, and by keyframe slot the Jacobian
+//            block and both message buffers -- kept, or empty and t_lin = t.
+
+template <typename R>
+__global__ void relayout_kernel(DevGraph<R> nw, RelayoutSrc<R> o, int phase) {
+    const int F1 = nw.n_f, F0 = o.n_f;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < F1; f += gridDim.x * blockDim.x) {
+        const int src = o.src_f[f];
+        if (phase == 0) {
+            if (src >= 0) {
+                for (int i = 0; i < 9; ++i) nw.x0[(size_t)i * F1 + f] = o.x0[(size_t)i * F0 + src];
+            } else {
+                const int m = nw.fm[f];
+                for (int i = 0; i < 6; ++i) nw.x0[(size_t)i * F1 + f] = R(0);
+                for (int i = 0; i < 3; ++i)
+                    nw.x0[(size_t)(6 + i) * F1 + f] = m < o.n_lm ? o.lm_bel[(size_t)m * LBEL + 9 + i] : R(0);
+            }
+            continue;
+        }
+        const int slot = nw.kpos[f];
+        R* mk_cur = (o.t & 1) ? nw.mk2 : nw.mk;
+        R* mk_oth = (o.t & 1) ? nw.mk : nw.mk2;
+        if (src >= 0) {
+            const int os = o.kpos[src];
+            nw.tlin[f] = o.tlin[src];
+            for (int i = 0; i < NML; ++i) nw.ml[(size_t)i * F1 + f] = o.ml[(size_t)i * F0 + src];
+            for (int i = 0; i < NLIN; ++i) nw.lin[(size_t)i * F1 + f] = o.lin[(size_t)i * F0 + src];
+            for (int i = 0; i < HIST; ++i) nw.hist[(size_t)i * F1 + f] = o.hist[(size_t)i * F0 + src];
+            for (int i = 0; i < KJ; ++i) nw.kj[(size_t)slot * KJ + i] = o.kj[(size_t)os * KJ + i];
+            for (int i = 0; i < KREC; ++i) {
+                mk_cur[(size_t)slot * KREC + i] = o.mk_cur[(size_t)os * KREC + i];
+                mk_oth[(size_t)slot * KREC + i] = o.mk_oth[(size_t)os * KREC + i];
+            }
+        } else {
+            nw.tlin[f] = o.t;
+            for (int i = 0; i < NML; ++i) nw.ml[(size_t)i * F1 + f] = R(0);
+            for (int i = 0; i < NLIN; ++i) nw.lin[(size_t)i * F1 + f] = R(0);
+            for (int i = 0; i < HIST; ++i) nw.hist[(size_t)i * F1 + f] = 0.0f;
+            for (int i = 0; i < KJ; ++i) nw.kj[(size_t)slot * KJ + i] = R(0);
+            for (int i = 0; i < KREC; ++i) {
+                mk_cur[(size_t)slot * KREC + i] = R(0);
+                mk_oth[(size_t)slot * KREC + i] = R(0);
+            }
+        }
+    }
+}
+
+template <typename R>
+cudaError_t launch_relayout(const DevGraph<R>& nw, const RelayoutSrc<R>& o, int phase, cudaStream_t s) {
+    const int blocks = std::max(1, std::min((nw.n_f + 255) / 256, 1024));
+    relayout_kernel<R><<<blocks, 256, 0, s>>>(nw, o, phase);
+    return cudaGetLastError();
+}
+
 #define GBP_INSTANTIATE(R)                                                                                 \
     template cudaError_t launch_factor<R>(const DevGraph<R>&, const KParams<R>&, cudaStream_t, int, bool, int); \
     template cudaError_t launch_capture_messages<R>(const DevGraph<R>&, int, R*, cudaStream_t);            \
@@ -2559,7 +2622,8 @@ cudaError_t launch_split_records(const DevGraph<R>& g, int kind, int put, int n,
     template cudaError_t launch_prior<R>(const DevGraph<R>&, const KParams<R>&, R*, R*, R*, R*, cudaStream_t); \
     template cudaError_t launch_metrics<R>(const DevGraph<R>&, const KParams<R>&, double*, int, double*, cudaStream_t); \
     template cudaError_t launch_residuals<R>(const DevGraph<R>&, const KParams<R>&, double*, cudaStream_t); \
-    template cudaError_t launch_split_records<R>(const DevGraph<R>&, int, int, int, const int32_t*, float*, cudaStream_t);
+    template cudaError_t launch_split_records<R>(const DevGraph<R>&, int, int, int, const int32_t*, float*, cudaStream_t); \
+    template cudaError_t launch_relayout<R>(const DevGraph<R>&, const RelayoutSrc<R>&, int, cudaStream_t);
 
 GBP_INSTANTIATE(float)
 GBP_INSTANTIATE(double)
