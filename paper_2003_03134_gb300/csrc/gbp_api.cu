@@ -10,6 +10,7 @@
 #include "../../include/gbp.h"
 
 #include <algorithm>
+#include <unordered_map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -33,6 +34,50 @@ cudaError_t dev_alloc(T** p, size_t n) {
     if (n == 0) n = 1;
     return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
 }
+
+// Device buffers of a graph's layout, kept for reuse when a layout is
+// replaced (a keyframe added): a released buffer goes back to the pool and
+// the next layout takes the smallest one that fits.  With headroom > 1 a
+// new buffer is allocated that much larger, so that the following layouts,
+// each a little larger, find their buffers here instead of in cudaMalloc.
+struct BufPool {
+    std::unordered_map<void*, size_t> cap;       // pool buffers in use or free: their size
+    std::vector<std::pair<size_t, void*>> spare; // released ones
+    template <typename T>
+    cudaError_t alloc(T** p, size_t n, double headroom) {
+        const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+        size_t best = SIZE_MAX, at = 0;
+        for (size_t i = 0; i < spare.size(); ++i)
+            if (spare[i].first >= bytes && spare[i].first < best) {
+                best = spare[i].first;
+                at = i;
+            }
+        if (best != SIZE_MAX) {
+            *p = static_cast<T*>(spare[at].second);
+            spare.erase(spare.begin() + (long)at);
+            return cudaSuccess;
+        }
+        const size_t want = std::max(bytes, size_t(double(bytes) * headroom));
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, want);
+        *p = static_cast<T*>(q);
+        if (e == cudaSuccess) cap[q] = want;
+        return e;
+    }
+    void put(void* p) {
+        if (!p) return;
+        auto it = cap.find(p);
+        if (it == cap.end()) cudaFree(p);   // not from the pool
+        else spare.emplace_back(it->second, p);
+    }
+    void clear() {
+        for (auto& f : spare) {
+            cap.erase(f.second);
+            cudaFree(f.second);
+        }
+        spare.clear();
+    }
+};
 
 template <typename R>
 struct DevState {
@@ -75,11 +120,15 @@ struct DevState {
     float* hist = nullptr;     // learned damping: HIST x n_f message-change history
     R* eta_inf = nullptr;      // record schedule: 9 x n_f reference messages (gbp_capture_messages)
 
-    void release() {
+    // every buffer freed, or (pool given) handed back to the pool
+    void release(BufPool* pool = nullptr) {
         void* ptrs[] = {z, fk, fm, kf_R, kf_c, lm_ref, kf_Rr, f_dlc, kf_off, kf_list, kpos, lm_off, tile_start, big_lm, deferred, orphan, kf_birth, lm_birth, kf_D, kf_A, lm_D,
                         uv_ref, x0, tlin, mk, mk2, kj, kjs, lin, ml, mlx, kf_bel, lm_bel, prior_s, hist, eta_inf};
         for (void* p : ptrs)
-            if (p) cudaFree(p);
+            if (p) {
+                if (pool) pool->put(p);
+                else cudaFree(p);
+            }
         *this = DevState<R>();
     }
 };
@@ -122,6 +171,8 @@ void kf_prior_record_host(const R* p, R* out) {
 
 struct gbp_graph {
     std::string err;
+    BufPool pool;                       // buffers of replaced layouts, for the next one
+    double headroom = 1.0;              // > 1 once keyframes are added: layouts grow
     cudaStream_t stream = nullptr;      // caller's stream (may be the legacy default)
     cudaStream_t capture = nullptr;     // private stream used only to record CUDA graphs
     gbp_intrinsics intr{};
@@ -272,7 +323,7 @@ template <typename R>
 // on the device from a previous layout (a keyframe was added), else zero.
 gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr, const RelayoutSrc<R>* rs = nullptr) {
     DevState<R>& s = state<R>(g);
-    s.release();
+    s.release(&g->pool);
     const int nk = g->n_kf, nl = g->n_lm, nf = g->n_f;
     // CSR lists
     std::vector<int32_t> kf_off(nk + 1, 0), lm_off(nl + 1, 0), kf_list(nf);
@@ -352,39 +403,39 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr, c
         if (g->anchored[v])
             for (int i = 0; i < 6; ++i) anc[6 * v + i] = R(1);   // scaled by D after the prior pass
 
-    CK(dev_alloc(&s.z, 2 * (size_t)nf));
-    CK(dev_alloc(&s.fk, nf));
-    CK(dev_alloc(&s.fm, nf));
-    CK(dev_alloc(&s.kf_R, 9 * (size_t)nk));
-    CK(dev_alloc(&s.kf_c, 3 * (size_t)nk));
-    CK(dev_alloc(&s.lm_ref, 3 * (size_t)nl));
-    CK(dev_alloc(&s.kf_Rr, 9 * (size_t)nk));
-    CK(dev_alloc(&s.f_dlc, 3 * (size_t)nf));
-    CK(dev_alloc(&s.kf_off, nk + 1));
-    CK(dev_alloc(&s.kf_list, nf));
-    CK(dev_alloc(&s.kpos, nf));
-    CK(dev_alloc(&s.lm_off, nl + 1));
-    CK(dev_alloc(&s.tile_start, tiles.size()));
-    CK(dev_alloc(&s.big_lm, big.size()));
-    CK(dev_alloc(&s.deferred, (size_t)n_tiles));
-    CK(dev_alloc(&s.orphan, orphan.size()));
-    CK(dev_alloc(&s.kf_birth, nk));
-    CK(dev_alloc(&s.lm_birth, nl));
-    CK(dev_alloc(&s.kf_D, 6 * (size_t)nk));
-    CK(dev_alloc(&s.kf_A, 6 * (size_t)nk));
-    CK(dev_alloc(&s.lm_D, 3 * (size_t)nl));
-    CK(dev_alloc(&s.x0, 9 * (size_t)nf));
-    CK(dev_alloc(&s.tlin, nf));
-    CK(dev_alloc(&s.mk, (size_t)KREC * nf));
-    CK(dev_alloc(&s.mk2, (size_t)KREC * nf));
-    CK(dev_alloc(&s.kj, (size_t)KJ * nf));
-    CK(dev_alloc(&s.kjs, (size_t)KJ * nf));
-    CK(dev_alloc(&s.lin, (size_t)NLIN * nf));
-    CK(dev_alloc(&s.ml, (size_t)NML * nf));
-    CK(dev_alloc(&s.mlx, 9 * (size_t)nf));
-    CK(dev_alloc(&s.kf_bel, (size_t)KBEL * nk));
-    CK(dev_alloc(&s.lm_bel, (size_t)LBEL * nl));
-    CK(dev_alloc(&s.hist, HIST * (size_t)std::max(nf, 1)));
+    CK(g->pool.alloc(&s.z, 2 * (size_t)nf, g->headroom));
+    CK(g->pool.alloc(&s.fk, nf, g->headroom));
+    CK(g->pool.alloc(&s.fm, nf, g->headroom));
+    CK(g->pool.alloc(&s.kf_R, 9 * (size_t)nk, g->headroom));
+    CK(g->pool.alloc(&s.kf_c, 3 * (size_t)nk, g->headroom));
+    CK(g->pool.alloc(&s.lm_ref, 3 * (size_t)nl, g->headroom));
+    CK(g->pool.alloc(&s.kf_Rr, 9 * (size_t)nk, g->headroom));
+    CK(g->pool.alloc(&s.f_dlc, 3 * (size_t)nf, g->headroom));
+    CK(g->pool.alloc(&s.kf_off, nk + 1, g->headroom));
+    CK(g->pool.alloc(&s.kf_list, nf, g->headroom));
+    CK(g->pool.alloc(&s.kpos, nf, g->headroom));
+    CK(g->pool.alloc(&s.lm_off, nl + 1, g->headroom));
+    CK(g->pool.alloc(&s.tile_start, tiles.size(), g->headroom));
+    CK(g->pool.alloc(&s.big_lm, big.size(), g->headroom));
+    CK(g->pool.alloc(&s.deferred, (size_t)n_tiles, g->headroom));
+    CK(g->pool.alloc(&s.orphan, orphan.size(), g->headroom));
+    CK(g->pool.alloc(&s.kf_birth, nk, g->headroom));
+    CK(g->pool.alloc(&s.lm_birth, nl, g->headroom));
+    CK(g->pool.alloc(&s.kf_D, 6 * (size_t)nk, g->headroom));
+    CK(g->pool.alloc(&s.kf_A, 6 * (size_t)nk, g->headroom));
+    CK(g->pool.alloc(&s.lm_D, 3 * (size_t)nl, g->headroom));
+    CK(g->pool.alloc(&s.x0, 9 * (size_t)nf, g->headroom));
+    CK(g->pool.alloc(&s.tlin, nf, g->headroom));
+    CK(g->pool.alloc(&s.mk, (size_t)KREC * nf, g->headroom));
+    CK(g->pool.alloc(&s.mk2, (size_t)KREC * nf, g->headroom));
+    CK(g->pool.alloc(&s.kj, (size_t)KJ * nf, g->headroom));
+    CK(g->pool.alloc(&s.kjs, (size_t)KJ * nf, g->headroom));
+    CK(g->pool.alloc(&s.lin, (size_t)NLIN * nf, g->headroom));
+    CK(g->pool.alloc(&s.ml, (size_t)NML * nf, g->headroom));
+    CK(g->pool.alloc(&s.mlx, 9 * (size_t)nf, g->headroom));
+    CK(g->pool.alloc(&s.kf_bel, (size_t)KBEL * nk, g->headroom));
+    CK(g->pool.alloc(&s.lm_bel, (size_t)LBEL * nl, g->headroom));
+    CK(g->pool.alloc(&s.hist, HIST * (size_t)std::max(nf, 1), g->headroom));
     cudaStream_t st = g->stream;
     CK(cudaMemcpyAsync(s.z, zr.data(), sizeof(R) * zr.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.fk, g->fk.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice, st));
@@ -518,7 +569,7 @@ gbp_status build_device(gbp_graph* g, const std::vector<R>* x0_init = nullptr, c
     if (!g->uv_ref.empty()) {
         std::vector<R> u(g->uv_ref.size());
         for (size_t i = 0; i < u.size(); ++i) u[i] = R(g->uv_ref[i]);
-        CK(dev_alloc(&s.uv_ref, u.size()));
+        CK(g->pool.alloc(&s.uv_ref, u.size(), g->headroom));
         CK(cudaMemcpyAsync(s.uv_ref, u.data(), sizeof(R) * u.size(), cudaMemcpyHostToDevice, st));
         d.uv_ref = s.uv_ref;
     }
@@ -556,8 +607,8 @@ gbp_status ensure_built(gbp_graph* g) {
     int want = g->prm.precision_mode == 2 ? 1 : 0;
     if (g->built && want == g->storage) return GBP_OK;
     destroy_exec(g);
-    g->sf.release();
-    g->sd.release();
+    g->sf.release(&g->pool);
+    g->sd.release(&g->pool);
     g->storage = want;
     gbp_status st = want ? build_device<double>(g) : build_device<float>(g);
     if (st != GBP_OK) return st;
@@ -962,7 +1013,9 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
     CK(cudaMemcpy(g->d_prob_f0, g->prob_f0.data(), sizeof(int32_t) * 2, cudaMemcpyHostToDevice));
     g->uv_ref.clear();   // the reference projections no longer cover every factor
 
-    // the previous layout stays alive until its state is gathered
+    // the previous layout stays alive until its state is gathered, then its
+    // buffers go back to the pool for the next addition
+    g->headroom = 1.25;
     DevState<R> old = state<R>(g);
     state<R>(g) = DevState<R>();
     int32_t* d_src = nullptr;
@@ -970,7 +1023,7 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_src, src_f.data(), sizeof(int32_t) * (size_t)F1, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) {
-        old.release();
+        old.release(&g->pool);
         if (d_src) cudaFree(d_src);
         return cuda_fail(g, e, "add_keyframe");
     }
@@ -1019,7 +1072,7 @@ gbp_status add_keyframe_impl(gbp_graph* g, const double* kf_Rt_init, int n_new_l
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         }
     }
-    old.release();
+    old.release(&g->pool);
     cudaFree(d_src);
     if (bst != GBP_OK) return bst;
     if (e != cudaSuccess) return cuda_fail(g, e, "add_keyframe");
@@ -1781,8 +1834,9 @@ gbp_status gbp_put_split_records(gbp_graph* g, int32_t kind, int32_t n, const in
 void gbp_destroy_graph(gbp_graph* g) {
     if (!g) return;
     destroy_exec(g);
-    g->sf.release();
-    g->sd.release();
+    g->sf.release(&g->pool);
+    g->sd.release(&g->pool);
+    g->pool.clear();
     if (g->ctl) cudaFree(g->ctl);
     if (g->partials) cudaFree(g->partials);
     if (g->met) cudaFree(g->met);

@@ -184,11 +184,12 @@ def test_split_across_gloo_ranks_equals_whole_graph(tmp_path, world):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("world", [2, 4])
-def test_split_parts_on_one_gpu_equal_whole_graph(world):
+@pytest.mark.parametrize("world,factor_shape", [(2, -1), (4, -1), (2, 4)])
+def test_split_parts_on_one_gpu_equal_whole_graph(world, factor_shape):
     """Every rank's part on this GPU, the ranks stepped in turn with the
     records handed over in memory: the whole graph's bits (FP32, the paper's
-    schedule, with relinearisations)."""
+    schedule, with relinearisations), also with the factor kernel that
+    defers FP64 tiles to a second kernel."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -196,11 +197,11 @@ def test_split_parts_on_one_gpu_equal_whole_graph(world):
     build.build()
     p = _loop()
     q, _, parts = split.partition(p, world)
-    ranks = [split.SplitRank(split.GpuEngine(q, r, **PARAMS), r) for r in parts]
+    ranks = [split.SplitRank(split.GpuEngine(q, r, factor_shape=factor_shape, **PARAMS), r) for r in parts]
     n = 40
     split.run_local(ranks, n)
     kf, lm = split.gather_means(parts, [r.engine.means() for r in ranks])
-    g = gbp.Graph(q, launch_mode=2, **PARAMS)
+    g = gbp.Graph(q, launch_mode=2, factor_shape=factor_shape, **PARAMS)
     g.iterate(n)
     gkf, glm = g.means()
     st = g.stats()
