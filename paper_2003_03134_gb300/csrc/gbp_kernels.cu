@@ -705,72 +705,73 @@ __device__ __noinline__ Msg5<R> lm_message64(Arr9<R> pq, Lin<R> Lf) {
 }
 
 // Message to the landmark: the keyframe's incoming precision b^t - m^t in
-// FP64 from the belief record's Lambda, eta and the factor's previous
-// message (its compact record and Jacobian block, exactly what the belief
-// summed).  If that is not positive definite (the FP32 belief's rounding,
-// summed over ~100 messages, can leave the difference indefinite where this
-// message dominates a direction), the incoming message is summed again
-// exactly from its parts: the keyframe's prior at iteration t plus every
-// other factor's current message, a loop over the keyframe's contiguous
-// slots [i0, i1) of the buffers this iteration only reads.
-template <typename R>
-struct KfCavity {
-    const R* kb;            // the keyframe's belief record (b^t)
-    const R* recs;          // m^t records, keyframe slot order
-    const R* jac;           // their Jacobian blocks
-    const R* D;             // the keyframe's prior diagonal (6) and anchor diagonal (6), sigma = 1
-    const R* A;
-    int i0, i1, self;
-    R s, anchor_scale, inv_sigma2;   // prior scale s(t), anchor factor, 1 / sigma^2
-};
+// FP64, formed once per factor and iteration and kept (packed A 21, q 6,
+// then A's Cholesky factor in place and its inverse diagonal 6) for both
+// uses, the decision and the message, so that the message sees the state
+// the decision saw.  First from the belief record's Lambda, eta and the
+// factor's previous message (its compact record and Jacobian block, exactly
+// what the belief summed).  If that is not positive definite (the FP32
+// belief's rounding, summed over ~100 messages, can leave the difference
+// indefinite where this message dominates a direction), the incoming
+// message is summed again exactly from its parts: the keyframe's prior at
+// iteration t plus every other factor's current message, a loop over the
+// keyframe's contiguous slots [i0, i1) of buffers this iteration only reads.
+constexpr int KC64 = 33;   // A 21, q 6, inv_d 6
 
 template <typename R>
-__device__ __forceinline__ void expand_slot64(const KfCavity<R>& kc, int j, double* lam, double* eta) {
-    const R* rec = kc.recs + (size_t)j * KREC;
-    const R* jr = kc.jac + (size_t)j * KJ;
+__device__ __forceinline__ void expand_slot64(const R* recs, const R* jac, int j, double* lam, double* eta) {
+    const R* rec = recs + (size_t)j * KREC;
+    const R* jr = jac + (size_t)j * KJ;
     double J[2][6];
     for (int i = 0; i < 6; ++i) { J[0][i] = double(__ldcg(jr + i)); J[1][i] = double(__ldcg(jr + 6 + i)); }
     expand_msg<double, 6>(J, double(__ldcg(rec)), double(__ldcg(rec + 1)), double(__ldcg(rec + 2)),
                           double(__ldcg(rec + 3)), double(__ldcg(rec + 4)), lam, eta);
 }
 
+__device__ __forceinline__ bool chol_kc64(double* A, const double* q, double* c) {
+    double inv_d[6], ratio;
+    const bool ok = chol_packed<double, 6>(A, inv_d, ratio);
+    for (int i = 0; i < 21; ++i) c[i] = A[i];
+    for (int i = 0; i < 6; ++i) { c[21 + i] = q[i]; c[27 + i] = inv_d[i]; }
+    return ok;
+}
+
+// b^t - m^t from the belief record kb and this factor's slot
 template <typename R>
-__device__ __forceinline__ bool kf_incoming64(const KfCavity<R>& kc, double* A, double* q, double* inv_d) {
-    double lam[21], eta[6], ratio;
-    expand_slot64<R>(kc, kc.self, lam, eta);
-    for (int i = 0; i < 21; ++i) A[i] = double(__ldcg(kc.kb + KB_LAM + i)) - lam[i];
-    for (int i = 0; i < 6; ++i) q[i] = double(__ldcg(kc.kb + KB_ETA + i)) - eta[i];
-    if (chol_packed<double, 6>(A, inv_d, ratio)) return true;
-    if (kc.i0 < 0) return false;   // the keyframe's other messages are not all on this rank
+__device__ __noinline__ bool kf_incoming_self64(const R* kb, const R* recs, const R* jac, int self, double* c) {
+    double lam[21], eta[6], A[21], q[6];
+    expand_slot64<R>(recs, jac, self, lam, eta);
+    for (int i = 0; i < 21; ++i) A[i] = double(__ldcg(kb + KB_LAM + i)) - lam[i];
+    for (int i = 0; i < 6; ++i) q[i] = double(__ldcg(kb + KB_ETA + i)) - eta[i];
+    return chol_kc64(A, q, c);
+}
+
+// prior(t) (as b^t added it, in the kernel's precision; its mean is the
+// chart origin) plus the messages of slots [i0, i1) other than self
+template <typename R>
+__device__ __noinline__ bool kf_resum64(const R* recs, const R* jac, int i0, int i1, int self, R s, const R* D,
+                                        const R* Aa, R anchor_scale, R inv_sigma2, double* c) {
+    double A[21], q[6], lam[21], eta[6];
     for (int i = 0; i < 21; ++i) A[i] = 0.0;
     for (int i = 0; i < 6; ++i) {
-        // as b^t added it, in the kernel's precision
-        A[pk(i, i)] = double((kc.s * kc.D[i] + kc.anchor_scale * kc.A[i]) * kc.inv_sigma2);
-        q[i] = 0.0;   // the prior mean is the chart origin
+        A[pk(i, i)] = double((s * D[i] + anchor_scale * Aa[i]) * inv_sigma2);
+        q[i] = 0.0;
     }
-    for (int j = kc.i0; j < kc.i1; ++j) {
-        if (j == kc.self) continue;
-        expand_slot64<R>(kc, j, lam, eta);
+    for (int j = i0; j < i1; ++j) {
+        if (j == self) continue;
+        expand_slot64<R>(recs, jac, j, lam, eta);
         for (int i = 0; i < 21; ++i) A[i] += lam[i];
         for (int i = 0; i < 6; ++i) q[i] += eta[i];
     }
-    return chol_packed<double, 6>(A, inv_d, ratio);
+    return chol_kc64(A, q, c);
 }
 
 template <typename R>
-__device__ __noinline__ bool kf_incoming_ok64(KfCavity<R> kc) {
-    double A[21], q[6], inv_d[6];
-    return kf_incoming64<R>(kc, A, q, inv_d);
-}
-
-template <typename R>
-__device__ __noinline__ Msg5<R> kf_message64(KfCavity<R> kc, Lin<R> Lf) {
-    double A[21], q[6], inv_d[6];
-    kf_incoming64<R>(kc, A, q, inv_d);
+__device__ __noinline__ Msg5<R> kf_message64(const double* c, Lin<R> Lf) {
     Lin<double> L;
     widen_lin<R>(Lf, L);
     double o[5];
-    message_chol<double, 6>(A, inv_d, q, L.Jk, L.y, L.W, o);
+    message_chol<double, 6>(c, c + 27, c + 21, L.Jk, L.y, L.W, o);
     Msg5<R> out;
     for (int i = 0; i < 5; ++i) out.v[i] = R(o[i]);
     return out;
@@ -1190,6 +1191,7 @@ __device__ __forceinline__ void form_messages(const DevGraph<R>& g, const KParam
     // iteration-t state only; the messages are formed after the
     // relinearisation test)
     bool m64 = false, k64 = false;
+    double kc[KC64];   // the keyframe's FP64 incoming precision, formed once for both uses
     if (FP64 && sizeof(R) == 4 && P.fallback && active) {
         if (!ok_m) {
             Arr9<R> pq;
@@ -1207,9 +1209,12 @@ __device__ __forceinline__ void form_messages(const DevGraph<R>& g, const KParam
             atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
         }
         if (!(ks.det >= P.cav_ratio)) {
-            ok_k = kf_incoming_ok64<R>(KfCavity<R>{kbp, mk_read(g, t), g.kj, g.kf_D + (size_t)k * 6,
-                                                   g.kf_A + (size_t)k * 6, kf_in_part(g, k) ? g.kf_off[k] : -1, g.kf_off[k + 1], slot,
-                                                   kf_prior_scale(g, P, k, t), P.anchor_scale, P.inv_sigma2});
+            const R* recs = mk_read(g, t);
+            ok_k = kf_incoming_self64<R>(kbp, recs, g.kj, slot, kc);
+            if (!ok_k && kf_in_part(g, k))   // else the keyframe's other messages are not all on this rank
+                ok_k = kf_resum64<R>(recs, g.kj, g.kf_off[k], g.kf_off[k + 1], slot, kf_prior_scale(g, P, k, t),
+                                     g.kf_D + (size_t)k * 6, g.kf_A + (size_t)k * 6, P.anchor_scale, P.inv_sigma2,
+                                     kc);
             k64 = ok_k;
             atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
         }
@@ -1274,11 +1279,7 @@ __device__ __forceinline__ void form_messages(const DevGraph<R>& g, const KParam
     }
     if (ok_k) {
         if (k64) {
-            const Msg5<R> o = kf_message64<R>(
-                KfCavity<R>{kbp, mk_read(g, t), g.kj, g.kf_D + (size_t)k * 6, g.kf_A + (size_t)k * 6,
-                            kf_in_part(g, k) ? g.kf_off[k] : -1, g.kf_off[k + 1], slot, kf_prior_scale(g, P, k, t),
-                            P.anchor_scale, P.inv_sigma2},
-                L);
+            const Msg5<R> o = kf_message64<R>(kc, L);
 #pragma unroll
             for (int i = 0; i < NML; ++i) cl[i] = o.v[i];
         } else if (!rebased) {
