@@ -91,6 +91,12 @@ typedef struct {
                                    Every shape gives bitwise identical results.                     */
     int32_t persistent_shape;   /* persistent launches: -1 (default) or 0, the one shape (no
                                    register budget); kept for the autotuner's report.               */
+    int32_t fp64_exact_cavity;  /* FP32 + FP64 fallback: 1 = every keyframe incoming precision
+                                   b^t - m^t (Sec. 5) that takes the FP64 redo is summed exactly
+                                   from its parts (the keyframe's prior plus every other factor's
+                                   message), not formed as belief minus message; 0 (default) = only
+                                   where belief minus message is not positive definite.  Slower;
+                                   the results differ from 0 by rounding only.                       */
 } gbp_params;
 
 typedef struct {
@@ -110,6 +116,10 @@ typedef struct {
                                    marginalised variable) was not positive definite even after the
                                    FP64 redo -- in FP32 mode, rounding of the stored messages in a
                                    direction that only the weak prior constrains                    */
+    int32_t fp64_resums;        /* keyframe incoming precisions b^t - m^t (Sec. 5) that the FP64 redo
+                                   had to sum again exactly from their parts (prior plus the other
+                                   factors' messages) because the FP32 belief's rounding left the
+                                   difference indefinite; counted with fp64_fallbacks              */
 } gbp_stats;
 
 /* Fill *out with the defaults listed above. */

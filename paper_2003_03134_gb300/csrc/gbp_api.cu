@@ -263,6 +263,7 @@ KParams<R> make_kparams(gbp_graph* g) {
     k.damp_hold = std::max(p.undamped_iters, 1);
     k.linear = p.linear;
     k.fallback = p.precision_mode == 0 ? 1 : 0;
+    k.exact_cavity = p.fp64_exact_cavity;
     k.mlp_frag = g->mlp_frag;
     k.mlp_bias = g->mlp_bias;
     return k;
@@ -706,6 +707,7 @@ gbp_status check_params(const gbp_params* p, std::string& why) {
     if (p->launch_mode < 0 || p->launch_mode > 2) { why = "launch_mode must be 0, 1 or 2"; return GBP_EINVAL; }
     if (p->damping_mode < 0 || p->damping_mode > 1) { why = "damping_mode must be 0 or 1"; return GBP_EINVAL; }
     if (p->factor_shape < -1 || p->factor_shape >= N_FACTOR_SHAPES) { why = "factor_shape must be -1 .. 5"; return GBP_EINVAL; }
+    if (p->fp64_exact_cavity != 0 && p->fp64_exact_cavity != 1) { why = "fp64_exact_cavity must be 0 or 1"; return GBP_EINVAL; }
     if (p->persistent_shape < -1 || p->persistent_shape >= N_PERSISTENT_SHAPES) {
         why = "persistent_shape must be -1 or 0";
         return GBP_EINVAL;
@@ -1124,6 +1126,7 @@ void gbp_default_params(gbp_params* p) {
     p->damping_mode = 0;
     p->factor_shape = -1;
     p->persistent_shape = -1;
+    p->fp64_exact_cavity = 0;
 }
 
 const char* gbp_status_string(gbp_status s) {
@@ -1492,6 +1495,7 @@ gbp_status gbp_get_stats(const gbp_graph* cg, gbp_stats* out) {
     out->fp64_fallbacks = g->h_ctl[CTL_FALLBACKS];
     out->relinearisations = g->h_ctl[CTL_RELINS];
     out->held_messages = g->h_ctl[CTL_HELD];
+    out->fp64_resums = g->h_ctl[CTL_RESUMS];
     out->launch_mode = g->last_mode;
     out->kernel_launches = g->launches;
     return st;

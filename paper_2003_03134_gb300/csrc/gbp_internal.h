@@ -90,6 +90,7 @@ struct KParams {
     int32_t damp_hold;        // damping applies when t - tlin >= damp_hold (>= 1)
     int32_t linear;
     int32_t fallback;         // FP32 path: redo ill-conditioned factorisations in FP64
+    int32_t exact_cavity;     // FP32 path: FP64 keyframe cavities always summed from their parts
     // learned damping (network weights packed by gbp_mlp.cu)
     const uint32_t* mlp_frag; // BF16 B-operand fragments of layers 1-3
     const float* mlp_bias;    // b1 (64), b2 (64), b3, pad, W3 (64)
@@ -182,6 +183,7 @@ enum Ctl : int {
     CTL_DEFER_N0 = 14,     // tiles listed for factor_deferred_kernel in even iterations
     CTL_DEFER_N1 = 15,     // in odd iterations
     CTL_DEFER_DONE = 16,   // blocks of factor_deferred_kernel done (its last block clears the list)
+    CTL_RESUMS = 17,       // keyframe incoming precisions summed again exactly from their parts (FP64)
     CTL_N = 20
 };
 

@@ -1210,11 +1210,15 @@ __device__ __forceinline__ void form_messages(const DevGraph<R>& g, const KParam
         }
         if (!(ks.det >= P.cav_ratio)) {
             const R* recs = mk_read(g, t);
-            ok_k = kf_incoming_self64<R>(kbp, recs, g.kj, slot, kc);
-            if (!ok_k && kf_in_part(g, k))   // else the keyframe's other messages are not all on this rank
+            // the sum from its parts needs all of the keyframe's messages on this rank
+            const bool exact = P.exact_cavity && kf_in_part(g, k);
+            ok_k = !exact && kf_incoming_self64<R>(kbp, recs, g.kj, slot, kc);
+            if (!ok_k && kf_in_part(g, k)) {
                 ok_k = kf_resum64<R>(recs, g.kj, g.kf_off[k], g.kf_off[k + 1], slot, kf_prior_scale(g, P, k, t),
                                      g.kf_D + (size_t)k * 6, g.kf_A + (size_t)k * 6, P.anchor_scale, P.inv_sigma2,
                                      kc);
+                atomicAdd(&g.ctl[CTL_RESUMS], 1);
+            }
             k64 = ok_k;
             atomicAdd(&g.ctl[CTL_FALLBACKS], 1);
         }

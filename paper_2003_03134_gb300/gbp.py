@@ -42,7 +42,7 @@ class gbp_params(C.Structure):
                 ("relin_interval", C.c_int32), ("undamped_iters", C.c_int32),
                 ("fp64_pivot_ratio", C.c_float), ("precision_mode", C.c_int32), ("linear", C.c_int32),
                 ("launch_mode", C.c_int32), ("damping_mode", C.c_int32), ("factor_shape", C.c_int32),
-                ("persistent_shape", C.c_int32)]
+                ("persistent_shape", C.c_int32), ("fp64_exact_cavity", C.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -77,7 +77,8 @@ class gbp_stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("max_dmu", C.c_float), ("are", C.c_double),
                 ("are_ref", C.c_double), ("n_are", C.c_int32), ("huber_count", C.c_int32),
                 ("fp64_fallbacks", C.c_int32), ("relinearisations", C.c_int32), ("launch_mode", C.c_int32),
-                ("kernel_launches", C.c_int64), ("held_messages", C.c_int32)]
+                ("kernel_launches", C.c_int64), ("held_messages", C.c_int32),
+                ("fp64_resums", C.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -43,6 +43,8 @@ def test_defaults_are_the_papers_constants(lib):
     assert p.undamped_iters == g["undamped_iters"]["value"]
     assert p.prior_anneal_iters == g["prior_anneal_iters"]["value"]
     assert p.prior_final_scale == pytest.approx(g["prior_final_scale"]["value"])
+    # the trailing fields, as the library wrote them: the binding's layout matches the header's
+    assert (p.factor_shape, p.persistent_shape, p.fp64_exact_cavity) == (-1, -1, 0)
 
 
 def test_status_strings(lib):

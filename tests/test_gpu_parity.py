@@ -182,6 +182,25 @@ def test_forced_fp64_fallback_matches_oracle(mode):
     assert st["fp64_fallbacks"] >= n * int((p.obs_kf >= 0).sum()) * 0.9
 
 
+@pytest.mark.parametrize("mode", [1, 2])
+def test_exact_fp64_cavities_match_oracle(mode):
+    """fp64_exact_cavity = 1 with fp64_pivot_ratio = 1: every keyframe
+    incoming precision b^t - m^t is summed again in FP64 from its parts (the
+    keyframe's prior plus every other factor's message), the form the FP64
+    redo falls back to where belief minus message is indefinite -- which the
+    usual workloads never reach.  The FP32 bar against the oracle holds and
+    every such sum is counted."""
+    p = synth.make_walk(2, n_kf=25, n_lm=300)
+    n = 60
+    kf, lm, st, okf, olm, o = run_pair(p, n, dict(huber_nsigma=2.0, fp64_pivot_ratio=1.0, fp64_exact_cavity=1,
+                                                  launch_mode=mode, **DET),
+                                       dict(huber_nsigma=2.0, **DET))
+    e = rel_err(kf, lm, okf, olm)
+    assert e.max() <= TOL32, (e.max(), np.median(e))
+    assert st["fp64_resums"] >= n * p.n_obs * 0.9
+    assert abs(st["are"] - o.are()[0]) <= 1e-3
+
+
 @pytest.mark.parametrize("hold", [0, 3, 8])
 def test_damping_starts_exactly_after_the_undamped_hold(hold):
     """Sec. 8, as pinned on the oracle: in linear mode runs with d = 0 and
@@ -304,7 +323,8 @@ def test_are_against_reference_solution():
 def test_invalid_params_rejected():
     p = synth.make_circle(0, n_kf=3, n_lm=5)
     g = gbp.Graph(p)
-    for bad in (dict(sigma_px=0.0), dict(damping=1.0), dict(relin_interval=0), dict(precision_mode=5)):
+    for bad in (dict(sigma_px=0.0), dict(damping=1.0), dict(relin_interval=0), dict(precision_mode=5),
+                dict(fp64_exact_cavity=2)):
         with pytest.raises(gbp.GBPError) as e:
             g.set_params(**bad)
         assert e.value.status == gbp.GBP_EINVAL
@@ -516,19 +536,24 @@ def test_add_keyframe_rejects_bad_input():
 
 
 
-def test_deferred_fp64_tiles_give_the_inline_results_bitwise():
+@pytest.mark.parametrize("exact", [0, 1])
+def test_deferred_fp64_tiles_give_the_inline_results_bitwise(exact):
     """The deferring launch shapes leave every tile with a factor that needs
     the FP64 redo to a second kernel; the results equal the inline shapes'
-    bit for bit, on batch problems whose early iterations do take the redo."""
+    bit for bit, on batch problems whose early iterations do take the redo
+    (with exact = 1 the redo's keyframe cavities are all summed from their
+    parts)."""
     probs = synth.make_batch(8, kf_range=(30, 120), lm_range=(300, 2000))
-    res, fallbacks = [], []
+    res, fallbacks, resums = [], [], []
     for shape in (0, 4, 5):
-        g = gbp.Graph(probs, huber_nsigma=2.0, launch_mode=2, factor_shape=shape)
+        g = gbp.Graph(probs, huber_nsigma=2.0, launch_mode=2, factor_shape=shape, fp64_exact_cavity=exact)
         g.iterate(60)
         res.append(g.means())
         fallbacks.append(g.stats()["fp64_fallbacks"])
+        resums.append(g.stats()["fp64_resums"])
         g.close()
     assert fallbacks[0] > 0 and len(set(fallbacks)) == 1
+    assert len(set(resums)) == 1 and (resums[0] > 0 or not exact)
     for other in res[1:]:
         for x, y in zip(res[0], other):
             np.testing.assert_array_equal(x, y)
