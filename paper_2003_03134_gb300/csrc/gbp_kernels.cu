@@ -1425,6 +1425,31 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) x0[i] = (fresh || due) ? g.x0[(size_t)i * n_f + f] : R(0);
+    // The learned schedule reads a factor's features only where it damps
+    // (t - t_lin >= damp_hold), and those read the history written in the
+    // two iterations before; earlier in the hold the features are neither
+    // formed nor stored (t_lin as stored: a relinearisation in this
+    // iteration only moves the factor back into its hold).  The record
+    // schedule writes every active factor's features.  Their loads join the
+    // second wave: g of m^{t-1} to the keyframe (still in the buffer this
+    // iteration writes), the history, the keyframe's degree.
+    const bool need_feat = active && (MODE != DAMP_LEARNED || t - tl >= P.damp_hold - 2);
+    R pr_g0 = R(0), pr_g1 = R(0);
+    float h[HIST];
+    int deg_k = 0;
+    if constexpr (FEAT) {
+        if (need_feat) {
+            const R* pp = mk_write(g, t) + (size_t)slot * KREC;
+            pr_g0 = pp[3];
+            pr_g1 = pp[4];
+#pragma unroll
+            for (int j = 0; j < HIST; ++j) h[j] = g.hist[(size_t)j * n_f + f];
+            deg_k = g.kf_off[k + 1] - g.kf_off[k];
+        } else {
+#pragma unroll
+            for (int j = 0; j < HIST; ++j) h[j] = 0.0f;
+        }
+    }
     const bool whole = active && lo >= ts && hi <= te;
     const int seg0 = whole ? lo - ts : lane;
     const int seg1 = whole ? hi - ts - 1 : lane;
@@ -1477,23 +1502,14 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
     // their basis, before a relinearisation replaces it
     R ek_old[6], ek_prev[6], em_old[3];
     R tr_pk = R(0), tr_pm = R(0);
-    float h[HIST];
-    int deg_k = 0, birth_m = 0;
     if constexpr (FEAT) {
-        msg_eta<R, 6>(L.Jk, mo[3], mo[4], ek_old);
-        // m^{t-1} to the keyframe: still in the buffer this iteration writes
-        R pr[KREC];
-        if (active) load_rec<R, KREC>(mk_write(g, t) + (size_t)slot * KREC, pr);
-        else
+        if (need_feat) {
+            msg_eta<R, 6>(L.Jk, mo[3], mo[4], ek_old);
+            msg_eta<R, 6>(L.Jk, pr_g0, pr_g1, ek_prev);
+            tr_pk = tr_b - msg_trace<R, 6>(L.Jk, mo[0], mo[1], mo[2]);
+        } else {
 #pragma unroll
-            for (int i = 0; i < KREC; ++i) pr[i] = R(0);
-        msg_eta<R, 6>(L.Jk, pr[3], pr[4], ek_prev);
-        tr_pk = tr_b - msg_trace<R, 6>(L.Jk, mo[0], mo[1], mo[2]);
-#pragma unroll
-        for (int j = 0; j < HIST; ++j) h[j] = active ? g.hist[(size_t)j * n_f + f] : 0.0f;
-        if (active) {
-            deg_k = g.kf_off[k + 1] - g.kf_off[k];
-            birth_m = g.lm_birth[m];
+            for (int i = 0; i < 6; ++i) { ek_old[i] = R(0); ek_prev[i] = R(0); }
         }
     }
 
@@ -1591,9 +1607,9 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
         for (int i = 0; i < N_FEAT; ++i) feat[i] = 0.0f;
         R ek_new[6], em_new[3];
         if constexpr (FEAT) {
-            msg_eta<R, 6>(L.Jk, ck[3], ck[4], ek_new);
-            msg_eta<R, 3>(L.Jl, cl[3], cl[4], em_new);
-            if (active) {
+            if (need_feat) {
+                msg_eta<R, 6>(L.Jk, ck[3], ck[4], ek_new);
+                msg_eta<R, 3>(L.Jl, cl[3], cl[4], em_new);
                 const float tr_lk = float(msg_trace<R, 6>(L.Jk, ck[0], ck[1], ck[2]));
                 const float tr_lm = float(msg_trace<R, 3>(L.Jl, cl[0], cl[1], cl[2]));
                 const float M = float(sqrt(L.r2) * P.inv_sigma);
@@ -1616,7 +1632,7 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
                 feat[12] = log1pf(float(deg_k)) * 0.2f;
                 feat[13] = log1pf(float(hi - lo)) * (1.0f / 3.0f);
                 feat[14] = float(min(t - tl, 50)) * 0.02f;
-                feat[15] = float(min(t - birth_m, 50)) * 0.02f;
+                feat[15] = float(min(t - lbirth, 50)) * 0.02f;
                 const float hn[HIST] = {cfk, h[0], cfm, h[2], float(em_old[0]), float(em_old[1]), float(em_old[2]), 0.0f};
 #pragma unroll
                 for (int j = 0; j < HIST; ++j) g.hist[(size_t)j * n_f + f] = hn[j];
