@@ -1088,6 +1088,14 @@ __device__ __forceinline__ void dmu_atomic_max_slot(int32_t* ctl, int slot, floa
 // vertex d_s = <u_s, eta_inf,s - eta_new,s> / |u_s|^2 (u_s = eta_old,s -
 // eta_new,s), so the minimiser is clip(mean_s d_s, 0, 0.9).
 
+// Square roots and quotients of the learned schedule's features.  In the
+// FP32 path the features are network inputs rounded to BF16 (8 significant
+// bits), so they take the hardware approximations (rsqrt, fast divide:
+// ~2 ulp of FP32) instead of the correctly rounded sequences, which sat on
+// every factor warp's path to the network.  x * rsqrt(max(x, 1e-30)) is
+// sqrt(x) for x >= 1e-30 and below 1e-15 otherwise (0 at x = 0).
+__device__ __forceinline__ float feat_sqrt(float x) { return x * rsqrtf(fmaxf(x, 1e-30f)); }
+
 template <typename R, int n>
 __device__ __forceinline__ float rel_change(const R* nw, const R* old) {
     R dd = R(0), a = R(0), b = R(0);
@@ -1097,7 +1105,10 @@ __device__ __forceinline__ float rel_change(const R* nw, const R* old) {
         a += nw[i] * nw[i];
         b += old[i] * old[i];
     }
-    return float(sqrt(dd) / (sqrt(a) + sqrt(b) + R(1e-30)));
+    if constexpr (sizeof(R) == 4)
+        return __fdividef(feat_sqrt(dd), feat_sqrt(a) + feat_sqrt(b) + 1e-30f);
+    else
+        return float(sqrt(dd) / (sqrt(a) + sqrt(b) + R(1e-30)));
 }
 
 template <typename R, int n>
@@ -1110,7 +1121,10 @@ __device__ __forceinline__ float step_cosine(const R* nw, const R* old, const R*
         aa += a * a;
         bb += b * b;
     }
-    return float(ab / (sqrt(aa) * sqrt(bb) + R(1e-30)));
+    if constexpr (sizeof(R) == 4)
+        return __fdividef(ab, feat_sqrt(aa) * feat_sqrt(bb) + 1e-30f);
+    else
+        return float(ab / (sqrt(aa) * sqrt(bb) + R(1e-30)));
 }
 
 // Vertex of one side's parabola (unclipped); valid = the side's message changed.
@@ -1617,9 +1631,15 @@ __device__ __forceinline__ float tile_work(const DevGraph<R>& g, const KParams<R
                 const float cfm = rel_change<R, 3>(em_new, em_old);
                 const R em_prev[3] = {R(h[4]), R(h[5]), R(h[6])};
                 feat[0] = log1pf(M) * (1.0f / 3.0f);
-                feat[1] = float(L.W / P.inv_sigma2);
-                feat[2] = tr_lk / (tr_lk + float(tr_pk) + 1e-30f);
-                feat[3] = tr_lm / (tr_lm + float(tr_pm) + 1e-30f);
+                if constexpr (sizeof(R) == 4) {
+                    feat[1] = __fdividef(L.W, P.inv_sigma2);
+                    feat[2] = __fdividef(tr_lk, tr_lk + tr_pk + 1e-30f);
+                    feat[3] = __fdividef(tr_lm, tr_lm + tr_pm + 1e-30f);
+                } else {
+                    feat[1] = float(L.W / P.inv_sigma2);
+                    feat[2] = tr_lk / (tr_lk + float(tr_pk) + 1e-30f);
+                    feat[3] = tr_lm / (tr_lm + float(tr_pm) + 1e-30f);
+                }
                 feat[4] = cfk;
                 feat[5] = h[0];
                 feat[6] = h[1];
