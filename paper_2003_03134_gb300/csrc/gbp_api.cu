@@ -199,6 +199,9 @@ struct gbp_graph {
     int32_t* h_ctl = nullptr;                   // pinned mirror of ctl
     double* h_met = nullptr;                    // pinned mirror of met
     cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t wexec = nullptr;            // device convergence loop (conditional WHILE node)
+    int wexec_every = 0;                        // its check_every
+    bool wexec_failed = false;                  // not available for this layout: the host checks
     bool built = false;
     int tuned_mode = 0;                         // autotuner's choice (1 or 2), 0 = not tuned
     int tuned_fshape = -1, tuned_pshape = -1;   // its launch shapes, -1 = not tuned
@@ -291,6 +294,11 @@ void destroy_exec(gbp_graph* g) {
         cudaGraphExecDestroy(g->exec);
         g->exec = nullptr;
     }
+    if (g->wexec) {
+        cudaGraphExecDestroy(g->wexec);
+        g->wexec = nullptr;
+    }
+    g->wexec_failed = false;
 }
 
 template <>
@@ -661,6 +669,88 @@ gbp_status ensure_exec(gbp_graph* g) {
     return fail(g, GBP_ECUDA, "capture");
 }
 
+// Device convergence loop.  With conv_tol > 0 the per-phase launches are
+// checked every check_every iterations; instead of a host round trip per
+// check (a device-to-host copy and a stream synchronisation, during which
+// the GPU idles), one graph launch runs the check blocks in a conditional
+// WHILE node: its body is check_every iterations followed by a one-thread
+// kernel that makes the host loop's test -- the largest mean change of the
+// last iteration below conv_tol, no error raised -- and sets the loop's
+// condition.  The kernels, their order and the check points are the host
+// loop's, so the results and the iteration count are the same.  Two control
+// slots past the kernels' own (the Ctl enum ends at CTL_RESUMS) carry the
+// loop's state.
+constexpr int CTL_WL_LEFT = 18;     // check blocks the loop may still run
+constexpr int CTL_WL_TOL = 19;      // conv_tol, float bits
+static_assert(CTL_WL_LEFT > CTL_RESUMS && CTL_WL_TOL < CTL_N, "control slots of the device loop");
+constexpr int WHILE_MAX_BODY = 64;  // longest check block recorded in the loop body
+
+__global__ void while_setup_kernel(int32_t* ctl, int32_t blocks, int32_t tol_bits) {
+    ctl[CTL_WL_LEFT] = blocks;
+    ctl[CTL_WL_TOL] = tol_bits;
+}
+
+__global__ void while_check_kernel(int32_t* ctl, cudaGraphConditionalHandle h) {
+    const int left = ctl[CTL_WL_LEFT] - 1;
+    ctl[CTL_WL_LEFT] = left;
+    const int t = ctl[CTL_ITER];
+    const float dmu = t > 0 ? __int_as_float(ctl[((t - 1) & 1) ? CTL_DMU_ACC1 : CTL_DMU_ACC]) : 0.0f;
+    const float tol = __int_as_float(ctl[CTL_WL_TOL]);
+    const bool go = left > 0 && !(dmu < tol) && ctl[CTL_ERR] == 0;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// Records the loop (after ensure_exec, which settles g->pdl).  Where the
+// driver does not take it (or check_every exceeds WHILE_MAX_BODY), the host
+// loop checks instead.
+gbp_status ensure_wexec(gbp_graph* g) {
+    const int every = g->prm.check_every;
+    if (g->wexec && g->wexec_every == every) return GBP_OK;
+    if (g->wexec) {
+        cudaGraphExecDestroy(g->wexec);
+        g->wexec = nullptr;
+    }
+    if (g->wexec_failed || every > WHILE_MAX_BODY) return GBP_OK;
+    cudaGraph_t graph = nullptr;
+    cudaGraphConditionalHandle h = 0;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node = nullptr;
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    }
+    if (e == cudaSuccess) {
+        e = cudaStreamBeginCaptureToGraph(g->capture, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = g->storage ? enqueue_iterations<double>(g, every, g->capture)
+                                        : enqueue_iterations<float>(g, every, g->capture);
+            if (e1 == cudaSuccess) {
+                while_check_kernel<<<1, 1, 0, g->capture>>>(g->ctl, h);
+                e1 = cudaGetLastError();
+            }
+            cudaGraph_t body = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(g->capture, &body);
+            e = e1 != cudaSuccess ? e1 : e2;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->wexec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g->wexec = nullptr;
+        g->wexec_failed = true;
+        (void)cudaGetLastError();   // the host loop takes over; nothing of this is the caller's error
+        return GBP_OK;
+    }
+    g->wexec_every = every;
+    return GBP_OK;
+}
+
 // max |dmu| of the last completed iteration, from the mirrored control
 // block: both launch modes leave it in the parity slot of that iteration.
 float last_dmu(const gbp_graph* g) {
@@ -827,6 +917,27 @@ gbp_status iterate_phases(gbp_graph* g, int n, float conv_tol, int* done_out) {
     if (st != GBP_OK) return st;
     const bool check = conv_tol > 0.0f;
     int done = 0;
+    if (check && n >= g->prm.check_every) {
+        // the whole check blocks in one launch of the device loop; the host
+        // loop below takes the rest (fewer than check_every iterations)
+        st = ensure_wexec(g);
+        if (st != GBP_OK) return st;
+        if (g->wexec) {
+            const int every = g->prm.check_every, blocks = n / every;
+            int32_t tol_bits;
+            std::memcpy(&tol_bits, &conv_tol, sizeof tol_bits);
+            while_setup_kernel<<<1, 1, 0, g->stream>>>(g->ctl, blocks, tol_bits);
+            CK(cudaGetLastError());
+            CK(cudaGraphLaunch(g->wexec, g->stream));
+            st = read_ctl(g);
+            const int runs = blocks - g->h_ctl[CTL_WL_LEFT];
+            done = runs * every;
+            g->launches += 2 * (int64_t)done + runs + 1;
+            *done_out = done;
+            if (st != GBP_OK) return st;
+            if (last_dmu(g) < conv_tol) return GBP_OK;
+        }
+    }
     while (done < n) {
         int block = check ? std::min(g->prm.check_every, n - done) : n - done;
         int full = block / GRAPH_CHUNK, rest = block % GRAPH_CHUNK;

@@ -408,6 +408,33 @@ def test_convergence_stops_at_the_same_iteration_in_both_modes():
     assert done[0] == done[1] < 2000
 
 
+@pytest.mark.parametrize("every,n,tol", [(5, 2000, 2e-5), (16, 203, 2e-5), (16, 1000, 1e-12), (16, 7, 2e-5),
+                                          (100, 1000, 2e-5)])
+def test_device_convergence_loop_matches_host_checks(every, n, tol):
+    """With conv_tol > 0 the per-phase launches run their check blocks in a
+    conditional graph loop that tests the largest mean change on the device
+    (check_every <= 64; longer blocks are checked by the host).  Against the
+    same test made here after every block of plain iterations: the same
+    iteration count and bitwise the same means."""
+    p = synth.make_circle(2)
+    a = gbp.Graph(p, conv_tol=tol, check_every=every, launch_mode=2)
+    done_a = a.iterate(n)
+    b = gbp.Graph(p, launch_mode=2)
+    done_b = 0
+    while done_b < n:
+        k = min(every, n - done_b)
+        assert b.iterate(k) == k
+        done_b += k
+        if b.stats()["max_dmu"] < tol:
+            break
+    assert done_a == done_b
+    assert a.stats()["iterations"] == b.stats()["iterations"] == done_b
+    for x, y in zip(a.means(), b.means()):
+        np.testing.assert_array_equal(x, y)
+    a.close()
+    b.close()
+
+
 def test_autotune_restores_the_state():
     p = synth.make_walk(5, n_kf=30, n_lm=300)
     a = gbp.Graph(p, launch_mode=2)
