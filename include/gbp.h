@@ -75,7 +75,9 @@ typedef struct {
     float   fp64_pivot_ratio;   /* FP32 Cholesky with min/max pivot below this is redone in FP64; 1e-6 */
     int32_t precision_mode;     /* 0: FP32 + FP64 fallback, 1: FP32 only, 2: FP64 throughout        */
     int32_t linear;             /* 1: never relinearise (linear GBP at the initial point)          */
-    int32_t launch_mode;        /* 0: auto (gbp_autotune on first use), 1: one persistent launch per
+    int32_t launch_mode;        /* 0: auto (gbp_autotune on first use; a graph whose device, storage,
+                                   precision and damping modes and sizes match one already tuned in
+                                   this process takes that graph's choice), 1: one persistent launch per
                                    gbp_iterate call with a grid barrier between phases, 2: one launch
                                    per phase (factor kernel, belief kernel) replayed as a CUDA graph.
                                    All modes give bitwise identical results.                        */

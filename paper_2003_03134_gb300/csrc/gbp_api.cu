@@ -10,6 +10,9 @@
 #include "../../include/gbp.h"
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <unordered_map>
 #include <cmath>
 #include <cstdio>
@@ -1483,6 +1486,52 @@ gbp_status gbp_reset(gbp_graph* g) {
     return g->storage ? reset_state<double>(g) : reset_state<float>(g);
 }
 
+// The auto launch mode's choices, per device and graph shape.  Every
+// candidate gives bitwise identical results, so a graph whose device,
+// storage, precision mode, damping schedule and sizes (keyframes, points, factors, warp
+// tiles, problems) match a graph already tuned in this process takes that
+// choice instead of timing the candidates again (gbp_autotune, called
+// explicitly, always times them and records its choice here).
+namespace {
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int>;
+struct TuneVal {
+    int mode, fshape, pshape;
+    gbp_tuning tuning;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+bool tune_key(const gbp_graph* g, TuneKey& key) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    const int n_tiles = g->storage ? g->sd.g.n_tiles : g->sf.g.n_tiles;
+    key = TuneKey(dev, g->storage, g->prm.precision_mode, g->prm.damping_mode, g->n_kf, g->n_lm, g->n_f, n_tiles,
+                  (int)g->prob_f0.size());
+    return true;
+}
+
+bool tune_cache_lookup(gbp_graph* g) {
+    TuneKey key;
+    if (!tune_key(g, key)) return false;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it == g_tune_cache.end()) return false;
+    g->tuned_mode = it->second.mode;
+    g->tuned_fshape = it->second.fshape;
+    g->tuned_pshape = it->second.pshape;
+    g->tuning = it->second.tuning;
+    destroy_exec(g);   // a graph recorded before with the default shapes
+    return true;
+}
+
+void tune_cache_store(const gbp_graph* g) {
+    TuneKey key;
+    if (!tune_key(g, key)) return;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = TuneVal{g->tuned_mode, g->tuned_fshape, g->tuned_pshape, g->tuning};
+}
+}  // namespace
+
 gbp_status gbp_iterate(gbp_graph* g, int32_t n_iters, int32_t* iters_done) {
     if (iters_done) *iters_done = 0;
     if (!g) return GBP_EINVAL;
@@ -1495,7 +1544,7 @@ gbp_status gbp_iterate(gbp_graph* g, int32_t n_iters, int32_t* iters_done) {
         return fail(g, GBP_ESTATE, "damping_mode 1 needs a network (gbp_set_damping_model)");
     int mode = g->prm.launch_mode;
     if (mode == 0) {
-        if (!g->tuned_mode) {
+        if (!g->tuned_mode && !tune_cache_lookup(g)) {
             st = gbp_autotune(g, 8, nullptr, nullptr);
             if (st != GBP_OK) return st;
         }
@@ -1818,6 +1867,7 @@ gbp_status gbp_autotune(gbp_graph* g, int32_t n_trial, int32_t* chosen, double* 
         T.cand_shape[c] = cand[c].second;
         T.cand_ms[c] = ms[c];
     }
+    tune_cache_store(g);
     if (chosen) *chosen = g->tuned_mode;
     if (ms_out) {
         ms_out[0] = best_mode[0];

@@ -435,6 +435,27 @@ def test_device_convergence_loop_matches_host_checks(every, n, tol):
     b.close()
 
 
+def test_auto_launch_choice_is_reused_for_a_graph_of_the_same_shape():
+    """launch_mode 0 times the candidates on a graph's first gbp_iterate; a
+    second graph of the same sizes in the same process takes the first one's
+    choice and its record (the very same candidate times, which a second
+    timing would not reproduce), and both give the same bits."""
+    p = synth.make_walk(7, n_kf=30, n_lm=300)
+    a = gbp.Graph(p)
+    assert a.tuning()["n_candidates"] == 0
+    a.iterate(12)
+    ta = a.tuning()
+    assert ta["n_candidates"] > 0
+    b = gbp.Graph(p)
+    b.iterate(12)
+    tb = b.tuning()
+    assert tb == ta
+    for x, y in zip(a.means(), b.means()):
+        np.testing.assert_array_equal(x, y)
+    a.close()
+    b.close()
+
+
 def test_autotune_restores_the_state():
     p = synth.make_walk(5, n_kf=30, n_lm=300)
     a = gbp.Graph(p, launch_mode=2)
