@@ -1500,6 +1500,7 @@ struct TuneVal {
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
+constexpr size_t TUNE_CACHE_MAX = 256;   // graph shapes remembered at once
 
 bool tune_key(const gbp_graph* g, TuneKey& key) {
     int dev = 0;
@@ -1528,6 +1529,7 @@ void tune_cache_store(const gbp_graph* g) {
     TuneKey key;
     if (!tune_key(g, key)) return;
     std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (g_tune_cache.size() >= TUNE_CACHE_MAX && !g_tune_cache.count(key)) g_tune_cache.clear();   // bounded
     g_tune_cache[key] = TuneVal{g->tuned_mode, g->tuned_fshape, g->tuned_pshape, g->tuning};
 }
 }  // namespace
