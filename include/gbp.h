@@ -64,7 +64,11 @@ typedef struct {
     float   sigma_px;           /* measurement noise std, pixels; default 1                         */
     int32_t iterations;         /* iterations per gbp_iterate() call when n_iters <= 0; default 200 */
     float   conv_tol;           /* stop once max |mu^{t+1} - mu^t|_inf < conv_tol; 0 = fixed count   */
-    int32_t check_every;        /* iterations between convergence checks; default 16               */
+    int32_t check_every;        /* iterations between convergence checks; default 16.  With
+                                   per-phase launches, check blocks of up to 64 iterations run in
+                                   one launch of a device-side graph loop that makes the check on
+                                   the GPU (no host round trip per block); the same checks, the
+                                   same results.                                                   */
     float   prior_final_scale;  /* priors end this fraction of one measurement's strength; 0.01   */
     int32_t prior_anneal_iters; /* geometric anneal from scale 1 over this many iterations; 10     */
     float   anchor_scale;       /* anchor prior = anchor_scale x the keyframe's prior; 1000        */
